@@ -1,0 +1,88 @@
+"""The synthetic workloads HRPP is measured and checked on.
+
+The paper's scenes (Teapot, Killeroo, Buddha, Sportscar; Table 1) are not
+available, so seeded procedural scenes of a similar range of triangle counts
+stand in for them.  Every array is made by `scenes` (scenegen.c) from the seeds
+given here.
+
+  small_scene   icosphere (3x subdivided, 1,280 triangles, radius 1, centre
+                (0,1,0)) on a 16x16-quad ground grid over [-4,4]^2 (512
+                triangles); binary BVH, <= 4 triangles per leaf; 256x256
+                pinhole primary rays from (0,2.5,6) toward (0,0.75,0), 45 deg
+                vertical field of view; one shadow ray per hit toward a point
+                light at (2,4,2); predictor 2^12 entries, direct-mapped.
+  terrain_scene value-noise terrain of 708x708 quads over [-50,50]^2 (1,002,528
+                triangles; 4 octaves, amplitude 8, base frequency 1/16) with 64
+                icospheres (5x subdivided, 20,480 triangles each, radius
+                log-uniform in [0.1, 2]) resting on it: 2,313,248 triangles;
+                4-wide BVH; 1920x1080 primary closest-hit rays from (0,25,-70)
+                toward the origin, 60 deg field of view; 4 cosine-weighted
+                ambient-occlusion any-hit rays per hit, tmax 0.5.
+Both take size parameters so tests can run the same recipe at reduced size.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import (ao_rays, build_bvh, icosphere, pinhole_rays, place_spheres, quad_grid, shadow_rays,
+               terrain)
+
+
+@dataclass
+class Scene:
+    name: str
+    tris: np.ndarray       # float32 [n, 9]
+    nodes: np.ndarray      # NODE_DTYPE [m]
+    prim_index: np.ndarray  # uint32 [n]
+    root: int
+    width: int
+    camera: dict
+
+    @property
+    def n_tris(self) -> int:
+        return int(self.tris.shape[0])
+
+    def primary_rays(self, frame: int = 0, seed: int | None = None) -> np.ndarray:
+        c = self.camera
+        return pinhole_rays(c["eye"], c["target"], c["vfov"], c["width"], c["height"],
+                            seed=c["seed"] if seed is None else seed, frame=frame)
+
+
+def small_scene(width: int = 2, subdiv: int = 3, grid: int = 16, res: int = 256) -> Scene:
+    sphere = icosphere(subdiv, (0.0, 1.0, 0.0), 1.0)
+    ground = quad_grid(grid, grid, -4.0, 4.0, -4.0, 4.0, 0.0)
+    tris = np.ascontiguousarray(np.concatenate([sphere, ground]), np.float32)
+    nodes, prim, root = build_bvh(tris, width=width)
+    cam = dict(eye=(0.0, 2.5, 6.0), target=(0.0, 0.75, 0.0), vfov=45.0, width=res, height=res, seed=0)
+    return Scene("small", tris, nodes, prim, root, width, cam)
+
+
+SMALL_LIGHT = (2.0, 4.0, 2.0)
+
+
+def terrain_scene(quads: int = 708, n_spheres: int = 64, subdiv: int = 5, width: int = 4, seed: int = 2,
+                  res=(1920, 1080), extent: float = 50.0) -> Scene:
+    ground = terrain(quads, quads, -extent, extent, -extent, extent, seed)
+    parts = [ground]
+    if n_spheres:
+        sp = place_spheres(n_spheres, seed, 0.1, 2.0, -extent, extent, -extent, extent, seed)
+        for cx, cy, cz, r in sp:
+            parts.append(icosphere(subdiv, (float(cx), float(cy), float(cz)), float(r)))
+    tris = np.ascontiguousarray(np.concatenate(parts), np.float32)
+    nodes, prim, root = build_bvh(tris, width=width)
+    cam = dict(eye=(0.0, 25.0, -70.0), target=(0.0, 0.0, 0.0), vfov=60.0, width=res[0], height=res[1], seed=seed)
+    return Scene("terrain", tris, nodes, prim, root, width, cam)
+
+
+def secondary_shadow(scene: Scene, rays: np.ndarray, hit_t, hit_prim, light=SMALL_LIGHT):
+    """Shadow rays from the hits of `rays` (hit_t, hit_prim: closest-hit result)."""
+    return shadow_rays(rays, hit_t, hit_prim, scene.tris, light)
+
+
+def secondary_ao(scene: Scene, rays: np.ndarray, hit_t, hit_prim, frame: int = 0, per_hit: int = 4,
+                 tmax: float = 0.5):
+    """Cosine-weighted ambient-occlusion rays from the hits of `rays`."""
+    return ao_rays(rays, hit_t, hit_prim, scene.tris, per_hit=per_hit, tmax=tmax,
+                   seed=scene.camera["seed"], frame=frame)

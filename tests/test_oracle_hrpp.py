@@ -1,0 +1,175 @@
+"""Pins for the oracle's HRPP simulation (Sec. 4.2-4.3, Sec. 5).
+
+Pinned against the plain result (HRPP must return exactly what plain traversal
+returns), against brute force restricted to the predicted leaf, and against
+invariants the method fixes: an empty table predicts nothing; in the
+unbounded limit-study table every ray that hit is, on a second pass, a
+positive whose own leaf is predicted; any-hit true positives do no interior
+work while every other ray does exactly its plain traversal.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def _leaf_of_prim(nodes, prim_index):
+    m = {}
+    for n in nodes:
+        if n["count"] > 0:
+            lid = (int(n["first"]) << 2) | (int(n["count"]) - 1)
+            for j in range(int(n["count"])):
+                m[int(prim_index[n["first"] + j])] = lid
+    return m
+
+
+def _check_identities(st, n):
+    assert st["rays"] == n and st["lookups"] == n
+    assert st["positives"] + st["negatives"] == n
+    assert st["true_pos"] + st["false_pos"] == st["positives"]
+    assert st["dup_inserts"] <= st["inserts"]
+
+
+@pytest.mark.parametrize("mode", [O.CLOSEST_HIT, O.ANY_HIT])
+def test_empty_table_is_plain_plus_one_lookup(small, mode):
+    rays = small.primary_rays()[::3]
+    hp, sp = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, mode)
+    tab = O.Table(16, 1, 6, O.TWO_PHASE)
+    hh, sh = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, mode, tab)
+    assert np.array_equal(hp, hh)
+    for k in ("interior_nodes", "box_tests", "leaves", "tri_tests", "hits"):
+        assert sp[k] == sh[k]
+    assert sh["negatives"] == len(rays) and sh["positives"] == 0
+    assert sh["inserts"] == sp["hits"]
+    _check_identities(sh, len(rays))
+
+
+@pytest.mark.parametrize("mode", [O.CLOSEST_HIT, O.ANY_HIT])
+@pytest.mark.parametrize("upd", [O.TWO_PHASE, O.SEQUENTIAL, O.UNBOUNDED])
+@pytest.mark.parametrize("ways", [1, 4])
+def test_results_equal_plain_over_frames(small, mode, upd, ways):
+    tab = O.Table(10, ways, 6, upd)
+    for frame in range(3):
+        rays = small.primary_rays(frame=frame)[::2]
+        hp, sp = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, mode)
+        hh, sh = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, mode, tab)
+        if mode == O.CLOSEST_HIT:
+            assert np.array_equal(hp, hh), (frame, upd)
+        else:
+            # any-hit: the occlusion bit is unique; the prim reported need
+            # only be a real hit of that ray
+            assert np.array_equal(hp == O.NO_HIT, hh == O.NO_HIT), (frame, upd)
+            for i in np.nonzero(hh != hp)[0]:
+                tr = small.tris[hh[i]]
+                assert O.ray_triangle(rays[i], tr[0:3], tr[3:6], tr[6:9])[0]
+        _check_identities(sh, len(rays))
+        assert sh["hits"] == sp["hits"]
+
+
+def test_unbounded_second_pass_predicts_every_hit(small):
+    rays = small.primary_rays()[::2]
+    leaf_of = _leaf_of_prim(small.nodes, small.prim_index)
+    for mode in (O.ANY_HIT, O.CLOSEST_HIT):
+        tab = O.Table(0, 1, 6, O.UNBOUNDED)
+        h1, s1 = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, mode, tab)
+        h2, s2, oc, _ = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, mode, tab, per_ray=True)
+        hit = (h2 if mode == O.ANY_HIT else h2["prim"]) != O.NO_HIT
+        # every ray that hit has its own leaf under its key: a true positive
+        assert np.all(oc[hit] == 3)
+        assert s2["true_pos"] == int(hit.sum())
+        assert s2["tp_inexact"] == 0 and s2["inserts"] == 0
+        keys, leaves = tab.unbounded_size()
+        # one key per distinct ray key that hit, each listing distinct leaves
+        hit_rays = rays[hit]
+        hk = {}
+        prims = (h1 if mode == O.ANY_HIT else h1["prim"])[hit]
+        for r, p in zip(hit_rays, prims):
+            hk.setdefault(O.ray_key(r, 6), set()).add(leaf_of[int(p)])
+        assert keys == len(hk)
+        assert leaves == sum(len(v) for v in hk.values())
+
+
+def test_any_hit_true_positives_skip_all_interior_work(small):
+    rays = small.primary_rays()[::2]
+    tab = O.Table(0, 1, 6, O.UNBOUNDED)
+    O.trace(small.tris, small.nodes, small.prim_index, 0, small.primary_rays(frame=1)[::2], O.ANY_HIT, tab)
+    _, sp, _, plain_boxes = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.ANY_HIT, per_ray=True)
+    _, sh, oc, hrpp_boxes = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.ANY_HIT, tab,
+                                    per_ray=True)
+    tp = oc == 3
+    assert tp.sum() > 1000
+    assert np.all(hrpp_boxes[tp] == 0)
+    assert np.array_equal(hrpp_boxes[~tp], plain_boxes[~tp])
+    assert sh["box_tests"] == int(plain_boxes[~tp].sum())
+
+
+def test_single_key_direct_mapped_winner_and_reuse(small):
+    """All rays share one key: the highest-index hitting ray's leaf wins the
+    slot; on the next pass exactly the rays that hit that leaf are true
+    positives (brute force over the leaf's own triangles)."""
+    rng = np.random.default_rng(0)
+    n = 500
+    o = np.array([0.0, 2.5, 6.0], np.float32)
+    d = np.array([0.3, -0.55, -0.78]) + rng.uniform(-0.005, 0.005, (n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    rays = np.zeros((n, 8), np.float32)
+    rays[:, 0:3], rays[:, 4:7], rays[:, 7] = o, d, np.inf
+    p = 1
+    keys = {O.ray_key(r, p) for r in rays}
+    assert len(keys) == 1
+    key = keys.pop()
+    leaf_of = _leaf_of_prim(small.nodes, small.prim_index)
+    tab = O.Table(8, 1, p, O.TWO_PHASE)
+    s, tag = O.set_and_tag(key, 8)
+    h1, s1 = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.ANY_HIT, tab)
+    hit_idx = np.nonzero(h1 != O.NO_HIT)[0]
+    assert len(hit_idx) > 10
+    last = int(hit_idx[-1])
+    winner_leaf = leaf_of[int(h1[last])]
+    assert int(tab.words[s]) == (tag << O.LEAF_BITS) | winner_leaf
+    assert np.count_nonzero(tab.words != np.uint64(O.EMPTY_WORD)) == 1
+    assert s1["inserts"] == len(hit_idx) and s1["dup_inserts"] == len(hit_idx) - 1
+    # second pass: brute force over the winner leaf's triangles decides TP
+    first, cnt = winner_leaf >> 2, (winner_leaf & 3) + 1
+    leaf_prims = small.prim_index[first:first + cnt]
+    expect_tp = np.array([any(O.ray_triangle(r, *np.split(small.tris[q], 3))[0] for q in leaf_prims)
+                          for r in rays])
+    _, s2, oc, _ = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.ANY_HIT, tab, per_ray=True)
+    assert np.array_equal(oc == 3, expect_tp)
+    assert s2["positives"] == n and s2["pred_leaves"] == n
+
+
+def test_two_phase_vs_sequential_within_a_batch(small):
+    """Two-phase lookups see the table as it was at batch start; sequential
+    lookups see earlier rays' inserts."""
+    r = small.primary_rays()[::2]
+    rays = np.concatenate([r, r])  # the second half repeats the first
+    t2 = O.Table(16, 1, 6, O.TWO_PHASE)
+    _, s2 = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.ANY_HIT, t2)
+    assert s2["positives"] == 0
+    tseq = O.Table(16, 1, 6, O.SEQUENTIAL)
+    _, sq = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.ANY_HIT, tseq)
+    assert sq["positives"] > 0 and sq["true_pos"] > 0
+
+
+@pytest.mark.parametrize("ways", [2, 4, 8])
+def test_ways_hold_distinct_leaves_of_one_key(small, ways):
+    tab = O.Table(12, ways, 6, O.TWO_PHASE)
+    for f in range(2):
+        O.trace(small.tris, small.nodes, small.prim_index, 0, small.primary_rays(frame=f), O.CLOSEST_HIT, tab)
+    w = tab.words.reshape(-1, ways)
+    valid = w != np.uint64(O.EMPTY_WORD)
+    leaves = (w & np.uint64((1 << O.LEAF_BITS) - 1)).astype(np.int64)
+    tags = (w >> np.uint64(O.LEAF_BITS)).astype(np.int64)
+    # a (tag, leaf) pair sits only in way way_of(leaf)
+    for s, k in zip(*np.nonzero(valid)):
+        assert O.way_of(int(leaves[s, k]), {2: 1, 4: 2, 8: 3}[ways]) == k
+    # some set holds several leaves under one tag (several predictions per key)
+    multi = 0
+    for s in range(w.shape[0]):
+        ts = tags[s][valid[s]]
+        multi += len(ts) - len(set(ts.tolist()))
+    assert multi > 0
+    # every stored leaf is a real leaf of the BVH
+    real = {(int(n["first"]) << 2) | (int(n["count"]) - 1) for n in small.nodes if n["count"] > 0}
+    assert set(leaves[valid].tolist()) <= real
