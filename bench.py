@@ -1,0 +1,438 @@
+"""HRPP throughput benchmark on GB300.
+
+One step = one frame of the terrain workload through the whole hot path:
+1920x1080 primary closest-hit rays, then 4 cosine-weighted ambient-occlusion
+any-hit rays per primary hit (tmax 0.5), each batch traced by HRPP against its
+own predictor table (two-phase updates included).  Scene: value-noise terrain
+of 708x708 quads plus 64 icospheres, 2,313,248 triangles, 4-wide BVH.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hrpp|reference]
+
+Prints one JSON line (rank 0).  `value` is HRPP Mrays/s over all ranks with
+the rays already resident on the GPU; `e2e` is the same through the C ABI with
+host buffers (upload and download inside the timed region); `plain` gives the
+same library with no table on the same rays.  The reference arm times the CPU
+oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s (any-hit, closest-hit) HRPP vs plain BVH on 1 GB300; % nodes skipped; HBM GB/s"
+WORKLOAD = ("terrain 708x708 quads + 64 icospheres (2,313,248 tris), 4-wide BVH; 1920x1080 primary closest-hit "
+            "rays + 4 cosine AO any-hit rays per hit (tmax 0.5); HRPP table per mode")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="hrpp", choices=["hrpp", "reference"])
+    ap.add_argument("--frames", type=int, default=4)
+    ap.add_argument("--log2-entries", type=int, default=18)
+    ap.add_argument("--ways", type=int, default=2)
+    ap.add_argument("--precision", type=int, default=6)
+    ap.add_argument("--update", default="two_phase", choices=["two_phase", "online"])
+    ap.add_argument("--quads", type=int, default=708)
+    ap.add_argument("--spheres", type=int, default=64)
+    ap.add_argument("--res", default="1920x1080")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------- helpers --
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.rows = []
+        self.proc = None
+        self.t0 = self.t1 = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(device_index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def mark(self, start: bool):
+        if start:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r for t, r in self.rows if self.t0 is not None and self.t0 - 0.2 <= t <= (self.t1 or t) + 0.2]
+        if not rows:
+            rows = [r for _, r in self.rows][-3:]
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                power.append(float(r[3]))
+            except (ValueError, IndexError):
+                continue
+            for k, name in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("trace_kernel.cuh", "device.cuh"):
+        with open(os.path.join(ROOT, "paper_1910_01304_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None, None
+    src = kernel_source_hash()
+    with open(path) as fh:
+        for line in fh:
+            parts = line.split()
+            if len(parts) >= 4 and parts[0] == "traffic" and parts[1] == kernel:
+                if parts[3] == src:
+                    return float(parts[2]), parts[3]
+                return None, parts[3]
+    return None, None
+
+
+def algorithmic_bytes(st: dict, mode_closest: bool, width: int, ways: int) -> float:
+    """Bytes the method must move for one batch: rays, results, table sets,
+    interior nodes, triangles (traversal and predicted leaves), insert records."""
+    node_b = 64 if width == 2 else 128
+    return (st["rays"] * (32 + (16 if mode_closest else 4)) + st["lookups"] * 8 * ways
+            + st["interior_nodes"] * node_b + (st["tri_tests"] + st["pred_tri_tests"]) * 48 + st["inserts"] * 16)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------- workload --
+
+def make_frames(args, rank, scene_w, H, g, torch):
+    """Primary rays per frame (jittered), their plain closest hits on the GPU,
+    and the ambient-occlusion rays generated from those hits on the host."""
+    from paper_1910_01304_gb300.scenes import workloads as W
+    frames = []
+    for f in range(args.frames):
+        prim = scene_w.primary_rays(frame=1 + f + 1000 * rank)
+        dprim = torch.from_numpy(prim).cuda()
+        hits, _ = H.trace(g, dprim, H.HRPP_CLOSEST_HIT)
+        hh = hits.cpu().numpy()
+        t, p = hh[:, 0], hh[:, 1].view(np.uint32)
+        ao, _ = W.secondary_ao(scene_w, prim, t, p, frame=1 + f + 1000 * rank)
+        frames.append({"prim": dprim, "ao": torch.from_numpy(ao).cuda(), "prim_h": prim, "ao_h": ao})
+    return frames
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_1910_01304_gb300.scenes import workloads as W
+    w, h = map(int, args.res.split("x"))
+    sw = W.terrain_scene(quads=args.quads, n_spheres=args.spheres, res=(w, h))
+    prim = sw.primary_rays(frame=1)
+    ph, _ = O.trace(sw.tris, sw.nodes, sw.prim_index, sw.root, prim[::64], O.CLOSEST_HIT)
+    ao, _ = W.secondary_ao(sw, prim[::64], ph["t"], ph["prim"], frame=1)
+    tc = O.Table(args.log2_entries, args.ways, args.precision, O.TWO_PHASE)
+    ta = O.Table(args.log2_entries, args.ways, args.precision, O.TWO_PHASE)
+    # each step: a bounded sample of one frame (every 256th primary ray and the AO rays of a matching share)
+    n_p = len(prim) // 256
+    n_a = len(ao) // 4
+    def step(k):
+        sp = prim[(k % 256)::256][:n_p]
+        sa = ao[(k % 4)::4][:n_a]
+        O.trace(sw.tris, sw.nodes, sw.prim_index, sw.root, sp, O.CLOSEST_HIT, tc)
+        O.trace(sw.tris, sw.nodes, sw.prim_index, sw.root, sa, O.ANY_HIT, ta)
+        return len(sp) + len(sa)
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    rays = sum(step(args.warmup + k) for k in range(args.steps))
+    dt = time.perf_counter() - t0
+    v = rays / dt / 1e6
+    sample = (f"per step: every 256th primary ray of a 1920x1080 frame ({n_p} closest-hit) and a quarter of the AO "
+              f"rays of every 64th primary hit ({n_a} any-hit), oracle HRPP two-phase")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mrays/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "Mrays/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(args, sw, frames):
+    """The oracle, as it stands, on a bounded sample of frame 0 (one core)."""
+    import oracle as O
+    prim = frames[0]["prim_h"]
+    ao = frames[0]["ao_h"]
+    tc = O.Table(args.log2_entries, args.ways, args.precision, O.TWO_PHASE)
+    ta = O.Table(args.log2_entries, args.ways, args.precision, O.TWO_PHASE)
+    # calibrate the sample to about cpu_seconds of work
+    probe_p, probe_a = prim[::512], ao[::512]
+    t0 = time.perf_counter()
+    O.trace(sw.tris, sw.nodes, sw.prim_index, sw.root, probe_p, O.CLOSEST_HIT, tc)
+    O.trace(sw.tris, sw.nodes, sw.prim_index, sw.root, probe_a, O.ANY_HIT, ta)
+    per = (time.perf_counter() - t0) / (len(probe_p) + len(probe_a))
+    n_total = int(max(10000, min(len(prim) + len(ao), args.cpu_seconds / max(per, 1e-9))))
+    frac = n_total / (len(prim) + len(ao))
+    stride = max(1, int(round(1 / max(frac, 1e-9))))
+    sp, sa = prim[::stride], ao[::stride]
+    tc = O.Table(args.log2_entries, args.ways, args.precision, O.TWO_PHASE)
+    ta = O.Table(args.log2_entries, args.ways, args.precision, O.TWO_PHASE)
+    t0 = time.perf_counter()
+    O.trace(sw.tris, sw.nodes, sw.prim_index, sw.root, sp, O.CLOSEST_HIT, tc)
+    O.trace(sw.tris, sw.nodes, sw.prim_index, sw.root, sa, O.ANY_HIT, ta)
+    dt = time.perf_counter() - t0
+    return {"value": (len(sp) + len(sa)) / dt / 1e6, "unit": "Mrays/s", "cores": 1, "kind": "oracle",
+            "sample": f"every {stride}th ray of frame 0: {len(sp)} primary closest-hit + {len(sa)} AO any-hit rays, "
+                      f"HRPP two-phase, {dt:.1f} s on one host core"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1910_01304_gb300 import hrpp as H
+    from paper_1910_01304_gb300.scenes import workloads as W
+
+    w, h = map(int, args.res.split("x"))
+    sw = W.terrain_scene(quads=args.quads, n_spheres=args.spheres, res=(w, h))
+    g = H.Scene.from_workload(sw)
+    frames = make_frames(args, rank, sw, H, g, torch)
+    upd = H.HRPP_UPDATE_TWO_PHASE if args.update == "two_phase" else H.HRPP_UPDATE_ONLINE
+    tab_c = H.Table(args.log2_entries, args.ways, args.precision, upd)
+    tab_a = H.Table(args.log2_entries, args.ways, args.precision, upd)
+    stream = torch.cuda.current_stream()
+    rays_per_frame = [int(f["prim"].shape[0] + f["ao"].shape[0]) for f in frames]
+    out_c = [torch.empty((f["prim"].shape[0], 4), dtype=torch.float32, device="cuda") for f in frames]
+    out_a = [torch.empty((f["ao"].shape[0],), dtype=torch.int32, device="cuda") for f in frames]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+
+    def run(steps, warm, tables, events=None, offset=0):
+        total = 0
+        for k in range(steps):
+            fi = (offset + k) % len(frames)
+            f = frames[fi]
+            ev = events[k] if events is not None else (None, None)
+            H.trace(g, f["prim"], H.HRPP_CLOSEST_HIT, tables[0], hits=out_c[fi],
+                    kernel_events=ev[0] if ev[0] else None)
+            H.trace(g, f["ao"], H.HRPP_ANY_HIT, tables[1], hits=out_a[fi], kernel_events=ev[1] if ev[1] else None)
+            total += rays_per_frame[fi]
+        return total
+
+    def timed(tables, with_kernel_events):
+        mk = lambda: torch.cuda.Event(enable_timing=True)
+        run(args.warmup, True, tables, offset=0)
+        events = [((mk(), mk()), (mk(), mk())) for _ in range(args.steps)] if with_kernel_events else None
+        barrier()
+        e0, e1 = mk(), mk()
+        e0.record(stream)
+        rays = run(args.steps, False, tables, events=events, offset=args.warmup)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        kt = None
+        if events is not None:
+            kt = {"closest": sum(a[0].elapsed_time(a[1]) for a, _ in events) / args.steps,
+                  "any": sum(b[0].elapsed_time(b[1]) for _, b in events) / args.steps}
+        return rays, ms, kt
+
+    def max_over_ranks(x):
+        if pg is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if pg is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t)
+        return float(t.item())
+
+    # --- HRPP, timed, with clocks sampled over the timed region
+    clocks = ClockSampler(local)
+    run(args.warmup, True, (tab_c, tab_a))
+    barrier()
+    clocks.mark(True)
+    rays, ms, kt = timed((tab_c, tab_a), True)
+    clocks.mark(False)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ms)
+    total_rays = sum_over_ranks(rays)
+    value = total_rays / (ms_max * 1e-3) / 1e6
+
+    # --- plain traversal on the same rays
+    p_rays, p_ms, p_kt = timed((None, None), True)
+    p_value = sum_over_ranks(p_rays) / (max_over_ranks(p_ms) * 1e-3) / 1e6
+
+    # --- counters for one frame (after the timed region: warm tables)
+    f0 = frames[0]
+    _, sc = H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tab_c, stats=True)
+    _, sa = H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tab_a, stats=True)
+    _, pc = H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, None, stats=True)
+    _, pa = H.trace(g, f0["ao"], H.HRPP_ANY_HIT, None, stats=True)
+    g.check()
+
+    # --- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = []
+        for f in frames:
+            hp = torch.from_numpy(f["prim_h"]).pin_memory()
+            ha = torch.from_numpy(f["ao_h"]).pin_memory()
+            oc = torch.empty((hp.shape[0], 4), dtype=torch.float32).pin_memory()
+            oa = torch.empty((ha.shape[0],), dtype=torch.int32).pin_memory()
+            host.append((hp, ha, oc, oa))
+        def e2e_step(k):
+            hp, ha, oc, oa = host[k % len(host)]
+            H.trace(g, hp, H.HRPP_CLOSEST_HIT, tab_c, hits=oc)
+            H.trace(g, ha, H.HRPP_ANY_HIT, tab_a, hits=oa)
+            return hp.shape[0] + ha.shape[0], hp.numel() * 4 + ha.numel() * 4, oc.numel() * 4 + oa.numel() * 4
+        for k in range(args.warmup):
+            e2e_step(k)
+        barrier()
+        t0 = time.perf_counter()
+        er, hb, db = 0, 0, 0
+        for k in range(args.steps):
+            a, b, c = e2e_step(args.warmup + k)
+            er, hb, db = er + a, hb + b, db + c
+        barrier()
+        dt = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": sum_over_ranks(er) / dt / 1e6, "unit": "Mrays/s", "h2d_bytes_per_step": hb // args.steps,
+               "d2h_bytes_per_step": db // args.steps}
+
+    if rank != 0:
+        return 0
+    # --- roofline of the dominant kernel
+    peak, peak_kind = load_peaks()
+    info = g.info()
+    width = info["width"]
+    dom = "any" if kt["any"] >= kt["closest"] else "closest"
+    st_dom = sa if dom == "any" else sc
+    bytes_launch = algorithmic_bytes(st_dom, dom == "closest", width, args.ways)
+    # counters are per frame 0; scale to the average frame of the timed loop
+    avg_rays = np.mean([f["ao" if dom == "any" else "prim"].shape[0] for f in frames])
+    bytes_launch *= avg_rays / st_dom["rays"]
+    achieved = bytes_launch / (kt[dom] * 1e-3) / 1e9
+    kname = f"k_trace<{width}, {'closest' if dom == 'closest' else 'any'}, hrpp>"
+    traffic, traffic_src = recorded_traffic(f"bvh{width}_{dom}")
+
+    def skipped(h, p):
+        return {"prediction_ratio": h["true_pos"] / max(1, h["rays"]),
+                "skipped_exact_box_tests": 1.0 - h["box_tests"] / max(1, p["box_tests"]),
+                "skipped_exact_interior_nodes": 1.0 - h["interior_nodes"] / max(1, p["interior_nodes"]),
+                "positives": h["positives"], "true_pos": h["true_pos"], "false_pos": h["false_pos"],
+                "tp_inexact": h["tp_inexact"], "rays": h["rays"]}
+
+    cpu = None if args.no_cpu else cpu_baseline(args, sw, frames)
+    launches_per_step = 2 + (2 if args.update == "two_phase" else 0)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tris": int(sw.n_tris), "bvh_width": width,
+                   "rays_per_step": float(np.mean(rays_per_frame)), "frames": args.frames,
+                   "table": {"log2_entries": args.log2_entries, "ways": args.ways, "precision": args.precision,
+                             "update": args.update},
+                   "l2": f"inputs larger than L2: {np.mean(rays_per_frame) * 32 / 1e6:.0f} MB of rays per step, "
+                         f"{args.frames} frames cycled; scene resident"},
+        "plain": {"value": p_value, "unit": "Mrays/s", "speedup_hrpp_over_plain": value / p_value,
+                  "kernel_ms": p_kt},
+        "per_mode_kernel_ms": kt,
+        "skipped": {"closest": skipped(sc, pc), "any": skipped(sa, pa),
+                    "paper_context": "paper Table 1 (PBRT limit study, no hardware stated): 30-69% hit-all, "
+                                     "<1-48% hit-any savings"},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "traffic_source_hash": traffic_src, "kernel_source_hash": kernel_source_hash()},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,224 @@
+/*
+ * hrpp.h -- C ABI of the GB300 Hash-Based Ray Path Prediction library.
+ *
+ * HRPP (Demoullin, Gubran, Aamodt: "Hash-Based Ray Path Prediction: Skipping
+ * BVH Traversal Computation by Exploiting Ray Locality") fronts BVH ray
+ * traversal with a predictor table.  Each ray is hashed from the IEEE-754 bits
+ * of its origin and direction (Sec. 5); the table maps the hash to leaf nodes
+ * that earlier rays with the same hash reached (Sec. 4.2).  A ray first tests
+ * the predicted leaves; when that answers the query the interior traversal is
+ * skipped, otherwise the ray traverses the BVH as usual and its leaf is
+ * inserted (Sec. 4.2-4.3, Sec. 5).  Results are exactly those of plain
+ * traversal: any-hit rays stop at a hit found in a predicted leaf, and
+ * closest-hit rays use the predicted hit only to bound an exact traversal.
+ *
+ * Conventions for every entry point:
+ *   - Errors are returned as hrpp_status codes; nothing aborts or throws.
+ *     hrpp_last_error() gives a message for the calling thread's last
+ *     non-OK status.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Device work is enqueued asynchronously on it.
+ *   - Handles are opaque; destroy(NULL) is a no-op.  The library copies every
+ *     host array it is given; the caller keeps ownership of its buffers.
+ *   - Objects live on the CUDA device that was current when they were made;
+ *     calls switch to that device and restore the caller's afterwards.
+ */
+#ifndef HRPP_H
+#define HRPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HRPP_VERSION 1
+#define HRPP_NO_HIT 0xFFFFFFFFu
+#define HRPP_EMPTY_WORD 0xFFFFFFFFFFFFFFFFull
+#define HRPP_MAX_LEAF_TRIS 4      /* triangles per leaf */
+#define HRPP_MAX_TRIS (1u << 26)  /* triangles per scene */
+#define HRPP_MAX_STACK 64         /* traversal stack entries per ray */
+
+typedef enum {
+    HRPP_OK = 0,
+    HRPP_ERR_INVALID_ARG = 1,     /* NULL where a pointer is required, bad size, mode or alignment */
+    HRPP_ERR_INVALID_BVH = 2,     /* the node array is not a tree over all triangles */
+    HRPP_ERR_OOM = 3,             /* a device or host allocation failed */
+    HRPP_ERR_CUDA = 4,            /* a CUDA runtime call failed */
+    HRPP_ERR_TRAVERSAL_LIMIT = 5, /* a ray exceeded its traversal step or stack bound */
+    HRPP_ERR_UNSUPPORTED = 6      /* valid but beyond this build's limits (HRPP_MAX_*) */
+} hrpp_status;
+
+/* Query paradigms (Sec. 4.1): shadow rays look for any intersection
+ * ("hit-any"); most others need the closest one ("hit-all"). */
+typedef enum { HRPP_ANY_HIT = 0, HRPP_CLOSEST_HIT = 1 } hrpp_mode;
+
+/* When a ray's insert lands in the table.
+ *   TWO_PHASE  every lookup of one hrpp_trace call sees the table as it was
+ *              when the call started; after the batch, each slot keeps the
+ *              insert of the highest ray index aimed at it.  Deterministic:
+ *              results, table and statistics repeat bit for bit.
+ *   ONLINE     inserts are written while the batch runs (64-bit atomic
+ *              exchange), so later rays may see them.  Results stay exact;
+ *              table contents and statistics depend on scheduling.
+ *   FROZEN     lookups only; the table is never written. */
+typedef enum { HRPP_UPDATE_TWO_PHASE = 0, HRPP_UPDATE_ONLINE = 1, HRPP_UPDATE_FROZEN = 2 } hrpp_update_mode;
+
+/* Canonical BVH node (48 bytes; host memory).  A node is a leaf iff count > 0;
+ * a leaf covers triangles prim_index[first .. first+count).  An interior
+ * node's non-negative child entries index the node array; -1 = no child.
+ * lo/hi bound the node's triangles; every child box must lie inside its
+ * parent's.  Width 2 uses child[0..1], width 4 child[0..3]. */
+typedef struct hrpp_bvh_node {
+    float lo[3], hi[3];
+    int32_t child[4];
+    uint32_t first, count;
+} hrpp_bvh_node;
+
+/* Ray (32 bytes, 16-byte aligned): origin, tmin, direction, tmax.  A hit at
+ * distance t counts iff tmin < t < tmax.  The direction is hashed exactly as
+ * given (callers normally pass unit vectors). */
+typedef struct hrpp_ray {
+    float ox, oy, oz, tmin;
+    float dx, dy, dz, tmax;
+} hrpp_ray;
+
+/* Closest-hit result (16 bytes): distance, triangle index in the caller's
+ * tri_verts order, barycentrics of v1 (u) and v2 (v).  A miss is
+ * (+inf, HRPP_NO_HIT, 0, 0).  Any-hit results are one uint32 per ray: the
+ * index of a triangle the ray hits, or HRPP_NO_HIT. */
+typedef struct hrpp_hit {
+    float t;
+    uint32_t prim;
+    float u, v;
+} hrpp_hit;
+
+/* Counters of one hrpp_trace call (Sec. 4.3 outcome classes and node work).
+ *   lookups           rays that consulted the table
+ *   positives         lookups that found at least one predicted leaf
+ *   true_pos          positives whose predicted leaves held a valid hit
+ *   false_pos         positives whose predicted leaves held none
+ *   negatives         lookups with no predicted leaf
+ *   tp_inexact        closest-hit true positives whose exact traversal found
+ *                     a closer hit than the predicted leaves (Sec. 4.3)
+ *   inserts           rays that asked to insert the leaf they reached
+ *   dup_inserts       two-phase: inserts that lost their slot to a later ray
+ *                     of the same batch; online: inserts of a value the slot
+ *                     already held
+ *   evictions         inserts that overwrote a valid table word
+ *   interior_nodes,   interior nodes entered, child boxes tested, leaves
+ *   box_tests,        entered and triangles tested by traversal
+ *   leaves, tri_tests
+ *   pred_leaves,      predicted leaves and their triangles tested before
+ *   pred_tri_tests    (or instead of) traversal */
+typedef struct hrpp_stats {
+    uint64_t rays, hits, lookups, positives, true_pos, false_pos, negatives, tp_inexact;
+    uint64_t inserts, dup_inserts, evictions;
+    uint64_t interior_nodes, box_tests, leaves, tri_tests, pred_leaves, pred_tri_tests;
+    uint64_t reserved[3];
+} hrpp_stats;
+
+typedef struct hrpp_scene_info {
+    uint32_t n_tris, n_interior, n_leaves, max_depth;
+    uint32_t width, root_is_leaf;
+    uint64_t device_bytes;
+} hrpp_scene_info;
+
+/* Per-call options of hrpp_trace_ex (all fields may be zero).
+ *   kernel_start/kernel_stop  cudaEvent_t (as void*) recorded on `stream`
+ *                             immediately before and after the traversal
+ *                             kernel, for timing it alone
+ *   block_threads             threads per block of the traversal kernel:
+ *                             0 = default, else 64, 128, 256 or 512 */
+typedef struct hrpp_trace_opts {
+    void *kernel_start, *kernel_stop;
+    uint32_t block_threads;
+    uint32_t reserved[7];
+} hrpp_trace_opts;
+
+typedef struct hrpp_scene hrpp_scene;
+typedef struct hrpp_table hrpp_table;
+
+/* Checks a scene description on the host without touching any GPU.
+ * tri_verts: 9 floats per triangle (v0, v1, v2).  nodes/root: the BVH
+ * (canonical format above).  prim_index: n_prim_index == n_tris entries, a
+ * permutation of 0..n_tris-1 in leaf order.  width: 2 or 4.  Accepts iff the
+ * nodes reachable from root form a tree (no cycles, no node reached twice),
+ * every triangle lies in exactly one leaf, leaves hold 1..HRPP_MAX_LEAF_TRIS
+ * triangles, every child box lies inside its parent's, every leaf box holds
+ * its triangles, and the traversal stack fits HRPP_MAX_STACK.  Fills *info
+ * when info != NULL.  Returns INVALID_ARG / INVALID_BVH / UNSUPPORTED. */
+hrpp_status hrpp_scene_validate(const float *tri_verts, uint32_t n_tris, const hrpp_bvh_node *nodes,
+                                uint32_t n_nodes, uint32_t root, const uint32_t *prim_index,
+                                uint32_t n_prim_index, int width, hrpp_scene_info *info);
+
+/* Validates (as hrpp_scene_validate), converts the BVH to the device layout
+ * (width 2: 64-byte nodes holding both child boxes; width 4: 128-byte SoA
+ * nodes; triangles stored as v0, v1-v0, v2-v0 in leaf order), and uploads it
+ * to the current device.  Blocking.  *out is set only on success. */
+hrpp_status hrpp_scene_create(const float *tri_verts, uint32_t n_tris, const hrpp_bvh_node *nodes,
+                              uint32_t n_nodes, uint32_t root, const uint32_t *prim_index,
+                              uint32_t n_prim_index, int width, hrpp_scene **out);
+hrpp_status hrpp_scene_get_info(const hrpp_scene *scene, hrpp_scene_info *info);
+/* Waits for `stream`, then reads and clears the scene's sticky device error
+ * flag: TRAVERSAL_LIMIT if a kernel on this scene stopped a ray early. */
+hrpp_status hrpp_scene_check(hrpp_scene *scene, void *stream);
+void hrpp_scene_destroy(hrpp_scene *scene);
+
+/* Predictor table of 2^log2_entries 64-bit words in 2^log2_entries / ways
+ * sets of `ways` words (ways in {1,2,4,8}; log2_entries in [ways' log2, 28]).
+ * A word holds (tag << 28 | leaf), leaf = first_prim_index_slot << 2 |
+ * (count - 1), or HRPP_EMPTY_WORD.  Paper Sec. 4.2: the table maps ray
+ * hashes to leaf nodes; the paper's table is unbounded (Sec. 4.3, 6), this
+ * one has fixed size: a leaf goes to way (leaf * 0x9E3779B1) >> (32 -
+ * log2 ways) of its set, so one hash can hold up to `ways` distinct leaves.
+ * Starts empty, precision 6 (Table 1), TWO_PHASE.  Blocking. */
+hrpp_status hrpp_table_create(int log2_entries, int ways, hrpp_table **out);
+/* precision_bits in [1, 7]: bits kept from each float's exponent and
+ * mantissa by the Sec. 5 hash.  update_mode: hrpp_update_mode. */
+hrpp_status hrpp_table_configure(hrpp_table *table, int precision_bits, int update_mode);
+/* Empties the table (asynchronous on stream) and unbinds it from its scene.
+ * A table binds to the first scene it is traced with; tracing it with
+ * another scene returns INVALID_ARG until it is reset. */
+hrpp_status hrpp_table_reset(hrpp_table *table, void *stream);
+/* Copies the 2^log2_entries table words to / from host memory (blocking;
+ * n_words must equal the table size).  Import validates nothing about the
+ * words' leaves: import only tables exported from the same scene. */
+hrpp_status hrpp_table_export(const hrpp_table *table, uint64_t *host_words, size_t n_words);
+hrpp_status hrpp_table_import(hrpp_table *table, const uint64_t *host_words, size_t n_words);
+hrpp_status hrpp_table_get_config(const hrpp_table *table, int *log2_entries, int *ways, int *precision_bits,
+                                  int *update_mode);
+void hrpp_table_destroy(hrpp_table *table);
+
+/* Traces n_rays rays against scene.  table == NULL: plain BVH traversal.
+ * Otherwise HRPP against table (Sec. 4.2-4.3), which it may update.
+ *   rays      n_rays hrpp_ray, 16-byte aligned, device or host memory
+ *   out_hits  closest: n_rays hrpp_hit (16-byte aligned); any: n_rays uint32
+ *             (4-byte aligned); device or host memory
+ *   out_stats NULL, or one hrpp_stats in device or host memory.  A host
+ *             pointer makes the call wait for its kernels.
+ * Host ray/hit buffers are staged through device memory the call allocates
+ * and frees (stream-ordered); the call then returns after the results are
+ * back in host memory.  Device buffers keep the call fully asynchronous.
+ * Calls that use the same table must be ordered on one stream.
+ * n_rays == 0 does nothing (stats, if requested, are zeroed); n_rays above
+ * 2^31 returns UNSUPPORTED.
+ * Returns TRAVERSAL_LIMIT when the call waited and a ray was stopped early
+ * (see hrpp_scene_check otherwise). */
+hrpp_status hrpp_trace(const hrpp_scene *scene, hrpp_table *table, const hrpp_ray *rays, uint32_t n_rays,
+                       hrpp_mode mode, void *out_hits, hrpp_stats *out_stats, void *stream);
+/* hrpp_trace with per-call options (opts may be NULL). */
+hrpp_status hrpp_trace_ex(const hrpp_scene *scene, hrpp_table *table, const hrpp_ray *rays, uint32_t n_rays,
+                          hrpp_mode mode, void *out_hits, hrpp_stats *out_stats, void *stream,
+                          const hrpp_trace_opts *opts);
+
+const char *hrpp_last_error(void);
+const char *hrpp_status_string(hrpp_status status);
+int hrpp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HRPP_H */

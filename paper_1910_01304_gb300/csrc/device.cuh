@@ -1,0 +1,192 @@
+// Device-side definitions of the HRPP library: layouts, launch parameters and
+// the per-ray arithmetic (Sec. 5 hash, table index, slab test, Moller-Trumbore).
+//
+// Every floating-point step below is written with an explicitly rounded
+// intrinsic (__fmul_rn, __fadd_rn, __fsub_rn, __fmaf_rn, __frcp_rn), so the
+// compiler cannot contract or reorder it: a given ray and triangle always give
+// the same bits.
+#pragma once
+
+#include <cstdint>
+
+#include "hrpp.h"
+
+namespace hrpp {
+
+constexpr int kTagBits = 36;
+constexpr int kLeafBits = 28;
+constexpr uint64_t kLeafMask = (1ull << kLeafBits) - 1ull;
+constexpr uint64_t kTagMask = (1ull << kTagBits) - 1ull;
+constexpr uint64_t kM48 = (1ull << 48) - 1ull;
+constexpr int32_t kEmptyRef = INT32_MIN;  // no child in this slot
+constexpr int kStack = HRPP_MAX_STACK;
+
+// error bits of a scene's sticky device flag
+constexpr uint32_t kErrStack = 1u;
+constexpr uint32_t kErrSteps = 2u;
+
+// statistics slots (hrpp_stats order)
+enum Stat : int {
+    ST_RAYS, ST_HITS, ST_LOOKUPS, ST_POSITIVES, ST_TRUE_POS, ST_FALSE_POS, ST_NEGATIVES, ST_TP_INEXACT,
+    ST_INSERTS, ST_DUP_INSERTS, ST_EVICTIONS, ST_INTERIOR, ST_BOX_TESTS, ST_LEAVES, ST_TRI_TESTS,
+    ST_PRED_LEAVES, ST_PRED_TRI_TESTS, ST_N = 20
+};
+
+// Per-call device control block: the ray pool's cursor, the insert-record
+// count and the statistics.  Zeroed before each call.
+struct __align__(16) Ctl {
+    unsigned int next_ray;
+    unsigned int n_records;
+    unsigned int pad[2];
+    unsigned long long stats[ST_N];
+};
+
+// Two-phase insert record: table slot, ray index + 1, table word.
+struct __align__(16) Record {
+    uint32_t slot;
+    uint32_t ray1;
+    uint64_t word;
+};
+
+struct TraceParams {
+    const float4 *nodes;     // width 2: 4 float4 per node; width 4: 8 float4 per node
+    const float4 *tris;      // 3 float4 per triangle: (v0, prim bits), (v1 - v0), (v2 - v0)
+    uint32_t n_tris;
+    int32_t root_ref;        // >= 0 interior node, else ~leaf
+    uint32_t max_steps;      // traversal steps per ray before the ray is stopped
+    const float4 *rays;      // 2 float4 per ray
+    uint32_t n_rays;
+    void *hits;              // hrpp_hit[n] (closest) or uint32_t[n] (any)
+    uint64_t *table;         // table words (NULL: plain traversal)
+    uint32_t *winner;        // two-phase: highest ray index + 1 per slot
+    Record *records;         // two-phase insert records
+    int log2_sets, log2_ways, precision, update_mode;
+    Ctl *ctl;
+    uint32_t *error;         // scene's sticky error flag
+};
+
+// ---------------------------------------------------------------- hashing --
+
+// Sec. 5: sign bit, then the p most significant exponent bits, then the p most
+// significant mantissa bits of the float's IEEE-754 encoding.
+__device__ __forceinline__ uint32_t hash_float(float f, int p)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t sign = b >> 31;
+    const uint32_t expo = (b >> 23) & 0xFFu;
+    const uint32_t mant = b & 0x7FFFFFu;
+    return (sign << (2 * p)) | ((expo >> (8 - p)) << p) | (mant >> (23 - p));
+}
+
+// Sec. 5: origin hashes XOR the swizzled direction hashes (o.x^d.z, o.y^d.y,
+// o.z^d.x), packed into 16-bit fields of a 48-bit key.
+__device__ __forceinline__ uint64_t ray_key(float4 o, float4 d, int p)
+{
+    const uint64_t h0 = hash_float(o.x, p) ^ hash_float(d.z, p);
+    const uint64_t h1 = hash_float(o.y, p) ^ hash_float(d.y, p);
+    const uint64_t h2 = hash_float(o.z, p) ^ hash_float(d.x, p);
+    return h0 | (h1 << 16) | (h2 << 32);
+}
+
+// Bijection of 48-bit keys; its low bits pick the set, the rest is the tag.
+__device__ __forceinline__ uint64_t mix48(uint64_t k)
+{
+    k &= kM48;
+    k ^= k >> 23;
+    k = (k * 0x9E3779B97F4Bull) & kM48;
+    k ^= k >> 25;
+    k = (k * 0xC2B2AE3D27D5ull) & kM48;
+    k ^= k >> 21;
+    return k;
+}
+
+__device__ __forceinline__ uint32_t way_of(uint32_t leaf, int log2_ways)
+{
+    return log2_ways == 0 ? 0u : (leaf * 0x9E3779B1u) >> (32 - log2_ways);
+}
+
+// ---------------------------------------------------------------- geometry --
+
+struct RayInv {
+    float ix, iy, iz;     // reciprocal direction
+    float oix, oiy, oiz;  // origin * reciprocal direction
+};
+
+__device__ __forceinline__ float safe_rcp(float d)
+{
+    // |d| < 2^-80 -> copysign(2^-80, d): keeps the reciprocal finite
+    const float m = 0x1p-80f;
+    if (fabsf(d) < m) d = copysignf(m, d);
+    return __frcp_rn(d);
+}
+
+__device__ __forceinline__ RayInv ray_inverse(float4 o, float4 d)
+{
+    RayInv r;
+    r.ix = safe_rcp(d.x);
+    r.iy = safe_rcp(d.y);
+    r.iz = safe_rcp(d.z);
+    r.oix = __fmul_rn(o.x, r.ix);
+    r.oiy = __fmul_rn(o.y, r.iy);
+    r.oiz = __fmul_rn(o.z, r.iz);
+    return r;
+}
+
+// Slab test: plane distances lo*inv - o*inv (one fused multiply-add each);
+// entry = max(tmin, nearest planes), exit = min(tcur, farthest planes).
+__device__ __forceinline__ bool slab(const RayInv &r, float tmin, float tcur, float lox, float hix, float loy,
+                                     float hiy, float loz, float hiz, float &tn)
+{
+    const float x0 = __fmaf_rn(lox, r.ix, -r.oix), x1 = __fmaf_rn(hix, r.ix, -r.oix);
+    const float y0 = __fmaf_rn(loy, r.iy, -r.oiy), y1 = __fmaf_rn(hiy, r.iy, -r.oiy);
+    const float z0 = __fmaf_rn(loz, r.iz, -r.oiz), z1 = __fmaf_rn(hiz, r.iz, -r.oiz);
+    const float nx = fminf(x0, x1), fx = fmaxf(x0, x1);
+    const float ny = fminf(y0, y1), fy = fmaxf(y0, y1);
+    const float nz = fminf(z0, z1), fz = fmaxf(z0, z1);
+    tn = fmaxf(fmaxf(nx, ny), fmaxf(nz, tmin));
+    const float tf = fminf(fminf(fx, fy), fminf(fz, tcur));
+    return tn <= tf;
+}
+
+__device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, float by, float bz)
+{
+    return __fmaf_rn(ax, bx, __fmaf_rn(ay, by, __fmul_rn(az, bz)));
+}
+
+// Moller-Trumbore on a stored triangle (v0, e1 = v1 - v0, e2 = v2 - v0).
+// Valid iff det != 0, u in [0,1], v >= 0, u + v <= 1, tmin < t < tmax.
+__device__ __forceinline__ bool tri_test(float4 o, float4 d, float4 v0, float4 e1, float4 e2, float &t_out,
+                                         float &u_out, float &v_out)
+{
+    // p = d x e2
+    const float px = __fmaf_rn(d.y, e2.z, -__fmul_rn(d.z, e2.y));
+    const float py = __fmaf_rn(d.z, e2.x, -__fmul_rn(d.x, e2.z));
+    const float pz = __fmaf_rn(d.x, e2.y, -__fmul_rn(d.y, e2.x));
+    const float det = dot3(e1.x, e1.y, e1.z, px, py, pz);
+    if (det == 0.0f) return false;
+    const float inv = __frcp_rn(det);
+    const float sx = __fsub_rn(o.x, v0.x), sy = __fsub_rn(o.y, v0.y), sz = __fsub_rn(o.z, v0.z);
+    const float u = __fmul_rn(dot3(sx, sy, sz, px, py, pz), inv);
+    // q = s x e1
+    const float qx = __fmaf_rn(sy, e1.z, -__fmul_rn(sz, e1.y));
+    const float qy = __fmaf_rn(sz, e1.x, -__fmul_rn(sx, e1.z));
+    const float qz = __fmaf_rn(sx, e1.y, -__fmul_rn(sy, e1.x));
+    const float v = __fmul_rn(dot3(d.x, d.y, d.z, qx, qy, qz), inv);
+    const float t = __fmul_rn(dot3(e2.x, e2.y, e2.z, qx, qy, qz), inv);
+    if (!(u >= 0.0f && u <= 1.0f && v >= 0.0f && __fadd_rn(u, v) <= 1.0f && t > o.w && t < d.w)) return false;
+    t_out = t;
+    u_out = u;
+    v_out = v;
+    return true;
+}
+
+// host launchers (trace_bvh2.cu, trace_bvh4.cu, table.cu)
+cudaError_t launch_trace_w2(bool closest, bool stats, const TraceParams &p, int block_threads,
+                            int blocks_per_sm_cap, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1);
+cudaError_t launch_trace_w4(bool closest, bool stats, const TraceParams &p, int block_threads,
+                            int blocks_per_sm_cap, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1);
+cudaError_t launch_table_apply(uint64_t *table, uint32_t *winner, const Record *records, Ctl *ctl,
+                               uint32_t max_records, cudaStream_t stream);
+cudaError_t launch_table_fill(uint64_t *words, uint64_t n_words, cudaStream_t stream);
+
+}  // namespace hrpp

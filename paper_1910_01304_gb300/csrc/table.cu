@@ -1,0 +1,68 @@
+// Predictor table maintenance kernels.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace hrpp {
+
+// Two-phase update, after the batch: each slot takes the word of the record
+// with the highest ray index aimed at it (its index + 1 is in winner[slot]).
+// The winning record writes the word and zeroes winner[slot] for the next
+// call; a losing record reads either the winner's index or zero, never its
+// own, so the outcome does not depend on scheduling.
+__global__ void __launch_bounds__(256) k_apply(uint64_t *table, uint32_t *winner, const Record *rec, Ctl *ctl,
+                                               uint32_t max_records)
+{
+    const uint32_t n = min(ctl->n_records, max_records);
+    uint32_t evict = 0, lost = 0;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const Record x = rec[r];
+        if (winner[x.slot] == x.ray1) {
+            const uint64_t old = table[x.slot];
+            table[x.slot] = x.word;
+            winner[x.slot] = 0u;
+            evict += old != HRPP_EMPTY_WORD;
+        } else {
+            ++lost;
+        }
+    }
+    evict = __reduce_add_sync(0xFFFFFFFFu, evict);
+    lost = __reduce_add_sync(0xFFFFFFFFu, lost);
+    if ((threadIdx.x & 31u) == 0) {
+        if (evict) atomicAdd(&ctl->stats[ST_EVICTIONS], (unsigned long long)evict);
+        if (lost) atomicAdd(&ctl->stats[ST_DUP_INSERTS], (unsigned long long)lost);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_fill(uint64_t *words, uint64_t n)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        words[i] = HRPP_EMPTY_WORD;
+}
+
+cudaError_t launch_table_apply(uint64_t *table, uint32_t *winner, const Record *records, Ctl *ctl,
+                               uint32_t max_records, cudaStream_t stream)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint32_t blocks = (max_records + 255u) / 256u;
+    if (blocks > (uint32_t)sms * 4u) blocks = (uint32_t)sms * 4u;
+    if (blocks < 1) blocks = 1;
+    k_apply<<<blocks, 256, 0, stream>>>(table, winner, records, ctl, max_records);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table_fill(uint64_t *words, uint64_t n_words, cudaStream_t stream)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint64_t blocks = (n_words + 255u) / 256u;
+    if (blocks > (uint64_t)sms * 8u) blocks = (uint64_t)sms * 8u;
+    if (blocks < 1) blocks = 1;
+    k_fill<<<(unsigned)blocks, 256, 0, stream>>>(words, n_words);
+    return cudaGetLastError();
+}
+
+}  // namespace hrpp

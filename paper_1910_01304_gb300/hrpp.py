@@ -1,0 +1,266 @@
+"""Python binding of the HRPP C ABI (include/hrpp.h), via ctypes.
+
+The functions named hrpp_* mirror the C entry points one to one and only
+marshal arguments.  `Scene`, `Table` and `trace` are thin conveniences over
+them that accept numpy arrays (host) and torch tensors (device or host) and
+turn non-OK statuses into HrppError.  All computation happens in libhrpp.so;
+there is no fallback: if the library is missing, importing fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhrpp.so")
+
+HRPP_OK, HRPP_ERR_INVALID_ARG, HRPP_ERR_INVALID_BVH, HRPP_ERR_OOM = 0, 1, 2, 3
+HRPP_ERR_CUDA, HRPP_ERR_TRAVERSAL_LIMIT, HRPP_ERR_UNSUPPORTED = 4, 5, 6
+HRPP_ANY_HIT, HRPP_CLOSEST_HIT = 0, 1
+HRPP_UPDATE_TWO_PHASE, HRPP_UPDATE_ONLINE, HRPP_UPDATE_FROZEN = 0, 1, 2
+HRPP_NO_HIT = 0xFFFFFFFF
+HRPP_EMPTY_WORD = 0xFFFFFFFFFFFFFFFF
+STAT_NAMES = ["rays", "hits", "lookups", "positives", "true_pos", "false_pos", "negatives", "tp_inexact",
+              "inserts", "dup_inserts", "evictions", "interior_nodes", "box_tests", "leaves", "tri_tests",
+              "pred_leaves", "pred_tri_tests"]
+
+
+class hrpp_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in STAT_NAMES] + [("reserved", ctypes.c_uint64 * 3)]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n in STAT_NAMES}
+
+
+class hrpp_scene_info(ctypes.Structure):
+    _fields_ = [("n_tris", ctypes.c_uint32), ("n_interior", ctypes.c_uint32), ("n_leaves", ctypes.c_uint32),
+                ("max_depth", ctypes.c_uint32), ("width", ctypes.c_uint32), ("root_is_leaf", ctypes.c_uint32),
+                ("device_bytes", ctypes.c_uint64)]
+
+
+class hrpp_trace_opts(ctypes.Structure):
+    _fields_ = [("kernel_start", ctypes.c_void_p), ("kernel_stop", ctypes.c_void_p),
+                ("block_threads", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 7)]
+
+
+class HrppError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(message)
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_1910_01304_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, u32, i32, sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t
+    st = ctypes.c_int
+    sig = {
+        "hrpp_scene_validate": (st, [P, u32, P, u32, u32, P, u32, i32, P]),
+        "hrpp_scene_create": (st, [P, u32, P, u32, u32, P, u32, i32, P]),
+        "hrpp_scene_get_info": (st, [P, P]),
+        "hrpp_scene_check": (st, [P, P]),
+        "hrpp_scene_destroy": (None, [P]),
+        "hrpp_table_create": (st, [i32, i32, P]),
+        "hrpp_table_configure": (st, [P, i32, i32]),
+        "hrpp_table_reset": (st, [P, P]),
+        "hrpp_table_export": (st, [P, P, sz]),
+        "hrpp_table_import": (st, [P, P, sz]),
+        "hrpp_table_get_config": (st, [P, P, P, P, P]),
+        "hrpp_table_destroy": (None, [P]),
+        "hrpp_trace": (st, [P, P, P, u32, i32, P, P, P]),
+        "hrpp_trace_ex": (st, [P, P, P, u32, i32, P, P, P, P]),
+        "hrpp_last_error": (ctypes.c_char_p, []),
+        "hrpp_status_string": (ctypes.c_char_p, [st]),
+        "hrpp_version": (i32, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+# ------------------------------------------------ one-to-one C entry points --
+
+hrpp_scene_validate = _lib.hrpp_scene_validate
+hrpp_scene_create = _lib.hrpp_scene_create
+hrpp_scene_get_info = _lib.hrpp_scene_get_info
+hrpp_scene_check = _lib.hrpp_scene_check
+hrpp_scene_destroy = _lib.hrpp_scene_destroy
+hrpp_table_create = _lib.hrpp_table_create
+hrpp_table_configure = _lib.hrpp_table_configure
+hrpp_table_reset = _lib.hrpp_table_reset
+hrpp_table_export = _lib.hrpp_table_export
+hrpp_table_import = _lib.hrpp_table_import
+hrpp_table_get_config = _lib.hrpp_table_get_config
+hrpp_table_destroy = _lib.hrpp_table_destroy
+hrpp_trace = _lib.hrpp_trace
+hrpp_trace_ex = _lib.hrpp_trace_ex
+hrpp_last_error = _lib.hrpp_last_error
+hrpp_status_string = _lib.hrpp_status_string
+hrpp_version = _lib.hrpp_version
+
+
+def check(status: int):
+    if status != HRPP_OK:
+        raise HrppError(status, (hrpp_last_error() or b"").decode())
+
+
+# --------------------------------------------------------- conveniences --
+
+def _ptr(x):
+    """Address of a numpy array or torch tensor (contiguous)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    assert x.is_contiguous()
+    return x.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def validate_scene(tris, nodes, prim_index, root: int, width: int) -> dict:
+    tris = np.ascontiguousarray(tris, np.float32).reshape(-1, 9)
+    nodes = np.ascontiguousarray(nodes)
+    prim_index = np.ascontiguousarray(prim_index, np.uint32)
+    info = hrpp_scene_info()
+    check(hrpp_scene_validate(_ptr(tris), tris.shape[0], _ptr(nodes), nodes.shape[0], root, _ptr(prim_index),
+                              prim_index.shape[0], width, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in info._fields_}
+
+
+class Scene:
+    """Device-resident scene (hrpp_scene_create)."""
+
+    def __init__(self, tris, nodes, prim_index, root: int = 0, width: int = 2):
+        tris = np.ascontiguousarray(tris, np.float32).reshape(-1, 9)
+        nodes = np.ascontiguousarray(nodes)
+        assert nodes.dtype.itemsize == 48
+        prim_index = np.ascontiguousarray(prim_index, np.uint32)
+        h = ctypes.c_void_p()
+        check(hrpp_scene_create(_ptr(tris), tris.shape[0], _ptr(nodes), nodes.shape[0], root, _ptr(prim_index),
+                                prim_index.shape[0], width, ctypes.byref(h)))
+        self.handle = h
+        self.width = width
+        self.n_tris = tris.shape[0]
+
+    @classmethod
+    def from_workload(cls, s):
+        return cls(s.tris, s.nodes, s.prim_index, s.root, s.width)
+
+    def info(self) -> dict:
+        info = hrpp_scene_info()
+        check(hrpp_scene_get_info(self.handle, ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in info._fields_}
+
+    def check(self, stream=None):
+        check(hrpp_scene_check(self.handle, _stream_handle(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hrpp_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Table:
+    """Predictor table (hrpp_table_create / hrpp_table_configure)."""
+
+    def __init__(self, log2_entries: int, ways: int = 1, precision: int = 6, update_mode: int = HRPP_UPDATE_TWO_PHASE):
+        h = ctypes.c_void_p()
+        check(hrpp_table_create(log2_entries, ways, ctypes.byref(h)))
+        self.handle = h
+        self.log2_entries = log2_entries
+        self.ways = ways
+        self.configure(precision, update_mode)
+
+    def configure(self, precision: int, update_mode: int):
+        check(hrpp_table_configure(self.handle, precision, update_mode))
+        self.precision = precision
+        self.update_mode = update_mode
+
+    def reset(self, stream=None):
+        check(hrpp_table_reset(self.handle, _stream_handle(stream)))
+
+    def export(self) -> np.ndarray:
+        out = np.empty(1 << self.log2_entries, np.uint64)
+        check(hrpp_table_export(self.handle, _ptr(out), out.shape[0]))
+        return out
+
+    def import_(self, words: np.ndarray):
+        words = np.ascontiguousarray(words, np.uint64)
+        check(hrpp_table_import(self.handle, _ptr(words), words.shape[0]))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hrpp_table_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, stats: bool = False,
+          stream=None, kernel_events=None, block_threads: int = 0):
+    """Traces rays ([n, 8] float32 torch tensor on the GPU, or a host numpy
+    array / torch tensor).  Returns (hits, stats dict or None).
+
+    closest-hit hits: [n, 4] float32 (t, prim bits, u, v); any-hit: [n] int32
+    (prim or -1).  Device rays give device hits unless `hits` is passed."""
+    is_np = isinstance(rays, np.ndarray)
+    n = int(rays.shape[0])
+    if hits is None:
+        if is_np:
+            hits = np.empty((n, 4), np.float32) if mode == HRPP_CLOSEST_HIT else np.empty(n, np.int32)
+        else:
+            import torch
+            shape = (n, 4) if mode == HRPP_CLOSEST_HIT else (n,)
+            dtype = torch.float32 if mode == HRPP_CLOSEST_HIT else torch.int32
+            hits = torch.empty(shape, dtype=dtype, device=rays.device)
+    st = hrpp_stats() if stats else None
+    opts = None
+    if kernel_events is not None or block_threads:
+        opts = hrpp_trace_opts()
+        if kernel_events is not None:
+            opts.kernel_start = kernel_events[0].cuda_event
+            opts.kernel_stop = kernel_events[1].cuda_event
+        opts.block_threads = block_threads
+    check(hrpp_trace_ex(scene.handle, table.handle if table is not None else None, _ptr(rays), n, mode, _ptr(hits),
+                        ctypes.byref(st) if st is not None else None, _stream_handle(stream),
+                        ctypes.byref(opts) if opts is not None else None))
+    return hits, (st.as_dict() if st is not None else None)
+
+
+def closest_fields(hits):
+    """Splits closest-hit output [n, 4] into (t, prim uint32, u, v) numpy arrays."""
+    if not isinstance(hits, np.ndarray):
+        hits = hits.cpu().numpy()
+    h = np.ascontiguousarray(hits, np.float32)
+    return h[:, 0].copy(), h[:, 1].view(np.uint32).copy(), h[:, 2].copy(), h[:, 3].copy()

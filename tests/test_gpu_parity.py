@@ -1,0 +1,225 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle.
+
+Traversal arithmetic is the same IEEE-754 sequence on both sides, so hits
+(t, prim, u, v bit patterns), any-hit prims, every statistics counter and,
+in two-phase mode, the table words must be identical.  The north-star
+tolerances (ties within 1e-6 relative t, t within 1e-5 relative) are applied
+where the GPU is compared with brute force instead of the oracle's traversal.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import (STAT_KEYS, any_prims, as_words, assert_same_hits, assert_same_stats, gpu_trace,
+                      hrpp_mod)
+from paper_1910_01304_gb300 import scenes as S
+from paper_1910_01304_gb300.scenes import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    return hrpp_mod()
+
+
+@pytest.fixture(scope="module")
+def small_pair(H):
+    s2, s4 = W.small_scene(width=2), W.small_scene(width=4)
+    return (s2, H.Scene.from_workload(s2)), (s4, H.Scene.from_workload(s4))
+
+
+def _oracle(s, rays, mode, table=None):
+    return O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, mode, table)
+
+
+@pytest.mark.parametrize("width_idx", [0, 1])
+@pytest.mark.parametrize("mode", [O.CLOSEST_HIT, O.ANY_HIT])
+def test_plain_small_scene(H, small_pair, width_idx, mode):
+    s, g = small_pair[width_idx]
+    rays = s.primary_rays(frame=1)
+    if mode == O.ANY_HIT:
+        h, _ = _oracle(s, rays, O.CLOSEST_HIT)
+        rays, _ = W.secondary_shadow(s, rays, h["t"], h["prim"])
+    oh, ost = _oracle(s, rays, mode)
+    gh, gst = gpu_trace(H, g, rays, mode)
+    assert_same_hits(mode, gh, oh, "plain")
+    assert_same_stats(gst, ost)
+
+
+@pytest.mark.parametrize("ways", [1, 2, 4])
+@pytest.mark.parametrize("width_idx", [0, 1])
+def test_hrpp_small_scene_frames(H, small_pair, ways, width_idx):
+    """Four jittered frames of primary (closest) and shadow (any) rays through
+    one table per mode: hits, counters and table words match every frame."""
+    s, g = small_pair[width_idx]
+    tabs = {m: H.Table(12, ways, 6) for m in (O.CLOSEST_HIT, O.ANY_HIT)}
+    otabs = {m: O.Table(12, ways, 6, O.TWO_PHASE) for m in (O.CLOSEST_HIT, O.ANY_HIT)}
+    for frame in range(4):
+        prim = s.primary_rays(frame=frame)
+        ph, _ = _oracle(s, prim, O.CLOSEST_HIT)
+        shadow, _ = W.secondary_shadow(s, prim, ph["t"], ph["prim"])
+        for mode, rays in ((O.CLOSEST_HIT, prim), (O.ANY_HIT, shadow)):
+            oh, ost = _oracle(s, rays, mode, otabs[mode])
+            gh, gst = gpu_trace(H, g, rays, mode, tabs[mode])
+            assert_same_hits(mode, gh, oh, f"frame {frame} mode {mode}")
+            assert_same_stats(gst, ost, msg=f"frame {frame} mode {mode}")
+            assert np.array_equal(tabs[mode].export(), otabs[mode].words), f"table words frame {frame}"
+    # later frames predict something
+    assert gst["positives"] > 0
+
+
+@pytest.mark.parametrize("width", [2, 4])
+def test_tiny_scenes_vs_brute_force(H, width):
+    """Random soups, coplanar grids and degenerate triangles: GPU plain and HRPP
+    against brute force under the benchmark spec's tolerances."""
+    rng = np.random.default_rng(width)
+    for seed in range(40):
+        n = int(rng.integers(1, 200))
+        tris = S.soup(n, seed, -1, 1, 0.6) if seed % 2 else S.quad_grid(7, 5, -1, 1, -1, 1, 0.0)
+        if seed % 5 == 0:
+            tris[: max(1, n // 4), 3:6] = tris[: max(1, n // 4), 0:3]
+        nodes, prim, root = S.build_bvh(tris, width=width)
+        g = H.Scene(tris, nodes, prim, root, width)
+        o = rng.uniform(-2, 2, (257, 3))
+        d = rng.uniform(-1, 1, (257, 3)) - o
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        rays = np.zeros((257, 8), np.float32)
+        rays[:, :3], rays[:, 4:7], rays[:, 7] = o, d, np.inf
+        rays[::9, 4:7] = [0, -1, 0]
+        bc, tie = O.brute(rays, tris, O.CLOSEST_HIT)
+        ba, _ = O.brute(rays, tris, O.ANY_HIT)
+        tab_c, tab_a = H.Table(8, 2, 3), H.Table(8, 2, 3)
+        for rep in range(2):
+            for table in (None, "t"):
+                gc, _ = gpu_trace(H, g, rays, O.CLOSEST_HIT, tab_c if table else None, stats=False)
+                ga, _ = gpu_trace(H, g, rays, O.ANY_HIT, tab_a if table else None, stats=False)
+                gw, bw = as_words(gc), as_words(bc)
+                ok = ~tie
+                assert np.array_equal(gw[ok, 1], bw[ok, 1]), seed           # prim ids
+                tg, tb = gc[ok, 0], bc["t"][ok]
+                fin = np.isfinite(tb)
+                assert np.array_equal(np.isfinite(tg), fin)
+                assert np.all(np.abs(tg[fin] - tb[fin]) <= 1e-5 * np.abs(tb[fin]))
+                assert np.array_equal(any_prims(ga) == O.NO_HIT, ba == O.NO_HIT), seed
+
+
+def test_edge_cases_ragged_and_degenerate(H, small_pair):
+    s, g = small_pair[0]
+    base = s.primary_rays()
+    tab = H.Table(10, 1, 6)
+    otab = O.Table(10, 1, 6, O.TWO_PHASE)
+    for n in (0, 1, 31, 33, 1000, 4097):
+        rays = base[:n].copy()
+        if n > 10:
+            rays[3, 3] = rays[3, 7] = 5.0            # tmin == tmax: empty interval
+            rays[4, 4:7] = [0.0, -1.0, 0.0]          # exactly axis-aligned
+            rays[5, 4:7] = [0.0, 0.0, -0.0]          # zero direction
+            rays[6, 0:3] = [0.0, 1.0, 0.0]           # origin inside the sphere
+            rays[7, 7] = 0.0                         # tmax 0
+        for mode in (O.CLOSEST_HIT, O.ANY_HIT):
+            oh, ost = _oracle(s, rays, mode, otab if mode == O.CLOSEST_HIT else None)
+            gh, gst = gpu_trace(H, g, rays, mode, tab if mode == O.CLOSEST_HIT else None)
+            if n:
+                assert_same_hits(mode, gh, oh, f"n={n}")
+            assert_same_stats(gst, ost, msg=f"n={n}")
+        assert np.array_equal(tab.export(), otab.words)
+
+
+def test_root_leaf_scene(H):
+    tris = S.soup(3, 2, 0, 1, 0.5)
+    nodes, prim, root = S.build_bvh(tris)
+    g = H.Scene(tris, nodes, prim, root, 2)
+    assert g.info()["root_is_leaf"] == 1
+    rays = S.sphere_rays(300, 1, -0.5, 1.5)
+    for mode in (O.CLOSEST_HIT, O.ANY_HIT):
+        oh, ost = O.trace(tris, nodes, prim, root, rays, mode)
+        gh, gst = gpu_trace(H, g, rays, mode)
+        assert_same_hits(mode, gh, oh)
+        assert_same_stats(gst, ost)
+
+
+@pytest.mark.parametrize("mode", [O.CLOSEST_HIT, O.ANY_HIT])
+def test_online_mode_is_exact(H, small_pair, mode):
+    s, g = small_pair[1]
+    tab = H.Table(12, 2, 6, H.HRPP_UPDATE_ONLINE)
+    for frame in range(3):
+        rays = s.primary_rays(frame=frame)
+        ph, _ = gpu_trace(H, g, rays, mode)
+        hh, st = gpu_trace(H, g, rays, mode, tab)
+        if mode == O.CLOSEST_HIT:
+            assert np.array_equal(as_words(ph), as_words(hh))
+        else:
+            assert np.array_equal(any_prims(ph) == O.NO_HIT, any_prims(hh) == O.NO_HIT)
+        assert st["positives"] + st["negatives"] == len(rays)
+    assert st["true_pos"] > 0
+
+
+def test_frozen_mode_never_writes(H, small_pair):
+    s, g = small_pair[0]
+    tab = H.Table(12, 1, 6)
+    gpu_trace(H, g, s.primary_rays(), O.CLOSEST_HIT, tab)
+    before = tab.export()
+    tab.configure(6, H.HRPP_UPDATE_FROZEN)
+    _, st = gpu_trace(H, g, s.primary_rays(frame=2), O.CLOSEST_HIT, tab)
+    assert st["inserts"] == 0 and np.array_equal(tab.export(), before)
+
+
+def test_host_buffers_match_device_path(H, small_pair):
+    s, g = small_pair[0]
+    rays = np.ascontiguousarray(s.primary_rays(frame=3))
+    for mode in (O.CLOSEST_HIT, O.ANY_HIT):
+        dev, _ = gpu_trace(H, g, rays, mode)
+        host, st = H.trace(g, rays, mode, stats=True)
+        assert isinstance(host, np.ndarray)
+        if mode == O.CLOSEST_HIT:
+            assert np.array_equal(as_words(dev), as_words(host))
+        else:
+            assert np.array_equal(any_prims(dev), any_prims(host))
+        assert st["rays"] == len(rays)
+
+
+def test_table_bound_to_its_scene_and_roundtrip(H, small_pair):
+    (s2, g2), (s4, g4) = small_pair
+    tab = H.Table(12, 1, 6)
+    gpu_trace(H, g2, s2.primary_rays(), O.CLOSEST_HIT, tab)
+    with pytest.raises(H.HrppError) as e:
+        gpu_trace(H, g4, s4.primary_rays(), O.CLOSEST_HIT, tab)
+    assert e.value.status == H.HRPP_ERR_INVALID_ARG
+    words = tab.export()
+    tab.reset()
+    assert np.all(tab.export() == np.uint64(H.HRPP_EMPTY_WORD))
+    gpu_trace(H, g4, s4.primary_rays(), O.CLOSEST_HIT, tab)   # rebinds after reset
+    tab.reset()
+    tab.import_(words)
+    assert np.array_equal(tab.export(), words)
+
+
+def test_block_sizes_give_identical_results(H, small_pair):
+    s, g = small_pair[1]
+    rays = s.primary_rays(frame=5)
+    ref, rst = gpu_trace(H, g, rays, O.CLOSEST_HIT)
+    for bt in (64, 256, 512):
+        h, st = gpu_trace(H, g, rays, O.CLOSEST_HIT, block_threads=bt)
+        assert np.array_equal(as_words(h), as_words(ref))
+        assert_same_stats(st, rst)
+
+
+def test_mid_terrain_bvh4_hrpp(H):
+    """The terrain recipe at reduced size (BVH4, several ragged tiles of rays):
+    primary closest-hit and ambient-occlusion any-hit rays over three frames."""
+    s = W.terrain_scene(quads=96, n_spheres=6, subdiv=3, res=(200, 120))
+    g = H.Scene.from_workload(s)
+    tabs = {m: H.Table(14, 2, 6) for m in (O.CLOSEST_HIT, O.ANY_HIT)}
+    otabs = {m: O.Table(14, 2, 6, O.TWO_PHASE) for m in (O.CLOSEST_HIT, O.ANY_HIT)}
+    for frame in range(3):
+        prim = s.primary_rays(frame=frame)
+        ph, _ = _oracle(s, prim, O.CLOSEST_HIT)
+        ao, _ = W.secondary_ao(s, prim, ph["t"], ph["prim"], frame=frame)
+        for mode, rays in ((O.CLOSEST_HIT, prim), (O.ANY_HIT, ao)):
+            oh, ost = _oracle(s, rays, mode, otabs[mode])
+            gh, gst = gpu_trace(H, g, rays, mode, tabs[mode])
+            assert_same_hits(mode, gh, oh, f"frame {frame}")
+            assert_same_stats(gst, ost, msg=f"frame {frame}")
+            assert np.array_equal(tabs[mode].export(), otabs[mode].words)
+    assert gst["true_pos"] > 0
