@@ -70,13 +70,13 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index: int):
+    def __init__(self, device_index: str):
         self.rows = []
         self.proc = None
         self.t0 = self.t1 = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(device_index)], stdout=subprocess.PIPE,
+                                          "-lms", "200", "-i", device_index], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -297,8 +297,15 @@ def main():
             total += rays_per_frame[fi]
         return total
 
+    def mk():
+        # torch only reports elapsed_time for events it recorded itself; the
+        # library re-records these on the same stream around the kernel, so a
+        # first record here just marks them as recorded
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
     def timed(tables, with_kernel_events):
-        mk = lambda: torch.cuda.Event(enable_timing=True)
         run(args.warmup, True, tables, offset=0)
         events = [((mk(), mk()), (mk(), mk())) for _ in range(args.steps)] if with_kernel_events else None
         barrier()
@@ -329,7 +336,11 @@ def main():
         return float(t.item())
 
     # --- HRPP, timed, with clocks sampled over the timed region
-    clocks = ClockSampler(local)
+    try:
+        dev_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        dev_id = str(local)
+    clocks = ClockSampler(dev_id)
     run(args.warmup, True, (tab_c, tab_a))
     barrier()
     clocks.mark(True)

@@ -125,16 +125,30 @@ typedef struct hrpp_scene_info {
     uint64_t device_bytes;
 } hrpp_scene_info;
 
-/* Per-call options of hrpp_trace_ex (all fields may be zero).
+/* Per-call options of hrpp_trace_ex (all fields may be zero).  None of them
+ * changes any result, counter or table word; they only change speed.
  *   kernel_start/kernel_stop  cudaEvent_t (as void*) recorded on `stream`
  *                             immediately before and after the traversal
  *                             kernel, for timing it alone
  *   block_threads             threads per block of the traversal kernel:
- *                             0 = default, else 64, 128, 256 or 512 */
+ *                             0 = default, else 64, 128, 256 or 512
+ *   schedule                  how warps take rays from the batch:
+ *                             HRPP_SCHEDULE_DEFAULT, HRPP_SCHEDULE_BATCH (a
+ *                             warp traces 32 rays to completion, then takes
+ *                             32 more) or HRPP_SCHEDULE_REFILL (lanes whose
+ *                             ray is done take new rays while the rest of
+ *                             the warp keeps traversing)
+ *   refill_min                REFILL: idle lanes needed before a warp refills,
+ *                             1..32 (0 = default) */
+#define HRPP_SCHEDULE_DEFAULT 0u
+#define HRPP_SCHEDULE_BATCH 1u
+#define HRPP_SCHEDULE_REFILL 2u
 typedef struct hrpp_trace_opts {
     void *kernel_start, *kernel_stop;
     uint32_t block_threads;
-    uint32_t reserved[7];
+    uint32_t schedule;
+    uint32_t refill_min;
+    uint32_t reserved[5];
 } hrpp_trace_opts;
 
 typedef struct hrpp_scene hrpp_scene;

@@ -40,6 +40,11 @@ struct hrpp_table {
 
 namespace {
 
+// launch defaults (measured on GB300, see bench.py / the autotuner)
+constexpr uint32_t kDefaultBlockThreads = 128;
+constexpr uint32_t kDefaultSchedule = HRPP_SCHEDULE_BATCH;
+constexpr uint32_t kDefaultRefillMin = 16;
+
 thread_local std::string g_last_error;
 std::atomic<uint64_t> g_next_scene_id{1};
 
@@ -499,11 +504,21 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
     if (((uintptr_t)out_hits & (closest ? 15u : 3u)) != 0)
         return fail(HRPP_ERR_INVALID_ARG, "out_hits must be %d-byte aligned", closest ? 16 : 4);
     if (((uintptr_t)out_stats & 7u) != 0) return fail(HRPP_ERR_INVALID_ARG, "out_stats must be 8-byte aligned");
-    uint32_t block_threads = 128;
+    uint32_t block_threads = kDefaultBlockThreads;
     if (opts && opts->block_threads) {
         block_threads = opts->block_threads;
         if (block_threads != 64 && block_threads != 128 && block_threads != 256 && block_threads != 512)
             return fail(HRPP_ERR_INVALID_ARG, "block_threads must be 64, 128, 256 or 512");
+    }
+    uint32_t schedule = kDefaultSchedule, refill_min = kDefaultRefillMin;
+    if (opts && opts->schedule) {
+        if (opts->schedule != HRPP_SCHEDULE_BATCH && opts->schedule != HRPP_SCHEDULE_REFILL)
+            return fail(HRPP_ERR_INVALID_ARG, "unknown schedule %u", opts->schedule);
+        schedule = opts->schedule;
+    }
+    if (opts && opts->refill_min) {
+        if (opts->refill_min > 32) return fail(HRPP_ERR_INVALID_ARG, "refill_min must be in [1, 32]");
+        refill_min = opts->refill_min;
     }
     if (table && table->device != sc->device) return fail(HRPP_ERR_INVALID_ARG, "table and scene on different devices");
     if (table && table->bound_scene && table->bound_scene != sc->id)
@@ -572,6 +587,7 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         p.hits = d_hits;
         p.ctl = ctl;
         p.error = sc->d_error;
+        p.refill_min = refill_min;
         if (table) {
             p.table = table->d_words;
             p.winner = table->d_winner;
@@ -583,8 +599,9 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         }
         cudaEvent_t ev0 = opts ? (cudaEvent_t)opts->kernel_start : nullptr;
         cudaEvent_t ev1 = opts ? (cudaEvent_t)opts->kernel_stop : nullptr;
-        e = sc->width == 2 ? launch_trace_w2(closest, out_stats != nullptr, p, (int)block_threads, 0, stream, ev0, ev1)
-                           : launch_trace_w4(closest, out_stats != nullptr, p, (int)block_threads, 0, stream, ev0, ev1);
+        const int sched = schedule == HRPP_SCHEDULE_REFILL ? 1 : 0;
+        e = sc->width == 2 ? launch_trace_w2(closest, out_stats != nullptr, sched, p, (int)block_threads, 0, stream, ev0, ev1)
+                           : launch_trace_w4(closest, out_stats != nullptr, sched, p, (int)block_threads, 0, stream, ev0, ev1);
         if (e != cudaSuccess) { status = cuda_fail(e, "trace launch"); break; }
         if (two_phase && (e = launch_table_apply(table->d_words, table->d_winner, p.records, ctl, n_rays, stream)) != cudaSuccess) {
             status = cuda_fail(e, "table update launch");

@@ -63,6 +63,7 @@ struct TraceParams {
     int log2_sets, log2_ways, precision, update_mode;
     Ctl *ctl;
     uint32_t *error;         // scene's sticky error flag
+    uint32_t refill_min;     // dynamic schedule: refill when this many lanes are idle
 };
 
 // ---------------------------------------------------------------- hashing --
@@ -132,19 +133,32 @@ __device__ __forceinline__ RayInv ray_inverse(float4 o, float4 d)
     return r;
 }
 
+// three-input min / max (one instruction each on sm_100 and later); for
+// non-NaN inputs they equal the two-input forms applied twice
+__device__ __forceinline__ float max3f(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // Slab test: plane distances lo*inv - o*inv (one fused multiply-add each);
 // entry = max(tmin, nearest planes), exit = min(tcur, farthest planes).
+// Plane distances are finite (the reciprocal is), so no operand is NaN.
 __device__ __forceinline__ bool slab(const RayInv &r, float tmin, float tcur, float lox, float hix, float loy,
                                      float hiy, float loz, float hiz, float &tn)
 {
     const float x0 = __fmaf_rn(lox, r.ix, -r.oix), x1 = __fmaf_rn(hix, r.ix, -r.oix);
     const float y0 = __fmaf_rn(loy, r.iy, -r.oiy), y1 = __fmaf_rn(hiy, r.iy, -r.oiy);
     const float z0 = __fmaf_rn(loz, r.iz, -r.oiz), z1 = __fmaf_rn(hiz, r.iz, -r.oiz);
-    const float nx = fminf(x0, x1), fx = fmaxf(x0, x1);
-    const float ny = fminf(y0, y1), fy = fmaxf(y0, y1);
-    const float nz = fminf(z0, z1), fz = fmaxf(z0, z1);
-    tn = fmaxf(fmaxf(nx, ny), fmaxf(nz, tmin));
-    const float tf = fminf(fminf(fx, fy), fminf(fz, tcur));
+    tn = max3f(fminf(x0, x1), fminf(y0, y1), fmaxf(fminf(z0, z1), tmin));
+    const float tf = min3f(fmaxf(x0, x1), fmaxf(y0, y1), fminf(fmaxf(z0, z1), tcur));
     return tn <= tf;
 }
 
@@ -181,9 +195,11 @@ __device__ __forceinline__ bool tri_test(float4 o, float4 d, float4 v0, float4 e
 }
 
 // host launchers (trace_bvh2.cu, trace_bvh4.cu, table.cu)
-cudaError_t launch_trace_w2(bool closest, bool stats, const TraceParams &p, int block_threads,
+// schedule: 0 = each warp traces 32 rays to completion before taking the next
+// 32; 1 = lanes that finish take new rays while the others keep traversing
+cudaError_t launch_trace_w2(bool closest, bool stats, int schedule, const TraceParams &p, int block_threads,
                             int blocks_per_sm_cap, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1);
-cudaError_t launch_trace_w4(bool closest, bool stats, const TraceParams &p, int block_threads,
+cudaError_t launch_trace_w4(bool closest, bool stats, int schedule, const TraceParams &p, int block_threads,
                             int blocks_per_sm_cap, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1);
 cudaError_t launch_table_apply(uint64_t *table, uint32_t *winner, const Record *records, Ctl *ctl,
                                uint32_t max_records, cudaStream_t stream);

@@ -3,10 +3,10 @@
 
 namespace hrpp {
 
-cudaError_t launch_trace_w4(bool closest, bool stats, const TraceParams &p, int block_threads, int blocks_per_sm_cap,
+cudaError_t launch_trace_w4(bool closest, bool stats, int schedule, const TraceParams &p, int block_threads, int blocks_per_sm_cap,
                             cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1)
 {
-    return launch_width<4>(closest, stats, p, block_threads, blocks_per_sm_cap, stream, ev0, ev1);
+    return launch_width<4>(closest, stats, schedule, p, block_threads, blocks_per_sm_cap, stream, ev0, ev1);
 }
 
 }  // namespace hrpp

@@ -1,8 +1,7 @@
-// Persistent HRPP traversal kernel (one template, instantiated per BVH width,
+// Persistent HRPP traversal kernels (templates instantiated per BVH width,
 // query mode and statistics switch in trace_bvh2.cu / trace_bvh4.cu).
 //
-// Each warp repeatedly takes the next 32 rays from the call's ray pool (one
-// atomic per warp on Ctl::next_ray) and traces one ray per lane:
+// Per ray:
 //   1. HRPP lookup (Sec. 4.2, Sec. 5): hash the ray, read its set, collect the
 //      ways whose tag matches; test those predicted leaves' triangles.
 //   2. Outcome (Sec. 4.3): no prediction -> negative; a predicted leaf holds a
@@ -15,6 +14,13 @@
 //   4. A ray whose traversal produced its final hit inserts that hit's leaf:
 //      two-phase mode records it (atomicMax on the slot's winner + a record
 //      appended with one atomic per warp); online mode exchanges the word.
+//
+// Two schedules over the ray pool (Ctl::next_ray), identical per-ray work:
+//   k_trace      a warp takes 32 rays, traces them to completion, repeats.
+//   k_trace_dyn  lanes whose ray finished take new rays (one atomic per warp
+//                for all of them) once refill_min lanes are idle, while the
+//                other lanes keep traversing; each round a lane descends
+//                interior nodes until a leaf is due, then tests that leaf.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,31 +29,14 @@
 
 namespace hrpp {
 
+constexpr int32_t kDoneRef = INT32_MIN + 1;  // traversal finished
+constexpr uint32_t kNoRay = 0xFFFFFFFFu;
+
 __device__ __forceinline__ uint32_t lanemask_lt()
 {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
-}
-
-// order-preserving float -> unsigned map (for (entry t, slot) sort keys);
-// -0 is folded into +0 first so equal distances compare equal
-__device__ __forceinline__ uint32_t ordered(float f)
-{
-    const uint32_t b = __float_as_uint(__fadd_rn(f, 0.0f));
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-
-__device__ __forceinline__ void cswap(uint64_t &a, uint64_t &b)
-{
-    const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
-    a = lo;
-    b = hi;
-}
-
-__device__ __forceinline__ int32_t pick4(int4 c, uint32_t s)
-{
-    return s == 0 ? c.x : s == 1 ? c.y : s == 2 ? c.z : c.w;
 }
 
 template <bool STATS>
@@ -62,12 +51,36 @@ struct Counters {
     {
         if (STATS) c[k] += v;
     }
+    __device__ __forceinline__ void flush(Ctl *ctl, uint32_t lane)
+    {
+        if (STATS) {
+#pragma unroll
+            for (int k = 0; k < ST_PRED_TRI_TESTS + 1; ++k) {
+                const uint32_t v = __reduce_add_sync(0xFFFFFFFFu, c[k]);
+                if (lane == 0 && v) atomicAdd(&ctl->stats[k], (unsigned long long)v);
+            }
+        }
+    }
 };
 
 struct Best {
     float t, u, v;
     uint32_t prim, leaf;
     bool found, from_trav;
+};
+
+// Everything one lane keeps about its ray between traversal rounds.
+struct RayState {
+    float4 o, d;
+    RayInv ri;
+    float tcur;
+    Best b;
+    int sp;
+    int32_t ref;
+    uint32_t steps;
+    bool predicted_hit;
+    uint32_t set;
+    uint64_t tag;
 };
 
 // Tests the triangles of one leaf.  Any-hit: returns true at the first valid
@@ -100,93 +113,214 @@ __device__ __forceinline__ bool test_leaf(const TraceParams &p, uint32_t leaf, f
     return false;
 }
 
-template <int W, bool CLOSEST, bool STATS>
-__device__ __forceinline__ void traverse(const TraceParams &p, float4 o, float4 d, Best &b, Counters<STATS> &cnt)
+// Loads ray i and runs the HRPP lookup.  Returns true when the ray still has
+// to traverse (then s.ref is the root).
+template <bool CLOSEST, bool STATS>
+__device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayState &s, Counters<STATS> &cnt)
 {
-    const RayInv ri = ray_inverse(o, d);
-    float tcur = (CLOSEST && b.found) ? b.t : d.w;
-    int32_t stack[kStack];
-    int sp = 0;
-    int32_t ref = p.root_ref;
-    uint32_t steps = 0;
-    for (;;) {
-        if (++steps > p.max_steps) {
-            atomicOr(p.error, kErrSteps);
-            return;
+    s.o = __ldg(p.rays + 2ull * i);
+    s.d = __ldg(p.rays + 2ull * i + 1);
+    s.b.t = __int_as_float(0x7F800000);
+    s.b.u = s.b.v = 0.0f;
+    s.b.prim = HRPP_NO_HIT;
+    s.b.leaf = 0;
+    s.b.found = s.b.from_trav = false;
+    s.set = 0;
+    s.tag = 0;
+    cnt.add(ST_RAYS);
+    bool traverse = true;
+    if (p.table) {
+        cnt.add(ST_LOOKUPS);
+        const uint64_t m = mix48(ray_key(s.o, s.d, p.precision));
+        s.set = (uint32_t)(m & ((1ull << p.log2_sets) - 1ull));
+        s.tag = (m >> p.log2_sets) & kTagMask;
+        const uint64_t *set = p.table + ((uint64_t)s.set << p.log2_ways);
+        const uint32_t ways = 1u << p.log2_ways;
+        float tdummy = 0.0f;
+        bool positive = false, done = false;
+        for (uint32_t w = 0; w < ways && !done; ++w) {
+            const uint64_t wd = p.update_mode == HRPP_UPDATE_ONLINE ? __ldcg(set + w) : __ldg(set + w);
+            if (wd == HRPP_EMPTY_WORD || (wd >> kLeafBits) != s.tag) continue;
+            positive = true;
+            const uint32_t leaf = (uint32_t)(wd & kLeafMask);
+            if ((leaf >> 2) + (leaf & 3u) + 1u > p.n_tris) continue;  // not a leaf of this scene
+            cnt.add(ST_PRED_LEAVES);
+            done = test_leaf<CLOSEST, STATS>(p, leaf, s.o, s.d, s.b, tdummy, false, cnt, ST_PRED_TRI_TESTS);
         }
-        if (ref >= 0) {
-            cnt.add(ST_INTERIOR);
-            if (W == 2) {
-                const float4 *n = p.nodes + 4ull * (uint32_t)ref;
-                const float4 a = __ldg(n), bb = __ldg(n + 1), c = __ldg(n + 2);
-                const int4 e = __ldg(reinterpret_cast<const int4 *>(n + 3));
-                float t0, t1;
-                const bool h0 = slab(ri, o.w, tcur, a.x, a.y, a.z, a.w, c.x, c.y, t0);
-                const bool v1 = e.y != kEmptyRef;
-                const bool h1 = v1 && slab(ri, o.w, tcur, bb.x, bb.y, bb.z, bb.w, c.z, c.w, t1);
-                cnt.add(ST_BOX_TESTS, 1u + (v1 ? 1u : 0u));
-                if (h0 && h1) {
-                    const bool swap = t1 < t0;
-                    if (sp >= kStack) {
-                        atomicOr(p.error, kErrStack);
-                        return;
-                    }
-                    stack[sp++] = swap ? e.x : e.y;
-                    ref = swap ? e.y : e.x;
-                    continue;
-                }
-                if (h0) { ref = e.x; continue; }
-                if (h1) { ref = e.y; continue; }
-            } else {
-                const float4 *n = p.nodes + 8ull * (uint32_t)ref;
-                const float4 lx = __ldg(n), hx = __ldg(n + 1), ly = __ldg(n + 2), hy = __ldg(n + 3);
-                const float4 lz = __ldg(n + 4), hz = __ldg(n + 5);
-                const int4 ch = __ldg(reinterpret_cast<const int4 *>(n + 6));
-                uint64_t k0 = ~0ull, k1 = ~0ull, k2 = ~0ull, k3 = ~0ull;
-                float t;
-                uint32_t nvalid = 0, nhit = 0;
-                if (ch.x != kEmptyRef) {
-                    ++nvalid;
-                    if (slab(ri, o.w, tcur, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, t)) { k0 = ((uint64_t)ordered(t) << 2) | 0u; ++nhit; }
-                }
-                if (ch.y != kEmptyRef) {
-                    ++nvalid;
-                    if (slab(ri, o.w, tcur, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, t)) { k1 = ((uint64_t)ordered(t) << 2) | 1u; ++nhit; }
-                }
-                if (ch.z != kEmptyRef) {
-                    ++nvalid;
-                    if (slab(ri, o.w, tcur, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, t)) { k2 = ((uint64_t)ordered(t) << 2) | 2u; ++nhit; }
-                }
-                if (ch.w != kEmptyRef) {
-                    ++nvalid;
-                    if (slab(ri, o.w, tcur, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, t)) { k3 = ((uint64_t)ordered(t) << 2) | 3u; ++nhit; }
-                }
-                cnt.add(ST_BOX_TESTS, nvalid);
-                if (nhit > 0) {
-                    // sort (entry t, slot) ascending: 5 compare-exchanges
-                    cswap(k0, k1);
-                    cswap(k2, k3);
-                    cswap(k0, k2);
-                    cswap(k1, k3);
-                    cswap(k1, k2);
-                    if (sp + (int)nhit - 1 > kStack) {
-                        atomicOr(p.error, kErrStack);
-                        return;
-                    }
-                    if (nhit > 3) stack[sp++] = pick4(ch, (uint32_t)k3 & 3u);
-                    if (nhit > 2) stack[sp++] = pick4(ch, (uint32_t)k2 & 3u);
-                    if (nhit > 1) stack[sp++] = pick4(ch, (uint32_t)k1 & 3u);
-                    ref = pick4(ch, (uint32_t)k0 & 3u);
-                    continue;
-                }
-            }
+        if (!positive) {
+            cnt.add(ST_NEGATIVES);
         } else {
-            // leaf
-            cnt.add(ST_LEAVES);
-            if (test_leaf<CLOSEST, STATS>(p, ~(uint32_t)ref, o, d, b, tcur, true, cnt, ST_TRI_TESTS)) return;
+            cnt.add(ST_POSITIVES);
+            if (s.b.found) {
+                cnt.add(ST_TRUE_POS);
+                if (!CLOSEST) traverse = false;
+            } else {
+                cnt.add(ST_FALSE_POS);
+            }
         }
-        if (sp == 0) return;
-        ref = stack[--sp];
+    }
+    s.predicted_hit = s.b.found;
+    if (traverse) {
+        s.ri = ray_inverse(s.o, s.d);
+        s.tcur = (CLOSEST && s.b.found) ? s.b.t : s.d.w;
+        s.sp = 0;
+        s.ref = p.root_ref;
+        s.steps = 0;
+    } else {
+        s.ref = kDoneRef;
+    }
+    return traverse;
+}
+
+__device__ __forceinline__ int32_t pop(int32_t *stack, int &sp) { return sp > 0 ? stack[--sp] : kDoneRef; }
+
+// Visits the interior node s.ref: tests its children's boxes against the
+// current bound and moves to the nearest hit child, pushing the others
+// (farthest deepest); with no hit child it pops.
+template <int W, bool STATS>
+__device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s, int32_t *stack, Counters<STATS> &cnt)
+{
+    cnt.add(ST_INTERIOR);
+    const float tmin = s.o.w;
+    if (W == 2) {
+        const float4 *n = p.nodes + 4ull * (uint32_t)s.ref;
+        const float4 a = __ldg(n), bb = __ldg(n + 1), c = __ldg(n + 2);
+        const int4 e = __ldg(reinterpret_cast<const int4 *>(n + 3));
+        float t0, t1;
+        const bool h0 = slab(s.ri, tmin, s.tcur, a.x, a.y, a.z, a.w, c.x, c.y, t0);
+        const bool v1 = e.y != kEmptyRef;
+        const bool h1 = v1 && slab(s.ri, tmin, s.tcur, bb.x, bb.y, bb.z, bb.w, c.z, c.w, t1);
+        cnt.add(ST_BOX_TESTS, 1u + (v1 ? 1u : 0u));
+        if (h0 && h1) {
+            if (s.sp >= kStack) {
+                atomicOr(p.error, kErrStack);
+                s.ref = kDoneRef;
+                return;
+            }
+            const bool swap = t1 < t0;
+            stack[s.sp++] = swap ? e.x : e.y;
+            s.ref = swap ? e.y : e.x;
+        } else if (h0) {
+            s.ref = e.x;
+        } else if (h1) {
+            s.ref = e.y;
+        } else {
+            s.ref = pop(stack, s.sp);
+        }
+        return;
+    }
+    const float4 *n = p.nodes + 8ull * (uint32_t)s.ref;
+    const float4 lx = __ldg(n), hx = __ldg(n + 1), ly = __ldg(n + 2), hy = __ldg(n + 3);
+    const float4 lz = __ldg(n + 4), hz = __ldg(n + 5);
+    const int4 ch = __ldg(reinterpret_cast<const int4 *>(n + 6));
+    const float inf = __int_as_float(0x7F800000);
+    float t0 = inf, t1 = inf, t2 = inf, t3 = inf, t;
+    bool h0 = false, h1 = false, h2 = false, h3 = false;
+    uint32_t nvalid = 0;
+    if (ch.x != kEmptyRef) { ++nvalid; if ((h0 = slab(s.ri, tmin, s.tcur, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, t))) t0 = t; }
+    if (ch.y != kEmptyRef) { ++nvalid; if ((h1 = slab(s.ri, tmin, s.tcur, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, t))) t1 = t; }
+    if (ch.z != kEmptyRef) { ++nvalid; if ((h2 = slab(s.ri, tmin, s.tcur, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, t))) t2 = t; }
+    if (ch.w != kEmptyRef) { ++nvalid; if ((h3 = slab(s.ri, tmin, s.tcur, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, t))) t3 = t; }
+    cnt.add(ST_BOX_TESTS, nvalid);
+    const int nhit = (int)h0 + (int)h1 + (int)h2 + (int)h3;
+    if (nhit == 0) {
+        s.ref = pop(stack, s.sp);
+        return;
+    }
+    if (s.sp + nhit - 1 > kStack) {
+        atomicOr(p.error, kErrStack);
+        s.ref = kDoneRef;
+        return;
+    }
+    // rank of each child in (entry t, slot) order; missed children sit at +inf
+    // behind every hit one.  For slots i < j, j goes first iff t_j < t_i.
+    int r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+    bool c;
+    c = t1 < t0; r0 += c; r1 += !c;
+    c = t2 < t0; r0 += c; r2 += !c;
+    c = t3 < t0; r0 += c; r3 += !c;
+    c = t2 < t1; r1 += c; r2 += !c;
+    c = t3 < t1; r1 += c; r3 += !c;
+    c = t3 < t2; r2 += c; r3 += !c;
+    // rank 0 is visited next; rank k > 0 goes to stack slot sp + nhit - 1 - k
+    const int top = s.sp + nhit - 1;
+    if (h0) { if (r0 == 0) s.ref = ch.x; else stack[top - r0] = ch.x; }
+    if (h1) { if (r1 == 0) s.ref = ch.y; else stack[top - r1] = ch.y; }
+    if (h2) { if (r2 == 0) s.ref = ch.z; else stack[top - r2] = ch.z; }
+    if (h3) { if (r3 == 0) s.ref = ch.w; else stack[top - r3] = ch.w; }
+    s.sp = top;
+}
+
+// Tests the leaf s.ref; any-hit rays end at the first valid hit, otherwise the
+// traversal pops the next node.
+template <bool CLOSEST, bool STATS>
+__device__ __forceinline__ void visit_leaf(const TraceParams &p, RayState &s, int32_t *stack, Counters<STATS> &cnt)
+{
+    cnt.add(ST_LEAVES);
+    if (test_leaf<CLOSEST, STATS>(p, ~(uint32_t)s.ref, s.o, s.d, s.b, s.tcur, true, cnt, ST_TRI_TESTS)) {
+        s.ref = kDoneRef;
+        return;
+    }
+    s.ref = pop(stack, s.sp);
+}
+
+__device__ __forceinline__ bool over_budget(const TraceParams &p, RayState &s)
+{
+    if (++s.steps > p.max_steps) {
+        atomicOr(p.error, kErrSteps);
+        s.ref = kDoneRef;
+        return true;
+    }
+    return false;
+}
+
+// Writes ray i's result and decides its insert (two-phase: returns the record
+// to append; online: exchanges the word now).
+template <bool CLOSEST, bool STATS>
+__device__ __forceinline__ bool finish_ray(const TraceParams &p, uint32_t i, const RayState &s, Counters<STATS> &cnt,
+                                           uint32_t &slot, uint64_t &word)
+{
+    bool want_record = false;
+    if (CLOSEST && s.predicted_hit && s.b.from_trav) cnt.add(ST_TP_INEXACT);
+    if (p.table && s.b.from_trav && p.update_mode != HRPP_UPDATE_FROZEN) {
+        cnt.add(ST_INSERTS);
+        slot = (s.set << p.log2_ways) | way_of(s.b.leaf, p.log2_ways);
+        word = (s.tag << kLeafBits) | s.b.leaf;
+        if (p.update_mode == HRPP_UPDATE_ONLINE) {
+            const unsigned long long old = atomicExch(reinterpret_cast<unsigned long long *>(p.table + slot), word);
+            if (old == word) cnt.add(ST_DUP_INSERTS);
+            else if (old != HRPP_EMPTY_WORD) cnt.add(ST_EVICTIONS);
+        } else {
+            atomicMax(p.winner + slot, i + 1u);
+            want_record = true;
+        }
+    }
+    if (s.b.found) cnt.add(ST_HITS);
+    if (CLOSEST) {
+        reinterpret_cast<float4 *>(p.hits)[i] = make_float4(s.b.t, __uint_as_float(s.b.prim), s.b.u, s.b.v);
+    } else {
+        reinterpret_cast<uint32_t *>(p.hits)[i] = s.b.found ? s.b.prim : HRPP_NO_HIT;
+    }
+    return want_record;
+}
+
+// Appends the two-phase insert records of the lanes that want one (all 32
+// lanes must call this together): one atomic per warp.
+__device__ __forceinline__ void append_records(const TraceParams &p, uint32_t lane, bool want, uint32_t slot,
+                                               uint32_t ray, uint64_t word)
+{
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, want);
+    if (!m) return;
+    const uint32_t leader = __ffs(m) - 1;
+    uint32_t rb = 0;
+    if (lane == leader) rb = atomicAdd(&p.ctl->n_records, (uint32_t)__popc(m));
+    rb = __shfl_sync(0xFFFFFFFFu, rb, leader);
+    if (want) {
+        Record r;
+        r.slot = slot;
+        r.ray1 = ray + 1u;
+        r.word = word;
+        p.records[rb + __popc(m & lanemask_lt())] = r;
     }
 }
 
@@ -196,116 +330,95 @@ __global__ void __launch_bounds__(512) k_trace(const TraceParams p)
     const uint32_t lane = threadIdx.x & 31u;
     Counters<STATS> cnt;
     cnt.init();
-    const bool hrpp = p.table != nullptr;
-    const uint32_t ways = 1u << p.log2_ways;
+    int32_t stack[kStack];
     for (;;) {
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(&p.ctl->next_ray, 32u);
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         if (base >= p.n_rays) break;
         const uint32_t i = base + lane;
-        bool want_insert = false;
+        bool want = false;
         uint32_t slot = 0;
         uint64_t word = 0;
         if (i < p.n_rays) {
-            const float4 o = __ldg(p.rays + 2ull * i), d = __ldg(p.rays + 2ull * i + 1);
-            Best b;
-            b.t = __int_as_float(0x7F800000);
-            b.u = b.v = 0.0f;
-            b.prim = HRPP_NO_HIT;
-            b.leaf = 0;
-            b.found = b.from_trav = false;
-            cnt.add(ST_RAYS);
-            bool run_traversal = true;
-            bool positive = false;
-            uint64_t set = 0, tag = 0;
-            if (hrpp) {
-                cnt.add(ST_LOOKUPS);
-                const uint64_t m = mix48(ray_key(o, d, p.precision));
-                set = m & ((1ull << p.log2_sets) - 1ull);
-                tag = (m >> p.log2_sets) & kTagMask;
-                const uint64_t *s = p.table + (set << p.log2_ways);
-                float tdummy = 0.0f;
-                bool done = false;
-                for (uint32_t w = 0; w < ways && !done; ++w) {
-                    const uint64_t wd = p.update_mode == HRPP_UPDATE_ONLINE ? __ldcg(s + w) : __ldg(s + w);
-                    if (wd == HRPP_EMPTY_WORD || (wd >> kLeafBits) != tag) continue;
-                    positive = true;
-                    const uint32_t leaf = (uint32_t)(wd & kLeafMask);
-                    if ((leaf >> 2) + (leaf & 3u) + 1u > p.n_tris) continue;  // not a leaf of this scene
-                    cnt.add(ST_PRED_LEAVES);
-                    done = test_leaf<CLOSEST, STATS>(p, leaf, o, d, b, tdummy, false, cnt, ST_PRED_TRI_TESTS);
-                }
-                if (!positive) {
-                    cnt.add(ST_NEGATIVES);
-                } else {
-                    cnt.add(ST_POSITIVES);
-                    if (b.found) {
-                        cnt.add(ST_TRUE_POS);
-                        if (!CLOSEST) run_traversal = false;
-                    } else {
-                        cnt.add(ST_FALSE_POS);
-                    }
+            RayState s;
+            if (start_ray<CLOSEST, STATS>(p, i, s, cnt)) {
+                while (s.ref != kDoneRef) {
+                    if (over_budget(p, s)) break;
+                    if (s.ref >= 0) visit_interior<W, STATS>(p, s, stack, cnt);
+                    else visit_leaf<CLOSEST, STATS>(p, s, stack, cnt);
                 }
             }
-            if (run_traversal) {
-                const bool predicted_hit = b.found;
-                traverse<W, CLOSEST, STATS>(p, o, d, b, cnt);
-                if (CLOSEST && predicted_hit && b.from_trav) cnt.add(ST_TP_INEXACT);
-                if (hrpp && b.from_trav && p.update_mode != HRPP_UPDATE_FROZEN) {
-                    cnt.add(ST_INSERTS);
-                    slot = (uint32_t)((set << p.log2_ways) | way_of(b.leaf, p.log2_ways));
-                    word = (tag << kLeafBits) | b.leaf;
-                    if (p.update_mode == HRPP_UPDATE_ONLINE) {
-                        const unsigned long long old =
-                            atomicExch(reinterpret_cast<unsigned long long *>(p.table + slot), word);
-                        if (old == word) cnt.add(ST_DUP_INSERTS);
-                        else if (old != HRPP_EMPTY_WORD) cnt.add(ST_EVICTIONS);
-                    } else {
-                        atomicMax(p.winner + slot, i + 1u);
-                        want_insert = true;
-                    }
-                }
-            }
-            if (b.found) cnt.add(ST_HITS);
-            if (CLOSEST) {
-                reinterpret_cast<float4 *>(p.hits)[i] = make_float4(b.t, __uint_as_float(b.prim), b.u, b.v);
-            } else {
-                reinterpret_cast<uint32_t *>(p.hits)[i] = b.found ? b.prim : HRPP_NO_HIT;
-            }
+            want = finish_ray<CLOSEST, STATS>(p, i, s, cnt, slot, word);
         }
-        // two-phase insert records: one atomic per warp
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, want_insert);
-        if (m) {
-            const uint32_t leader = __ffs(m) - 1;
-            uint32_t rb = 0;
-            if (lane == leader) rb = atomicAdd(&p.ctl->n_records, (uint32_t)__popc(m));
-            rb = __shfl_sync(0xFFFFFFFFu, rb, leader);
-            if (want_insert) {
-                Record r;
-                r.slot = slot;
-                r.ray1 = i + 1u;
-                r.word = word;
-                p.records[rb + __popc(m & lanemask_lt())] = r;
-            }
-        }
+        append_records(p, lane, want, slot, i, word);
     }
-    if (STATS) {
-#pragma unroll
-        for (int k = 0; k < ST_PRED_TRI_TESTS + 1; ++k) {
-            const uint32_t v = __reduce_add_sync(0xFFFFFFFFu, cnt.c[k]);
-            if (lane == 0 && v) atomicAdd(&p.ctl->stats[k], (unsigned long long)v);
+    cnt.flush(p.ctl, lane);
+}
+
+template <int W, bool CLOSEST, bool STATS>
+__global__ void __launch_bounds__(512) k_trace_dyn(const TraceParams p)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    Counters<STATS> cnt;
+    cnt.init();
+    int32_t stack[kStack];
+    RayState s;
+    uint32_t ray = kNoRay;
+    bool pool_open = true;  // warp-uniform
+    for (;;) {
+        // refill idle lanes from the ray pool
+        const uint32_t idle = __ballot_sync(0xFFFFFFFFu, ray == kNoRay);
+        if (pool_open && (uint32_t)__popc(idle) >= p.refill_min) {
+            const uint32_t need = __popc(idle);
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&p.ctl->next_ray, need);
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            if (base + need >= p.n_rays) pool_open = false;
+            if (ray == kNoRay) {
+                const uint32_t mine = base + __popc(idle & lanemask_lt());
+                if (mine < p.n_rays) {
+                    ray = mine;
+                    start_ray<CLOSEST, STATS>(p, ray, s, cnt);
+                }
+            }
         }
+        if (__ballot_sync(0xFFFFFFFFu, ray != kNoRay) == 0) {
+            if (!pool_open) break;
+            continue;
+        }
+        // one round: descend interior nodes until a leaf is due, then test it
+        if (ray != kNoRay && s.ref != kDoneRef) {
+            while (s.ref >= 0) {
+                if (over_budget(p, s)) break;
+                visit_interior<W, STATS>(p, s, stack, cnt);
+            }
+            if (s.ref != kDoneRef && !over_budget(p, s)) visit_leaf<CLOSEST, STATS>(p, s, stack, cnt);
+        }
+        // lanes whose ray is done write it out and free themselves
+        bool want = false;
+        uint32_t slot = 0;
+        uint64_t word = 0;
+        const bool done = ray != kNoRay && s.ref == kDoneRef;
+        if (done) want = finish_ray<CLOSEST, STATS>(p, ray, s, cnt, slot, word);
+        append_records(p, lane, want, slot, ray, word);
+        if (done) ray = kNoRay;
     }
+    cnt.flush(p.ctl, lane);
 }
 
 template <int W>
-cudaError_t launch_width(bool closest, bool stats, const TraceParams &p, int block_threads, int blocks_per_sm_cap,
-                         cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1)
+cudaError_t launch_width(bool closest, bool stats, int schedule, const TraceParams &p, int block_threads,
+                         int blocks_per_sm_cap, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     const void *fn;
-    if (closest) fn = stats ? (const void *)k_trace<W, true, true> : (const void *)k_trace<W, true, false>;
-    else fn = stats ? (const void *)k_trace<W, false, true> : (const void *)k_trace<W, false, false>;
+    if (schedule == 1) {
+        if (closest) fn = stats ? (const void *)k_trace_dyn<W, true, true> : (const void *)k_trace_dyn<W, true, false>;
+        else fn = stats ? (const void *)k_trace_dyn<W, false, true> : (const void *)k_trace_dyn<W, false, false>;
+    } else {
+        if (closest) fn = stats ? (const void *)k_trace<W, true, true> : (const void *)k_trace<W, true, false>;
+        else fn = stats ? (const void *)k_trace<W, false, true> : (const void *)k_trace<W, false, false>;
+    }
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;

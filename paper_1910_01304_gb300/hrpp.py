@@ -42,7 +42,11 @@ class hrpp_scene_info(ctypes.Structure):
 
 class hrpp_trace_opts(ctypes.Structure):
     _fields_ = [("kernel_start", ctypes.c_void_p), ("kernel_stop", ctypes.c_void_p),
-                ("block_threads", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 7)]
+                ("block_threads", ctypes.c_uint32), ("schedule", ctypes.c_uint32), ("refill_min", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 5)]
+
+
+HRPP_SCHEDULE_DEFAULT, HRPP_SCHEDULE_BATCH, HRPP_SCHEDULE_REFILL = 0, 1, 2
 
 
 class HrppError(RuntimeError):
@@ -228,7 +232,7 @@ class Table:
 
 
 def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, stats: bool = False,
-          stream=None, kernel_events=None, block_threads: int = 0):
+          stream=None, kernel_events=None, block_threads: int = 0, schedule: int = 0, refill_min: int = 0):
     """Traces rays ([n, 8] float32 torch tensor on the GPU, or a host numpy
     array / torch tensor).  Returns (hits, stats dict or None).
 
@@ -246,12 +250,14 @@ def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, 
             hits = torch.empty(shape, dtype=dtype, device=rays.device)
     st = hrpp_stats() if stats else None
     opts = None
-    if kernel_events is not None or block_threads:
+    if kernel_events is not None or block_threads or schedule or refill_min:
         opts = hrpp_trace_opts()
         if kernel_events is not None:
             opts.kernel_start = kernel_events[0].cuda_event
             opts.kernel_stop = kernel_events[1].cuda_event
         opts.block_threads = block_threads
+        opts.schedule = schedule
+        opts.refill_min = refill_min
     check(hrpp_trace_ex(scene.handle, table.handle if table is not None else None, _ptr(rays), n, mode, _ptr(hits),
                         ctypes.byref(st) if st is not None else None, _stream_handle(stream),
                         ctypes.byref(opts) if opts is not None else None))

@@ -212,6 +212,7 @@ def test_mid_terrain_bvh4_hrpp(H):
     g = H.Scene.from_workload(s)
     tabs = {m: H.Table(14, 2, 6) for m in (O.CLOSEST_HIT, O.ANY_HIT)}
     otabs = {m: O.Table(14, 2, 6, O.TWO_PHASE) for m in (O.CLOSEST_HIT, O.ANY_HIT)}
+    tp = {O.CLOSEST_HIT: 0, O.ANY_HIT: 0}
     for frame in range(3):
         prim = s.primary_rays(frame=frame)
         ph, _ = _oracle(s, prim, O.CLOSEST_HIT)
@@ -222,4 +223,34 @@ def test_mid_terrain_bvh4_hrpp(H):
             assert_same_hits(mode, gh, oh, f"frame {frame}")
             assert_same_stats(gst, ost, msg=f"frame {frame}")
             assert np.array_equal(tabs[mode].export(), otabs[mode].words)
-    assert gst["true_pos"] > 0
+            tp[mode] += gst["true_pos"]
+    # primary rays of later frames find their leaves predicted
+    assert tp[O.CLOSEST_HIT] > 0
+
+
+@pytest.mark.parametrize("width_idx", [0, 1])
+@pytest.mark.parametrize("mode", [O.CLOSEST_HIT, O.ANY_HIT])
+def test_schedules_give_identical_results(H, small_pair, width_idx, mode):
+    """Batch and refill schedules, any refill threshold and block size: the
+    same hits, counters and table words as the oracle."""
+    s, g = small_pair[width_idx]
+    variants = [dict(schedule=H.HRPP_SCHEDULE_BATCH), dict(schedule=H.HRPP_SCHEDULE_REFILL, refill_min=1),
+                dict(schedule=H.HRPP_SCHEDULE_REFILL, refill_min=8, block_threads=256),
+                dict(schedule=H.HRPP_SCHEDULE_REFILL, refill_min=32, block_threads=64)]
+    prim = s.primary_rays(frame=2)
+    ph, _ = _oracle(s, prim, O.CLOSEST_HIT)
+    rays = prim if mode == O.CLOSEST_HIT else W.secondary_shadow(s, prim, ph["t"], ph["prim"])[0]
+    otab = O.Table(12, 2, 6, O.TWO_PHASE)
+    _oracle(s, s.primary_rays(frame=1), mode, otab)
+    warm = otab.words.copy()
+    oh, ost = _oracle(s, rays, mode, otab)
+    import torch
+    dr = torch.from_numpy(rays).cuda()
+    for v in variants:
+        tab = H.Table(12, 2, 6)
+        tab.import_(warm)
+        gh, gst = H.trace(g, dr, mode, tab, stats=True, **v)
+        torch.cuda.synchronize()
+        assert_same_hits(mode, gh.cpu().numpy(), oh, str(v))
+        assert_same_stats(gst, ost, msg=str(v))
+        assert np.array_equal(tab.export(), otab.words), str(v)
