@@ -227,6 +227,32 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *scene, hrpp_table *table, const hrpp
                           hrpp_mode mode, void *out_hits, hrpp_stats *out_stats, void *stream,
                           const hrpp_trace_opts *opts);
 
+/* hrpp_trace for callers that must not allocate device memory.  The paper
+ * has no counterpart; this is a library-usage entry point.  hrpp_trace takes
+ * its per-call scratch from a stream-ordered pool, which some callers cannot
+ * allow: an engine whose own allocator reserved all device memory up front
+ * (any further allocation would fail), or a real-time loop that bans
+ * allocation calls because they can stall or synchronise the device.  This
+ * variant allocates nothing: its scratch (a 256-byte control block plus one
+ * 16-byte insert record per ray) lives in one fixed array of 256 B +
+ * 16 B x HRPP_NOALLOC_MAX_RAYS (16 MiB) that every device loading the
+ * library holds until the process exits.
+ *   - rays and out_hits must be device memory (host buffers would need
+ *     staging); out_stats may be NULL, device or host (host waits).
+ *   - n_rays above HRPP_NOALLOC_MAX_RAYS returns INVALID_ARG; split larger
+ *     batches into several calls.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream
+ *     capture.
+ *   - All calls on a device share its one array, which keeps the last
+ *     call's contents (each call clears the control block it needs): calls
+ *     whose work overlaps on the GPU, e.g. on two streams, race; order them,
+ *     for instance on one stream.
+ * Results, statistics and table updates equal hrpp_trace's. */
+#define HRPP_NOALLOC_MAX_RAYS (1u << 20)
+hrpp_status hrpp_trace_noalloc(const hrpp_scene *scene, hrpp_table *table, const hrpp_ray *rays, uint32_t n_rays,
+                               hrpp_mode mode, void *out_hits, hrpp_stats *out_stats, void *stream);
+
 const char *hrpp_last_error(void);
 const char *hrpp_status_string(hrpp_status status);
 int hrpp_version(void);

@@ -13,30 +13,10 @@
 #include <vector>
 
 #include "device.cuh"
+#include "handles.h"
 #include "hrpp.h"
 
 using namespace hrpp;
-
-struct hrpp_scene {
-    int device;
-    uint64_t id;
-    int width;
-    uint32_t n_tris, n_interior, n_leaves, max_depth;
-    int32_t root_ref;
-    float4 *d_nodes;
-    float4 *d_tris;
-    uint32_t *d_error;
-    uint64_t bytes;
-};
-
-struct hrpp_table {
-    int device;
-    int log2_entries, log2_ways, log2_sets;
-    int precision, update_mode;
-    uint64_t *d_words;
-    uint32_t *d_winner;
-    uint64_t bound_scene;
-};
 
 namespace {
 
@@ -211,6 +191,12 @@ hrpp_status validate(const float *tri_verts, uint32_t n_tris, const hrpp_bvh_nod
 }
 
 }  // namespace
+
+hrpp_status hrpp::report(hrpp_status s, const char *message)
+{
+    g_last_error = std::string(hrpp_status_string(s)) + ": " + message;
+    return s;
+}
 
 extern "C" {
 

@@ -1,0 +1,35 @@
+// Internal definitions of the library's opaque handles, shared by the host
+// translation units (api.cu, noalloc.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hrpp.h"
+
+struct hrpp_scene {
+    int device;
+    uint64_t id;
+    int width;
+    uint32_t n_tris, n_interior, n_leaves, max_depth;
+    int32_t root_ref;
+    float4 *d_nodes;
+    float4 *d_tris;
+    uint32_t *d_error;
+    uint64_t bytes;
+};
+
+struct hrpp_table {
+    int device;
+    int log2_entries, log2_ways, log2_sets;
+    int precision, update_mode;
+    uint64_t *d_words;
+    uint32_t *d_winner;
+    uint64_t bound_scene;
+};
+
+namespace hrpp {
+// Stores `message` as the calling thread's hrpp_last_error() text; returns s.
+hrpp_status report(hrpp_status s, const char *message);
+}  // namespace hrpp

@@ -21,6 +21,7 @@ HRPP_ERR_CUDA, HRPP_ERR_TRAVERSAL_LIMIT, HRPP_ERR_UNSUPPORTED = 4, 5, 6
 HRPP_ANY_HIT, HRPP_CLOSEST_HIT = 0, 1
 HRPP_UPDATE_TWO_PHASE, HRPP_UPDATE_ONLINE, HRPP_UPDATE_FROZEN = 0, 1, 2
 HRPP_NO_HIT = 0xFFFFFFFF
+HRPP_NOALLOC_MAX_RAYS = 1 << 20
 HRPP_EMPTY_WORD = 0xFFFFFFFFFFFFFFFF
 STAT_NAMES = ["rays", "hits", "lookups", "positives", "true_pos", "false_pos", "negatives", "tp_inexact",
               "inserts", "dup_inserts", "evictions", "interior_nodes", "box_tests", "leaves", "tri_tests",
@@ -76,6 +77,7 @@ def _load():
         "hrpp_table_destroy": (None, [P]),
         "hrpp_trace": (st, [P, P, P, u32, i32, P, P, P]),
         "hrpp_trace_ex": (st, [P, P, P, u32, i32, P, P, P, P]),
+        "hrpp_trace_noalloc": (st, [P, P, P, u32, i32, P, P, P]),
         "hrpp_last_error": (ctypes.c_char_p, []),
         "hrpp_status_string": (ctypes.c_char_p, [st]),
         "hrpp_version": (i32, []),
@@ -105,6 +107,7 @@ hrpp_table_get_config = _lib.hrpp_table_get_config
 hrpp_table_destroy = _lib.hrpp_table_destroy
 hrpp_trace = _lib.hrpp_trace
 hrpp_trace_ex = _lib.hrpp_trace_ex
+hrpp_trace_noalloc = _lib.hrpp_trace_noalloc
 hrpp_last_error = _lib.hrpp_last_error
 hrpp_status_string = _lib.hrpp_status_string
 hrpp_version = _lib.hrpp_version
