@@ -64,6 +64,36 @@ def dist_env():
     return rank, world, local
 
 
+def frame_index(f: int, rank: int) -> int:
+    """Jitter frame of local frame f on `rank`: every rank renders its own
+    frames (weak scaling: per-rank work is fixed as ranks are added)."""
+    return 1 + f + 1000 * rank
+
+
+def reduce_max(x: float, dist, device) -> float:
+    """Max over ranks (the job's time is its slowest rank's); identity alone."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x: float, dist, device) -> float:
+    """Sum over ranks (rays processed by the whole job); identity alone."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t)
+    return float(t.item())
+
+
+def job_mrays_per_s(total_rays: float, max_ms: float) -> float:
+    return total_rays / (max_ms * 1e-3) / 1e6
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -171,12 +201,12 @@ def make_frames(args, rank, scene_w, H, g, torch):
     from paper_1910_01304_gb300.scenes import workloads as W
     frames = []
     for f in range(args.frames):
-        prim = scene_w.primary_rays(frame=1 + f + 1000 * rank)
+        prim = scene_w.primary_rays(frame=frame_index(f, rank))
         dprim = torch.from_numpy(prim).cuda()
         hits, _ = H.trace(g, dprim, H.HRPP_CLOSEST_HIT)
         hh = hits.cpu().numpy()
         t, p = hh[:, 0], hh[:, 1].view(np.uint32)
-        ao, _ = W.secondary_ao(scene_w, prim, t, p, frame=1 + f + 1000 * rank)
+        ao, _ = W.secondary_ao(scene_w, prim, t, p, frame=frame_index(f, rank))
         frames.append({"prim": dprim, "ao": torch.from_numpy(ao).cuda(), "prim_h": prim, "ao_h": ao})
     return frames
 
@@ -322,18 +352,10 @@ def main():
         return rays, ms, kt
 
     def max_over_ranks(x):
-        if pg is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, pg, "cuda")
 
     def sum_over_ranks(x):
-        if pg is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t)
-        return float(t.item())
+        return reduce_sum(x, pg, "cuda")
 
     # --- HRPP, timed, with clocks sampled over the timed region
     try:
@@ -349,7 +371,7 @@ def main():
     clk = clocks.stop()
     ms_max = max_over_ranks(ms)
     total_rays = sum_over_ranks(rays)
-    value = total_rays / (ms_max * 1e-3) / 1e6
+    value = job_mrays_per_s(total_rays, ms_max)
 
     # --- plain traversal on the same rays
     p_rays, p_ms, p_kt = timed((None, None), True)
