@@ -110,13 +110,17 @@ typedef struct hrpp_hit {
  *   interior_nodes,   interior nodes entered, child boxes tested, leaves
  *   box_tests,        entered and triangles tested by traversal
  *   leaves, tri_tests
- *   pred_leaves,      predicted leaves and their triangles tested before
- *   pred_tri_tests    (or instead of) traversal */
+ *   pred_leaves,      leaves and triangles tested inside predicted leaves or
+ *   pred_tri_tests    subtrees, before (or instead of) traversal from the root
+ *   pred_interior_nodes, pred_box_tests
+ *                     interior nodes entered and child boxes tested inside
+ *                     predicted subtrees (Go Up Level > 0, Sec. 6.2) */
 typedef struct hrpp_stats {
     uint64_t rays, hits, lookups, positives, true_pos, false_pos, negatives, tp_inexact;
     uint64_t inserts, dup_inserts, evictions;
     uint64_t interior_nodes, box_tests, leaves, tri_tests, pred_leaves, pred_tri_tests;
-    uint64_t reserved[3];
+    uint64_t pred_interior_nodes, pred_box_tests;
+    uint64_t reserved[1];
 } hrpp_stats;
 
 typedef struct hrpp_scene_info {
@@ -192,6 +196,14 @@ hrpp_status hrpp_table_create(int log2_entries, int ways, hrpp_table **out);
 /* precision_bits in [1, 7]: bits kept from each float's exponent and
  * mantissa by the Sec. 5 hash.  update_mode: hrpp_update_mode. */
 hrpp_status hrpp_table_configure(hrpp_table *table, int precision_bits, int update_mode);
+/* Go Up Level (Sec. 6.2), 0..15, default 0.  0: the table predicts leaves
+ * (word leaf field = first_prim_index_slot << 2 | count - 1).  G > 0: it
+ * predicts the ancestor G levels above the leaf a ray reached (the root if
+ * the leaf is shallower), stored as that interior node's preorder rank
+ * (children in slot order); a predicted ray traverses that subtree first.
+ * Scenes whose root is a leaf store nothing for G > 0.  Changing G makes the
+ * stored words meaningless: reset the table with it. */
+hrpp_status hrpp_table_set_go_up(hrpp_table *table, int go_up_level);
 /* Empties the table (asynchronous on stream) and unbinds it from its scene.
  * A table binds to the first scene it is traced with; tracing it with
  * another scene returns INVALID_ARG until it is reset. */

@@ -30,7 +30,7 @@ HIT_DTYPE = np.dtype([("t", "<f4"), ("prim", "<u4"), ("u", "<f4"), ("v", "<f4")]
 OUTCOME = {0: "plain", 1: "negative", 2: "false_pos", 3: "true_pos"}
 STAT_NAMES = ["rays", "hits", "lookups", "positives", "true_pos", "false_pos", "negatives", "tp_inexact",
               "inserts", "dup_inserts", "evictions", "interior_nodes", "box_tests", "leaves", "tri_tests",
-              "pred_leaves", "pred_tri_tests"]
+              "pred_leaves", "pred_tri_tests", "pred_interior_nodes", "pred_box_tests"]
 N_STATS = 20
 
 
@@ -52,7 +52,8 @@ class _Scene(ctypes.Structure):
 
 class _Table(ctypes.Structure):
     _fields_ = [("words", ctypes.c_void_p), ("log2_sets", ctypes.c_int), ("log2_ways", ctypes.c_int),
-                ("precision", ctypes.c_int), ("update_mode", ctypes.c_int), ("unbounded", ctypes.c_void_p)]
+                ("precision", ctypes.c_int), ("update_mode", ctypes.c_int), ("unbounded", ctypes.c_void_p),
+                ("go_up", ctypes.c_int)]
 
 
 def _L():
@@ -169,7 +170,8 @@ def brute(rays: np.ndarray, tris: np.ndarray, mode: int):
 class Table:
     """Predictor table state held by the oracle (bounded modes: numpy words)."""
 
-    def __init__(self, log2_entries: int, ways: int = 1, precision: int = 6, update_mode: int = TWO_PHASE):
+    def __init__(self, log2_entries: int, ways: int = 1, precision: int = 6, update_mode: int = TWO_PHASE,
+                 go_up: int = 0):
         log2_ways = {1: 0, 2: 1, 4: 2, 8: 3}[ways]
         if log2_entries - log2_ways < 0:
             raise ValueError("fewer entries than ways")
@@ -180,7 +182,8 @@ class Table:
         self.update_mode = update_mode
         n_words = 1 << log2_entries if update_mode != UNBOUNDED else 1
         self.words = np.full(n_words, EMPTY_WORD, np.uint64)
-        self._c = _Table(self.words.ctypes.data, self.log2_sets, self.log2_ways, precision, update_mode, None)
+        self.go_up = go_up
+        self._c = _Table(self.words.ctypes.data, self.log2_sets, self.log2_ways, precision, update_mode, None, go_up)
 
     def reset(self):
         self.words[:] = EMPTY_WORD

@@ -68,13 +68,14 @@ typedef struct {
     int log2_sets, log2_ways, precision;
     int update_mode;
     void *unbounded;  /* private state of the unbounded map */
+    int go_up;        /* Sec. 6.2 Go Up Level: 0 = leaves, G > 0 = the ancestor G levels up */
 } orc_table;
 
 /* statistics counters, in this order */
 enum {
     S_RAYS, S_HITS, S_LOOKUPS, S_POSITIVES, S_TRUE_POS, S_FALSE_POS, S_NEGATIVES, S_TP_INEXACT,
     S_INSERTS, S_DUP_INSERTS, S_EVICTIONS, S_INTERIOR, S_BOX_TESTS, S_LEAVES, S_TRI_TESTS,
-    S_PRED_LEAVES, S_PRED_TRI_TESTS, S_COUNT = 20
+    S_PRED_LEAVES, S_PRED_TRI_TESTS, S_PRED_INTERIOR, S_PRED_BOX_TESTS, S_COUNT = 20
 };
 
 /* per-ray outcome codes */
@@ -296,30 +297,40 @@ static int test_leaf(const orc_scene *sc, const orc_node *n, const float *ray, i
     return 0;
 }
 
-/* Stack traversal from the root.  Interior nodes test each child's box with
- * the current bound (the ray's tmax, or the best hit so far in closest mode);
- * children that are hit are visited nearest first, ordered by (entry t, slot).
- * Returns 1 if the best hit changed during this traversal. */
-static int traverse(const orc_scene *sc, const float *ray, int mode, best_hit *b, workspace *ws, uint64_t *st,
-                    uint32_t *box_tests_out)
+/* Which counters a traversal adds to: the main traversal, or the traversal
+ * of a predicted subtree. */
+typedef struct {
+    int interior, box_tests, leaves, tri_tests;
+} counter_set;
+
+static const counter_set MAIN_COUNTERS = {S_INTERIOR, S_BOX_TESTS, S_LEAVES, S_TRI_TESTS};
+static const counter_set PRED_COUNTERS = {S_PRED_INTERIOR, S_PRED_BOX_TESTS, S_PRED_LEAVES, S_PRED_TRI_TESTS};
+
+/* Stack traversal of the subtree under `start` (the root for the main
+ * traversal).  Interior nodes test each child's box with the current bound
+ * (the ray's tmax, or the best hit so far in closest mode); children that are
+ * hit are visited nearest first, ordered by (entry t, slot).  Returns 1 if
+ * the best hit changed during this traversal. */
+static int traverse_from(const orc_scene *sc, uint32_t start, const float *ray, int mode, best_hit *b,
+                         workspace *ws, uint64_t *st, counter_set cs, uint32_t *box_tests_out)
 {
     float inv[3], oinv[3];
     orc_ray_inverse(ray, inv, oinv);
     uint32_t sp = 0;
-    ws->stack[sp++] = sc->root;
+    ws->stack[sp++] = start;
     int changed = 0;
     uint32_t box_tests = 0;
     while (sp > 0) {
         const orc_node *n = &sc->nodes[ws->stack[--sp]];
         if (n->count > 0) {
-            st[S_LEAVES] += 1;
+            st[cs.leaves] += 1;
             best_hit before = *b;
-            int done = test_leaf(sc, n, ray, mode, b, &st[S_TRI_TESTS]);
+            int done = test_leaf(sc, n, ray, mode, b, &st[cs.tri_tests]);
             if (b->found && (!before.found || b->prim != before.prim || b->t != before.t)) changed = 1;
             if (done) break;
             continue;
         }
-        st[S_INTERIOR] += 1;
+        st[cs.interior] += 1;
         float tcur = (mode == ORC_CLOSEST && b->found) ? b->t : ray[7];
         float tn[4];
         int slot[4], cnt = 0;
@@ -348,9 +359,83 @@ static int traverse(const orc_scene *sc, const float *ray, int mode, best_hit *b
         }
         for (int i = cnt - 1; i >= 0; --i) ws->stack[sp++] = (uint32_t)n->child[slot[i]];
     }
-    st[S_BOX_TESTS] += box_tests;
+    st[cs.box_tests] += box_tests;
     if (box_tests_out) *box_tests_out = box_tests;
     return changed;
+}
+
+static int traverse(const orc_scene *sc, const float *ray, int mode, best_hit *b, workspace *ws, uint64_t *st,
+                    uint32_t *box_tests_out)
+{
+    return traverse_from(sc, sc->root, ray, mode, b, ws, st, MAIN_COUNTERS, box_tests_out);
+}
+
+/* Tree facts the Go Up Level needs (Sec. 6.2): each node's parent, and each
+ * interior node's identity = its rank in preorder from the root with
+ * children taken in slot order. */
+typedef struct {
+    int32_t *parent;      /* per node; -1 for the root and unreached nodes */
+    int32_t *rank;        /* per node: preorder rank among interior nodes, else -1 */
+    int32_t *by_rank;     /* rank -> node */
+    int32_t *leaf_at;     /* prim_index slot -> the leaf node starting there, else -1 */
+    uint32_t n_interior;
+} tree_info;
+
+static void tree_info_free(tree_info *t)
+{
+    free(t->parent);
+    free(t->rank);
+    free(t->by_rank);
+    free(t->leaf_at);
+}
+
+static int tree_info_build(const orc_scene *sc, tree_info *t)
+{
+    memset(t, 0, sizeof *t);
+    t->parent = (int32_t *)malloc(sizeof(int32_t) * sc->n_nodes);
+    t->rank = (int32_t *)malloc(sizeof(int32_t) * sc->n_nodes);
+    t->by_rank = (int32_t *)malloc(sizeof(int32_t) * sc->n_nodes);
+    t->leaf_at = (int32_t *)malloc(sizeof(int32_t) * (sc->n_prim_index ? sc->n_prim_index : 1));
+    uint32_t *stack = (uint32_t *)malloc(sizeof(uint32_t) * (sc->n_nodes + 4));
+    if (!t->parent || !t->rank || !t->by_rank || !t->leaf_at || !stack) {
+        free(stack);
+        tree_info_free(t);
+        return 1;
+    }
+    for (uint32_t i = 0; i < sc->n_nodes; ++i) t->parent[i] = t->rank[i] = -1;
+    for (uint32_t i = 0; i < sc->n_prim_index; ++i) t->leaf_at[i] = -1;
+    uint32_t sp = 0;
+    stack[sp++] = sc->root;
+    while (sp > 0) {
+        uint32_t ni = stack[--sp];
+        const orc_node *n = &sc->nodes[ni];
+        if (n->count > 0) {
+            if (n->first < sc->n_prim_index) t->leaf_at[n->first] = (int32_t)ni;
+            continue;
+        }
+        t->rank[ni] = (int32_t)t->n_interior;
+        t->by_rank[t->n_interior++] = (int32_t)ni;
+        for (int s = 3; s >= 0; --s)
+            if (n->child[s] >= 0) {
+                t->parent[n->child[s]] = (int32_t)ni;
+                stack[sp++] = (uint32_t)n->child[s];
+            }
+    }
+    free(stack);
+    return 0;
+}
+
+/* Table node of the leaf where a hit was found: the leaf itself (G = 0) or
+ * its ancestor G levels up, stopping at the root (G > 0; then the preorder
+ * rank).  Returns -1 when there is nothing to store (the root is a leaf). */
+static int64_t predicted_node(const orc_scene *sc, const tree_info *t, uint32_t leaf, int go_up)
+{
+    if (go_up == 0) return leaf;
+    int32_t n = t->leaf_at[leaf >> 2];
+    if (n < 0 || t->parent[n] < 0) return -1;
+    n = t->parent[n];
+    for (int g = 1; g < go_up && t->parent[n] >= 0; ++g) n = t->parent[n];
+    return t->rank[n];
 }
 
 /* ------------------------------------------------------- unbounded map -- */
@@ -480,7 +565,9 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
     uint32_t ways = tab ? (1u << tab->log2_ways) : 1u;
     if (tab && tab->update_mode == ORC_TWO_PHASE) recs = (record *)malloc(sizeof(record) * (n_rays ? n_rays : 1));
     if (tab && tab->update_mode == ORC_UNBOUNDED && !tab->unbounded) tab->unbounded = calloc(1, sizeof(ub_map));
-    if (!ws.stack || (tab && tab->update_mode == ORC_TWO_PHASE && !recs)) {
+    tree_info ti;
+    int go_up = tab ? tab->go_up : 0;
+    if (!ws.stack || (tab && tab->update_mode == ORC_TWO_PHASE && !recs) || tree_info_build(sc, &ti)) {
         free(ws.stack);
         free(recs);
         return 1;
@@ -525,10 +612,18 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
                 stats[S_POSITIVES] += 1;
                 int answered = 0;
                 for (uint32_t k = 0; k < n_cand && !answered; ++k) {
-                    const orc_node *lf = find_leaf(sc, cand[k]);
-                    if (!lf) continue;
-                    stats[S_PRED_LEAVES] += 1;
-                    answered = test_leaf(sc, lf, ray, mode, &b, &stats[S_PRED_TRI_TESTS]);
+                    if (go_up == 0) {
+                        const orc_node *lf = find_leaf(sc, cand[k]);
+                        if (!lf) continue;
+                        stats[S_PRED_LEAVES] += 1;
+                        answered = test_leaf(sc, lf, ray, mode, &b, &stats[S_PRED_TRI_TESTS]);
+                    } else {
+                        /* Sec. 6.2: a predicted interior node; the ray traverses its subtree */
+                        if (cand[k] >= ti.n_interior) continue;
+                        best_hit before = b;
+                        traverse_from(sc, (uint32_t)ti.by_rank[cand[k]], ray, mode, &b, &ws, stats, PRED_COUNTERS, NULL);
+                        answered = mode == ORC_ANY && b.found && !before.found;
+                    }
                 }
                 if (b.found) {
                     oc = OUT_TRUE_POS;
@@ -544,14 +639,15 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
             best_hit pred = b;
             int changed = traverse(sc, ray, mode, &b, &ws, stats, ray_box_tests ? &ray_box_tests[i] : NULL);
             if (oc == OUT_TRUE_POS && changed && (b.prim != pred.prim || b.t != pred.t)) stats[S_TP_INEXACT] += 1;
-            if (tab && b.found) {
+            int64_t node = (tab && b.found) ? predicted_node(sc, &ti, b.leaf, go_up) : -1;
+            if (node >= 0) {
                 int is_cand = 0;
-                for (uint32_t k = 0; k < n_cand; ++k) is_cand |= cand[k] == b.leaf;
+                for (uint32_t k = 0; k < n_cand; ++k) is_cand |= cand[k] == (uint32_t)node;
                 if (!is_cand) {
                     stats[S_INSERTS] += 1;
                     if (bounded) {
-                        uint32_t slot = (uint32_t)(set * ways + way_of(b.leaf, tab->log2_ways));
-                        uint64_t value = (tag << LEAF_BITS) | b.leaf;
+                        uint32_t slot = (uint32_t)(set * ways + way_of((uint32_t)node, tab->log2_ways));
+                        uint64_t value = (tag << LEAF_BITS) | (uint64_t)node;
                         if (tab->update_mode == ORC_SEQUENTIAL) {
                             uint64_t old = tab->words[slot];
                             if (old == value) stats[S_DUP_INSERTS] += 1;
@@ -568,7 +664,7 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
                             e->cap = e->cap ? 2 * e->cap : 4;
                             e->leaves = (uint32_t *)realloc(e->leaves, sizeof(uint32_t) * e->cap);
                         }
-                        e->leaves[e->n++] = b.leaf;
+                        e->leaves[e->n++] = (uint32_t)node;
                     }
                 }
             }
@@ -608,5 +704,6 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
     }
     free(recs);
     free(ws.stack);
+    tree_info_free(&ti);
     return 0;
 }

@@ -282,6 +282,18 @@ hrpp_status hrpp_scene_create(const float *tri_verts, uint32_t n_tris, const hrp
             d[7] = make_float4(0, 0, 0, 0);
         }
     }
+    // parent links for the Go Up Level (Sec. 6.2): interior node -> parent,
+    // and a leaf's first prim_index slot -> the leaf's parent (-1 at the root)
+    std::vector<int32_t> h_parent(std::max<size_t>(1, v.order.size()), -1), h_leaf_parent(n_tris, -1);
+    for (uint32_t k = 0; k < v.order.size(); ++k) {
+        const hrpp_bvh_node &n = nodes[v.order[k]];
+        for (int q = 0; q < 4; ++q) {
+            const int32_t c = n.child[q];
+            if (c == -1) continue;
+            if (nodes[c].count > 0) h_leaf_parent[nodes[c].first] = (int32_t)k;
+            else h_parent[dev_index[c]] = (int32_t)k;
+        }
+    }
     // triangles in leaf (prim_index) order: v0 with the prim id, then the edges
     std::vector<float4> h_tris(3ull * n_tris);
     for (uint32_t k = 0; k < n_tris; ++k) {
@@ -309,11 +321,15 @@ hrpp_status hrpp_scene_create(const float *tri_verts, uint32_t n_tris, const hrp
     sc->max_depth = v.info.max_depth;
     sc->root_ref = nodes[root].count > 0 ? (int32_t)~leaf_id(nodes[root]) : 0;
     const size_t nb = h_nodes.size() * sizeof(float4), tb = h_tris.size() * sizeof(float4);
-    sc->bytes = nb + tb + sizeof(uint32_t);
+    const size_t pb = h_parent.size() * sizeof(int32_t), lb = h_leaf_parent.size() * sizeof(int32_t);
+    sc->bytes = nb + tb + pb + lb + sizeof(uint32_t);
     if ((e = cudaMalloc(&sc->d_nodes, nb)) != cudaSuccess || (e = cudaMalloc(&sc->d_tris, tb)) != cudaSuccess ||
         (e = cudaMalloc(&sc->d_error, sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMalloc(&sc->d_parent, pb)) != cudaSuccess || (e = cudaMalloc(&sc->d_leaf_parent, lb)) != cudaSuccess ||
         (e = cudaMemcpy(sc->d_nodes, h_nodes.data(), nb, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(sc->d_tris, h_tris.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(sc->d_parent, h_parent.data(), pb, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(sc->d_leaf_parent, h_leaf_parent.data(), lb, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(sc->d_error, 0, sizeof(uint32_t))) != cudaSuccess) {
         hrpp_scene_destroy(sc);
         return cuda_fail(e, "scene upload");
@@ -361,6 +377,8 @@ void hrpp_scene_destroy(hrpp_scene *sc)
     cudaFree(sc->d_nodes);
     cudaFree(sc->d_tris);
     cudaFree(sc->d_error);
+    cudaFree(sc->d_parent);
+    cudaFree(sc->d_leaf_parent);
     delete sc;
 }
 
@@ -408,6 +426,14 @@ hrpp_status hrpp_table_configure(hrpp_table *t, int precision_bits, int update_m
         return fail(HRPP_ERR_INVALID_ARG, "unknown update_mode %d", update_mode);
     t->precision = precision_bits;
     t->update_mode = update_mode;
+    return HRPP_OK;
+}
+
+hrpp_status hrpp_table_set_go_up(hrpp_table *t, int go_up_level)
+{
+    if (!t) return fail(HRPP_ERR_INVALID_ARG, "table is NULL");
+    if (go_up_level < 0 || go_up_level > 15) return fail(HRPP_ERR_INVALID_ARG, "go_up_level must be in [0, 15]");
+    t->go_up = go_up_level;
     return HRPP_OK;
 }
 
@@ -574,6 +600,9 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         p.ctl = ctl;
         p.error = sc->d_error;
         p.refill_min = refill_min;
+        p.n_interior = sc->n_interior;
+        p.parent = sc->d_parent;
+        p.leaf_parent = sc->d_leaf_parent;
         if (table) {
             p.table = table->d_words;
             p.winner = table->d_winner;
@@ -582,6 +611,7 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
             p.log2_ways = table->log2_ways;
             p.precision = table->precision;
             p.update_mode = table->update_mode;
+            p.go_up = table->go_up;
         }
         cudaEvent_t ev0 = opts ? (cudaEvent_t)opts->kernel_start : nullptr;
         cudaEvent_t ev1 = opts ? (cudaEvent_t)opts->kernel_stop : nullptr;

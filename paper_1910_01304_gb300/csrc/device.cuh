@@ -29,7 +29,7 @@ constexpr uint32_t kErrSteps = 2u;
 enum Stat : int {
     ST_RAYS, ST_HITS, ST_LOOKUPS, ST_POSITIVES, ST_TRUE_POS, ST_FALSE_POS, ST_NEGATIVES, ST_TP_INEXACT,
     ST_INSERTS, ST_DUP_INSERTS, ST_EVICTIONS, ST_INTERIOR, ST_BOX_TESTS, ST_LEAVES, ST_TRI_TESTS,
-    ST_PRED_LEAVES, ST_PRED_TRI_TESTS, ST_N = 20
+    ST_PRED_LEAVES, ST_PRED_TRI_TESTS, ST_PRED_INTERIOR, ST_PRED_BOX_TESTS, ST_N = 20
 };
 
 // Per-call device control block: the ray pool's cursor, the insert-record
@@ -64,6 +64,10 @@ struct TraceParams {
     Ctl *ctl;
     uint32_t *error;         // scene's sticky error flag
     uint32_t refill_min;     // dynamic schedule: refill when this many lanes are idle
+    int go_up;               // Go Up Level (Sec. 6.2): 0 = leaves are predicted
+    uint32_t n_interior;
+    const int32_t *parent;       // interior node -> parent (-1 at the root)
+    const int32_t *leaf_parent;  // leaf's first prim_index slot -> parent (-1: root leaf)
 };
 
 // ---------------------------------------------------------------- hashing --

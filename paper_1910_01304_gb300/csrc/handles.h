@@ -17,6 +17,8 @@ struct hrpp_scene {
     float4 *d_nodes;
     float4 *d_tris;
     uint32_t *d_error;
+    int32_t *d_parent;       // per interior node (preorder index): its parent, -1 at the root
+    int32_t *d_leaf_parent;  // per prim_index slot starting a leaf: the leaf's parent, else -1
     uint64_t bytes;
 };
 
@@ -24,6 +26,7 @@ struct hrpp_table {
     int device;
     int log2_entries, log2_ways, log2_sets;
     int precision, update_mode;
+    int go_up;
     uint64_t *d_words;
     uint32_t *d_winner;
     uint64_t bound_scene;

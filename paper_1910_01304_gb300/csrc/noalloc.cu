@@ -148,6 +148,9 @@ extern "C" hrpp_status hrpp_trace_noalloc(const hrpp_scene *sc, hrpp_table *tabl
         p.ctl = ctl;
         p.error = sc->d_error;
         p.refill_min = 16;
+        p.n_interior = sc->n_interior;
+        p.parent = sc->d_parent;
+        p.leaf_parent = sc->d_leaf_parent;
         const bool two_phase = table && table->update_mode == HRPP_UPDATE_TWO_PHASE;
         if (table) {
             p.table = table->d_words;
@@ -157,6 +160,7 @@ extern "C" hrpp_status hrpp_trace_noalloc(const hrpp_scene *sc, hrpp_table *tabl
             p.log2_ways = table->log2_ways;
             p.precision = table->precision;
             p.update_mode = table->update_mode;
+            p.go_up = table->go_up;
         }
         e = sc->width == 2 ? launch_trace_w2(closest, out_stats != nullptr, 0, p, 128, 0, stream, nullptr, nullptr)
                            : launch_trace_w4(closest, out_stats != nullptr, 0, p, 128, 0, stream, nullptr, nullptr);

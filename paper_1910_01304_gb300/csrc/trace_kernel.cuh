@@ -55,7 +55,7 @@ struct Counters {
     {
         if (STATS) {
 #pragma unroll
-            for (int k = 0; k < ST_PRED_TRI_TESTS + 1; ++k) {
+            for (int k = 0; k < ST_PRED_BOX_TESTS + 1; ++k) {
                 const uint32_t v = __reduce_add_sync(0xFFFFFFFFu, c[k]);
                 if (lane == 0 && v) atomicAdd(&ctl->stats[k], (unsigned long long)v);
             }
@@ -113,74 +113,18 @@ __device__ __forceinline__ bool test_leaf(const TraceParams &p, uint32_t leaf, f
     return false;
 }
 
-// Loads ray i and runs the HRPP lookup.  Returns true when the ray still has
-// to traverse (then s.ref is the root).
-template <bool CLOSEST, bool STATS>
-__device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayState &s, Counters<STATS> &cnt)
-{
-    s.o = __ldg(p.rays + 2ull * i);
-    s.d = __ldg(p.rays + 2ull * i + 1);
-    s.b.t = __int_as_float(0x7F800000);
-    s.b.u = s.b.v = 0.0f;
-    s.b.prim = HRPP_NO_HIT;
-    s.b.leaf = 0;
-    s.b.found = s.b.from_trav = false;
-    s.set = 0;
-    s.tag = 0;
-    cnt.add(ST_RAYS);
-    bool traverse = true;
-    if (p.table) {
-        cnt.add(ST_LOOKUPS);
-        const uint64_t m = mix48(ray_key(s.o, s.d, p.precision));
-        s.set = (uint32_t)(m & ((1ull << p.log2_sets) - 1ull));
-        s.tag = (m >> p.log2_sets) & kTagMask;
-        const uint64_t *set = p.table + ((uint64_t)s.set << p.log2_ways);
-        const uint32_t ways = 1u << p.log2_ways;
-        float tdummy = 0.0f;
-        bool positive = false, done = false;
-        for (uint32_t w = 0; w < ways && !done; ++w) {
-            const uint64_t wd = p.update_mode == HRPP_UPDATE_ONLINE ? __ldcg(set + w) : __ldg(set + w);
-            if (wd == HRPP_EMPTY_WORD || (wd >> kLeafBits) != s.tag) continue;
-            positive = true;
-            const uint32_t leaf = (uint32_t)(wd & kLeafMask);
-            if ((leaf >> 2) + (leaf & 3u) + 1u > p.n_tris) continue;  // not a leaf of this scene
-            cnt.add(ST_PRED_LEAVES);
-            done = test_leaf<CLOSEST, STATS>(p, leaf, s.o, s.d, s.b, tdummy, false, cnt, ST_PRED_TRI_TESTS);
-        }
-        if (!positive) {
-            cnt.add(ST_NEGATIVES);
-        } else {
-            cnt.add(ST_POSITIVES);
-            if (s.b.found) {
-                cnt.add(ST_TRUE_POS);
-                if (!CLOSEST) traverse = false;
-            } else {
-                cnt.add(ST_FALSE_POS);
-            }
-        }
-    }
-    s.predicted_hit = s.b.found;
-    if (traverse) {
-        s.ri = ray_inverse(s.o, s.d);
-        s.tcur = (CLOSEST && s.b.found) ? s.b.t : s.d.w;
-        s.sp = 0;
-        s.ref = p.root_ref;
-        s.steps = 0;
-    } else {
-        s.ref = kDoneRef;
-    }
-    return traverse;
-}
-
 __device__ __forceinline__ int32_t pop(int32_t *stack, int &sp) { return sp > 0 ? stack[--sp] : kDoneRef; }
 
 // Visits the interior node s.ref: tests its children's boxes against the
 // current bound and moves to the nearest hit child, pushing the others
 // (farthest deepest); with no hit child it pops.
-template <int W, bool STATS>
+// PRED: the node belongs to a predicted subtree (Go Up Level > 0), counted
+// apart from the traversal from the root.
+template <int W, bool STATS, bool PRED = false>
 __device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s, int32_t *stack, Counters<STATS> &cnt)
 {
-    cnt.add(ST_INTERIOR);
+    constexpr int kBoxStat = PRED ? ST_PRED_BOX_TESTS : ST_BOX_TESTS;
+    cnt.add(PRED ? ST_PRED_INTERIOR : ST_INTERIOR);
     const float tmin = s.o.w;
     if (W == 2) {
         const float4 *n = p.nodes + 4ull * (uint32_t)s.ref;
@@ -190,7 +134,7 @@ __device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s
         const bool h0 = slab(s.ri, tmin, s.tcur, a.x, a.y, a.z, a.w, c.x, c.y, t0);
         const bool v1 = e.y != kEmptyRef;
         const bool h1 = v1 && slab(s.ri, tmin, s.tcur, bb.x, bb.y, bb.z, bb.w, c.z, c.w, t1);
-        cnt.add(ST_BOX_TESTS, 1u + (v1 ? 1u : 0u));
+        cnt.add(kBoxStat, 1u + (v1 ? 1u : 0u));
         if (h0 && h1) {
             if (s.sp >= kStack) {
                 atomicOr(p.error, kErrStack);
@@ -221,7 +165,7 @@ __device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s
     if (ch.y != kEmptyRef) { ++nvalid; if ((h1 = slab(s.ri, tmin, s.tcur, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, t))) t1 = t; }
     if (ch.z != kEmptyRef) { ++nvalid; if ((h2 = slab(s.ri, tmin, s.tcur, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, t))) t2 = t; }
     if (ch.w != kEmptyRef) { ++nvalid; if ((h3 = slab(s.ri, tmin, s.tcur, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, t))) t3 = t; }
-    cnt.add(ST_BOX_TESTS, nvalid);
+    cnt.add(kBoxStat, nvalid);
     const int nhit = (int)h0 + (int)h1 + (int)h2 + (int)h3;
     if (nhit == 0) {
         s.ref = pop(stack, s.sp);
@@ -253,11 +197,12 @@ __device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s
 
 // Tests the leaf s.ref; any-hit rays end at the first valid hit, otherwise the
 // traversal pops the next node.
-template <bool CLOSEST, bool STATS>
+template <bool CLOSEST, bool STATS, bool PRED = false>
 __device__ __forceinline__ void visit_leaf(const TraceParams &p, RayState &s, int32_t *stack, Counters<STATS> &cnt)
 {
-    cnt.add(ST_LEAVES);
-    if (test_leaf<CLOSEST, STATS>(p, ~(uint32_t)s.ref, s.o, s.d, s.b, s.tcur, true, cnt, ST_TRI_TESTS)) {
+    cnt.add(PRED ? ST_PRED_LEAVES : ST_LEAVES);
+    if (test_leaf<CLOSEST, STATS>(p, ~(uint32_t)s.ref, s.o, s.d, s.b, s.tcur, !PRED, cnt,
+                                  PRED ? ST_PRED_TRI_TESTS : ST_TRI_TESTS)) {
         s.ref = kDoneRef;
         return;
     }
@@ -274,6 +219,86 @@ __device__ __forceinline__ bool over_budget(const TraceParams &p, RayState &s)
     return false;
 }
 
+// Loads ray i and runs the HRPP lookup (Sec. 4.2): each predicted leaf is
+// tested; with Go Up Level > 0 each predicted interior node's subtree is
+// traversed (Sec. 6.2).  Returns true when the ray still has to traverse from
+// the root (then s.ref is the root).
+template <int W, bool CLOSEST, bool STATS>
+__device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayState &s, int32_t *stack,
+                                          Counters<STATS> &cnt)
+{
+    s.o = __ldg(p.rays + 2ull * i);
+    s.d = __ldg(p.rays + 2ull * i + 1);
+    s.b.t = __int_as_float(0x7F800000);
+    s.b.u = s.b.v = 0.0f;
+    s.b.prim = HRPP_NO_HIT;
+    s.b.leaf = 0;
+    s.b.found = s.b.from_trav = false;
+    s.set = 0;
+    s.tag = 0;
+    cnt.add(ST_RAYS);
+    bool traverse = true, have_inverse = false;
+    if (p.table) {
+        cnt.add(ST_LOOKUPS);
+        const uint64_t m = mix48(ray_key(s.o, s.d, p.precision));
+        s.set = (uint32_t)(m & ((1ull << p.log2_sets) - 1ull));
+        s.tag = (m >> p.log2_sets) & kTagMask;
+        const uint64_t *set = p.table + ((uint64_t)s.set << p.log2_ways);
+        const uint32_t ways = 1u << p.log2_ways;
+        float tdummy = 0.0f;
+        bool positive = false, done = false;
+        for (uint32_t w = 0; w < ways && !done; ++w) {
+            const uint64_t wd = p.update_mode == HRPP_UPDATE_ONLINE ? __ldcg(set + w) : __ldg(set + w);
+            if (wd == HRPP_EMPTY_WORD || (wd >> kLeafBits) != s.tag) continue;
+            positive = true;
+            const uint32_t node = (uint32_t)(wd & kLeafMask);
+            if (p.go_up == 0) {
+                if ((node >> 2) + (node & 3u) + 1u > p.n_tris) continue;  // not a leaf of this scene
+                cnt.add(ST_PRED_LEAVES);
+                done = test_leaf<CLOSEST, STATS>(p, node, s.o, s.d, s.b, tdummy, false, cnt, ST_PRED_TRI_TESTS);
+            } else {
+                if (node >= p.n_interior) continue;  // not an interior node of this scene
+                if (!have_inverse) {
+                    s.ri = ray_inverse(s.o, s.d);
+                    have_inverse = true;
+                }
+                s.tcur = (CLOSEST && s.b.found) ? s.b.t : s.d.w;
+                s.sp = 0;
+                s.ref = (int32_t)node;
+                s.steps = 0;
+                while (s.ref != kDoneRef) {
+                    if (over_budget(p, s)) break;
+                    if (s.ref >= 0) visit_interior<W, STATS, true>(p, s, stack, cnt);
+                    else visit_leaf<CLOSEST, STATS, true>(p, s, stack, cnt);
+                }
+                done = !CLOSEST && s.b.found;
+            }
+        }
+        if (!positive) {
+            cnt.add(ST_NEGATIVES);
+        } else {
+            cnt.add(ST_POSITIVES);
+            if (s.b.found) {
+                cnt.add(ST_TRUE_POS);
+                if (!CLOSEST) traverse = false;
+            } else {
+                cnt.add(ST_FALSE_POS);
+            }
+        }
+    }
+    s.predicted_hit = s.b.found;
+    if (traverse) {
+        if (!have_inverse) s.ri = ray_inverse(s.o, s.d);
+        s.tcur = (CLOSEST && s.b.found) ? s.b.t : s.d.w;
+        s.sp = 0;
+        s.ref = p.root_ref;
+        s.steps = 0;
+    } else {
+        s.ref = kDoneRef;
+    }
+    return traverse;
+}
+
 // Writes ray i's result and decides its insert (two-phase: returns the record
 // to append; online: exchanges the word now).
 template <bool CLOSEST, bool STATS>
@@ -282,17 +307,40 @@ __device__ __forceinline__ bool finish_ray(const TraceParams &p, uint32_t i, con
 {
     bool want_record = false;
     if (CLOSEST && s.predicted_hit && s.b.from_trav) cnt.add(ST_TP_INEXACT);
-    if (p.table && s.b.from_trav && p.update_mode != HRPP_UPDATE_FROZEN) {
-        cnt.add(ST_INSERTS);
-        slot = (s.set << p.log2_ways) | way_of(s.b.leaf, p.log2_ways);
-        word = (s.tag << kLeafBits) | s.b.leaf;
-        if (p.update_mode == HRPP_UPDATE_ONLINE) {
-            const unsigned long long old = atomicExch(reinterpret_cast<unsigned long long *>(p.table + slot), word);
-            if (old == word) cnt.add(ST_DUP_INSERTS);
-            else if (old != HRPP_EMPTY_WORD) cnt.add(ST_EVICTIONS);
-        } else {
-            atomicMax(p.winner + slot, i + 1u);
-            want_record = true;
+    // Sec. 5: a ray that traversed inserts the node of its final hit (the leaf,
+    // or its ancestor go_up levels up, Sec. 6.2) unless its entry holds it
+    // already.  Any-hit true positives were answered by the predictor.
+    const bool traversed = CLOSEST || !s.predicted_hit;
+    if (p.table && traversed && s.b.found && p.update_mode != HRPP_UPDATE_FROZEN) {
+        uint32_t node = s.b.leaf;
+        bool storable = true;
+        if (p.go_up > 0) {
+            int32_t a = __ldg(p.leaf_parent + (s.b.leaf >> 2));
+            storable = a >= 0;
+            for (int g = 1; storable && g < p.go_up; ++g) {
+                const int32_t q = __ldg(p.parent + a);
+                if (q < 0) break;
+                a = q;
+            }
+            node = (uint32_t)a;
+        }
+        const uint64_t w = (s.tag << kLeafBits) | node;
+        const uint64_t *set = p.table + ((uint64_t)s.set << p.log2_ways);
+        bool present = false;
+        for (uint32_t k = 0; k < (1u << p.log2_ways); ++k)
+            present |= (p.update_mode == HRPP_UPDATE_ONLINE ? __ldcg(set + k) : __ldg(set + k)) == w;
+        if (storable && !present) {
+            cnt.add(ST_INSERTS);
+            slot = (s.set << p.log2_ways) | way_of(node, p.log2_ways);
+            word = w;
+            if (p.update_mode == HRPP_UPDATE_ONLINE) {
+                const unsigned long long old = atomicExch(reinterpret_cast<unsigned long long *>(p.table + slot), word);
+                if (old == word) cnt.add(ST_DUP_INSERTS);
+                else if (old != HRPP_EMPTY_WORD) cnt.add(ST_EVICTIONS);
+            } else {
+                atomicMax(p.winner + slot, i + 1u);
+                want_record = true;
+            }
         }
     }
     if (s.b.found) cnt.add(ST_HITS);
@@ -342,7 +390,7 @@ __global__ void __launch_bounds__(512) k_trace(const TraceParams p)
         uint64_t word = 0;
         if (i < p.n_rays) {
             RayState s;
-            if (start_ray<CLOSEST, STATS>(p, i, s, cnt)) {
+            if (start_ray<W, CLOSEST, STATS>(p, i, s, stack, cnt)) {
                 while (s.ref != kDoneRef) {
                     if (over_budget(p, s)) break;
                     if (s.ref >= 0) visit_interior<W, STATS>(p, s, stack, cnt);
@@ -379,7 +427,7 @@ __global__ void __launch_bounds__(512) k_trace_dyn(const TraceParams p)
                 const uint32_t mine = base + __popc(idle & lanemask_lt());
                 if (mine < p.n_rays) {
                     ray = mine;
-                    start_ray<CLOSEST, STATS>(p, ray, s, cnt);
+                    start_ray<W, CLOSEST, STATS>(p, ray, s, stack, cnt);
                 }
             }
         }

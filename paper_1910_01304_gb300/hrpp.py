@@ -25,11 +25,11 @@ HRPP_NOALLOC_MAX_RAYS = 1 << 20
 HRPP_EMPTY_WORD = 0xFFFFFFFFFFFFFFFF
 STAT_NAMES = ["rays", "hits", "lookups", "positives", "true_pos", "false_pos", "negatives", "tp_inexact",
               "inserts", "dup_inserts", "evictions", "interior_nodes", "box_tests", "leaves", "tri_tests",
-              "pred_leaves", "pred_tri_tests"]
+              "pred_leaves", "pred_tri_tests", "pred_interior_nodes", "pred_box_tests"]
 
 
 class hrpp_stats(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_uint64) for n in STAT_NAMES] + [("reserved", ctypes.c_uint64 * 3)]
+    _fields_ = [(n, ctypes.c_uint64) for n in STAT_NAMES] + [("reserved", ctypes.c_uint64 * 1)]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n in STAT_NAMES}
@@ -70,6 +70,7 @@ def _load():
         "hrpp_scene_destroy": (None, [P]),
         "hrpp_table_create": (st, [i32, i32, P]),
         "hrpp_table_configure": (st, [P, i32, i32]),
+        "hrpp_table_set_go_up": (st, [P, i32]),
         "hrpp_table_reset": (st, [P, P]),
         "hrpp_table_export": (st, [P, P, sz]),
         "hrpp_table_import": (st, [P, P, sz]),
@@ -100,6 +101,7 @@ hrpp_scene_check = _lib.hrpp_scene_check
 hrpp_scene_destroy = _lib.hrpp_scene_destroy
 hrpp_table_create = _lib.hrpp_table_create
 hrpp_table_configure = _lib.hrpp_table_configure
+hrpp_table_set_go_up = _lib.hrpp_table_set_go_up
 hrpp_table_reset = _lib.hrpp_table_reset
 hrpp_table_export = _lib.hrpp_table_export
 hrpp_table_import = _lib.hrpp_table_import
@@ -197,13 +199,19 @@ class Scene:
 class Table:
     """Predictor table (hrpp_table_create / hrpp_table_configure)."""
 
-    def __init__(self, log2_entries: int, ways: int = 1, precision: int = 6, update_mode: int = HRPP_UPDATE_TWO_PHASE):
+    def __init__(self, log2_entries: int, ways: int = 1, precision: int = 6, update_mode: int = HRPP_UPDATE_TWO_PHASE,
+                 go_up: int = 0):
         h = ctypes.c_void_p()
         check(hrpp_table_create(log2_entries, ways, ctypes.byref(h)))
         self.handle = h
         self.log2_entries = log2_entries
         self.ways = ways
         self.configure(precision, update_mode)
+        self.set_go_up(go_up)
+
+    def set_go_up(self, go_up: int):
+        check(hrpp_table_set_go_up(self.handle, go_up))
+        self.go_up = go_up
 
     def configure(self, precision: int, update_mode: int):
         check(hrpp_table_configure(self.handle, precision, update_mode))

@@ -6,7 +6,7 @@ import oracle as O
 
 STAT_KEYS = ["rays", "hits", "lookups", "positives", "true_pos", "false_pos", "negatives", "tp_inexact",
              "inserts", "dup_inserts", "evictions", "interior_nodes", "box_tests", "leaves", "tri_tests",
-             "pred_leaves", "pred_tri_tests"]
+             "pred_leaves", "pred_tri_tests", "pred_interior_nodes", "pred_box_tests"]
 
 
 def hrpp_mod():
@@ -54,4 +54,4 @@ def assert_same_stats(gpu_stats, oracle_stats, keys=STAT_KEYS, msg=""):
 
 
 def oracle_table_like(t):
-    return O.Table(t.log2_entries, t.ways, t.precision, O.TWO_PHASE)
+    return O.Table(t.log2_entries, t.ways, t.precision, O.TWO_PHASE, go_up=getattr(t, "go_up", 0))

@@ -254,3 +254,42 @@ def test_schedules_give_identical_results(H, small_pair, width_idx, mode):
         assert_same_hits(mode, gh.cpu().numpy(), oh, str(v))
         assert_same_stats(gst, ost, msg=str(v))
         assert np.array_equal(tab.export(), otab.words), str(v)
+
+
+@pytest.mark.parametrize("go_up", [1, 2, 5])
+@pytest.mark.parametrize("width_idx", [0, 1])
+def test_go_up_levels_match_oracle(H, small_pair, go_up, width_idx):
+    """Go Up Level (Sec. 6.2): predicted subtrees, their counters and the
+    ancestor words stored in the table, over three frames of both modes."""
+    s, g = small_pair[width_idx]
+    tabs = {m: H.Table(12, 2, 6, go_up=go_up) for m in (O.CLOSEST_HIT, O.ANY_HIT)}
+    otabs = {m: O.Table(12, 2, 6, O.TWO_PHASE, go_up=go_up) for m in (O.CLOSEST_HIT, O.ANY_HIT)}
+    pred = 0
+    for frame in range(3):
+        prim = s.primary_rays(frame=frame)
+        ph, _ = _oracle(s, prim, O.CLOSEST_HIT)
+        shadow, _ = W.secondary_shadow(s, prim, ph["t"], ph["prim"])
+        for mode, rays in ((O.CLOSEST_HIT, prim), (O.ANY_HIT, shadow)):
+            oh, ost = _oracle(s, rays, mode, otabs[mode])
+            gh, gst = gpu_trace(H, g, rays, mode, tabs[mode])
+            assert_same_hits(mode, gh, oh, f"frame {frame}")
+            assert_same_stats(gst, ost, msg=f"frame {frame} go_up {go_up}")
+            assert np.array_equal(tabs[mode].export(), otabs[mode].words)
+            pred += gst["pred_interior_nodes"]
+    assert pred > 0
+
+
+def test_go_up_mid_terrain_bvh4(H):
+    s = W.terrain_scene(quads=64, n_spheres=4, subdiv=2, res=(160, 96))
+    g = H.Scene.from_workload(s)
+    tab = H.Table(14, 4, 6, go_up=1)
+    otab = O.Table(14, 4, 6, O.TWO_PHASE, go_up=1)
+    for frame in range(2):
+        prim = s.primary_rays(frame=frame)
+        ph, _ = _oracle(s, prim, O.CLOSEST_HIT)
+        ao, _ = W.secondary_ao(s, prim, ph["t"], ph["prim"], frame=frame)
+        oh, ost = _oracle(s, ao, O.ANY_HIT, otab)
+        gh, gst = gpu_trace(H, g, ao, O.ANY_HIT, tab)
+        assert_same_hits(O.ANY_HIT, gh, oh)
+        assert_same_stats(gst, ost)
+        assert np.array_equal(tab.export(), otab.words)

@@ -173,3 +173,97 @@ def test_ways_hold_distinct_leaves_of_one_key(small, ways):
     # every stored leaf is a real leaf of the BVH
     real = {(int(n["first"]) << 2) | (int(n["count"]) - 1) for n in small.nodes if n["count"] > 0}
     assert set(leaves[valid].tolist()) <= real
+
+
+# ------------------------------------------------------------ Go Up Level --
+
+def _preorder_and_parents(nodes, root=0):
+    """Independent restatement: interior preorder ranks (children in slot
+    order) and parent links of a canonical BVH."""
+    rank, parent, stack = {}, {}, [root]
+    while stack:
+        i = stack.pop()
+        if nodes[i]["count"] > 0:
+            continue
+        rank[i] = len(rank)
+        for c in reversed([int(c) for c in nodes[i]["child"] if c >= 0]):
+            parent[c] = i
+            stack.append(c)
+    return rank, parent
+
+
+@pytest.mark.parametrize("go_up", [1, 2, 3])
+@pytest.mark.parametrize("mode", [O.CLOSEST_HIT, O.ANY_HIT])
+def test_go_up_results_equal_plain(small, go_up, mode):
+    tab = O.Table(12, 2, 6, O.TWO_PHASE, go_up=go_up)
+    for frame in range(3):
+        rays = small.primary_rays(frame=frame)[::2]
+        hp, _ = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, mode)
+        hh, sh = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, mode, tab)
+        if mode == O.CLOSEST_HIT:
+            assert np.array_equal(hp, hh)
+        else:
+            assert np.array_equal(hp == O.NO_HIT, hh == O.NO_HIT)
+        _check_identities(sh, len(rays))
+    assert sh["true_pos"] > 0 and sh["pred_interior_nodes"] > 0
+
+
+@pytest.mark.parametrize("go_up", [1, 2])
+def test_go_up_table_holds_ancestors_of_hit_leaves(small, go_up):
+    """Every stored node is the G-th ancestor (preorder rank) of a leaf that a
+    ray of the batch hit; the insert goes to way way_of(rank)."""
+    rank, parent = _preorder_and_parents(small.nodes)
+    leaf_node = {int(n["first"]): i for i, n in enumerate(small.nodes) if n["count"] > 0}
+    prim_leaf = {}
+    for first, i in leaf_node.items():
+        for j in range(int(small.nodes[i]["count"])):
+            prim_leaf[int(small.prim_index[first + j])] = i
+    rays = small.primary_rays()[::2]
+    tab = O.Table(14, 2, 6, O.TWO_PHASE, go_up=go_up)
+    h, _ = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.CLOSEST_HIT, tab)
+    expect = set()
+    for p in h["prim"][h["prim"] != O.NO_HIT]:
+        n = prim_leaf[int(p)]
+        for _ in range(go_up):
+            n = parent.get(n, n)
+        expect.add(rank[n])
+    w = tab.words.reshape(-1, 2)
+    valid = w != np.uint64(O.EMPTY_WORD)
+    stored = (w & np.uint64((1 << O.LEAF_BITS) - 1)).astype(np.int64)
+    assert valid.sum() > 50
+    assert set(stored[valid].tolist()) <= expect
+    for s_, k in zip(*np.nonzero(valid)):
+        assert O.way_of(int(stored[s_, k]), 1) == k
+
+
+def test_go_up_past_the_root_predicts_the_whole_tree(small):
+    """G larger than the tree's depth stores the root: a predicted ray then
+    traverses the whole tree as its 'subtree', so a true positive's predicted
+    work equals its plain traversal."""
+    rays = small.primary_rays()[::4]
+    tab = O.Table(16, 1, 6, O.UNBOUNDED, go_up=64)
+    O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.ANY_HIT, tab)
+    keys, nodes_stored = tab.unbounded_size()
+    assert keys > 0 and nodes_stored == keys          # one node (the root) per key
+    _, sp, _, plain_boxes = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.ANY_HIT, per_ray=True)
+    h, sh, oc, boxes = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.ANY_HIT, tab, per_ray=True)
+    tp = oc == 3
+    hit = h != O.NO_HIT
+    assert np.array_equal(tp, hit)                     # every ray that hits is a true positive
+    assert np.all(boxes[tp] == 0)                      # no main traversal for them
+    fp = oc == 2                                       # predicted but no hit: full subtree + full traversal
+    assert sh["pred_box_tests"] == int(plain_boxes[tp].sum() + plain_boxes[fp].sum())
+
+
+def test_go_up_unbounded_second_pass(small):
+    rays = small.primary_rays()[::2]
+    tab = O.Table(0, 1, 6, O.UNBOUNDED, go_up=1)
+    h1, _ = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.ANY_HIT, tab)
+    keys1 = tab.unbounded_size()
+    h2, s2, oc, _ = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.ANY_HIT, tab, per_ray=True)
+    hit = h2 != O.NO_HIT
+    assert np.all(oc[hit] == 3) and s2["inserts"] == 0
+    # go-up 1 needs no more nodes than go-up 0 (Sec. 6.2: fewer entries)
+    tab0 = O.Table(0, 1, 6, O.UNBOUNDED, go_up=0)
+    O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.ANY_HIT, tab0)
+    assert keys1[1] <= tab0.unbounded_size()[1]
