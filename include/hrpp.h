@@ -265,6 +265,40 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *scene, hrpp_table *table, const hrpp
 hrpp_status hrpp_trace_noalloc(const hrpp_scene *scene, hrpp_table *table, const hrpp_ray *rays, uint32_t n_rays,
                                hrpp_mode mode, void *out_hits, hrpp_stats *out_stats, void *stream);
 
+/* Batched traces: many (scene, table, rays) items -- scenes of different
+ * sizes, batches of uneven lengths -- traced by ONE persistent kernel launch
+ * (plus one launch applying every two-phase table's inserts), recorded once
+ * into a CUDA graph and replayed by hrpp_batch_run.  Per item the results,
+ * counters and table updates are exactly those of hrpp_trace on that item.
+ *   scene, table  as for hrpp_trace; all scenes of a batch share one device
+ *                 and one BVH width; a table may serve one item only.
+ *   rays, out_hits  device memory (16-byte aligned; hits 16/4-byte for
+ *                 closest/any); the batch keeps these addresses: refill the
+ *                 same buffers between runs.
+ * Table settings (precision, update mode, Go Up Level) are read when the
+ * batch is created. */
+typedef struct hrpp_batch_item {
+    const hrpp_scene *scene;
+    hrpp_table *table;
+    const hrpp_ray *rays;
+    uint32_t n_rays;
+    int mode;  /* hrpp_mode */
+    void *out_hits;
+} hrpp_batch_item;
+typedef struct hrpp_batch hrpp_batch;
+/* Validates the items, uploads the work list (32-ray chunks, each within one
+ * item), allocates the batch's scratch and captures its graph.  collect_stats
+ * != 0 keeps per-item counters (hrpp_batch_get_stats).  block_threads: 0
+ * (default) or 64/128/256/512.  Blocking. */
+hrpp_status hrpp_batch_create(const hrpp_batch_item *items, uint32_t n_items, int collect_stats,
+                              uint32_t block_threads, hrpp_batch **out);
+/* Replays the batch's graph on `stream` (asynchronous).  Runs of one batch,
+ * and of batches sharing a table, must be ordered. */
+hrpp_status hrpp_batch_run(hrpp_batch *batch, void *stream);
+/* Waits for the batch's last run and copies item `item`'s counters. */
+hrpp_status hrpp_batch_get_stats(hrpp_batch *batch, uint32_t item, hrpp_stats *host_stats);
+void hrpp_batch_destroy(hrpp_batch *batch);
+
 const char *hrpp_last_error(void);
 const char *hrpp_status_string(hrpp_status status);
 int hrpp_version(void);

@@ -1,0 +1,125 @@
+"""Autotuner for HRPP launch and predictor-table parameters.
+
+Nothing it picks can change a result: every candidate traces the same rays
+and the tuner checks that all of them return bit-identical hits.  It times,
+with CUDA events on the current stream:
+  1. the traversal launch shape (threads per block, ray schedule) on plain
+     traversal;
+  2. predictor tables over a grid of sizes, associativities, hash precisions
+     (Sec. 5.1's tight-vs-loose trade-off) and Go Up Levels (Sec. 6.2): each
+     table is warmed on one ray set (a previous frame) and then frozen while
+     a second ray set is timed, so the timing sees realistic prediction rates
+     and no self-prediction.
+It returns the fastest table (or none, when no table beats plain traversal)
+with the timings it measured.
+"""
+from __future__ import annotations
+
+import hashlib
+import itertools
+import json
+
+import numpy as np
+
+from . import hrpp as H
+
+LAUNCH_GRID = [dict(block_threads=b, schedule=s) for b in (64, 128, 256)
+               for s in (H.HRPP_SCHEDULE_BATCH, H.HRPP_SCHEDULE_REFILL)]
+TABLE_GRID = dict(log2_entries=(14, 16, 18, 20), ways=(1, 2, 4), precision=(4, 5, 6, 7), go_up=(0, 1))
+
+
+def _time(fn, reps: int) -> float:
+    import torch
+    fn()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def _digest(t) -> str:
+    return hashlib.sha1(t.cpu().numpy().tobytes()).hexdigest()
+
+
+def tune(scene: H.Scene, rays_warm, rays_eval, mode: int, table_grid: dict | None = None, reps: int = 5,
+         launch_grid: list | None = None) -> dict:
+    """Tunes one (scene, mode) workload.  rays_*: [n, 8] device tensors."""
+    import torch
+    grid = TABLE_GRID if table_grid is None else table_grid
+    launches = LAUNCH_GRID if launch_grid is None else launch_grid
+    n = int(rays_eval.shape[0])
+    shape = (n, 4) if mode == H.HRPP_CLOSEST_HIT else (n,)
+    dtype = torch.float32 if mode == H.HRPP_CLOSEST_HIT else torch.int32
+    out = torch.empty(shape, dtype=dtype, device=rays_eval.device)
+    reference = None
+    launch_times = []
+    for cfg in launches:
+        ms = _time(lambda: H.trace(scene, rays_eval, mode, None, hits=out, **cfg), reps)
+        d = _digest(out)
+        reference = reference or d
+        if d != reference:
+            raise AssertionError(f"launch shape {cfg} changed the result")
+        launch_times.append((ms, cfg))
+    plain_ms, launch = min(launch_times, key=lambda x: x[0])
+    best = dict(table=None, ms=plain_ms)
+    table_times = []
+    keys = list(grid)
+    for values in itertools.product(*(grid[k] for k in keys)):
+        tc = dict(zip(keys, values))
+        t = H.Table(tc["log2_entries"], tc["ways"], tc["precision"], H.HRPP_UPDATE_TWO_PHASE, go_up=tc["go_up"])
+        H.trace(scene, rays_warm, mode, t, **launch)
+        t.configure(tc["precision"], H.HRPP_UPDATE_FROZEN)
+        ms = _time(lambda: H.trace(scene, rays_eval, mode, t, hits=out, **launch), reps)
+        if _digest(out) != reference:
+            raise AssertionError(f"table {tc} changed the result")
+        table_times.append(dict(tc, ms=ms))
+        if ms < best["ms"]:
+            best = dict(table=tc, ms=ms)
+        t.close()
+    return dict(mode="closest" if mode == H.HRPP_CLOSEST_HIT else "any", rays=n, launch=launch, plain_ms=plain_ms,
+                best_table=best["table"], best_ms=best["ms"], speedup_over_plain=plain_ms / best["ms"],
+                launch_times=[dict(c, ms=m) for m, c in launch_times], table_times=table_times)
+
+
+def main():
+    import argparse
+
+    import torch
+
+    from .scenes import workloads as W
+    ap = argparse.ArgumentParser(description="tune HRPP launch and table parameters on a workload")
+    ap.add_argument("--workload", default="terrain", choices=["terrain", "small"])
+    ap.add_argument("--quick", action="store_true", help="a reduced table grid")
+    args = ap.parse_args()
+    if args.workload == "terrain":
+        s = W.terrain_scene()
+    else:
+        s = W.small_scene()
+    g = H.Scene.from_workload(s)
+    grid = dict(log2_entries=(16, 18), ways=(1, 2), precision=(5, 6), go_up=(0,)) if args.quick else None
+    results = []
+    prims = [torch.from_numpy(s.primary_rays(frame=f)).cuda() for f in (1, 2)]
+    results.append(tune(g, prims[0], prims[1], H.HRPP_CLOSEST_HIT, grid))
+    secondary = []
+    for f, pr in zip((1, 2), prims):
+        hits, _ = H.trace(g, pr, H.HRPP_CLOSEST_HIT)
+        h = hits.cpu().numpy()
+        rays_np = pr.cpu().numpy()
+        if args.workload == "terrain":
+            sec, _ = W.secondary_ao(s, rays_np, h[:, 0], h[:, 1].view(np.uint32), frame=f)
+        else:
+            sec, _ = W.secondary_shadow(s, rays_np, h[:, 0], h[:, 1].view(np.uint32))
+        secondary.append(torch.from_numpy(sec).cuda())
+    results.append(tune(g, secondary[0], secondary[1], H.HRPP_ANY_HIT, grid))
+    for r in results:
+        r.pop("table_times")
+        print(json.dumps(r))
+
+
+if __name__ == "__main__":
+    main()

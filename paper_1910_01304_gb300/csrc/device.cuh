@@ -68,6 +68,7 @@ struct TraceParams {
     uint32_t n_interior;
     const int32_t *parent;       // interior node -> parent (-1 at the root)
     const int32_t *leaf_parent;  // leaf's first prim_index slot -> parent (-1: root leaf)
+    int closest;                 // batched launches: this item's query mode
 };
 
 // ---------------------------------------------------------------- hashing --
@@ -207,6 +208,21 @@ cudaError_t launch_trace_w4(bool closest, bool stats, int schedule, const TraceP
                             int blocks_per_sm_cap, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1);
 cudaError_t launch_table_apply(uint64_t *table, uint32_t *winner, const Record *records, Ctl *ctl,
                                uint32_t max_records, cudaStream_t stream);
+// batched launches (batch.cu): every item of one BVH width in one kernel, then
+// the two-phase updates of every item's table in one kernel
+struct BatchDesc {
+    const TraceParams *items;    // per item; ctl/records point at the item's own scratch
+    const uint32_t *chunk_item;  // item of each chunk
+    const uint32_t *chunk_first; // first ray (within its item) of each chunk
+    uint32_t n_chunks;
+    unsigned int *cursor;        // the batch's chunk cursor (zeroed before each run)
+};
+
+
+cudaError_t launch_batch_w2(bool stats, const BatchDesc &b, int block_threads, cudaStream_t stream);
+cudaError_t launch_batch_w4(bool stats, const BatchDesc &b, int block_threads, cudaStream_t stream);
+cudaError_t launch_table_apply_batch(const TraceParams *items, uint32_t n_items, uint32_t max_records,
+                                     cudaStream_t stream);
 cudaError_t launch_table_fill(uint64_t *words, uint64_t n_words, cudaStream_t stream);
 
 }  // namespace hrpp

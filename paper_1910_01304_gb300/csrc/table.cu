@@ -10,8 +10,8 @@ namespace hrpp {
 // The winning record writes the word and zeroes winner[slot] for the next
 // call; a losing record reads either the winner's index or zero, never its
 // own, so the outcome does not depend on scheduling.
-__global__ void __launch_bounds__(256) k_apply(uint64_t *table, uint32_t *winner, const Record *rec, Ctl *ctl,
-                                               uint32_t max_records)
+__device__ __forceinline__ void apply_records(uint64_t *table, uint32_t *winner, const Record *rec, Ctl *ctl,
+                                              uint32_t max_records)
 {
     const uint32_t n = min(ctl->n_records, max_records);
     uint32_t evict = 0, lost = 0;
@@ -34,6 +34,20 @@ __global__ void __launch_bounds__(256) k_apply(uint64_t *table, uint32_t *winner
     }
 }
 
+__global__ void __launch_bounds__(256) k_apply(uint64_t *table, uint32_t *winner, const Record *rec, Ctl *ctl,
+                                               uint32_t max_records)
+{
+    apply_records(table, winner, rec, ctl, max_records);
+}
+
+// one grid row per item of a batch (blockIdx.y)
+__global__ void __launch_bounds__(256) k_apply_batch(const TraceParams *items, uint32_t max_records)
+{
+    const TraceParams &p = items[blockIdx.y];
+    if (!p.table || p.update_mode != HRPP_UPDATE_TWO_PHASE) return;
+    apply_records(p.table, p.winner, p.records, p.ctl, min(max_records, p.n_rays));
+}
+
 __global__ void __launch_bounds__(256) k_fill(uint64_t *words, uint64_t n)
 {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
@@ -50,6 +64,16 @@ cudaError_t launch_table_apply(uint64_t *table, uint32_t *winner, const Record *
     if (blocks > (uint32_t)sms * 4u) blocks = (uint32_t)sms * 4u;
     if (blocks < 1) blocks = 1;
     k_apply<<<blocks, 256, 0, stream>>>(table, winner, records, ctl, max_records);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table_apply_batch(const TraceParams *items, uint32_t n_items, uint32_t max_records,
+                                     cudaStream_t stream)
+{
+    uint32_t bx = (max_records + 255u) / 256u;
+    if (bx > 64u) bx = 64u;
+    if (bx < 1u) bx = 1u;
+    k_apply_batch<<<dim3(bx, n_items), 256, 0, stream>>>(items, max_records);
     return cudaGetLastError();
 }
 

@@ -372,6 +372,22 @@ __device__ __forceinline__ void append_records(const TraceParams &p, uint32_t la
     }
 }
 
+// The whole of one ray: lookup, traversal, result, insert decision.
+template <int W, bool CLOSEST, bool STATS>
+__device__ __forceinline__ bool trace_one(const TraceParams &p, uint32_t i, int32_t *stack, Counters<STATS> &cnt,
+                                          uint32_t &slot, uint64_t &word)
+{
+    RayState s;
+    if (start_ray<W, CLOSEST, STATS>(p, i, s, stack, cnt)) {
+        while (s.ref != kDoneRef) {
+            if (over_budget(p, s)) break;
+            if (s.ref >= 0) visit_interior<W, STATS>(p, s, stack, cnt);
+            else visit_leaf<CLOSEST, STATS>(p, s, stack, cnt);
+        }
+    }
+    return finish_ray<CLOSEST, STATS>(p, i, s, cnt, slot, word);
+}
+
 template <int W, bool CLOSEST, bool STATS>
 __global__ void __launch_bounds__(512) k_trace(const TraceParams p)
 {
@@ -388,20 +404,76 @@ __global__ void __launch_bounds__(512) k_trace(const TraceParams p)
         bool want = false;
         uint32_t slot = 0;
         uint64_t word = 0;
-        if (i < p.n_rays) {
-            RayState s;
-            if (start_ray<W, CLOSEST, STATS>(p, i, s, stack, cnt)) {
-                while (s.ref != kDoneRef) {
-                    if (over_budget(p, s)) break;
-                    if (s.ref >= 0) visit_interior<W, STATS>(p, s, stack, cnt);
-                    else visit_leaf<CLOSEST, STATS>(p, s, stack, cnt);
-                }
-            }
-            want = finish_ray<CLOSEST, STATS>(p, i, s, cnt, slot, word);
-        }
+        if (i < p.n_rays) want = trace_one<W, CLOSEST, STATS>(p, i, stack, cnt, slot, word);
         append_records(p, lane, want, slot, i, word);
     }
     cnt.flush(p.ctl, lane);
+}
+
+// Many (scene, table, rays) items in one persistent launch.  The rays of all
+// items are cut into 32-ray chunks (a chunk never spans two items); a warp
+// takes the next chunk from the batch cursor, copies that item's parameters
+// into shared memory when the item changes, traces the chunk exactly as
+// k_trace would, and adds its counters to the item's own control block.
+constexpr int kBatchMaxWarps = 16;  // up to 512 threads per block
+
+template <int W, bool STATS>
+__global__ void __launch_bounds__(512) k_trace_batch(const BatchDesc b)
+{
+    __shared__ TraceParams item_params[kBatchMaxWarps];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    TraceParams &p = item_params[warp];
+    Counters<STATS> cnt;
+    cnt.init();
+    int32_t stack[kStack];
+    uint32_t cur = 0xFFFFFFFFu;
+    for (;;) {
+        uint32_t chunk = 0;
+        if (lane == 0) chunk = atomicAdd(b.cursor, 1u);
+        chunk = __shfl_sync(0xFFFFFFFFu, chunk, 0);
+        if (chunk >= b.n_chunks) break;
+        const uint32_t item = __ldg(b.chunk_item + chunk);
+        if (item != cur) {
+            if (cur != 0xFFFFFFFFu) cnt.flush(p.ctl, lane);
+            cnt.init();
+            __syncwarp();
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(b.items + item);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&p);
+            for (uint32_t k = lane; k < sizeof(TraceParams) / 4; k += 32) dst[k] = __ldg(src + k);
+            __syncwarp();
+            cur = item;
+        }
+        const uint32_t i = __ldg(b.chunk_first + chunk) + lane;
+        bool want = false;
+        uint32_t slot = 0;
+        uint64_t word = 0;
+        if (i < p.n_rays) {
+            if (p.closest) want = trace_one<W, true, STATS>(p, i, stack, cnt, slot, word);
+            else want = trace_one<W, false, STATS>(p, i, stack, cnt, slot, word);
+        }
+        append_records(p, lane, want, slot, i, word);
+    }
+    if (cur != 0xFFFFFFFFu) cnt.flush(p.ctl, lane);
+}
+
+template <int W>
+cudaError_t launch_batch_width(bool stats, const BatchDesc &b, int block_threads, cudaStream_t stream)
+{
+    const void *fn = stats ? (const void *)k_trace_batch<W, true> : (const void *)k_trace_batch<W, false>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block_threads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t warps_per_block = block_threads / 32;
+    uint64_t blocks = (uint64_t)sms * per_sm;
+    if (blocks * warps_per_block > b.n_chunks) blocks = (b.n_chunks + warps_per_block - 1) / warps_per_block;
+    if (blocks < 1) blocks = 1;
+    void *args[] = {(void *)&b};
+    return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(block_threads), args, 0, stream);
 }
 
 template <int W, bool CLOSEST, bool STATS>

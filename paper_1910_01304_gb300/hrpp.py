@@ -50,6 +50,11 @@ class hrpp_trace_opts(ctypes.Structure):
 HRPP_SCHEDULE_DEFAULT, HRPP_SCHEDULE_BATCH, HRPP_SCHEDULE_REFILL = 0, 1, 2
 
 
+class hrpp_batch_item(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_void_p), ("table", ctypes.c_void_p), ("rays", ctypes.c_void_p),
+                ("n_rays", ctypes.c_uint32), ("mode", ctypes.c_int), ("out_hits", ctypes.c_void_p)]
+
+
 class HrppError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(message)
@@ -79,6 +84,10 @@ def _load():
         "hrpp_trace": (st, [P, P, P, u32, i32, P, P, P]),
         "hrpp_trace_ex": (st, [P, P, P, u32, i32, P, P, P, P]),
         "hrpp_trace_noalloc": (st, [P, P, P, u32, i32, P, P, P]),
+        "hrpp_batch_create": (st, [P, u32, i32, u32, P]),
+        "hrpp_batch_run": (st, [P, P]),
+        "hrpp_batch_get_stats": (st, [P, u32, P]),
+        "hrpp_batch_destroy": (None, [P]),
         "hrpp_last_error": (ctypes.c_char_p, []),
         "hrpp_status_string": (ctypes.c_char_p, [st]),
         "hrpp_version": (i32, []),
@@ -110,6 +119,10 @@ hrpp_table_destroy = _lib.hrpp_table_destroy
 hrpp_trace = _lib.hrpp_trace
 hrpp_trace_ex = _lib.hrpp_trace_ex
 hrpp_trace_noalloc = _lib.hrpp_trace_noalloc
+hrpp_batch_create = _lib.hrpp_batch_create
+hrpp_batch_run = _lib.hrpp_batch_run
+hrpp_batch_get_stats = _lib.hrpp_batch_get_stats
+hrpp_batch_destroy = _lib.hrpp_batch_destroy
 hrpp_last_error = _lib.hrpp_last_error
 hrpp_status_string = _lib.hrpp_status_string
 hrpp_version = _lib.hrpp_version
@@ -281,3 +294,48 @@ def closest_fields(hits):
         hits = hits.cpu().numpy()
     h = np.ascontiguousarray(hits, np.float32)
     return h[:, 0].copy(), h[:, 1].view(np.uint32).copy(), h[:, 2].copy(), h[:, 3].copy()
+
+
+class Batch:
+    """Many (scene, table, rays) items traced by one persistent launch replayed
+    from a CUDA graph (hrpp_batch_create / hrpp_batch_run).
+
+    items: sequence of (Scene, Table or None, rays [n, 8] device tensor, mode).
+    Output tensors are allocated here and refilled by every run()."""
+
+    def __init__(self, items, stats: bool = False, block_threads: int = 0):
+        import torch
+        self.items = list(items)
+        self.hits = []
+        arr = (hrpp_batch_item * len(self.items))()
+        for k, (scene, table, rays, mode) in enumerate(self.items):
+            n = int(rays.shape[0])
+            if mode == HRPP_CLOSEST_HIT:
+                out = torch.empty((n, 4), dtype=torch.float32, device=rays.device)
+            else:
+                out = torch.empty((n,), dtype=torch.int32, device=rays.device)
+            self.hits.append(out)
+            arr[k] = hrpp_batch_item(scene.handle.value, table.handle.value if table is not None else None,
+                                     _ptr(rays), n, mode, _ptr(out))
+        h = ctypes.c_void_p()
+        check(hrpp_batch_create(arr, len(self.items), 1 if stats else 0, block_threads, ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None):
+        check(hrpp_batch_run(self.handle, _stream_handle(stream)))
+
+    def stats(self, k: int) -> dict:
+        st = hrpp_stats()
+        check(hrpp_batch_get_stats(self.handle, k, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hrpp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -27,7 +27,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import (ao_rays, build_bvh, icosphere, pinhole_rays, place_spheres, quad_grid, shadow_rays,
-               terrain)
+               soup, sphere_rays, terrain)
 
 
 @dataclass
@@ -86,3 +86,60 @@ def secondary_ao(scene: Scene, rays: np.ndarray, hit_t, hit_prim, frame: int = 0
     """Cosine-weighted ambient-occlusion rays from the hits of `rays`."""
     return ao_rays(rays, hit_t, hit_prim, scene.tris, per_hit=per_hit, tmax=tmax,
                    seed=scene.camera["seed"], frame=frame)
+
+
+# ------------------------------------------------------------ batched --
+
+def _camera_for(tris: np.ndarray):
+    v = tris.reshape(-1, 3)
+    lo, hi = v.min(0).astype(np.float64), v.max(0).astype(np.float64)
+    c = 0.5 * (lo + hi)
+    ext = float(np.max(hi - lo))
+    eye = c + ext * np.array([0.35, 0.9, -1.7])
+    return tuple(eye), tuple(c), lo, hi
+
+
+def batched_item(kind: str, n_tris: int, n_rays: int, seed: int, width: int = 4) -> tuple:
+    """One scene of the batched workload and its rays.
+
+    kind: 'terrain' (value-noise quad grid over [-1,1]^2, amplitude 0.16),
+    'spheres' (icospheres of 320 triangles, centres uniform in [0,1]^3), or
+    'soup' (uniform triangle soup in the unit cube).  Rays: half from a
+    pinhole camera outside the scene looking at its centre, half with origins
+    uniform in the scene's box and directions uniform on the sphere."""
+    rng = np.random.default_rng(seed)
+    if kind == "terrain":
+        q = max(2, int(round(np.sqrt(n_tris / 2))))
+        tris = terrain(q, q, -1.0, 1.0, -1.0, 1.0, seed, amp=0.16, freq=1.0 / 0.32)
+    elif kind == "spheres":
+        m = max(1, n_tris // 320)
+        r = 0.35 * m ** (-1.0 / 3.0)
+        cs = rng.uniform(r, 1 - r, (m, 3))
+        tris = np.concatenate([icosphere(2, tuple(c), r) for c in cs])
+    else:
+        tris = soup(n_tris, seed)
+    tris = np.ascontiguousarray(tris, np.float32)
+    nodes, prim, root = build_bvh(tris, width=width)
+    eye, tgt, lo, hi = _camera_for(tris)
+    n_cam = n_rays // 2
+    w = max(1, int(np.ceil(np.sqrt(n_cam * 16 / 9))))
+    h = max(1, int(np.ceil(n_cam / w)))
+    cam = pinhole_rays(eye, tgt, 60.0, w, h, seed=seed)[:n_cam]
+    rnd = sphere_rays(n_rays - n_cam, seed, float(lo.min()), float(hi.max()))
+    rays = np.ascontiguousarray(np.concatenate([cam, rnd]), np.float32)
+    s = Scene(f"{kind}{seed}", tris, nodes, prim, root, width,
+              dict(eye=eye, target=tgt, vfov=60.0, width=w, height=h, seed=seed))
+    return s, rays
+
+
+def batched_workload(n_scenes: int = 64, tris_range=(10_000, 2_000_000), rays_range=(4_096, 2_000_000),
+                     seed: int = 3, width: int = 4):
+    """The uneven batched workload: n_scenes scenes with log-uniform triangle
+    counts in tris_range (terrain, icosphere clusters and triangle soup in
+    turn) and log-uniform ray batch sizes in rays_range.  Yields (scene, rays)."""
+    rng = np.random.default_rng(seed)
+    kinds = ("terrain", "spheres", "soup")
+    for k in range(n_scenes):
+        nt = int(np.exp(rng.uniform(np.log(tris_range[0]), np.log(tris_range[1]))))
+        nr = int(np.exp(rng.uniform(np.log(rays_range[0]), np.log(rays_range[1]))))
+        yield batched_item(kinds[k % 3], nt, nr, seed * 1000 + k, width)
