@@ -63,3 +63,26 @@ def test_full_terrain_primary_and_ao(full):
     gc, _ = gpu_trace(H, g, ao[idx], O.CLOSEST_HIT)
     oc, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, ao[idx], O.CLOSEST_HIT)
     assert np.array_equal(as_words(gc), as_words(oc))
+
+
+def test_full_batched_workload_sampled():
+    """The 64-scene uneven batch at full size in one graph-replayed launch:
+    every item checked against the oracle on a random sample of its rays."""
+    import torch
+    H = hrpp_mod()
+    rng = np.random.default_rng(1)
+    items, data = [], []
+    for s, rays in W.batched_workload(n_scenes=64, seed=3):
+        g = H.Scene.from_workload(s)
+        d = torch.from_numpy(rays).cuda()
+        items.append((g, H.Table(16, 2, 6), d, H.HRPP_CLOSEST_HIT))
+        data.append((s, rays))
+    batch = H.Batch(items)
+    for _ in range(2):
+        batch.run()
+    torch.cuda.synchronize()
+    for k, (s, rays) in enumerate(data):
+        idx = np.sort(rng.choice(len(rays), min(len(rays), 300), replace=False))
+        oh, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays[idx], O.CLOSEST_HIT)
+        gh = batch.hits[k].cpu().numpy()[idx]
+        assert np.array_equal(as_words(gh), as_words(oh)), f"item {k}"
