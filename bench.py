@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="terrain", choices=["terrain", "batched"],
+    ap.add_argument("--workload", default="terrain", choices=["terrain", "batched", "pathtrace"],
                     help="terrain: the headline step; batched: the 64-scene uneven mix in one graph-replayed launch")
     ap.add_argument("--scenes", type=int, default=64)
     return ap.parse_args()
@@ -356,12 +356,91 @@ def run_batched(args):
     return 0
 
 
+def run_pathtrace(args):
+    """Config 5: 1280x720 x 4 spp x 5 diffuse bounces (+ one shadow ray per
+    bounce) on the 4.28M-triangle closed terrain, HRPP vs plain per bounce."""
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1910_01304_gb300 import hrpp as H
+    from paper_1910_01304_gb300.scenes import workloads as W
+    s = W.pathtrace_scene()
+    g = H.Scene.from_workload(s)
+
+    def gpu_closest(rays):
+        hits, _ = H.trace(g, torch.from_numpy(np.ascontiguousarray(rays)).cuda(), H.HRPP_CLOSEST_HIT)
+        h = hits.cpu().numpy()
+        return h[:, 0].copy(), h[:, 1].view(np.uint32).copy()
+
+    frames = []
+    for f in range(args.frames):
+        bs = W.path_bounces(s, W.path_primary(s, spp=4, frame=f), gpu_closest, bounces=5, frame=f)
+        frames.append([(torch.from_numpy(c).cuda(), torch.from_numpy(sh).cuda()) for c, sh in bs])
+    nb = len(frames[0])
+    stream = torch.cuda.current_stream()
+    tab_c = H.Table(args.log2_entries, args.ways, args.precision)
+    tab_a = H.Table(args.log2_entries, args.ways, args.precision)
+
+    def step(k, tables, ev=None):
+        for b, (c, sh) in enumerate(frames[k % len(frames)]):
+            H.trace(g, c, H.HRPP_CLOSEST_HIT, tables[0], kernel_events=ev[b][0] if ev else None)
+            H.trace(g, sh, H.HRPP_ANY_HIT, tables[1], kernel_events=ev[b][1] if ev else None)
+
+    def mk():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    out = {}
+    for name, tables in (("hrpp", (tab_c, tab_a)), ("plain", (None, None))):
+        for k in range(args.warmup):
+            step(k, tables)
+        evs = [[[(mk(), mk()), (mk(), mk())] for _ in range(nb)] for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        e0, e1 = mk(), mk()
+        e0.record(stream)
+        for k in range(args.steps):
+            step(args.warmup + k, tables, evs[k])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per_b = [[sum(evs[k][b][m][0].elapsed_time(evs[k][b][m][1]) for k in range(args.steps)) / args.steps
+                  for m in range(2)] for b in range(nb)]
+        out[name] = (e0.elapsed_time(e1) / args.steps, per_b)
+    rays_frame = sum(int(c.shape[0] + sh.shape[0]) for c, sh in frames[0])
+    per_bounce = []
+    for b, (c, sh) in enumerate(frames[0]):
+        _, sc = H.trace(g, c, H.HRPP_CLOSEST_HIT, tab_c, stats=True)
+        _, sa = H.trace(g, sh, H.HRPP_ANY_HIT, tab_a, stats=True)
+        hc, ha = out["hrpp"][1][b]
+        pc, pa = out["plain"][1][b]
+        per_bounce.append({"bounce": b, "closest_rays": int(c.shape[0]), "shadow_rays": int(sh.shape[0]),
+                           "closest_mrays": {"hrpp": c.shape[0] / hc / 1e3, "plain": c.shape[0] / pc / 1e3},
+                           "shadow_mrays": {"hrpp": sh.shape[0] / ha / 1e3, "plain": sh.shape[0] / pa / 1e3},
+                           "prediction_ratio": {"closest": sc["true_pos"] / sc["rays"], "any": sa["true_pos"] / sa["rays"]}})
+    line = {"metric": METRIC, "value": rays_frame / (out["hrpp"][0] * 1e-3) / 1e6, "unit": "Mrays/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["hrpp"][0], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"path tracing: {s.n_tris} tris (2048x1024-quad terrain, 256 icospheres, dome), "
+                                   "1280x720 x 4 spp x 5 diffuse bounces + 1 shadow ray per bounce",
+                       "rays_per_step": rays_frame, "frames": args.frames,
+                       "table": {"log2_entries": args.log2_entries, "ways": args.ways, "precision": args.precision}},
+            "plain": {"value": rays_frame / (out["plain"][0] * 1e-3) / 1e6, "ms_per_step": out["plain"][0],
+                      "speedup_hrpp_over_plain": out["plain"][0] / out["hrpp"][0]},
+            "per_bounce": per_bounce, "gpu_launches": 4 * nb * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "pathtrace":
+        return run_pathtrace(args)
     rank, world, local = dist_env()
     import torch
     if not torch.cuda.is_available():

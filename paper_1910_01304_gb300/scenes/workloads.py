@@ -143,3 +143,60 @@ def batched_workload(n_scenes: int = 64, tris_range=(10_000, 2_000_000), rays_ra
         nt = int(np.exp(rng.uniform(np.log(tris_range[0]), np.log(tris_range[1]))))
         nr = int(np.exp(rng.uniform(np.log(rays_range[0]), np.log(rays_range[1]))))
         yield batched_item(kinds[k % 3], nt, nr, seed * 1000 + k, width)
+
+
+# ------------------------------------------------------- path tracing --
+
+PATH_LIGHT = (30.0, 80.0, -40.0)
+
+
+def pathtrace_scene(quads=(2048, 1024), n_spheres: int = 256, subdiv: int = 2, width: int = 4, seed: int = 5,
+                    res=(1280, 720), dome_subdiv: int = 4, dome_radius: float = 160.0) -> Scene:
+    """Incoherent path-tracing scene: a value-noise terrain of quads[0] x
+    quads[1] quads over [-100,100] x [-50,50] (4 octaves, amplitude 8, base
+    frequency 1/16) with n_spheres icospheres (subdiv x subdivided, radius
+    log-uniform in [0.1, 2]) resting on it, closed by a dome (an icosphere of
+    radius dome_radius about the origin) so that no path escapes and every
+    path runs all its bounces.  At the defaults: 4,194,304 + 81,920 + 5,120
+    = 4,281,344 triangles."""
+    nx, nz = quads
+    ground = terrain(nx, nz, -100.0, 100.0, -50.0, 50.0, seed)
+    parts = [ground]
+    if dome_subdiv >= 0:
+        parts.append(icosphere(dome_subdiv, (0.0, 0.0, 0.0), dome_radius))
+    if n_spheres:
+        sp = place_spheres(n_spheres, seed, 0.1, 2.0, -100.0, 100.0, -50.0, 50.0, seed)
+        for cx, cy, cz, r in sp:
+            parts.append(icosphere(subdiv, (float(cx), float(cy), float(cz)), float(r)))
+    tris = np.ascontiguousarray(np.concatenate(parts), np.float32)
+    nodes, prim, root = build_bvh(tris, width=width)
+    cam = dict(eye=(0.0, 30.0, -90.0), target=(0.0, 0.0, 0.0), vfov=60.0, width=res[0], height=res[1], seed=seed)
+    return Scene("pathtrace", tris, nodes, prim, root, width, cam)
+
+
+def path_primary(scene: Scene, spp: int = 4, frame: int = 0) -> np.ndarray:
+    """spp jittered samples per pixel: spp pinhole images concatenated."""
+    return np.ascontiguousarray(np.concatenate([scene.primary_rays(frame=1 + spp * frame + k) for k in range(spp)]))
+
+
+def path_bounces(scene: Scene, primary: np.ndarray, trace_closest, bounces: int = 5, light=PATH_LIGHT,
+                 frame: int = 0):
+    """Rays of a diffuse path tracer, bounce by bounce.
+
+    trace_closest(rays) -> (t float32[n], prim uint32[n]) is the caller's
+    closest-hit tracer (the oracle in tests, the library in benchmarks).
+    Bounce b traces its closest-hit rays; each hit spawns one shadow ray
+    toward the point light (any-hit) and one cosine-weighted diffuse ray
+    (the next bounce).  Returns [(closest_rays_b, shadow_rays_b)]."""
+    out = []
+    rays = primary
+    for b in range(bounces):
+        t, p = trace_closest(rays)
+        shadow, _ = shadow_rays(rays, t, p, scene.tris, light)
+        out.append((rays, shadow))
+        if b + 1 < bounces:
+            rays, _ = ao_rays(rays, t, p, scene.tris, per_hit=1, tmax=float("inf"),
+                              seed=scene.camera["seed"] + 7919 * (b + 1), frame=frame)
+            if len(rays) == 0:
+                break
+    return out
