@@ -299,6 +299,15 @@ hrpp_status hrpp_batch_run(hrpp_batch *batch, void *stream);
 hrpp_status hrpp_batch_get_stats(hrpp_batch *batch, uint32_t item, hrpp_stats *host_stats);
 void hrpp_batch_destroy(hrpp_batch *batch);
 
+/* Utility (no counterpart in the paper; the learned treelet proposal's
+ * building block, exposed for testing): C[m, n] = A[m, k] * B[n, k]^T on the
+ * tensor cores (tcgen05.mma, fp32 accumulation in tensor memory, operands
+ * loaded by TMA).  A, B: bf16, row-major with k contiguous (K-major), device
+ * memory, 16-byte aligned; C: fp32 row-major [m, n], device memory.  m and n
+ * must be multiples of 128 and k of 64 (INVALID_ARG otherwise).  Waits for
+ * the result. */
+hrpp_status hrpp_gemm_bf16(const void *a, const void *b, float *c, int m, int n, int k, void *stream);
+
 const char *hrpp_last_error(void);
 const char *hrpp_status_string(hrpp_status status);
 int hrpp_version(void);

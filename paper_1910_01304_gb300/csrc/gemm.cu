@@ -1,0 +1,138 @@
+// Host launchers of the tcgen05 GEMM (umma.cuh): TMA tensor maps, tile and
+// split choices, and the utility entry point hrpp_gemm_bf16.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+
+#include "gemm.h"
+#include "handles.h"
+#include "hrpp.h"
+#include "umma.cuh"
+
+namespace hrpp {
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::mutex g_encode_mutex;
+
+cudaError_t encoder(PFN_cuTensorMapEncodeTiled_v12000 *out)
+{
+    std::lock_guard<std::mutex> lk(g_encode_mutex);
+    if (!g_encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    *out = g_encode;
+    return cudaSuccess;
+}
+
+// K-major bf16 matrix [rows, k] as a TMA map with 64 x box_rows boxes and
+// 128-byte swizzle (the layout the tcgen05 shared-memory descriptor expects).
+cudaError_t make_map(CUtensorMap *map, const void *ptr, uint64_t rows, uint64_t k, uint32_t box_rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 encode;
+    cudaError_t e = encoder(&encode);
+    if (e != cudaSuccess) return e;
+    cuuint64_t dims[2] = {k, rows};
+    cuuint64_t strides[1] = {k * 2};
+    cuuint32_t box[2] = {(cuuint32_t)umma::BK, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int BN, int EPI>
+cudaError_t launch(const void *a, const void *b, const umma::GemmArgs &g, int splits, cudaStream_t s)
+{
+    static bool configured = false;  // per template instance; attribute setting is idempotent
+    const size_t smem = umma::gemm_smem_bytes<BN>();
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(umma::k_gemm<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    CUtensorMap ma, mb;
+    cudaError_t e = make_map(&ma, a, (uint64_t)g.M, (uint64_t)g.K, umma::BM);
+    if (e == cudaSuccess) e = make_map(&mb, b, (uint64_t)g.N, (uint64_t)g.K, BN);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)(g.N / BN), (unsigned)(g.M / umma::BM), (unsigned)splits);
+    umma::k_gemm<BN, EPI><<<grid, 128, smem, s>>>(ma, mb, g);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool gemm_shape_ok(int m, int n, int k, int bn)
+{
+    return m > 0 && n > 0 && k > 0 && m % umma::BM == 0 && n % bn == 0 && k % umma::BK == 0;
+}
+
+cudaError_t gemm_bf16(const void *a, const void *b, int epi, int bn, const umma::GemmArgs &g0, int splits,
+                      cudaStream_t s)
+{
+    umma::GemmArgs g = g0;
+    const int kb = g.K / umma::BK;
+    if (splits < 1) splits = 1;
+    if (splits > kb) splits = kb;
+    g.k_blocks_per_split = (kb + splits - 1) / splits;
+    splits = (kb + g.k_blocks_per_split - 1) / g.k_blocks_per_split;
+    if (((uintptr_t)a & 15u) || ((uintptr_t)b & 15u)) return cudaErrorInvalidValue;
+#define HRPP_GEMM_CASE(BN_, EPI_) \
+    if (bn == BN_ && epi == EPI_) return launch<BN_, EPI_>(a, b, g, splits, s);
+    HRPP_GEMM_CASE(128, umma::EPI_F32)
+    HRPP_GEMM_CASE(256, umma::EPI_F32)
+    HRPP_GEMM_CASE(128, umma::EPI_F32_ATOMIC)
+    HRPP_GEMM_CASE(256, umma::EPI_F32_ATOMIC)
+    HRPP_GEMM_CASE(256, umma::EPI_BIAS_RELU)
+    HRPP_GEMM_CASE(256, umma::EPI_RELU_GRAD)
+    HRPP_GEMM_CASE(256, umma::EPI_ARGMAX)
+#undef HRPP_GEMM_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace hrpp
+
+extern "C" hrpp_status hrpp_gemm_bf16(const void *a, const void *b, float *c, int m, int n, int k, void *stream)
+{
+    char msg[160];
+    if (!a || !b || !c) return hrpp::report(HRPP_ERR_INVALID_ARG, "NULL matrix");
+    const int bn = (n % 256 == 0) ? 256 : 128;
+    if (!hrpp::gemm_shape_ok(m, n, k, bn)) {
+        snprintf(msg, sizeof msg, "shape %d x %d x %d: M must be a multiple of 128, N of 128, K of 64", m, n, k);
+        return hrpp::report(HRPP_ERR_INVALID_ARG, msg);
+    }
+    unsigned int *err = nullptr;
+    cudaError_t e = cudaMalloc(&err, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(unsigned int), (cudaStream_t)stream);
+    if (e == cudaSuccess) {
+        hrpp::umma::GemmArgs g = {};
+        g.M = m;
+        g.N = n;
+        g.K = k;
+        g.c32 = c;
+        g.m_valid = m;
+        g.error = err;
+        e = hrpp::gemm_bf16(a, b, hrpp::umma::EPI_F32, bn, g, 1, (cudaStream_t)stream);
+    }
+    unsigned int flag = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, err, sizeof flag, cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess) {
+        snprintf(msg, sizeof msg, "gemm: %s", cudaGetErrorString(e));
+        return hrpp::report(HRPP_ERR_CUDA, msg);
+    }
+    if (flag) return hrpp::report(HRPP_ERR_CUDA, "gemm: a pipeline wait timed out");
+    return HRPP_OK;
+}

@@ -1,0 +1,14 @@
+// Internal interface of the tcgen05 GEMM launchers (gemm.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "umma.cuh"
+
+namespace hrpp {
+bool gemm_shape_ok(int m, int n, int k, int bn);
+// C = A[M, K] * B[N, K]^T with the given epilogue (umma::Epilogue) and tile
+// width bn (128 or 256); splits > 1 divides K across CTAs (EPI_F32_ATOMIC).
+cudaError_t gemm_bf16(const void *a, const void *b, int epi, int bn, const umma::GemmArgs &g, int splits,
+                      cudaStream_t s);
+}  // namespace hrpp

@@ -1,0 +1,299 @@
+// Tensor-core GEMM for sm_103a: tcgen05.mma with the accumulator in tensor
+// memory (TMEM), operands staged in shared memory by TMA.
+//
+//   C[M, N] = A[M, K] * B[N, K]^T        A, B: bf16, K-major (rows of K)
+//                                         accumulation: fp32 in TMEM
+//
+// One CTA computes a 128 x BN tile of C (BN = 128 or 256) over a K range:
+//   warp 0 lane 0   TMA producer: per 64-wide K block, one 128 x 64 A tile
+//                   and one BN x 64 B tile (128-byte swizzle) into a 4-stage
+//                   ring guarded by full/empty mbarriers
+//   warp 1 lane 0   MMA issuer: 4 x tcgen05.mma (K = 16 each) per K block,
+//                   tcgen05.commit frees the stage; a last commit signals the
+//                   accumulator
+//   warps 0-3       epilogue: thread t of warp w owns row 32w + t, reads its
+//                   TMEM lane 16 columns at a time (tcgen05.ld 32x32b.x16)
+// Every mbarrier wait is bounded; a wait that gives up sets an error flag,
+// the kernel drains its outstanding copies (bounded again), frees its TMEM
+// and returns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace hrpp {
+namespace umma {
+
+constexpr int BM = 128;
+constexpr int BK = 64;  // bf16 elements per 128-byte swizzle row
+constexpr int STAGES = 4;
+constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait rounds before giving up
+
+enum Epilogue : int {
+    EPI_F32 = 0,        // C (+ bias per column) -> fp32 row-major
+    EPI_F32_ATOMIC = 1, // split-K: atomicAdd into fp32 row-major
+    EPI_BIAS_RELU = 2,  // relu(C + bias) -> bf16 row-major and bf16 transposed
+    EPI_RELU_GRAD = 3,  // C * (act > 0) -> bf16 row-major and bf16 transposed
+    EPI_ARGMAX = 4      // per row: max over columns of C + bias -> packed atomicMax
+};
+
+struct GemmArgs {
+    int M, N, K;             // full problem (M, N multiples of 128/BN; K of 64)
+    int k_blocks_per_split;  // K blocks handled by one CTA (gridDim.z splits)
+    float *c32;              // EPI_F32 / EPI_F32_ATOMIC output [M, N]
+    __nv_bfloat16 *c16;      // bf16 output [M, N] (may be null)
+    __nv_bfloat16 *c16t;     // bf16 transposed output [N, M] (may be null)
+    const float *bias;       // per column (may be null)
+    const __nv_bfloat16 *act;   // EPI_RELU_GRAD: activation [M, N] whose > 0 mask is applied
+    unsigned long long *argmax; // EPI_ARGMAX: per row (ordered max << 32) | ~column
+    int m_valid;             // rows >= m_valid are padding: not written (argmax / stores)
+    unsigned int *error;     // set to 1 when a bounded wait gives up
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// true once the phase with the given parity has completed; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t addr = smem_u32(bar);
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row core groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)(16u >> 4) << 16;           // leading byte offset (unused when swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;         // stride byte offset between 8-row groups
+    d |= (uint64_t)1u << 46;                   // descriptor version
+    d |= (uint64_t)2u << 61;                   // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, both
+// K-major, M x N tile.
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t ordered_f32(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+template <int BN>
+constexpr size_t gemm_smem_bytes()
+{
+    return (size_t)STAGES * ((size_t)BM * BK * 2 + (size_t)BN * BK * 2) + 1024;
+}
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtensorMap tma_a,
+                                                 const __grid_constant__ CUtensorMap tma_b, const GemmArgs g)
+{
+    static_assert(BN == 128 || BN == 256, "tile width");
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accum_bar;
+    __shared__ uint32_t tmem_base;
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr uint32_t kABytes = BM * BK * 2, kBBytes = BN * BK * 2;
+    unsigned char *a_s = smem;
+    unsigned char *b_s = smem + STAGES * kABytes;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kb0 = blockIdx.z * g.k_blocks_per_split;
+    int kb_end = kb0 + g.k_blocks_per_split;
+    if (kb_end > g.K / BK) kb_end = g.K / BK;
+    const int n_kb = kb_end > kb0 ? kb_end - kb0 : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&accum_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"((uint32_t)BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    bool failed = false;
+    int issued = 0;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int i = 0; i < n_kb; ++i) {
+            const int s = i % STAGES;
+            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+            if (!mbar_wait(&empty_bar[s], ph ^ 1u)) {
+                failed = true;
+                break;
+            }
+            mbar_expect_tx(&full_bar[s], kABytes + kBBytes);
+            tma_load_2d(a_s + s * kABytes, &tma_a, (kb0 + i) * BK, m0, &full_bar[s]);
+            tma_load_2d(b_s + s * kBBytes, &tma_b, (kb0 + i) * BK, n0, &full_bar[s]);
+            ++issued;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = instr_desc(BM, BN);
+        for (int i = 0; i < n_kb; ++i) {
+            const int s = i % STAGES;
+            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+            if (!mbar_wait(&full_bar[s], ph)) {
+                failed = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(a_s + s * kABytes), b0 = smem_u32(b_s + s * kBBytes);
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k)
+                mma_bf16(tmem, smem_desc(a0 + 32u * k), smem_desc(b0 + 32u * k), idesc, (i > 0 || k > 0) ? 1u : 0u);
+            mma_commit(&empty_bar[s]);
+        }
+        // tracks every MMA issued above, even after a timeout
+        mma_commit(&accum_bar);
+    }
+    __syncwarp();
+
+    // epilogue
+    bool ready = n_kb > 0 && mbar_wait(&accum_bar, 0);
+    if (!ready && n_kb > 0) failed = true;
+    // tcgen05.ld is warp-collective: a warp reads TMEM only if all its lanes may
+    ready = __all_sync(0xFFFFFFFFu, ready);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int row = m0 + warp * 32 + lane;
+    if (ready) {
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        float best = -__int_as_float(0x7F800000);
+        int best_col = 0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tmem_ld16(taddr + (uint32_t)c0, v);
+            const int col0 = n0 + c0;
+            if (row >= g.m_valid) continue;
+            if (EPI == EPI_F32 || EPI == EPI_F32_ATOMIC) {
+                float *dst = g.c32 + (size_t)row * g.N + col0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float x = v[j] + (g.bias ? g.bias[col0 + j] : 0.0f);
+                    if (EPI == EPI_F32) dst[j] = x;
+                    else atomicAdd(dst + j, x);
+                }
+            } else if (EPI == EPI_BIAS_RELU || EPI == EPI_RELU_GRAD) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float x;
+                    if (EPI == EPI_BIAS_RELU) x = fmaxf(v[j] + (g.bias ? g.bias[col0 + j] : 0.0f), 0.0f);
+                    else x = __bfloat162float(g.act[(size_t)row * g.N + col0 + j]) > 0.0f ? v[j] : 0.0f;
+                    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                    if (g.c16) g.c16[(size_t)row * g.N + col0 + j] = h;
+                    if (g.c16t) g.c16t[(size_t)(col0 + j) * g.M + row] = h;
+                }
+            } else if (EPI == EPI_ARGMAX) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float x = v[j] + (g.bias ? g.bias[col0 + j] : 0.0f);
+                    if (x > best) {
+                        best = x;
+                        best_col = col0 + j;
+                    }
+                }
+            }
+        }
+        if (EPI == EPI_ARGMAX && row < g.m_valid) {
+            const unsigned long long key =
+                ((unsigned long long)ordered_f32(best) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)best_col);
+            atomicMax(g.argmax + row, key);
+        }
+    }
+    if (failed && g.error) atomicExch(g.error, 1u);
+    // a producer that gave up may still have copies in flight: wait for them
+    if (warp == 0 && lane == 0 && failed) {
+        for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; ++i)
+            mbar_wait(&full_bar[i % STAGES], (uint32_t)(i / STAGES) & 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+}
+
+}  // namespace umma
+}  // namespace hrpp

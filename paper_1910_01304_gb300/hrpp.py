@@ -88,6 +88,7 @@ def _load():
         "hrpp_batch_run": (st, [P, P]),
         "hrpp_batch_get_stats": (st, [P, u32, P]),
         "hrpp_batch_destroy": (None, [P]),
+        "hrpp_gemm_bf16": (st, [P, P, P, i32, i32, i32, P]),
         "hrpp_last_error": (ctypes.c_char_p, []),
         "hrpp_status_string": (ctypes.c_char_p, [st]),
         "hrpp_version": (i32, []),
@@ -123,6 +124,7 @@ hrpp_batch_create = _lib.hrpp_batch_create
 hrpp_batch_run = _lib.hrpp_batch_run
 hrpp_batch_get_stats = _lib.hrpp_batch_get_stats
 hrpp_batch_destroy = _lib.hrpp_batch_destroy
+hrpp_gemm_bf16 = _lib.hrpp_gemm_bf16
 hrpp_last_error = _lib.hrpp_last_error
 hrpp_status_string = _lib.hrpp_status_string
 hrpp_version = _lib.hrpp_version
