@@ -149,10 +149,14 @@ typedef struct hrpp_scene_info {
 #define HRPP_SCHEDULE_REFILL 2u
 typedef struct hrpp_trace_opts {
     void *kernel_start, *kernel_stop;
+    const int32_t *predicted_nodes;  /* device, one canonical node index per ray
+                                        (-1 = none), e.g. from
+                                        hrpp_proposal_predict: the ray
+                                        traverses that node's subtree first */
     uint32_t block_threads;
     uint32_t schedule;
     uint32_t refill_min;
-    uint32_t reserved[5];
+    uint32_t reserved[3];
 } hrpp_trace_opts;
 
 typedef struct hrpp_scene hrpp_scene;
@@ -298,6 +302,60 @@ hrpp_status hrpp_batch_run(hrpp_batch *batch, void *stream);
 /* Waits for the batch's last run and copies item `item`'s counters. */
 hrpp_status hrpp_batch_get_stats(hrpp_batch *batch, uint32_t item, hrpp_stats *host_stats);
 void hrpp_batch_destroy(hrpp_batch *batch);
+
+/* Learned treelet proposal (BASELINE's learned-proposal extension; no
+ * counterpart in the paper, whose predictor is the hash table).  A small
+ * BF16 MLP, 96 -> 256 -> 256 -> 4096 with ReLU and fp32 accumulation on the
+ * tensor cores, predicts for each ray a BVH treelet: one of 4096 classes,
+ * each a 12-bit path code from the root (BVH2: one child-slot bit per level;
+ * BVH4: two bits per level), whose root is the deepest node that code
+ * reaches.  A ray traverses its predicted treelet first (hrpp_trace_opts
+ * predicted_nodes), so an any-hit ray answered there skips the rest, and
+ * then traverses from the root exactly as without a prediction.
+ * Inputs (96): the origin quantised to 16 bits per axis within the root
+ * box, the octahedral-encoded direction quantised to 16 bits per component,
+ * those 5 values as bf16(q / 32768 - 1), their Fourier terms
+ * sin/cos(2 pi ((q << k) mod 2^16) / 2^16) for k = 0..8 from a bf16 sine
+ * table, and a constant 1.  Training minimises the mean softmax
+ * cross-entropy against the class of the leaf holding each ray's closest
+ * hit (Adam, fp32 master weights). */
+#define HRPP_PROPOSAL_FEATURES 96
+#define HRPP_PROPOSAL_HIDDEN 256
+#define HRPP_PROPOSAL_CLASSES 4096
+/* weights as floats: W1 [256][96], b1 [256], W2 [256][256], b2 [256],
+ * W3 [4096][256], b3 [4096] */
+#define HRPP_PROPOSAL_PARAMS (256u * 96u + 256u + 256u * 256u + 256u + 4096u * 256u + 4096u)
+typedef struct hrpp_proposal hrpp_proposal;
+/* Makes a proposal network for `scene`, whose canonical BVH (as given to
+ * hrpp_scene_create) defines the classes; weights drawn from `seed`
+ * (He-uniform weights, zero biases).  Blocking. */
+hrpp_status hrpp_proposal_create(const hrpp_scene *scene, const hrpp_bvh_node *nodes, uint32_t n_nodes, uint32_t root,
+                                 const uint32_t *prim_index, uint32_t n_prim_index, uint64_t seed,
+                                 hrpp_proposal **out);
+/* Network inputs of n rays: bf16 [n][128] (96 features, 32 zeros), device. */
+hrpp_status hrpp_proposal_features(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, void *out_bf16, void *stream);
+/* Training labels from closest-hit results (device): the class of the leaf
+ * holding each hit's triangle, -1 for a miss. */
+hrpp_status hrpp_proposal_labels(hrpp_proposal *p, const hrpp_hit *hits, uint32_t n, int32_t *out_labels,
+                                 void *stream);
+/* One Adam step per minibatch of up to 8192 rays (device rays and labels;
+ * label -1 = no target).  *out_mean_loss (host, may be NULL) receives the
+ * mean loss of the last minibatch (the call then waits). */
+hrpp_status hrpp_proposal_train(hrpp_proposal *p, const hrpp_ray *rays, const int32_t *labels, uint32_t n, float lr,
+                                float *out_mean_loss, void *stream);
+/* Loss and gradients of one batch (n <= 8192) without updating: host_grads
+ * receives HRPP_PROPOSAL_PARAMS floats in the weight layout above.  Waits. */
+hrpp_status hrpp_proposal_gradients(hrpp_proposal *p, const hrpp_ray *rays, const int32_t *labels, uint32_t n,
+                                    float *host_grads, float *out_mean_loss);
+/* Predicted treelet root (canonical node index) and class per ray, device
+ * outputs (out_classes may be NULL). */
+hrpp_status hrpp_proposal_predict(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, int32_t *out_nodes,
+                                  int32_t *out_classes, void *stream);
+hrpp_status hrpp_proposal_get_weights(const hrpp_proposal *p, float *host, size_t n_floats);
+hrpp_status hrpp_proposal_set_weights(hrpp_proposal *p, const float *host, size_t n_floats);
+/* Class -> treelet root (canonical node) table, 4096 entries, host. */
+hrpp_status hrpp_proposal_class_nodes(const hrpp_proposal *p, int32_t *host_nodes);
+void hrpp_proposal_destroy(hrpp_proposal *p);
 
 /* Utility (no counterpart in the paper; the learned treelet proposal's
  * building block, exposed for testing): C[m, n] = A[m, k] * B[n, k]^T on the

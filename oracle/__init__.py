@@ -71,7 +71,7 @@ def _L():
                 "orc_ray_inverse": (None, [P, P, P]),
                 "orc_ray_box": (i32, [P, P, f32, f32, P, P, P]),
                 "orc_brute": (None, [P, u32, P, u32, i32, P, P]),
-                "orc_trace": (i32, [ctypes.POINTER(_Scene), P, u32, i32, ctypes.POINTER(_Table), P, P, P, P]),
+                "orc_trace": (i32, [ctypes.POINTER(_Scene), P, u32, i32, ctypes.POINTER(_Table), P, P, P, P, P]),
                 "orc_unbounded_size": (None, [ctypes.POINTER(_Table), P, P]),
                 "orc_unbounded_free": (None, [ctypes.POINTER(_Table)]),
             }
@@ -205,8 +205,11 @@ class Table:
 
 # ---------------------------------------------------------------- trace --
 
-def trace(tris, nodes, prim_index, root, rays, mode: int, table: Table | None = None, per_ray: bool = False):
+def trace(tris, nodes, prim_index, root, rays, mode: int, table: Table | None = None, per_ray: bool = False,
+          predicted=None):
     """Plain traversal (table None) or HRPP against `table` (mutated).
+    predicted: optional int32 [n] canonical node per ray whose subtree is
+    traversed first (learned proposal; -1 = none).
 
     Returns (hits, stats dict[, outcome uint8[n], box_tests uint32[n]])."""
     tris = _f(tris).reshape(-1, 9)
@@ -222,7 +225,9 @@ def trace(tris, nodes, prim_index, root, rays, mode: int, table: Table | None = 
     outcome = np.zeros(n, np.uint8) if per_ray else None
     boxes = np.zeros(n, np.uint32) if per_ray else None
     tptr = ctypes.byref(table._c) if table is not None else None
-    rc = _L().orc_trace(ctypes.byref(sc), _p(rays), n, mode, tptr, _p(out), _p(stats), _p(outcome), _p(boxes))
+    pred = None if predicted is None else np.ascontiguousarray(predicted, np.int32)
+    rc = _L().orc_trace(ctypes.byref(sc), _p(rays), n, mode, tptr, _p(out), _p(stats), _p(outcome), _p(boxes),
+                        _p(pred))
     if rc != 0:
         raise RuntimeError("orc_trace failed")
     sd = {k: int(stats[i]) for i, k in enumerate(STAT_NAMES)}

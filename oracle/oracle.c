@@ -553,7 +553,7 @@ static const orc_node *find_leaf(const orc_scene *sc, uint32_t leaf)
  * each ray's traversal made.  Returns 0, or 1 on bad arguments / no memory.
  */
 int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode, orc_table *tab, void *out,
-              uint64_t *stats, uint8_t *outcome, uint32_t *ray_box_tests)
+              uint64_t *stats, uint8_t *outcome, uint32_t *ray_box_tests, const int32_t *predicted)
 {
     if (!sc || (!rays && n_rays) || (!out && n_rays) || !stats) return 1;
     workspace ws;
@@ -586,10 +586,27 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
         uint32_t n_cand = 0;
         uint64_t set = 0, tag = 0;
         uint64_t key = 0;
-        if (tab) {
+        int learned_positive = 0;
+        if (predicted) {
+            /* a predicted treelet (learned proposal): traverse the subtree of
+             * the given node first, when it is a node of the tree */
+            int32_t c = predicted[i];
+            int reachable = 0;
+            if (c >= 0 && (uint32_t)c < sc->n_nodes) {
+                const orc_node *pn = &sc->nodes[c];
+                reachable = pn->count > 0 ? (pn->first < sc->n_prim_index && ti.leaf_at[pn->first] == c)
+                                          : ti.rank[c] >= 0;
+            }
+            if (reachable) {
+                learned_positive = 1;
+                traverse_from(sc, (uint32_t)c, ray, mode, &b, &ws, stats, PRED_COUNTERS, NULL);
+            }
+        }
+        if (tab || predicted) {
             stats[S_LOOKUPS] += 1;
-            key = orc_ray_key(ray, tab->precision);
-            if (bounded) {
+            if (!tab) {
+                /* learned proposal only */
+            } else if ((key = orc_ray_key(ray, tab->precision)), bounded) {
                 uint64_t m = orc_mix48(key);
                 set = m & ((1ull << tab->log2_sets) - 1ull);
                 tag = (m >> tab->log2_sets) & ((1ull << TAG_BITS) - 1ull);
@@ -605,12 +622,12 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
                     n_cand = e->n;
                 }
             }
-            if (n_cand == 0) {
+            if (n_cand == 0 && !learned_positive) {
                 oc = OUT_NEGATIVE;
                 stats[S_NEGATIVES] += 1;
             } else {
                 stats[S_POSITIVES] += 1;
-                int answered = 0;
+                int answered = mode == ORC_ANY && b.found;
                 for (uint32_t k = 0; k < n_cand && !answered; ++k) {
                     if (go_up == 0) {
                         const orc_node *lf = find_leaf(sc, cand[k]);

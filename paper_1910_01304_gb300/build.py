@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhrpp.so")
-SOURCES = ["api.cu", "trace_bvh2.cu", "trace_bvh4.cu", "table.cu", "noalloc.cu", "batch.cu", "gemm.cu"]
+SOURCES = ["api.cu", "trace_bvh2.cu", "trace_bvh4.cu", "table.cu", "noalloc.cu", "batch.cu", "gemm.cu", "proposal.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -282,6 +282,15 @@ hrpp_status hrpp_scene_create(const float *tri_verts, uint32_t n_tris, const hrp
             d[7] = make_float4(0, 0, 0, 0);
         }
     }
+    // canonical node -> device ref, for per-ray predicted nodes
+    std::vector<int32_t> h_canon(n_nodes, kEmptyRef);
+    for (uint32_t k = 0; k < v.order.size(); ++k) {
+        const hrpp_bvh_node &n = nodes[v.order[k]];
+        h_canon[v.order[k]] = (int32_t)k;
+        for (int q = 0; q < 4; ++q)
+            if (n.child[q] != -1 && nodes[n.child[q]].count > 0) h_canon[n.child[q]] = (int32_t)~leaf_id(nodes[n.child[q]]);
+    }
+    if (nodes[root].count > 0) h_canon[root] = (int32_t)~leaf_id(nodes[root]);
     // parent links for the Go Up Level (Sec. 6.2): interior node -> parent,
     // and a leaf's first prim_index slot -> the leaf's parent (-1 at the root)
     std::vector<int32_t> h_parent(std::max<size_t>(1, v.order.size()), -1), h_leaf_parent(n_tris, -1);
@@ -322,10 +331,14 @@ hrpp_status hrpp_scene_create(const float *tri_verts, uint32_t n_tris, const hrp
     sc->root_ref = nodes[root].count > 0 ? (int32_t)~leaf_id(nodes[root]) : 0;
     const size_t nb = h_nodes.size() * sizeof(float4), tb = h_tris.size() * sizeof(float4);
     const size_t pb = h_parent.size() * sizeof(int32_t), lb = h_leaf_parent.size() * sizeof(int32_t);
-    sc->bytes = nb + tb + pb + lb + sizeof(uint32_t);
+    const size_t cb = h_canon.size() * sizeof(int32_t);
+    sc->n_nodes = n_nodes;
+    sc->bytes = nb + tb + pb + lb + cb + sizeof(uint32_t);
     if ((e = cudaMalloc(&sc->d_nodes, nb)) != cudaSuccess || (e = cudaMalloc(&sc->d_tris, tb)) != cudaSuccess ||
         (e = cudaMalloc(&sc->d_error, sizeof(uint32_t))) != cudaSuccess ||
         (e = cudaMalloc(&sc->d_parent, pb)) != cudaSuccess || (e = cudaMalloc(&sc->d_leaf_parent, lb)) != cudaSuccess ||
+        (e = cudaMalloc(&sc->d_canon_ref, cb)) != cudaSuccess ||
+        (e = cudaMemcpy(sc->d_canon_ref, h_canon.data(), cb, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(sc->d_nodes, h_nodes.data(), nb, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(sc->d_tris, h_tris.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(sc->d_parent, h_parent.data(), pb, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -379,6 +392,7 @@ void hrpp_scene_destroy(hrpp_scene *sc)
     cudaFree(sc->d_error);
     cudaFree(sc->d_parent);
     cudaFree(sc->d_leaf_parent);
+    cudaFree(sc->d_canon_ref);
     delete sc;
 }
 
@@ -603,6 +617,9 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         p.n_interior = sc->n_interior;
         p.parent = sc->d_parent;
         p.leaf_parent = sc->d_leaf_parent;
+        p.canon_ref = sc->d_canon_ref;
+        p.n_nodes = sc->n_nodes;
+        p.predicted = opts ? opts->predicted_nodes : nullptr;
         if (table) {
             p.table = table->d_words;
             p.winner = table->d_winner;

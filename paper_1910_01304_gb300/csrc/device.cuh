@@ -69,6 +69,9 @@ struct TraceParams {
     const int32_t *parent;       // interior node -> parent (-1 at the root)
     const int32_t *leaf_parent;  // leaf's first prim_index slot -> parent (-1: root leaf)
     int closest;                 // batched launches: this item's query mode
+    const int32_t *predicted;    // per ray: canonical node whose subtree is traversed first (-1: none)
+    const int32_t *canon_ref;    // canonical node -> device ref
+    uint32_t n_nodes;            // canonical node count
 };
 
 // ---------------------------------------------------------------- hashing --

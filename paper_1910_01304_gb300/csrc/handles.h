@@ -19,6 +19,8 @@ struct hrpp_scene {
     uint32_t *d_error;
     int32_t *d_parent;       // per interior node (preorder index): its parent, -1 at the root
     int32_t *d_leaf_parent;  // per prim_index slot starting a leaf: the leaf's parent, else -1
+    int32_t *d_canon_ref;    // per canonical node: its device ref (interior index or ~leaf), or empty
+    uint32_t n_nodes;        // canonical node count
     uint64_t bytes;
 };
 

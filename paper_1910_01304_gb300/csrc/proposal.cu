@@ -1,0 +1,702 @@
+// Learned treelet proposal: a BF16 MLP 96 -> 256 -> 256 -> 4096 trained and
+// evaluated on the tensor cores (tcgen05 GEMMs of gemm.cu), predicting per
+// ray the root of a BVH treelet to traverse first.
+//
+// Training step on a minibatch of rows padded to a multiple of 128:
+//   X  = features(rays)                      bf16 [B, 128] and [128, B]
+//   H1 = relu(X W1^T + b1), H2 = relu(H1 W2^T + b2)   bf16, both layouts
+//   Z  = H2 W3^T + b3                        fp32 [B, 4096]
+//   dZ = softmax(Z) - onehot(label)          bf16 [B, 4096] and [4096, B]
+//   dW3 = dZ^T H2, dZ2 = (dZ W3) * (H2 > 0), dW2 = dZ2^T H1,
+//   dZ1 = (dZ2 W2) * (H1 > 0), dW1 = dZ1^T X, db = column sums
+//   Adam on fp32 master weights, scaled by 1 / (labelled rows); bf16 copies
+//   refreshed in the [out, in] and [in, out] layouts the GEMMs read.
+// Every GEMM is C = A B^T with K-major operands, so activations and
+// gradients are written in both layouts by the producing epilogue.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "device.cuh"
+#include "gemm.h"
+#include "handles.h"
+#include "hrpp.h"
+
+using namespace hrpp;
+
+namespace {
+
+constexpr int kIn = 128;    // 96 features padded with zeros to a 64-multiple K
+constexpr int kFeat = HRPP_PROPOSAL_FEATURES;
+constexpr int kHid = HRPP_PROPOSAL_HIDDEN;
+constexpr int kCls = HRPP_PROPOSAL_CLASSES;
+constexpr uint32_t kBmax = 8192;  // rows per minibatch
+// master parameter layout (W1 padded to [256][128])
+constexpr size_t oW1 = 0, ob1 = oW1 + (size_t)kHid * kIn, oW2 = ob1 + kHid, ob2 = oW2 + (size_t)kHid * kHid,
+                 oW3 = ob2 + kHid, ob3 = oW3 + (size_t)kCls * kHid, kMaster = ob3 + kCls;
+
+hrpp_status pfail(hrpp_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return hrpp::report(s, buf);
+}
+
+uint16_t bf16_bits_rne(float f)
+{
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    if ((b & 0x7F800000u) == 0x7F800000u && (b & 0x7FFFFFu)) return (uint16_t)((b >> 16) | 0x40u);
+    const uint32_t rounded = b + 0x7FFFu + ((b >> 16) & 1u);
+    return (uint16_t)(rounded >> 16);
+}
+
+uint64_t splitmix(uint64_t &x)
+{
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ------------------------------------------------------------- kernels --
+
+__device__ __forceinline__ uint32_t quantise16(float u)
+{
+    if (!(u > 0.0f)) return 0u;
+    if (u >= 65535.0f) return 65535u;
+    return (uint32_t)u;
+}
+
+__global__ void __launch_bounds__(128) k_featurize(const float4 *rays, uint32_t n, uint32_t npad, float lox, float loy,
+                                                   float loz, float sx, float sy, float sz,
+                                                   const __nv_bfloat16 *sin_t, __nv_bfloat16 *X, __nv_bfloat16 *XT)
+{
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= npad) return;
+    uint32_t q[5] = {0, 0, 0, 0, 0};
+    const bool live = r < n;
+    if (live) {
+        const float4 o = rays[2ull * r], d = rays[2ull * r + 1];
+        q[0] = quantise16(__fmul_rn(__fsub_rn(o.x, lox), sx));
+        q[1] = quantise16(__fmul_rn(__fsub_rn(o.y, loy), sy));
+        q[2] = quantise16(__fmul_rn(__fsub_rn(o.z, loz), sz));
+        const float l1 = __fadd_rn(__fadd_rn(fabsf(d.x), fabsf(d.y)), fabsf(d.z));
+        const float px = __fdiv_rn(d.x, l1), py = __fdiv_rn(d.y, l1);
+        const float sgx = px >= 0.0f ? 1.0f : -1.0f, sgy = py >= 0.0f ? 1.0f : -1.0f;
+        float ux = px, uy = py;
+        if (d.z < 0.0f) {
+            ux = __fmul_rn(__fsub_rn(1.0f, fabsf(py)), sgx);
+            uy = __fmul_rn(__fsub_rn(1.0f, fabsf(px)), sgy);
+        }
+        q[3] = quantise16(__fmul_rn(__fadd_rn(ux, 1.0f), 32767.5f));
+        q[4] = quantise16(__fmul_rn(__fadd_rn(uy, 1.0f), 32767.5f));
+    }
+    __nv_bfloat16 *row = X + (size_t)r * kIn;
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+    for (int c = 0; c < kIn; ++c) {
+        __nv_bfloat16 v = zero;
+        if (live) {
+            if (c < 5) {
+                v = __float2bfloat16_rn(__fsub_rn(__fmul_rn((float)q[c], 1.0f / 32768.0f), 1.0f));
+            } else if (c < 95) {
+                const int i = (c - 5) / 18, k = ((c - 5) % 18) >> 1;
+                uint32_t ph = (q[i] << k) & 0xFFFFu;
+                if ((c - 5) & 1) ph = (ph + 16384u) & 0xFFFFu;
+                v = sin_t[ph];
+            } else if (c == 95) {
+                v = __float2bfloat16_rn(1.0f);
+            }
+        }
+        row[c] = v;
+        if (XT) XT[(size_t)c * npad + r] = v;
+    }
+}
+
+// softmax cross-entropy per row (one block of 256 threads per row):
+// loss summed into loss_sum, labelled rows counted, dZ = p - onehot in bf16
+__global__ void __launch_bounds__(256) k_softmax_ce(const float *logits, const int32_t *labels, uint32_t n,
+                                                    uint32_t npad, __nv_bfloat16 *dz, __nv_bfloat16 *dzt,
+                                                    float *loss_sum, unsigned int *count)
+{
+    __shared__ float red[8];
+    const uint32_t r = blockIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int lab = r < n ? labels[r] : -1;
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
+    if (lab < 0 || lab >= kCls) {
+        for (int c = t; c < kCls; c += 256) {
+            dz[(size_t)r * kCls + c] = zero;
+            dzt[(size_t)c * npad + r] = zero;
+        }
+        return;
+    }
+    const float *z = logits + (size_t)r * kCls;
+    float m = -INFINITY;
+    for (int c = t; c < kCls; c += 256) m = fmaxf(m, z[c]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    if (lane == 0) red[warp] = m;
+    __syncthreads();
+    m = red[0];
+    for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+    __syncthreads();
+    float s = 0.0f;
+    for (int c = t; c < kCls; c += 256) s += expf(z[c] - m);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    s = 0.0f;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    const float inv = 1.0f / s;
+    for (int c = t; c < kCls; c += 256) {
+        float g = expf(z[c] - m) * inv - (c == lab ? 1.0f : 0.0f);
+        const __nv_bfloat16 h = __float2bfloat16_rn(g);
+        dz[(size_t)r * kCls + c] = h;
+        dzt[(size_t)c * npad + r] = h;
+    }
+    if (t == 0) {
+        atomicAdd(loss_sum, logf(s) - (z[lab] - m));
+        atomicAdd(count, 1u);
+    }
+}
+
+// out[i] = sum over the row i of a bf16 [rows, cols] matrix (256 threads per row)
+__global__ void __launch_bounds__(256) k_rowsum(const __nv_bfloat16 *a, uint32_t cols, float *out)
+{
+    __shared__ float red[8];
+    const __nv_bfloat16 *row = a + (size_t)blockIdx.x * cols;
+    float s = 0.0f;
+    for (uint32_t c = threadIdx.x; c < cols; c += 256) s += __bfloat162float(row[c]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float tot = 0.0f;
+        for (int w = 0; w < 8; ++w) tot += red[w];
+        out[blockIdx.x] = tot;
+    }
+}
+
+// Adam on a [rows, cols] parameter (cols = 1 for biases); optional bf16
+// copies in [rows, cols] and [cols, rows] layouts
+__global__ void __launch_bounds__(256) k_adam(float *w, const float *g, float *m, float *v, uint32_t rows,
+                                              uint32_t cols, float lr, float bc1, float bc2, const unsigned int *count,
+                                              __nv_bfloat16 *wh, __nv_bfloat16 *wt)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * cols) return;
+    const float scale = 1.0f / (float)(*count > 0u ? *count : 1u);
+    const float gi = g[i] * scale;
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+    w[i] = wi;
+    const __nv_bfloat16 h = __float2bfloat16_rn(wi);
+    if (wh) wh[i] = h;
+    if (wt) wt[(size_t)(i % cols) * rows + i / cols] = h;
+}
+
+__global__ void k_to_bf16(const float *w, uint32_t rows, uint32_t cols, __nv_bfloat16 *wh, __nv_bfloat16 *wt)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * cols) return;
+    const __nv_bfloat16 h = __float2bfloat16_rn(w[i]);
+    if (wh) wh[i] = h;
+    if (wt) wt[(size_t)(i % cols) * rows + i / cols] = h;
+}
+
+__global__ void k_argmax_finish(const unsigned long long *amax, uint32_t n, const int32_t *class_node,
+                                int32_t *nodes, int32_t *classes)
+{
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const uint32_t cls = 0xFFFFFFFFu - (uint32_t)(amax[r] & 0xFFFFFFFFull);
+    const uint32_t c = cls < (uint32_t)kCls ? cls : 0u;
+    if (nodes) nodes[r] = class_node[c];
+    if (classes) classes[r] = (int32_t)c;
+}
+
+__global__ void k_labels(const float4 *hits, uint32_t n, const int32_t *prim_class, uint32_t n_tris, int32_t *out)
+{
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const uint32_t prim = __float_as_uint(hits[r].y);
+    out[r] = prim < n_tris ? prim_class[prim] : -1;
+}
+
+}  // namespace
+
+struct hrpp_proposal {
+    int device, width;
+    uint32_t n_tris, n_nodes;
+    float lo[3], scale[3];
+    __nv_bfloat16 *sin_t;
+    int32_t *class_node, *prim_class;
+    std::vector<int32_t> h_class_node;
+    float *master, *grad, *m, *v;
+    __nv_bfloat16 *w1h, *w2h, *w3h, *w2t, *w3t;
+    int step;
+    __nv_bfloat16 *X, *XT, *H1, *H1T, *H2, *H2T, *dZ3, *dZ3T, *dZ2, *dZ2T, *dZ1T;
+    float *logits, *loss_sum;
+    unsigned int *count, *err;
+    int32_t *lab;
+    unsigned long long *amax;
+};
+
+namespace {
+
+void proposal_free(hrpp_proposal *p)
+{
+    if (!p) return;
+    void *ptrs[] = {p->sin_t, p->class_node, p->prim_class, p->master, p->grad, p->m, p->v, p->w1h, p->w2h,
+                    p->w3h, p->w2t, p->w3t, p->X, p->XT, p->H1, p->H1T, p->H2, p->H2T, p->dZ3, p->dZ3T,
+                    p->dZ2, p->dZ2T, p->dZ1T, p->logits, p->loss_sum, p->count, p->err, p->lab, p->amax};
+    for (void *q : ptrs) cudaFree(q);
+    delete p;
+}
+
+struct Dev {
+    int prev = -1;
+    cudaError_t err;
+    explicit Dev(int d)
+    {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != d) err = cudaSetDevice(d);
+    }
+    ~Dev()
+    {
+        int c = -1;
+        if (prev >= 0 && cudaGetDevice(&c) == cudaSuccess && c != prev) cudaSetDevice(prev);
+    }
+};
+
+cudaError_t refresh_bf16(hrpp_proposal *p, cudaStream_t s)
+{
+    auto run = [&](size_t off, uint32_t rows, uint32_t cols, __nv_bfloat16 *wh, __nv_bfloat16 *wt) {
+        const uint32_t n = rows * cols;
+        k_to_bf16<<<(n + 255) / 256, 256, 0, s>>>(p->master + off, rows, cols, wh, wt);
+    };
+    run(oW1, kHid, kIn, p->w1h, nullptr);
+    run(oW2, kHid, kHid, p->w2h, p->w2t);
+    run(oW3, kCls, kHid, p->w3h, p->w3t);
+    return cudaGetLastError();
+}
+
+uint32_t pad128(uint32_t n) { return (n + 127u) & ~127u; }
+
+umma::GemmArgs args(int m, int n, int k, hrpp_proposal *p)
+{
+    umma::GemmArgs g = {};
+    g.M = m;
+    g.N = n;
+    g.K = k;
+    g.m_valid = m;
+    g.error = p->err;
+    return g;
+}
+
+int splits_for(int m_tiles, int k)
+{
+    const int kb = k / umma::BK;
+    int s = 128 / (m_tiles > 0 ? m_tiles : 1);
+    if (s < 1) s = 1;
+    if (s > kb) s = kb;
+    return s;
+}
+
+// forward (and, when train, the backward into p->grad) on rows [0, n) of
+// rays, padded to npad rows; labels (device) when train
+cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const int32_t *labels, bool train,
+                      bool argmax, cudaStream_t s)
+{
+    const uint32_t npad = pad128(n);
+    cudaError_t e;
+    k_featurize<<<(npad + 127) / 128, 128, 0, s>>>(reinterpret_cast<const float4 *>(rays), n, npad, p->lo[0],
+                                                    p->lo[1], p->lo[2], p->scale[0], p->scale[1], p->scale[2],
+                                                    p->sin_t, p->X, train ? p->XT : nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    umma::GemmArgs g = args((int)npad, kHid, kIn, p);
+    g.bias = p->master + ob1;
+    g.c16 = p->H1;
+    g.c16t = train ? p->H1T : nullptr;
+    if ((e = gemm_bf16(p->X, p->w1h, umma::EPI_BIAS_RELU, 256, g, 1, s)) != cudaSuccess) return e;
+    g = args((int)npad, kHid, kHid, p);
+    g.bias = p->master + ob2;
+    g.c16 = p->H2;
+    g.c16t = train ? p->H2T : nullptr;
+    if ((e = gemm_bf16(p->H1, p->w2h, umma::EPI_BIAS_RELU, 256, g, 1, s)) != cudaSuccess) return e;
+    g = args((int)npad, kCls, kHid, p);
+    g.bias = p->master + ob3;
+    if (argmax) {
+        g.argmax = p->amax;
+        g.m_valid = (int)n;
+        if ((e = cudaMemsetAsync(p->amax, 0, sizeof(unsigned long long) * npad, s)) != cudaSuccess) return e;
+        return gemm_bf16(p->H2, p->w3h, umma::EPI_ARGMAX, 256, g, 1, s);
+    }
+    g.c32 = p->logits;
+    if ((e = gemm_bf16(p->H2, p->w3h, umma::EPI_F32, 256, g, 1, s)) != cudaSuccess) return e;
+    if (!train) return cudaSuccess;
+    if ((e = cudaMemcpyAsync(p->lab, labels, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->loss_sum, 0, sizeof(float), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->count, 0, sizeof(unsigned int), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->grad, 0, sizeof(float) * kMaster, s)) != cudaSuccess)
+        return e;
+    k_softmax_ce<<<npad, 256, 0, s>>>(p->logits, p->lab, n, npad, p->dZ3, p->dZ3T, p->loss_sum, p->count);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // dW3 = dZ3^T H2
+    g = args(kCls, kHid, (int)npad, p);
+    g.c32 = p->grad + oW3;
+    if ((e = gemm_bf16(p->dZ3T, p->H2T, umma::EPI_F32_ATOMIC, 256, g, splits_for(kCls / 128, (int)npad), s)) !=
+        cudaSuccess)
+        return e;
+    // dZ2 = (dZ3 W3) * (H2 > 0)
+    g = args((int)npad, kHid, kCls, p);
+    g.act = p->H2;
+    g.c16 = p->dZ2;
+    g.c16t = p->dZ2T;
+    if ((e = gemm_bf16(p->dZ3, p->w3t, umma::EPI_RELU_GRAD, 256, g, 1, s)) != cudaSuccess) return e;
+    // dW2 = dZ2^T H1
+    g = args(kHid, kHid, (int)npad, p);
+    g.c32 = p->grad + oW2;
+    if ((e = gemm_bf16(p->dZ2T, p->H1T, umma::EPI_F32_ATOMIC, 256, g, splits_for(kHid / 128, (int)npad), s)) !=
+        cudaSuccess)
+        return e;
+    // dZ1 = (dZ2 W2) * (H1 > 0), transposed only
+    g = args((int)npad, kHid, kHid, p);
+    g.act = p->H1;
+    g.c16t = p->dZ1T;
+    if ((e = gemm_bf16(p->dZ2, p->w2t, umma::EPI_RELU_GRAD, 256, g, 1, s)) != cudaSuccess) return e;
+    // dW1 = dZ1^T X
+    g = args(kHid, kIn, (int)npad, p);
+    g.c32 = p->grad + oW1;
+    if ((e = gemm_bf16(p->dZ1T, p->XT, umma::EPI_F32_ATOMIC, 128, g, splits_for(kHid / 128, (int)npad), s)) !=
+        cudaSuccess)
+        return e;
+    k_rowsum<<<kCls, 256, 0, s>>>(p->dZ3T, npad, p->grad + ob3);
+    k_rowsum<<<kHid, 256, 0, s>>>(p->dZ2T, npad, p->grad + ob2);
+    k_rowsum<<<kHid, 256, 0, s>>>(p->dZ1T, npad, p->grad + ob1);
+    return cudaGetLastError();
+}
+
+cudaError_t adam(hrpp_proposal *p, float lr, cudaStream_t s)
+{
+    p->step += 1;
+    const float bc1 = 1.0f - std::pow(0.9f, (float)p->step), bc2 = 1.0f - std::pow(0.999f, (float)p->step);
+    auto run = [&](size_t off, uint32_t rows, uint32_t cols, __nv_bfloat16 *wh, __nv_bfloat16 *wt) {
+        const uint32_t n = rows * cols;
+        k_adam<<<(n + 255) / 256, 256, 0, s>>>(p->master + off, p->grad + off, p->m + off, p->v + off, rows, cols, lr,
+                                                bc1, bc2, p->count, wh, wt);
+    };
+    run(oW1, kHid, kIn, p->w1h, nullptr);
+    run(ob1, kHid, 1, nullptr, nullptr);
+    run(oW2, kHid, kHid, p->w2h, p->w2t);
+    run(ob2, kHid, 1, nullptr, nullptr);
+    run(oW3, kCls, kHid, p->w3h, p->w3t);
+    run(ob3, kCls, 1, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+hrpp_status check_err(hrpp_proposal *p)
+{
+    unsigned int flag = 0;
+    cudaError_t e = cudaMemcpy(&flag, p->err, sizeof flag, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return pfail(HRPP_ERR_CUDA, "proposal: %s", cudaGetErrorString(e));
+    if (flag) {
+        cudaMemset(p->err, 0, sizeof(unsigned int));
+        return pfail(HRPP_ERR_CUDA, "proposal: a tensor-core pipeline wait timed out");
+    }
+    return HRPP_OK;
+}
+
+// host copy of the masters in the API layout (W1 without its padding)
+void masters_to_api(const std::vector<float> &m, float *out)
+{
+    size_t o = 0;
+    for (int r = 0; r < kHid; ++r)
+        for (int c = 0; c < kFeat; ++c) out[o++] = m[oW1 + (size_t)r * kIn + c];
+    for (size_t i = ob1; i < kMaster; ++i) out[o++] = m[i];
+}
+
+void api_to_masters(const float *in, std::vector<float> &m)
+{
+    m.assign(kMaster, 0.0f);
+    size_t o = 0;
+    for (int r = 0; r < kHid; ++r)
+        for (int c = 0; c < kFeat; ++c) m[oW1 + (size_t)r * kIn + c] = in[o++];
+    for (size_t i = ob1; i < kMaster; ++i) m[i] = in[o++];
+}
+
+}  // namespace
+
+extern "C" {
+
+hrpp_status hrpp_proposal_create(const hrpp_scene *sc, const hrpp_bvh_node *nodes, uint32_t n_nodes, uint32_t root,
+                                 const uint32_t *prim_index, uint32_t n_prim_index, uint64_t seed,
+                                 hrpp_proposal **out)
+{
+    if (!sc || !nodes || !prim_index || !out) return pfail(HRPP_ERR_INVALID_ARG, "NULL argument");
+    if (n_nodes != sc->n_nodes || n_prim_index != sc->n_tris || root >= n_nodes)
+        return pfail(HRPP_ERR_INVALID_ARG, "the BVH does not match the scene");
+    Dev dv(sc->device);
+    if (dv.err != cudaSuccess) return pfail(HRPP_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(dv.err));
+    hrpp_proposal *p = new (std::nothrow) hrpp_proposal();
+    if (!p) return pfail(HRPP_ERR_OOM, "host allocation");
+    p->device = sc->device;
+    p->width = sc->width;
+    p->n_tris = sc->n_tris;
+    p->n_nodes = n_nodes;
+    const hrpp_bvh_node &rn = nodes[root];
+    for (int a = 0; a < 3; ++a) {
+        p->lo[a] = rn.lo[a];
+        p->scale[a] = 65535.0f / (rn.hi[a] - rn.lo[a]);
+    }
+    // classes: 12-bit path codes (one bit per level in BVH2, two in BVH4)
+    const int bits = p->width == 2 ? 1 : 2, levels = 12 / bits;
+    std::vector<int32_t> prim_class(sc->n_tris, -1);
+    struct Item {
+        uint32_t node;
+        uint32_t code;
+        int depth;
+    };
+    std::vector<Item> st{{root, 0u, 0}};
+    while (!st.empty()) {
+        const Item it = st.back();
+        st.pop_back();
+        const hrpp_bvh_node &n = nodes[it.node];
+        if (n.count > 0) {
+            const uint32_t code = it.depth <= levels ? it.code << (bits * (levels - it.depth)) : it.code;
+            for (uint32_t j = 0; j < n.count && n.first + j < n_prim_index; ++j)
+                if (prim_index[n.first + j] < sc->n_tris) prim_class[prim_index[n.first + j]] = (int32_t)code;
+            continue;
+        }
+        for (int q = 0; q < 4; ++q) {
+            const int32_t c = n.child[q];
+            if (c < 0 || (uint32_t)c >= n_nodes) continue;
+            if (it.depth < levels) st.push_back({(uint32_t)c, (it.code << bits) | (uint32_t)q, it.depth + 1});
+            else st.push_back({(uint32_t)c, it.code, it.depth + 1});
+        }
+    }
+    p->h_class_node.assign(kCls, (int32_t)root);
+    for (int cls = 0; cls < kCls; ++cls) {
+        uint32_t node = root;
+        for (int lv = 0; lv < levels; ++lv) {
+            if (nodes[node].count > 0) break;
+            const int q = (cls >> (bits * (levels - 1 - lv))) & ((1 << bits) - 1);
+            const int32_t c = nodes[node].child[q];
+            if (c < 0 || (uint32_t)c >= n_nodes) break;
+            node = (uint32_t)c;
+        }
+        p->h_class_node[cls] = (int32_t)node;
+    }
+    // sine table: sin(2 pi j / 65536) in double, rounded to float, then bf16
+    std::vector<uint16_t> sin_h(65536);
+    for (int j = 0; j < 65536; ++j) sin_h[j] = bf16_bits_rne((float)std::sin(2.0 * M_PI * j / 65536.0));
+    // initial weights: He-uniform, zero biases, W1's padding columns zero
+    std::vector<float> mh(kMaster, 0.0f);
+    uint64_t rs = seed;
+    auto uni = [&](float a) { return (float)(((splitmix(rs) >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0) * a; };
+    for (int r = 0; r < kHid; ++r)
+        for (int c = 0; c < kFeat; ++c) mh[oW1 + (size_t)r * kIn + c] = uni(std::sqrt(6.0f / kFeat));
+    for (size_t i = oW2; i < ob2; ++i) mh[i] = uni(std::sqrt(6.0f / kHid));
+    for (size_t i = oW3; i < ob3; ++i) mh[i] = uni(std::sqrt(6.0f / kHid));
+    const size_t rows = kBmax;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](auto **ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc((void **)ptr, bytes);
+    };
+    alloc(&p->sin_t, 65536 * 2);
+    alloc(&p->class_node, kCls * 4);
+    alloc(&p->prim_class, (size_t)sc->n_tris * 4);
+    alloc(&p->master, kMaster * 4);
+    alloc(&p->grad, kMaster * 4);
+    alloc(&p->m, kMaster * 4);
+    alloc(&p->v, kMaster * 4);
+    alloc(&p->w1h, (size_t)kHid * kIn * 2);
+    alloc(&p->w2h, (size_t)kHid * kHid * 2);
+    alloc(&p->w3h, (size_t)kCls * kHid * 2);
+    alloc(&p->w2t, (size_t)kHid * kHid * 2);
+    alloc(&p->w3t, (size_t)kCls * kHid * 2);
+    alloc(&p->X, rows * kIn * 2);
+    alloc(&p->XT, rows * kIn * 2);
+    alloc(&p->H1, rows * kHid * 2);
+    alloc(&p->H1T, rows * kHid * 2);
+    alloc(&p->H2, rows * kHid * 2);
+    alloc(&p->H2T, rows * kHid * 2);
+    alloc(&p->dZ3, rows * kCls * 2);
+    alloc(&p->dZ3T, rows * kCls * 2);
+    alloc(&p->dZ2, rows * kHid * 2);
+    alloc(&p->dZ2T, rows * kHid * 2);
+    alloc(&p->dZ1T, rows * kHid * 2);
+    alloc(&p->logits, rows * kCls * 4);
+    alloc(&p->loss_sum, 4);
+    alloc(&p->count, 4);
+    alloc(&p->err, 4);
+    alloc(&p->lab, rows * 4);
+    alloc(&p->amax, rows * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(p->sin_t, sin_h.data(), 65536 * 2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->class_node, p->h_class_node.data(), kCls * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->prim_class, prim_class.data(), (size_t)sc->n_tris * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->master, mh.data(), kMaster * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(p->m, 0, kMaster * 4);
+    if (e == cudaSuccess) e = cudaMemset(p->v, 0, kMaster * 4);
+    if (e == cudaSuccess) e = cudaMemset(p->err, 0, 4);
+    if (e == cudaSuccess) e = refresh_bf16(p, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        proposal_free(p);
+        return pfail(e == cudaErrorMemoryAllocation ? HRPP_ERR_OOM : HRPP_ERR_CUDA, "proposal: %s",
+                     cudaGetErrorString(e));
+    }
+    *out = p;
+    return HRPP_OK;
+}
+
+hrpp_status hrpp_proposal_features(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, void *out_bf16, void *stream)
+{
+    if (!p || (n && (!rays || !out_bf16))) return pfail(HRPP_ERR_INVALID_ARG, "NULL argument");
+    Dev dv(p->device);
+    if (n == 0) return HRPP_OK;
+    k_featurize<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const float4 *>(rays), n, n, p->lo[0], p->lo[1], p->lo[2], p->scale[0], p->scale[1],
+        p->scale[2], p->sin_t, static_cast<__nv_bfloat16 *>(out_bf16), nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return pfail(HRPP_ERR_CUDA, "features: %s", cudaGetErrorString(e));
+    return HRPP_OK;
+}
+
+hrpp_status hrpp_proposal_labels(hrpp_proposal *p, const hrpp_hit *hits, uint32_t n, int32_t *out_labels, void *stream)
+{
+    if (!p || (n && (!hits || !out_labels))) return pfail(HRPP_ERR_INVALID_ARG, "NULL argument");
+    Dev dv(p->device);
+    if (n == 0) return HRPP_OK;
+    k_labels<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float4 *>(hits), n,
+                                                                 p->prim_class, p->n_tris, out_labels);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return pfail(HRPP_ERR_CUDA, "labels: %s", cudaGetErrorString(e));
+    return HRPP_OK;
+}
+
+hrpp_status hrpp_proposal_train(hrpp_proposal *p, const hrpp_ray *rays, const int32_t *labels, uint32_t n, float lr,
+                                float *out_mean_loss, void *stream)
+{
+    if (!p || (n && (!rays || !labels))) return pfail(HRPP_ERR_INVALID_ARG, "NULL argument");
+    if (!(lr > 0.0f)) return pfail(HRPP_ERR_INVALID_ARG, "lr must be positive");
+    Dev dv(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    for (uint32_t off = 0; off < n && e == cudaSuccess; off += kBmax) {
+        const uint32_t b = n - off < kBmax ? n - off : kBmax;
+        e = run_batch(p, rays + off, b, labels + off, true, false, s);
+        if (e == cudaSuccess) e = adam(p, lr, s);
+    }
+    if (e != cudaSuccess) return pfail(HRPP_ERR_CUDA, "train: %s", cudaGetErrorString(e));
+    if (out_mean_loss) {
+        float sum = 0.0f;
+        unsigned int cnt = 0;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess ||
+            (e = cudaMemcpy(&sum, p->loss_sum, 4, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(&cnt, p->count, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return pfail(HRPP_ERR_CUDA, "train: %s", cudaGetErrorString(e));
+        *out_mean_loss = cnt ? sum / (float)cnt : 0.0f;
+        return check_err(p);
+    }
+    return HRPP_OK;
+}
+
+hrpp_status hrpp_proposal_gradients(hrpp_proposal *p, const hrpp_ray *rays, const int32_t *labels, uint32_t n,
+                                    float *host_grads, float *out_mean_loss)
+{
+    if (!p || !rays || !labels || !host_grads || n == 0) return pfail(HRPP_ERR_INVALID_ARG, "NULL argument or n = 0");
+    if (n > kBmax) return pfail(HRPP_ERR_INVALID_ARG, "at most %u rays", kBmax);
+    Dev dv(p->device);
+    cudaError_t e = run_batch(p, rays, n, labels, true, false, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    std::vector<float> g(kMaster);
+    float sum = 0.0f;
+    unsigned int cnt = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(g.data(), p->grad, kMaster * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&sum, p->loss_sum, 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&cnt, p->count, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return pfail(HRPP_ERR_CUDA, "gradients: %s", cudaGetErrorString(e));
+    const float scale = 1.0f / (float)(cnt ? cnt : 1u);
+    for (float &x : g) x *= scale;
+    masters_to_api(g, host_grads);
+    if (out_mean_loss) *out_mean_loss = cnt ? sum / (float)cnt : 0.0f;
+    return check_err(p);
+}
+
+hrpp_status hrpp_proposal_predict(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, int32_t *out_nodes,
+                                  int32_t *out_classes, void *stream)
+{
+    if (!p || (n && (!rays || (!out_nodes && !out_classes)))) return pfail(HRPP_ERR_INVALID_ARG, "NULL argument");
+    Dev dv(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    for (uint32_t off = 0; off < n && e == cudaSuccess; off += kBmax) {
+        const uint32_t b = n - off < kBmax ? n - off : kBmax;
+        e = run_batch(p, rays + off, b, nullptr, false, true, s);
+        if (e == cudaSuccess) {
+            k_argmax_finish<<<(b + 255) / 256, 256, 0, s>>>(p->amax, b, p->class_node, out_nodes ? out_nodes + off : nullptr,
+                                                            out_classes ? out_classes + off : nullptr);
+            e = cudaGetLastError();
+        }
+    }
+    if (e != cudaSuccess) return pfail(HRPP_ERR_CUDA, "predict: %s", cudaGetErrorString(e));
+    return HRPP_OK;
+}
+
+hrpp_status hrpp_proposal_get_weights(const hrpp_proposal *p, float *host, size_t n_floats)
+{
+    if (!p || !host || n_floats != HRPP_PROPOSAL_PARAMS) return pfail(HRPP_ERR_INVALID_ARG, "need %u floats", HRPP_PROPOSAL_PARAMS);
+    Dev dv(p->device);
+    std::vector<float> mh(kMaster);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(mh.data(), p->master, kMaster * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return pfail(HRPP_ERR_CUDA, "get_weights: %s", cudaGetErrorString(e));
+    masters_to_api(mh, host);
+    return HRPP_OK;
+}
+
+hrpp_status hrpp_proposal_set_weights(hrpp_proposal *p, const float *host, size_t n_floats)
+{
+    if (!p || !host || n_floats != HRPP_PROPOSAL_PARAMS) return pfail(HRPP_ERR_INVALID_ARG, "need %u floats", HRPP_PROPOSAL_PARAMS);
+    Dev dv(p->device);
+    std::vector<float> mh;
+    api_to_masters(host, mh);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(p->master, mh.data(), kMaster * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(p->m, 0, kMaster * 4);
+    if (e == cudaSuccess) e = cudaMemset(p->v, 0, kMaster * 4);
+    if (e == cudaSuccess) e = refresh_bf16(p, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return pfail(HRPP_ERR_CUDA, "set_weights: %s", cudaGetErrorString(e));
+    p->step = 0;
+    return HRPP_OK;
+}
+
+hrpp_status hrpp_proposal_class_nodes(const hrpp_proposal *p, int32_t *host_nodes)
+{
+    if (!p || !host_nodes) return pfail(HRPP_ERR_INVALID_ARG, "NULL argument");
+    memcpy(host_nodes, p->h_class_node.data(), sizeof(int32_t) * kCls);
+    return HRPP_OK;
+}
+
+void hrpp_proposal_destroy(hrpp_proposal *p)
+{
+    if (!p) return;
+    Dev dv(p->device);
+    cudaDeviceSynchronize();
+    proposal_free(p);
+}
+
+}  // extern "C"

@@ -238,15 +238,39 @@ __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayS
     s.tag = 0;
     cnt.add(ST_RAYS);
     bool traverse = true, have_inverse = false;
-    if (p.table) {
+    const bool learned = p.predicted != nullptr;
+    if (p.table || learned) {
         cnt.add(ST_LOOKUPS);
-        const uint64_t m = mix48(ray_key(s.o, s.d, p.precision));
-        s.set = (uint32_t)(m & ((1ull << p.log2_sets) - 1ull));
-        s.tag = (m >> p.log2_sets) & kTagMask;
-        const uint64_t *set = p.table + ((uint64_t)s.set << p.log2_ways);
-        const uint32_t ways = 1u << p.log2_ways;
         float tdummy = 0.0f;
         bool positive = false, done = false;
+        if (learned) {
+            // a predicted treelet (learned proposal): traverse its subtree first
+            const int32_t c = __ldg(p.predicted + i);
+            const int32_t ref = (c >= 0 && (uint32_t)c < p.n_nodes) ? __ldg(p.canon_ref + c) : kEmptyRef;
+            if (ref != kEmptyRef) {
+                positive = true;
+                s.ri = ray_inverse(s.o, s.d);
+                have_inverse = true;
+                s.tcur = s.d.w;
+                s.sp = 0;
+                s.ref = ref;
+                s.steps = 0;
+                while (s.ref != kDoneRef) {
+                    if (over_budget(p, s)) break;
+                    if (s.ref >= 0) visit_interior<W, STATS, true>(p, s, stack, cnt);
+                    else visit_leaf<CLOSEST, STATS, true>(p, s, stack, cnt);
+                }
+                done = !CLOSEST && s.b.found;
+            }
+        }
+        const uint32_t ways = p.table ? (1u << p.log2_ways) : 0u;
+        const uint64_t *set = nullptr;
+        if (p.table) {
+            const uint64_t m = mix48(ray_key(s.o, s.d, p.precision));
+            s.set = (uint32_t)(m & ((1ull << p.log2_sets) - 1ull));
+            s.tag = (m >> p.log2_sets) & kTagMask;
+            set = p.table + ((uint64_t)s.set << p.log2_ways);
+        }
         for (uint32_t w = 0; w < ways && !done; ++w) {
             const uint64_t wd = p.update_mode == HRPP_UPDATE_ONLINE ? __ldcg(set + w) : __ldg(set + w);
             if (wd == HRPP_EMPTY_WORD || (wd >> kLeafBits) != s.tag) continue;

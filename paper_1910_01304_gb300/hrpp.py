@@ -22,6 +22,7 @@ HRPP_ANY_HIT, HRPP_CLOSEST_HIT = 0, 1
 HRPP_UPDATE_TWO_PHASE, HRPP_UPDATE_ONLINE, HRPP_UPDATE_FROZEN = 0, 1, 2
 HRPP_NO_HIT = 0xFFFFFFFF
 HRPP_NOALLOC_MAX_RAYS = 1 << 20
+HRPP_PROPOSAL_PARAMS = 256 * 96 + 256 + 256 * 256 + 256 + 4096 * 256 + 4096
 HRPP_EMPTY_WORD = 0xFFFFFFFFFFFFFFFF
 STAT_NAMES = ["rays", "hits", "lookups", "positives", "true_pos", "false_pos", "negatives", "tp_inexact",
               "inserts", "dup_inserts", "evictions", "interior_nodes", "box_tests", "leaves", "tri_tests",
@@ -43,8 +44,8 @@ class hrpp_scene_info(ctypes.Structure):
 
 class hrpp_trace_opts(ctypes.Structure):
     _fields_ = [("kernel_start", ctypes.c_void_p), ("kernel_stop", ctypes.c_void_p),
-                ("block_threads", ctypes.c_uint32), ("schedule", ctypes.c_uint32), ("refill_min", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 5)]
+                ("predicted_nodes", ctypes.c_void_p), ("block_threads", ctypes.c_uint32),
+                ("schedule", ctypes.c_uint32), ("refill_min", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
 
 
 HRPP_SCHEDULE_DEFAULT, HRPP_SCHEDULE_BATCH, HRPP_SCHEDULE_REFILL = 0, 1, 2
@@ -89,6 +90,16 @@ def _load():
         "hrpp_batch_get_stats": (st, [P, u32, P]),
         "hrpp_batch_destroy": (None, [P]),
         "hrpp_gemm_bf16": (st, [P, P, P, i32, i32, i32, P]),
+        "hrpp_proposal_create": (st, [P, P, u32, u32, P, u32, ctypes.c_uint64, P]),
+        "hrpp_proposal_features": (st, [P, P, u32, P, P]),
+        "hrpp_proposal_labels": (st, [P, P, u32, P, P]),
+        "hrpp_proposal_train": (st, [P, P, P, u32, ctypes.c_float, P, P]),
+        "hrpp_proposal_gradients": (st, [P, P, P, u32, P, P]),
+        "hrpp_proposal_predict": (st, [P, P, u32, P, P, P]),
+        "hrpp_proposal_get_weights": (st, [P, P, sz]),
+        "hrpp_proposal_set_weights": (st, [P, P, sz]),
+        "hrpp_proposal_class_nodes": (st, [P, P]),
+        "hrpp_proposal_destroy": (None, [P]),
         "hrpp_last_error": (ctypes.c_char_p, []),
         "hrpp_status_string": (ctypes.c_char_p, [st]),
         "hrpp_version": (i32, []),
@@ -125,6 +136,16 @@ hrpp_batch_run = _lib.hrpp_batch_run
 hrpp_batch_get_stats = _lib.hrpp_batch_get_stats
 hrpp_batch_destroy = _lib.hrpp_batch_destroy
 hrpp_gemm_bf16 = _lib.hrpp_gemm_bf16
+hrpp_proposal_create = _lib.hrpp_proposal_create
+hrpp_proposal_features = _lib.hrpp_proposal_features
+hrpp_proposal_labels = _lib.hrpp_proposal_labels
+hrpp_proposal_train = _lib.hrpp_proposal_train
+hrpp_proposal_gradients = _lib.hrpp_proposal_gradients
+hrpp_proposal_predict = _lib.hrpp_proposal_predict
+hrpp_proposal_get_weights = _lib.hrpp_proposal_get_weights
+hrpp_proposal_set_weights = _lib.hrpp_proposal_set_weights
+hrpp_proposal_class_nodes = _lib.hrpp_proposal_class_nodes
+hrpp_proposal_destroy = _lib.hrpp_proposal_destroy
 hrpp_last_error = _lib.hrpp_last_error
 hrpp_status_string = _lib.hrpp_status_string
 hrpp_version = _lib.hrpp_version
@@ -258,7 +279,8 @@ class Table:
 
 
 def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, stats: bool = False,
-          stream=None, kernel_events=None, block_threads: int = 0, schedule: int = 0, refill_min: int = 0):
+          stream=None, kernel_events=None, block_threads: int = 0, schedule: int = 0, refill_min: int = 0,
+          predicted=None):
     """Traces rays ([n, 8] float32 torch tensor on the GPU, or a host numpy
     array / torch tensor).  Returns (hits, stats dict or None).
 
@@ -276,8 +298,10 @@ def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, 
             hits = torch.empty(shape, dtype=dtype, device=rays.device)
     st = hrpp_stats() if stats else None
     opts = None
-    if kernel_events is not None or block_threads or schedule or refill_min:
+    if kernel_events is not None or block_threads or schedule or refill_min or predicted is not None:
         opts = hrpp_trace_opts()
+        if predicted is not None:
+            opts.predicted_nodes = _ptr(predicted)
         if kernel_events is not None:
             opts.kernel_start = kernel_events[0].cuda_event
             opts.kernel_stop = kernel_events[1].cuda_event
@@ -334,6 +358,82 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             hrpp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Proposal:
+    """Learned treelet proposal (hrpp_proposal_*): a BF16 MLP on the tensor
+    cores that predicts, per ray, a BVH node whose subtree is traversed first."""
+
+    def __init__(self, scene: Scene, nodes, prim_index, root: int = 0, seed: int = 0):
+        nodes = np.ascontiguousarray(nodes)
+        prim_index = np.ascontiguousarray(prim_index, np.uint32)
+        h = ctypes.c_void_p()
+        check(hrpp_proposal_create(scene.handle, _ptr(nodes), nodes.shape[0], root, _ptr(prim_index),
+                                   prim_index.shape[0], seed, ctypes.byref(h)))
+        self.handle = h
+
+    @classmethod
+    def for_workload(cls, scene: Scene, s, seed: int = 0):
+        return cls(scene, s.nodes, s.prim_index, s.root, seed)
+
+    def features(self, rays, stream=None):
+        import torch
+        out = torch.empty((int(rays.shape[0]), 128), dtype=torch.bfloat16, device=rays.device)
+        check(hrpp_proposal_features(self.handle, _ptr(rays), int(rays.shape[0]), _ptr(out), _stream_handle(stream)))
+        return out
+
+    def labels(self, closest_hits, stream=None):
+        import torch
+        out = torch.empty((int(closest_hits.shape[0]),), dtype=torch.int32, device=closest_hits.device)
+        check(hrpp_proposal_labels(self.handle, _ptr(closest_hits), int(closest_hits.shape[0]), _ptr(out),
+                                   _stream_handle(stream)))
+        return out
+
+    def train(self, rays, labels, lr: float = 1e-3, want_loss: bool = False, stream=None):
+        loss = ctypes.c_float()
+        check(hrpp_proposal_train(self.handle, _ptr(rays), _ptr(labels), int(rays.shape[0]), lr,
+                                  ctypes.byref(loss) if want_loss else None, _stream_handle(stream)))
+        return loss.value if want_loss else None
+
+    def gradients(self, rays, labels):
+        g = np.empty(HRPP_PROPOSAL_PARAMS, np.float32)
+        loss = ctypes.c_float()
+        check(hrpp_proposal_gradients(self.handle, _ptr(rays), _ptr(labels), int(rays.shape[0]), _ptr(g),
+                                      ctypes.byref(loss)))
+        return loss.value, g
+
+    def predict(self, rays, stream=None):
+        import torch
+        n = int(rays.shape[0])
+        nodes = torch.empty((n,), dtype=torch.int32, device=rays.device)
+        classes = torch.empty((n,), dtype=torch.int32, device=rays.device)
+        check(hrpp_proposal_predict(self.handle, _ptr(rays), n, _ptr(nodes), _ptr(classes), _stream_handle(stream)))
+        return nodes, classes
+
+    def get_weights(self) -> np.ndarray:
+        w = np.empty(HRPP_PROPOSAL_PARAMS, np.float32)
+        check(hrpp_proposal_get_weights(self.handle, _ptr(w), w.shape[0]))
+        return w
+
+    def set_weights(self, w: np.ndarray):
+        w = np.ascontiguousarray(w, np.float32)
+        check(hrpp_proposal_set_weights(self.handle, _ptr(w), w.shape[0]))
+
+    def class_nodes(self) -> np.ndarray:
+        out = np.empty(4096, np.int32)
+        check(hrpp_proposal_class_nodes(self.handle, _ptr(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hrpp_proposal_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

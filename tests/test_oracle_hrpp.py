@@ -267,3 +267,42 @@ def test_go_up_unbounded_second_pass(small):
     tab0 = O.Table(0, 1, 6, O.UNBOUNDED, go_up=0)
     O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.ANY_HIT, tab0)
     assert keys1[1] <= tab0.unbounded_size()[1]
+
+
+# ------------------------------------------------- predicted treelets --
+
+def test_predicted_leaf_of_the_hit_is_a_true_positive(small):
+    """A prediction naming the very leaf (or an ancestor) holding a ray's
+    hit makes that ray a true positive; results never change."""
+    rays = small.primary_rays()[::3]
+    h, _ = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.CLOSEST_HIT)
+    leaf_node = {}
+    for i, n in enumerate(small.nodes):
+        if n["count"] > 0:
+            for j in range(int(n["count"])):
+                leaf_node[int(small.prim_index[n["first"] + j])] = i
+    parent = {int(c): i for i, n in enumerate(small.nodes) for c in n["child"] if c >= 0}
+    hit = h["prim"] != O.NO_HIT
+    for lift in (0, 2):
+        pred = np.full(len(rays), -1, np.int32)
+        for k in np.nonzero(hit)[0]:
+            n = leaf_node[int(h["prim"][k])]
+            for _ in range(lift):
+                n = parent.get(n, n)
+            pred[k] = n
+        for mode in (O.ANY_HIT, O.CLOSEST_HIT):
+            hp, sp = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, mode)
+            hh, sh, oc, boxes = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, mode, per_ray=True,
+                                        predicted=pred)
+            if mode == O.CLOSEST_HIT:
+                assert np.array_equal(hp, hh)
+            else:
+                assert np.array_equal(hp == O.NO_HIT, hh == O.NO_HIT)
+            assert np.array_equal(oc == 3, hit) and sh["inserts"] == 0
+            assert sh["positives"] == int(hit.sum()) and sh["lookups"] == len(rays)
+            if mode == O.ANY_HIT:
+                assert np.all(boxes[hit] == 0)
+    # out-of-range or unreachable predictions are ignored
+    bad = np.full(len(rays), len(small.nodes) + 5, np.int32)
+    _, sb = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.ANY_HIT, predicted=bad)
+    assert sb["positives"] == 0
