@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="terrain", choices=["terrain", "batched", "pathtrace"],
+    ap.add_argument("--traces", type=int, default=50_000_000, help="learned workload: training traces")
+    ap.add_argument("--workload", default="terrain", choices=["terrain", "batched", "pathtrace", "learned"],
                     help="terrain: the headline step; batched: the 64-scene uneven mix in one graph-replayed launch")
     ap.add_argument("--scenes", type=int, default=64)
     return ap.parse_args()
@@ -433,6 +434,115 @@ def run_pathtrace(args):
     return 0
 
 
+def run_learned(args):
+    """Config 4: the learned treelet proposal trained on traversal traces of
+    the small scene's camera, compared with the hash table on held-out
+    primary (closest-hit) and shadow (any-hit) rays of that scene."""
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1910_01304_gb300 import hrpp as H
+    from paper_1910_01304_gb300.scenes import workloads as W
+    s = W.small_scene()
+    g = H.Scene.from_workload(s)
+    stream = torch.cuda.current_stream()
+    models = {"closest": H.Proposal.for_workload(g, s, seed=1), "any": H.Proposal.for_workload(g, s, seed=2)}
+    tables = {"closest": H.Table(12, 1, 6), "any": H.Table(12, 1, 6)}
+
+    def frame_rays(f):
+        prim = torch.from_numpy(s.primary_rays(frame=f)).cuda()
+        hits, _ = H.trace(g, prim, H.HRPP_CLOSEST_HIT, tables["closest"])
+        hh = hits.cpu().numpy()
+        sh, _ = W.secondary_shadow(s, s.primary_rays(frame=f), hh[:, 0], hh[:, 1].view(np.uint32))
+        shadow = torch.from_numpy(sh).cuda()
+        H.trace(g, shadow, H.HRPP_ANY_HIT, tables["any"])
+        sh_hits, _ = H.trace(g, shadow, H.HRPP_CLOSEST_HIT)
+        return {"closest": (prim, hits), "any": (shadow, sh_hits)}
+
+    t_train = 0.0
+    traces = 0
+    losses = {"closest": [], "any": []}
+    gemm_flops_per_row = 2.0 * (128 * 256 + 256 * 256 + 256 * 4096) * 3.0
+    f = 0
+    while traces < args.traces:
+        f += 1
+        fr = frame_rays(f)
+        last = traces + sum(int(fr[m][0].shape[0]) for m in fr) >= args.traces
+        for mode in ("closest", "any"):
+            rays, hits = fr[mode]
+            lab = models[mode].labels(hits)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            loss = models[mode].train(rays, lab, lr=1e-3, want_loss=(f % 50 == 0 or f == 1 or last))
+            e1.record(stream)
+            e1.synchronize()
+            t_train += e0.elapsed_time(e1) * 1e-3
+            traces += int(rays.shape[0])
+            if loss is not None:
+                losses[mode].append(loss)
+    train_tflops = traces * gemm_flops_per_row / t_train / 1e12 if t_train else None
+    # evaluation on held-out frames: plain, hash table (frozen), learned treelets
+    res = {}
+    for mode_name, mode in (("closest", H.HRPP_CLOSEST_HIT), ("any", H.HRPP_ANY_HIT)):
+        tables[mode_name].configure(6, H.HRPP_UPDATE_FROZEN)
+        acc = {"plain": [0.0, None], "hash": [0.0, None], "learned": [0.0, None], "learned_incl_inference": [0.0, None]}
+        rays_total = 0
+        stats = {}
+        for f in range(100000, 100000 + 4):
+            fr = frame_rays(f)
+            rays = fr[mode_name][0]
+            rays_total += int(rays.shape[0])
+            for _ in range(2):   # warm
+                H.trace(g, rays, mode)
+            def timed(fn):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                out = fn()
+                e1.record(stream)
+                e1.synchronize()
+                return e0.elapsed_time(e1), out
+            ms, _ = timed(lambda: H.trace(g, rays, mode))
+            acc["plain"][0] += ms
+            ms, _ = timed(lambda: H.trace(g, rays, mode, tables[mode_name]))
+            acc["hash"][0] += ms
+            ms_pred, (nodes, _) = timed(lambda: models[mode_name].predict(rays))
+            ms, _ = timed(lambda: H.trace(g, rays, mode, predicted=nodes))
+            acc["learned"][0] += ms
+            acc["learned_incl_inference"][0] += ms + ms_pred
+            for name, kw in (("plain", {}), ("hash", {"table": tables[mode_name]}), ("learned", {"predicted": nodes})):
+                _, st = H.trace(g, rays, mode, stats=True, **kw)
+                for k, v in st.items():
+                    stats.setdefault(name, {}).setdefault(k, 0)
+                    stats[name][k] += v
+        res[mode_name] = {
+            "rays": rays_total,
+            "mrays": {k: rays_total / (v[0] * 1e-3) / 1e6 for k, v in acc.items()},
+            "prediction_ratio": {k: stats[k]["true_pos"] / stats[k]["rays"] for k in ("hash", "learned")},
+            "box_tests_vs_plain": {k: (stats[k]["box_tests"] + stats[k]["pred_box_tests"]) / stats["plain"]["box_tests"]
+                                   for k in ("hash", "learned")},
+        }
+    peak = None
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as fh:
+            peak = float(json.load(fh)["bf16_tflops_sustained"])
+    line = {"metric": METRIC, "value": res["any"]["mrays"]["learned"], "unit": "Mrays/s", "n_gpus": 1,
+            "steps": 4, "warmup": 2, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 (MLP, fp32 accumulate) / f32 (traversal)", "data": "synthetic",
+            "config": {"workload": "learned treelet proposal on the small scene (1,792 tris, BVH2): "
+                                   "96-256-256-4096 BF16 MLP, one model per query mode",
+                       "traces": traces, "frames": f},
+            "train": {"seconds_in_train_calls": t_train, "traces": traces, "loss_first_last": {
+                k: (v[0], v[-1]) if v else None for k, v in losses.items()},
+                "gemm_tflops": train_tflops, "tensor_peak_sustained_tflops": peak,
+                "frac": (train_tflops / peak) if (train_tflops and peak) else None},
+            "eval": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -441,6 +551,8 @@ def main():
         return run_batched(args)
     if args.workload == "pathtrace":
         return run_pathtrace(args)
+    if args.workload == "learned":
+        return run_learned(args)
     rank, world, local = dist_env()
     import torch
     if not torch.cuda.is_available():

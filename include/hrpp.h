@@ -338,12 +338,13 @@ hrpp_status hrpp_proposal_features(hrpp_proposal *p, const hrpp_ray *rays, uint3
  * holding each hit's triangle, -1 for a miss. */
 hrpp_status hrpp_proposal_labels(hrpp_proposal *p, const hrpp_hit *hits, uint32_t n, int32_t *out_labels,
                                  void *stream);
-/* One Adam step per minibatch of up to 8192 rays (device rays and labels;
+/* One Adam step per minibatch of up to 16384 rays (device rays and labels;
  * label -1 = no target).  *out_mean_loss (host, may be NULL) receives the
- * mean loss of the last minibatch (the call then waits). */
+ * mean loss over every labelled ray of the call, each minibatch's loss
+ * taken before its own step (the call then waits); 0 if none was labelled. */
 hrpp_status hrpp_proposal_train(hrpp_proposal *p, const hrpp_ray *rays, const int32_t *labels, uint32_t n, float lr,
                                 float *out_mean_loss, void *stream);
-/* Loss and gradients of one batch (n <= 8192) without updating: host_grads
+/* Loss and gradients of one batch (n <= 16384) without updating: host_grads
  * receives HRPP_PROPOSAL_PARAMS floats in the weight layout above.  Waits. */
 hrpp_status hrpp_proposal_gradients(hrpp_proposal *p, const hrpp_ray *rays, const int32_t *labels, uint32_t n,
                                     float *host_grads, float *out_mean_loss);

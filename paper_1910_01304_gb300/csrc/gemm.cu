@@ -52,13 +52,14 @@ cudaError_t make_map(CUtensorMap *map, const void *ptr, uint64_t rows, uint64_t 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int BN, int EPI>
-cudaError_t launch(const void *a, const void *b, const umma::GemmArgs &g, int splits, cudaStream_t s)
+template <int BN, int EPI, int NST>
+cudaError_t launch_stages(const void *a, const void *b, const umma::GemmArgs &g, int splits, cudaStream_t s)
 {
     static bool configured = false;  // per template instance; attribute setting is idempotent
-    const size_t smem = umma::gemm_smem_bytes<BN>();
+    const size_t smem = umma::gemm_smem_bytes<BN, NST>();
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(umma::k_gemm<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(umma::k_gemm<BN, EPI, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
@@ -67,8 +68,16 @@ cudaError_t launch(const void *a, const void *b, const umma::GemmArgs &g, int sp
     if (e == cudaSuccess) e = make_map(&mb, b, (uint64_t)g.N, (uint64_t)g.K, BN);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(g.N / BN), (unsigned)(g.M / umma::BM), (unsigned)splits);
-    umma::k_gemm<BN, EPI><<<grid, 128, smem, s>>>(ma, mb, g);
+    umma::k_gemm<BN, EPI, NST><<<grid, 128, smem, s>>>(ma, mb, g);
     return cudaGetLastError();
+}
+
+// short K ranges (at most 4 K blocks per CTA) take the 2-stage variant
+template <int BN, int EPI>
+cudaError_t launch(const void *a, const void *b, const umma::GemmArgs &g, int splits, cudaStream_t s)
+{
+    if (g.k_blocks_per_split <= 4) return launch_stages<BN, EPI, 2>(a, b, g, splits, s);
+    return launch_stages<BN, EPI, umma::STAGES>(a, b, g, splits, s);
 }
 
 }  // namespace
@@ -95,7 +104,10 @@ cudaError_t gemm_bf16(const void *a, const void *b, int epi, int bn, const umma:
     HRPP_GEMM_CASE(128, umma::EPI_F32_ATOMIC)
     HRPP_GEMM_CASE(256, umma::EPI_F32_ATOMIC)
     HRPP_GEMM_CASE(256, umma::EPI_BIAS_RELU)
+    HRPP_GEMM_CASE(128, umma::EPI_BIAS_RELU)
     HRPP_GEMM_CASE(256, umma::EPI_RELU_GRAD)
+    HRPP_GEMM_CASE(128, umma::EPI_RELU_GRAD)
+    HRPP_GEMM_CASE(128, umma::EPI_ARGMAX)
     HRPP_GEMM_CASE(256, umma::EPI_ARGMAX)
 #undef HRPP_GEMM_CASE
     return cudaErrorInvalidValue;

@@ -35,7 +35,8 @@ constexpr int kIn = 128;    // 96 features padded with zeros to a 64-multiple K
 constexpr int kFeat = HRPP_PROPOSAL_FEATURES;
 constexpr int kHid = HRPP_PROPOSAL_HIDDEN;
 constexpr int kCls = HRPP_PROPOSAL_CLASSES;
-constexpr uint32_t kBmax = 8192;  // rows per minibatch
+constexpr uint32_t kBmax = 16384;   // rows per training minibatch
+constexpr uint32_t kBinfer = 65536; // rows per inference chunk
 // master parameter layout (W1 padded to [256][128])
 constexpr size_t oW1 = 0, ob1 = oW1 + (size_t)kHid * kIn, oW2 = ob1 + kHid, ob2 = oW2 + (size_t)kHid * kHid,
                  oW3 = ob2 + kHid, ob3 = oW3 + (size_t)kCls * kHid, kMaster = ob3 + kCls;
@@ -206,6 +207,14 @@ __global__ void __launch_bounds__(256) k_adam(float *w, const float *g, float *m
     if (wt) wt[(size_t)(i % cols) * rows + i / cols] = h;
 }
 
+// adds one minibatch's loss total and labelled-row count to the call's
+__global__ void k_accumulate_loss(const float *loss_sum, const unsigned int *count, float *call_loss,
+                                  unsigned int *call_count)
+{
+    *call_loss += *loss_sum;
+    *call_count += *count;
+}
+
 __global__ void k_to_bf16(const float *w, uint32_t rows, uint32_t cols, __nv_bfloat16 *wh, __nv_bfloat16 *wt)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -249,8 +258,13 @@ struct hrpp_proposal {
     __nv_bfloat16 *X, *XT, *H1, *H1T, *H2, *H2T, *dZ3, *dZ3T, *dZ2, *dZ2T, *dZ1T;
     float *logits, *loss_sum;
     unsigned int *count, *err;
+    float *call_loss;           // loss and labelled rows summed over one train call
+    unsigned int *call_count;
     int32_t *lab;
     unsigned long long *amax;
+    // inference chunk buffers (allocated on the first prediction)
+    __nv_bfloat16 *Xi, *H1i, *H2i;
+    unsigned long long *amaxi;
 };
 
 namespace {
@@ -260,7 +274,8 @@ void proposal_free(hrpp_proposal *p)
     if (!p) return;
     void *ptrs[] = {p->sin_t, p->class_node, p->prim_class, p->master, p->grad, p->m, p->v, p->w1h, p->w2h,
                     p->w3h, p->w2t, p->w3t, p->X, p->XT, p->H1, p->H1T, p->H2, p->H2T, p->dZ3, p->dZ3T,
-                    p->dZ2, p->dZ2T, p->dZ1T, p->logits, p->loss_sum, p->count, p->err, p->lab, p->amax};
+                    p->dZ2, p->dZ2T, p->dZ1T, p->logits, p->loss_sum, p->count, p->err, p->call_loss, p->call_count,
+                    p->lab, p->amax, p->Xi, p->H1i, p->H2i, p->amaxi};
     for (void *q : ptrs) cudaFree(q);
     delete p;
 }
@@ -294,6 +309,13 @@ cudaError_t refresh_bf16(hrpp_proposal *p, cudaStream_t s)
 
 uint32_t pad128(uint32_t n) { return (n + 127u) & ~127u; }
 
+// 256-wide tiles unless that leaves fewer than two CTAs per SM (152 SMs)
+int tile_n(int m, int n)
+{
+    const bool wide_ok = n % 256 == 0 && (m / 128) * (n / 256) >= 2 * 152;
+    return wide_ok ? 256 : 128;
+}
+
 umma::GemmArgs args(int m, int n, int k, hrpp_proposal *p)
 {
     umma::GemmArgs g = {};
@@ -321,30 +343,32 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
 {
     const uint32_t npad = pad128(n);
     cudaError_t e;
+    __nv_bfloat16 *X = argmax ? p->Xi : p->X, *H1 = argmax ? p->H1i : p->H1, *H2 = argmax ? p->H2i : p->H2;
+    unsigned long long *amax = argmax ? p->amaxi : p->amax;
     k_featurize<<<(npad + 127) / 128, 128, 0, s>>>(reinterpret_cast<const float4 *>(rays), n, npad, p->lo[0],
                                                     p->lo[1], p->lo[2], p->scale[0], p->scale[1], p->scale[2],
-                                                    p->sin_t, p->X, train ? p->XT : nullptr);
+                                                    p->sin_t, X, train ? p->XT : nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     umma::GemmArgs g = args((int)npad, kHid, kIn, p);
     g.bias = p->master + ob1;
-    g.c16 = p->H1;
+    g.c16 = H1;
     g.c16t = train ? p->H1T : nullptr;
-    if ((e = gemm_bf16(p->X, p->w1h, umma::EPI_BIAS_RELU, 256, g, 1, s)) != cudaSuccess) return e;
+    if ((e = gemm_bf16(X, p->w1h, umma::EPI_BIAS_RELU, tile_n((int)npad, kHid), g, 1, s)) != cudaSuccess) return e;
     g = args((int)npad, kHid, kHid, p);
     g.bias = p->master + ob2;
-    g.c16 = p->H2;
+    g.c16 = H2;
     g.c16t = train ? p->H2T : nullptr;
-    if ((e = gemm_bf16(p->H1, p->w2h, umma::EPI_BIAS_RELU, 256, g, 1, s)) != cudaSuccess) return e;
+    if ((e = gemm_bf16(H1, p->w2h, umma::EPI_BIAS_RELU, tile_n((int)npad, kHid), g, 1, s)) != cudaSuccess) return e;
     g = args((int)npad, kCls, kHid, p);
     g.bias = p->master + ob3;
     if (argmax) {
-        g.argmax = p->amax;
+        g.argmax = amax;
         g.m_valid = (int)n;
-        if ((e = cudaMemsetAsync(p->amax, 0, sizeof(unsigned long long) * npad, s)) != cudaSuccess) return e;
-        return gemm_bf16(p->H2, p->w3h, umma::EPI_ARGMAX, 256, g, 1, s);
+        if ((e = cudaMemsetAsync(amax, 0, sizeof(unsigned long long) * npad, s)) != cudaSuccess) return e;
+        return gemm_bf16(H2, p->w3h, umma::EPI_ARGMAX, tile_n((int)npad, kCls), g, 1, s);
     }
     g.c32 = p->logits;
-    if ((e = gemm_bf16(p->H2, p->w3h, umma::EPI_F32, 256, g, 1, s)) != cudaSuccess) return e;
+    if ((e = gemm_bf16(H2, p->w3h, umma::EPI_F32, 256, g, 1, s)) != cudaSuccess) return e;
     if (!train) return cudaSuccess;
     if ((e = cudaMemcpyAsync(p->lab, labels, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->loss_sum, 0, sizeof(float), s)) != cudaSuccess ||
@@ -364,7 +388,7 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     g.act = p->H2;
     g.c16 = p->dZ2;
     g.c16t = p->dZ2T;
-    if ((e = gemm_bf16(p->dZ3, p->w3t, umma::EPI_RELU_GRAD, 256, g, 1, s)) != cudaSuccess) return e;
+    if ((e = gemm_bf16(p->dZ3, p->w3t, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid), g, 1, s)) != cudaSuccess) return e;
     // dW2 = dZ2^T H1
     g = args(kHid, kHid, (int)npad, p);
     g.c32 = p->grad + oW2;
@@ -375,7 +399,7 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     g = args((int)npad, kHid, kHid, p);
     g.act = p->H1;
     g.c16t = p->dZ1T;
-    if ((e = gemm_bf16(p->dZ2, p->w2t, umma::EPI_RELU_GRAD, 256, g, 1, s)) != cudaSuccess) return e;
+    if ((e = gemm_bf16(p->dZ2, p->w2t, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid), g, 1, s)) != cudaSuccess) return e;
     // dW1 = dZ1^T X
     g = args(kHid, kIn, (int)npad, p);
     g.c32 = p->grad + oW1;
@@ -541,6 +565,8 @@ hrpp_status hrpp_proposal_create(const hrpp_scene *sc, const hrpp_bvh_node *node
     alloc(&p->loss_sum, 4);
     alloc(&p->count, 4);
     alloc(&p->err, 4);
+    alloc(&p->call_loss, 4);
+    alloc(&p->call_count, 4);
     alloc(&p->lab, rows * 4);
     alloc(&p->amax, rows * 8);
     if (e == cudaSuccess) e = cudaMemcpy(p->sin_t, sin_h.data(), 65536 * 2, cudaMemcpyHostToDevice);
@@ -594,18 +620,26 @@ hrpp_status hrpp_proposal_train(hrpp_proposal *p, const hrpp_ray *rays, const in
     Dev dv(p->device);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
+    if (out_mean_loss) {
+        if ((e = cudaMemsetAsync(p->call_loss, 0, 4, s)) == cudaSuccess)
+            e = cudaMemsetAsync(p->call_count, 0, 4, s);
+    }
     for (uint32_t off = 0; off < n && e == cudaSuccess; off += kBmax) {
         const uint32_t b = n - off < kBmax ? n - off : kBmax;
         e = run_batch(p, rays + off, b, labels + off, true, false, s);
         if (e == cudaSuccess) e = adam(p, lr, s);
+        if (e == cudaSuccess && out_mean_loss) {
+            k_accumulate_loss<<<1, 1, 0, s>>>(p->loss_sum, p->count, p->call_loss, p->call_count);
+            e = cudaGetLastError();
+        }
     }
     if (e != cudaSuccess) return pfail(HRPP_ERR_CUDA, "train: %s", cudaGetErrorString(e));
     if (out_mean_loss) {
         float sum = 0.0f;
         unsigned int cnt = 0;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess ||
-            (e = cudaMemcpy(&sum, p->loss_sum, 4, cudaMemcpyDeviceToHost)) != cudaSuccess ||
-            (e = cudaMemcpy(&cnt, p->count, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            (e = cudaMemcpy(&sum, p->call_loss, 4, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(&cnt, p->call_count, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
             return pfail(HRPP_ERR_CUDA, "train: %s", cudaGetErrorString(e));
         *out_mean_loss = cnt ? sum / (float)cnt : 0.0f;
         return check_err(p);
@@ -642,11 +676,18 @@ hrpp_status hrpp_proposal_predict(hrpp_proposal *p, const hrpp_ray *rays, uint32
     Dev dv(p->device);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
-    for (uint32_t off = 0; off < n && e == cudaSuccess; off += kBmax) {
-        const uint32_t b = n - off < kBmax ? n - off : kBmax;
+    if (!p->Xi) {
+        if ((e = cudaMalloc(&p->Xi, (size_t)kBinfer * kIn * 2)) != cudaSuccess ||
+            (e = cudaMalloc(&p->H1i, (size_t)kBinfer * kHid * 2)) != cudaSuccess ||
+            (e = cudaMalloc(&p->H2i, (size_t)kBinfer * kHid * 2)) != cudaSuccess ||
+            (e = cudaMalloc(&p->amaxi, (size_t)kBinfer * 8)) != cudaSuccess)
+            return pfail(HRPP_ERR_OOM, "predict buffers: %s", cudaGetErrorString(e));
+    }
+    for (uint32_t off = 0; off < n && e == cudaSuccess; off += kBinfer) {
+        const uint32_t b = n - off < kBinfer ? n - off : kBinfer;
         e = run_batch(p, rays + off, b, nullptr, false, true, s);
         if (e == cudaSuccess) {
-            k_argmax_finish<<<(b + 255) / 256, 256, 0, s>>>(p->amax, b, p->class_node, out_nodes ? out_nodes + off : nullptr,
+            k_argmax_finish<<<(b + 255) / 256, 256, 0, s>>>(p->amaxi, b, p->class_node, out_nodes ? out_nodes + off : nullptr,
                                                             out_classes ? out_classes + off : nullptr);
             e = cudaGetLastError();
         }

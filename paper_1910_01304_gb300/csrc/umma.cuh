@@ -150,24 +150,28 @@ __device__ __forceinline__ uint32_t ordered_f32(float f)
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
-template <int BN>
+template <int BN, int NST = STAGES>
 constexpr size_t gemm_smem_bytes()
 {
-    return (size_t)STAGES * ((size_t)BM * BK * 2 + (size_t)BN * BK * 2) + 1024;
+    return (size_t)NST * ((size_t)BM * BK * 2 + (size_t)BN * BK * 2) + 1024;
 }
 
-template <int BN, int EPI>
+// NST pipeline stages: 4 for long K; 2 for short K, which halves the shared
+// memory so two CTAs share an SM (their TMEM accumulators fit its 512
+// columns) and one CTA's epilogue overlaps the other's loads
+template <int BN, int EPI, int NST = STAGES>
 __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtensorMap tma_a,
                                                  const __grid_constant__ CUtensorMap tma_b, const GemmArgs g)
 {
     static_assert(BN == 128 || BN == 256, "tile width");
+    static_assert(NST >= 2 && NST <= STAGES, "stages");
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accum_bar;
+    __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], accum_bar;
     __shared__ uint32_t tmem_base;
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr uint32_t kABytes = BM * BK * 2, kBBytes = BN * BK * 2;
     unsigned char *a_s = smem;
-    unsigned char *b_s = smem + STAGES * kABytes;
+    unsigned char *b_s = smem + NST * kABytes;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int kb0 = blockIdx.z * g.k_blocks_per_split;
@@ -176,7 +180,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
     const int n_kb = kb_end > kb0 ? kb_end - kb0 : 0;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
@@ -198,8 +202,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
     if (warp == 0 && lane == 0) {
         // TMA producer
         for (int i = 0; i < n_kb; ++i) {
-            const int s = i % STAGES;
-            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+            const int s = i % NST;
+            const uint32_t ph = (uint32_t)(i / NST) & 1u;
             if (!mbar_wait(&empty_bar[s], ph ^ 1u)) {
                 failed = true;
                 break;
@@ -213,8 +217,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
         // MMA issuer
         constexpr uint32_t idesc = instr_desc(BM, BN);
         for (int i = 0; i < n_kb; ++i) {
-            const int s = i % STAGES;
-            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+            const int s = i % NST;
+            const uint32_t ph = (uint32_t)(i / NST) & 1u;
             if (!mbar_wait(&full_bar[s], ph)) {
                 failed = true;
                 break;
@@ -250,21 +254,38 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
             if (row >= g.m_valid) continue;
             if (EPI == EPI_F32 || EPI == EPI_F32_ATOMIC) {
                 float *dst = g.c32 + (size_t)row * g.N + col0;
+                if (g.bias) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    float x = v[j] + (g.bias ? g.bias[col0 + j] : 0.0f);
-                    if (EPI == EPI_F32) dst[j] = x;
-                    else atomicAdd(dst + j, x);
+                    for (int j = 0; j < 16; ++j) v[j] += g.bias[col0 + j];
+                }
+#pragma unroll
+                for (int j = 0; j < 16; j += 4) {
+                    const float4 x = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    if (EPI == EPI_F32) *reinterpret_cast<float4 *>(dst + j) = x;
+                    else atomicAdd(reinterpret_cast<float4 *>(dst + j), x);
                 }
             } else if (EPI == EPI_BIAS_RELU || EPI == EPI_RELU_GRAD) {
+                __align__(16) __nv_bfloat16 h[16];
+                if (EPI == EPI_RELU_GRAD) {
+                    __align__(16) __nv_bfloat16 a[16];
+                    const uint4 *src = reinterpret_cast<const uint4 *>(g.act + (size_t)row * g.N + col0);
+                    *reinterpret_cast<uint4 *>(a) = src[0];
+                    *reinterpret_cast<uint4 *>(a + 8) = src[1];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    float x;
-                    if (EPI == EPI_BIAS_RELU) x = fmaxf(v[j] + (g.bias ? g.bias[col0 + j] : 0.0f), 0.0f);
-                    else x = __bfloat162float(g.act[(size_t)row * g.N + col0 + j]) > 0.0f ? v[j] : 0.0f;
-                    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-                    if (g.c16) g.c16[(size_t)row * g.N + col0 + j] = h;
-                    if (g.c16t) g.c16t[(size_t)(col0 + j) * g.M + row] = h;
+                    for (int j = 0; j < 16; ++j) h[j] = __float2bfloat16_rn(__bfloat162float(a[j]) > 0.0f ? v[j] : 0.0f);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        h[j] = __float2bfloat16_rn(fmaxf(v[j] + (g.bias ? g.bias[col0 + j] : 0.0f), 0.0f));
+                }
+                if (g.c16) {
+                    uint4 *dst = reinterpret_cast<uint4 *>(g.c16 + (size_t)row * g.N + col0);
+                    dst[0] = *reinterpret_cast<const uint4 *>(h);
+                    dst[1] = *reinterpret_cast<const uint4 *>(h + 8);
+                }
+                if (g.c16t) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) g.c16t[(size_t)(col0 + j) * g.M + row] = h[j];
                 }
             } else if (EPI == EPI_ARGMAX) {
 #pragma unroll
@@ -286,8 +307,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
     if (failed && g.error) atomicExch(g.error, 1u);
     // a producer that gave up may still have copies in flight: wait for them
     if (warp == 0 && lane == 0 && failed) {
-        for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; ++i)
-            mbar_wait(&full_bar[i % STAGES], (uint32_t)(i / STAGES) & 1u);
+        for (int i = (issued > NST ? issued - NST : 0); i < issued; ++i)
+            mbar_wait(&full_bar[i % NST], (uint32_t)(i / NST) & 1u);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

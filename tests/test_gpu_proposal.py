@@ -173,3 +173,94 @@ def test_training_beats_the_hash_predictor():
     assert torch.equal(plain.view(torch.int32), learned.view(torch.int32))
     assert torch.equal(plain.view(torch.int32), hashed.view(torch.int32))
     assert sl["true_pos"] > 1.5 * sh["true_pos"], (sl["true_pos"], sh["true_pos"])
+
+
+def _many_rays(s, n, seed):
+    """n rays from jittered camera frames of the small scene, with random
+    origins mixed in so that rows differ across chunk boundaries."""
+    rng = np.random.default_rng(seed)
+    out, f = [], 1
+    while sum(len(r) for r in out) < n:
+        out.append(s.primary_rays(frame=f))
+        f += 1
+    r = np.concatenate(out)[:n].copy()
+    r[::5, 0:3] = rng.uniform(-6, 6, (len(r[::5]), 3))
+    return np.ascontiguousarray(r)
+
+
+def test_predictions_across_inference_chunks(env):
+    """Prediction runs in chunks of 65,536 rows: 140,001 rays cover two
+    full chunks and a ragged tail.  Rows sampled around every chunk and tile
+    boundary are an argmax of the oracle's logits."""
+    import torch
+    H, s, g, prop = env
+    w = P.Weights.random(13, scale=1.5)
+    prop.set_weights(w.flat())
+    n = 140_001
+    rays = _many_rays(s, n, 4)
+    nodes, classes = prop.predict(torch.from_numpy(rays).cuda())
+    classes = classes.cpu().numpy()
+    edges = [0, 127, 128, 65535, 65536, 65537, 131071, 131072, 131073, n - 2, n - 1]
+    rng = np.random.default_rng(5)
+    rows = np.unique(np.concatenate([edges, rng.integers(0, n, 1500)]))
+    lo, hi = _box(s)
+    _, _, z = P.forward(P.Weights.from_flat(w.flat()), P.features(rays[rows], lo, hi))
+    zmax, span = z.max(axis=1), z.max(axis=1) - z.min(axis=1)
+    picked = z[np.arange(len(rows)), classes[rows]]
+    assert np.all(zmax - picked <= 0.02 * span)
+    assert np.mean(classes[rows] == np.argmax(z, axis=1)) > 0.97
+    _, to_node = P.leaf_codes(s.nodes, s.root, s.width)
+    assert np.array_equal(nodes.cpu().numpy(), to_node[classes])
+
+
+def test_gradients_of_a_ragged_batch(env):
+    """9,000 rays (70 full 128-row tiles and a tail of 40)."""
+    import torch
+    H, s, g, prop = env
+    w = P.Weights.random(17, scale=0.4)
+    prop.set_weights(w.flat())
+    rays = _many_rays(s, 9000, 6)
+    labels = np.random.default_rng(7).integers(-1, 4096, len(rays)).astype(np.int32)
+    loss_g, grads = prop.gradients(torch.from_numpy(rays).cuda(), torch.from_numpy(labels).cuda())
+    lo, hi = _box(s)
+    loss_o, go = P.loss_and_grads(P.Weights.from_flat(w.flat()), P.features(rays, lo, hi), labels)
+    assert loss_g == pytest.approx(loss_o, rel=2e-3)
+    gg = P.Weights.from_flat(grads)
+    for k, _ in P.Weights.SHAPES:
+        a, b = gg.a[k].ravel(), go[k].ravel()
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
+        assert rel < 3e-2 and cos > 0.999, (k, rel, cos)
+
+
+def test_gradients_reject_an_oversized_batch(env):
+    import torch
+    H, s, g, prop = env
+    rays = torch.zeros((16385, 8), dtype=torch.float32, device="cuda")
+    labels = torch.zeros(16385, dtype=torch.int32, device="cuda")
+    with pytest.raises(RuntimeError):
+        prop.gradients(rays, labels)
+
+
+def test_train_loss_covers_every_minibatch(env):
+    """A train call over 20,000 rays takes two minibatches (16,384 + 3,616).
+    With a step far below bf16 resolution the weights do not move, so the
+    reported loss is the oracle's mean loss over all labelled rays."""
+    import torch
+    H, s, g, prop = env
+    w = P.Weights.random(19, scale=0.4)
+    prop.set_weights(w.flat())
+    rays = _many_rays(s, 20_000, 8)
+    labels = np.random.default_rng(9).integers(-1, 4096, len(rays)).astype(np.int32)
+    labels[16384:] = np.where(labels[16384:] >= 0, 7, -1)   # the second minibatch differs in loss
+    loss = prop.train(torch.from_numpy(rays).cuda(), torch.from_numpy(labels).cuda(), lr=1e-20, want_loss=True)
+    lo, hi = _box(s)
+    wo = P.Weights.from_flat(w.flat())
+    total, count = 0.0, 0
+    for a in range(0, len(rays), 5000):
+        lab = labels[a:a + 5000]
+        l, _ = P.loss_and_grads(wo, P.features(rays[a:a + 5000], lo, hi), lab)
+        k = int((lab >= 0).sum())
+        total += l * k
+        count += k
+    assert loss == pytest.approx(total / count, rel=2e-3)
