@@ -332,7 +332,8 @@ typedef struct hrpp_proposal hrpp_proposal;
 hrpp_status hrpp_proposal_create(const hrpp_scene *scene, const hrpp_bvh_node *nodes, uint32_t n_nodes, uint32_t root,
                                  const uint32_t *prim_index, uint32_t n_prim_index, uint64_t seed,
                                  hrpp_proposal **out);
-/* Network inputs of n rays: bf16 [n][128] (96 features, 32 zeros), device. */
+/* Network inputs of n rays: bf16 [n][128] (96 features, 32 zeros), device;
+ * out_bf16 must be 16-byte aligned (HRPP_ERR_INVALID_ARG otherwise). */
 hrpp_status hrpp_proposal_features(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, void *out_bf16, void *stream);
 /* Training labels from closest-hit results (device): the class of the leaf
  * holding each hit's triangle, -1 for a miss. */

@@ -77,12 +77,20 @@ __device__ __forceinline__ uint32_t quantise16(float u)
     return (uint32_t)u;
 }
 
-__global__ void __launch_bounds__(128) k_featurize(const float4 *rays, uint32_t n, uint32_t npad, float lox, float loy,
-                                                   float loz, float sx, float sy, float sz,
-                                                   const __nv_bfloat16 *sin_t, __nv_bfloat16 *X, __nv_bfloat16 *XT)
+// Features of 128 rows per block.  Each thread builds its row's 128 bf16
+// inputs in shared memory; the block then writes the tile row-major (one
+// contiguous 32 KB span of X) and, when XT is given, column-major (256
+// contiguous bytes per feature), both with 16-byte stores.
+constexpr int kFeatRows = 128;
+constexpr int kFeatPitch = kIn + 8;  // bf16 elements per shared row (16-byte aligned, staggers banks)
+
+__global__ void __launch_bounds__(kFeatRows) k_featurize(const float4 *rays, uint32_t n, uint32_t npad, float lox,
+                                                         float loy, float loz, float sx, float sy, float sz,
+                                                         const __nv_bfloat16 *sin_t, __nv_bfloat16 *X,
+                                                         __nv_bfloat16 *XT)
 {
-    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= npad) return;
+    __shared__ __align__(16) __nv_bfloat16 tile[kFeatRows * kFeatPitch];
+    const uint32_t t = threadIdx.x, r0 = blockIdx.x * kFeatRows, r = r0 + t;
     uint32_t q[5] = {0, 0, 0, 0, 0};
     const bool live = r < n;
     if (live) {
@@ -101,7 +109,7 @@ __global__ void __launch_bounds__(128) k_featurize(const float4 *rays, uint32_t 
         q[3] = quantise16(__fmul_rn(__fadd_rn(ux, 1.0f), 32767.5f));
         q[4] = quantise16(__fmul_rn(__fadd_rn(uy, 1.0f), 32767.5f));
     }
-    __nv_bfloat16 *row = X + (size_t)r * kIn;
+    __nv_bfloat16 *row = tile + t * kFeatPitch;
     const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
     for (int c = 0; c < kIn; ++c) {
         __nv_bfloat16 v = zero;
@@ -118,54 +126,103 @@ __global__ void __launch_bounds__(128) k_featurize(const float4 *rays, uint32_t 
             }
         }
         row[c] = v;
-        if (XT) XT[(size_t)c * npad + r] = v;
+    }
+    __syncthreads();
+    // row-major: the tile's rows are consecutive in X
+    const uint32_t rows_here = npad - r0 < (uint32_t)kFeatRows ? npad - r0 : (uint32_t)kFeatRows;
+    uint4 *dst = reinterpret_cast<uint4 *>(X + (size_t)r0 * kIn);
+    for (uint32_t k = t; k < rows_here * (kIn / 8); k += kFeatRows) {
+        const uint32_t rr = k / (kIn / 8), cc = (k % (kIn / 8)) * 8;
+        dst[k] = *reinterpret_cast<const uint4 *>(tile + rr * kFeatPitch + cc);
+    }
+    if (!XT) return;
+    // column-major: feature c of rows r0.. is contiguous in XT
+    for (uint32_t k = t; k < kIn * (rows_here / 8); k += kFeatRows) {
+        const uint32_t c = k / (rows_here / 8), rr = (k % (rows_here / 8)) * 8;
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = tile[(rr + j) * kFeatPitch + c];
+        *reinterpret_cast<uint4 *>(XT + (size_t)c * npad + r0 + rr) = *reinterpret_cast<const uint4 *>(v);
     }
 }
 
-// softmax cross-entropy per row (one block of 256 threads per row):
-// loss summed into loss_sum, labelled rows counted, dZ = p - onehot in bf16
+// Softmax cross-entropy over 16 rows per block (8 warps, two rows each for
+// the row statistics): the loss of every labelled row is summed into
+// loss_sum and the row counted; dZ = softmax - onehot (zero for unlabelled
+// rows) is written in bf16 row-major and, through a shared-memory transpose,
+// column-major, both with 16-byte stores.
+constexpr int kSmRows = 16;
+constexpr int kSmCols = 128;  // columns per transposed chunk
+
 __global__ void __launch_bounds__(256) k_softmax_ce(const float *logits, const int32_t *labels, uint32_t n,
                                                     uint32_t npad, __nv_bfloat16 *dz, __nv_bfloat16 *dzt,
                                                     float *loss_sum, unsigned int *count)
 {
-    __shared__ float red[8];
-    const uint32_t r = blockIdx.x;
+    __shared__ float row_m[kSmRows], row_inv[kSmRows];
+    __shared__ int row_lab[kSmRows];
+    __shared__ __align__(16) __nv_bfloat16 tileT[kSmCols * (kSmRows + 8)];
+    const uint32_t r0 = blockIdx.x * kSmRows;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int lab = r < n ? labels[r] : -1;
-    const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-    if (lab < 0 || lab >= kCls) {
-        for (int c = t; c < kCls; c += 256) {
-            dz[(size_t)r * kCls + c] = zero;
-            dzt[(size_t)c * npad + r] = zero;
+    for (int k = 0; k < kSmRows / 8; ++k) {
+        const int lr = warp * (kSmRows / 8) + k;
+        const uint32_t r = r0 + lr;
+        int lab = r < n ? labels[r] : -1;
+        if (lab >= kCls) lab = -1;
+        float m = 0.0f, inv = 0.0f;
+        if (lab >= 0) {
+            const float4 *z = reinterpret_cast<const float4 *>(logits + (size_t)r * kCls);
+            m = -INFINITY;
+            for (int c = lane; c < kCls / 4; c += 32) {
+                const float4 v = z[c];
+                m = fmaxf(m, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+            }
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+            float sum = 0.0f;
+            for (int c = lane; c < kCls / 4; c += 32) {
+                const float4 v = z[c];
+                sum += expf(v.x - m) + expf(v.y - m) + expf(v.z - m) + expf(v.w - m);
+            }
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+            inv = 1.0f / sum;
+            if (lane == 0) {
+                atomicAdd(loss_sum, logf(sum) - (logits[(size_t)r * kCls + lab] - m));
+                atomicAdd(count, 1u);
+            }
         }
-        return;
+        if (lane == 0) {
+            row_m[lr] = m;
+            row_inv[lr] = inv;
+            row_lab[lr] = lab;
+        }
     }
-    const float *z = logits + (size_t)r * kCls;
-    float m = -INFINITY;
-    for (int c = t; c < kCls; c += 256) m = fmaxf(m, z[c]);
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
-    if (lane == 0) red[warp] = m;
     __syncthreads();
-    m = red[0];
-    for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
-    __syncthreads();
-    float s = 0.0f;
-    for (int c = t; c < kCls; c += 256) s += expf(z[c] - m);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-    if (lane == 0) red[warp] = s;
-    __syncthreads();
-    s = 0.0f;
-    for (int w = 0; w < 8; ++w) s += red[w];
-    const float inv = 1.0f / s;
-    for (int c = t; c < kCls; c += 256) {
-        float g = expf(z[c] - m) * inv - (c == lab ? 1.0f : 0.0f);
-        const __nv_bfloat16 h = __float2bfloat16_rn(g);
-        dz[(size_t)r * kCls + c] = h;
-        dzt[(size_t)c * npad + r] = h;
-    }
-    if (t == 0) {
-        atomicAdd(loss_sum, logf(s) - (z[lab] - m));
-        atomicAdd(count, 1u);
+    const int lr = t >> 4, cg = (t & 15) * 8;  // this thread's row and 8 columns within a chunk
+    const uint32_t r = r0 + lr;
+    const float m = row_m[lr], inv = row_inv[lr];
+    const int lab = row_lab[lr];
+    for (int c0 = 0; c0 < kCls; c0 += kSmCols) {
+        __align__(16) __nv_bfloat16 g[8];
+        if (lab >= 0) {
+            const float4 *z = reinterpret_cast<const float4 *>(logits + (size_t)r * kCls + c0 + cg);
+            const float4 a = z[0], b = z[1];
+            const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                g[j] = __float2bfloat16_rn(expf(v[j] - m) * inv - (c0 + cg + j == lab ? 1.0f : 0.0f));
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) g[j] = __float2bfloat16_rn(0.0f);
+        }
+        *reinterpret_cast<uint4 *>(dz + (size_t)r * kCls + c0 + cg) = *reinterpret_cast<const uint4 *>(g);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) tileT[(cg + j) * (kSmRows + 8) + lr] = g[j];
+        __syncthreads();
+        {
+            const int cc = t >> 1, h = (t & 1) * 8;  // column and half of the 16 rows
+            *reinterpret_cast<uint4 *>(dzt + (size_t)(c0 + cc) * npad + r0 + h) =
+                *reinterpret_cast<const uint4 *>(tileT + cc * (kSmRows + 8) + h);
+        }
+        __syncthreads();
     }
 }
 
@@ -345,7 +402,7 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     cudaError_t e;
     __nv_bfloat16 *X = argmax ? p->Xi : p->X, *H1 = argmax ? p->H1i : p->H1, *H2 = argmax ? p->H2i : p->H2;
     unsigned long long *amax = argmax ? p->amaxi : p->amax;
-    k_featurize<<<(npad + 127) / 128, 128, 0, s>>>(reinterpret_cast<const float4 *>(rays), n, npad, p->lo[0],
+    k_featurize<<<npad / kFeatRows, kFeatRows, 0, s>>>(reinterpret_cast<const float4 *>(rays), n, npad, p->lo[0],
                                                     p->lo[1], p->lo[2], p->scale[0], p->scale[1], p->scale[2],
                                                     p->sin_t, X, train ? p->XT : nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -375,7 +432,7 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
         (e = cudaMemsetAsync(p->count, 0, sizeof(unsigned int), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->grad, 0, sizeof(float) * kMaster, s)) != cudaSuccess)
         return e;
-    k_softmax_ce<<<npad, 256, 0, s>>>(p->logits, p->lab, n, npad, p->dZ3, p->dZ3T, p->loss_sum, p->count);
+    k_softmax_ce<<<npad / kSmRows, 256, 0, s>>>(p->logits, p->lab, n, npad, p->dZ3, p->dZ3T, p->loss_sum, p->count);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // dW3 = dZ3^T H2
     g = args(kCls, kHid, (int)npad, p);
@@ -590,9 +647,10 @@ hrpp_status hrpp_proposal_create(const hrpp_scene *sc, const hrpp_bvh_node *node
 hrpp_status hrpp_proposal_features(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, void *out_bf16, void *stream)
 {
     if (!p || (n && (!rays || !out_bf16))) return pfail(HRPP_ERR_INVALID_ARG, "NULL argument");
+    if (reinterpret_cast<uintptr_t>(out_bf16) % 16) return pfail(HRPP_ERR_INVALID_ARG, "out_bf16 not 16-byte aligned");
     Dev dv(p->device);
     if (n == 0) return HRPP_OK;
-    k_featurize<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
+    k_featurize<<<(n + kFeatRows - 1) / kFeatRows, kFeatRows, 0, (cudaStream_t)stream>>>(
         reinterpret_cast<const float4 *>(rays), n, n, p->lo[0], p->lo[1], p->lo[2], p->scale[0], p->scale[1],
         p->scale[2], p->sin_t, static_cast<__nv_bfloat16 *>(out_bf16), nullptr);
     cudaError_t e = cudaGetLastError();
