@@ -143,7 +143,16 @@ typedef struct hrpp_scene_info {
  *                             ray is done take new rays while the rest of
  *                             the warp keeps traversing)
  *   refill_min                REFILL: idle lanes needed before a warp refills,
- *                             1..32 (0 = default) */
+ *                             1..32 (0 = default)
+ *   max_steps                 node visits allowed per traversal (0 = the
+ *                             default, interior nodes + leaves + 8, which a
+ *                             traversal of a valid tree never reaches; larger
+ *                             values are clamped to it).  A ray that runs out
+ *                             keeps its best hit so far and sets the scene's
+ *                             error flag: the call returns
+ *                             HRPP_ERR_TRAVERSAL_LIMIT when it synchronises
+ *                             (host stats), else the next hrpp_scene_check
+ *                             does.  For failure-detection tests. */
 #define HRPP_SCHEDULE_DEFAULT 0u
 #define HRPP_SCHEDULE_BATCH 1u
 #define HRPP_SCHEDULE_REFILL 2u
@@ -156,7 +165,8 @@ typedef struct hrpp_trace_opts {
     uint32_t block_threads;
     uint32_t schedule;
     uint32_t refill_min;
-    uint32_t reserved[3];
+    uint32_t max_steps;
+    uint32_t reserved[2];
 } hrpp_trace_opts;
 
 typedef struct hrpp_scene hrpp_scene;

@@ -608,6 +608,7 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         p.n_tris = sc->n_tris;
         p.root_ref = sc->root_ref;
         p.max_steps = sc->n_interior + sc->n_leaves + 8u;
+        if (opts && opts->max_steps > 0u && opts->max_steps < p.max_steps) p.max_steps = opts->max_steps;
         p.rays = reinterpret_cast<const float4 *>(d_rays);
         p.n_rays = n_rays;
         p.hits = d_hits;

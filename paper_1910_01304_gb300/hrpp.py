@@ -45,7 +45,8 @@ class hrpp_scene_info(ctypes.Structure):
 class hrpp_trace_opts(ctypes.Structure):
     _fields_ = [("kernel_start", ctypes.c_void_p), ("kernel_stop", ctypes.c_void_p),
                 ("predicted_nodes", ctypes.c_void_p), ("block_threads", ctypes.c_uint32),
-                ("schedule", ctypes.c_uint32), ("refill_min", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("schedule", ctypes.c_uint32), ("refill_min", ctypes.c_uint32), ("max_steps", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 HRPP_SCHEDULE_DEFAULT, HRPP_SCHEDULE_BATCH, HRPP_SCHEDULE_REFILL = 0, 1, 2
@@ -280,7 +281,7 @@ class Table:
 
 def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, stats: bool = False,
           stream=None, kernel_events=None, block_threads: int = 0, schedule: int = 0, refill_min: int = 0,
-          predicted=None):
+          predicted=None, max_steps: int = 0):
     """Traces rays ([n, 8] float32 torch tensor on the GPU, or a host numpy
     array / torch tensor).  Returns (hits, stats dict or None).
 
@@ -298,7 +299,7 @@ def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, 
             hits = torch.empty(shape, dtype=dtype, device=rays.device)
     st = hrpp_stats() if stats else None
     opts = None
-    if kernel_events is not None or block_threads or schedule or refill_min or predicted is not None:
+    if kernel_events is not None or block_threads or schedule or refill_min or max_steps or predicted is not None:
         opts = hrpp_trace_opts()
         if predicted is not None:
             opts.predicted_nodes = _ptr(predicted)
@@ -308,6 +309,7 @@ def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, 
         opts.block_threads = block_threads
         opts.schedule = schedule
         opts.refill_min = refill_min
+        opts.max_steps = max_steps
     check(hrpp_trace_ex(scene.handle, table.handle if table is not None else None, _ptr(rays), n, mode, _ptr(hits),
                         ctypes.byref(st) if st is not None else None, _stream_handle(stream),
                         ctypes.byref(opts) if opts is not None else None))

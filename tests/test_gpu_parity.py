@@ -293,3 +293,31 @@ def test_go_up_mid_terrain_bvh4(H):
         assert_same_hits(O.ANY_HIT, gh, oh)
         assert_same_stats(gst, ost)
         assert np.array_equal(tab.export(), otab.words)
+
+
+@pytest.mark.parametrize("width_idx", [0, 1])
+def test_step_budget_reports_traversal_limit(H, small_pair, width_idx):
+    """Failure detection without a fault: a per-traversal step budget far
+    below what the rays need stops them early.  The kernel's bounded loop sets
+    the scene's device flag; the host sees HRPP_ERR_TRAVERSAL_LIMIT (from
+    hrpp_scene_check, or from the call itself when it synchronises for host
+    stats), the flag is cleared, and the scene then traces exactly."""
+    import torch
+    s, g = small_pair[width_idx]
+    rays_np = s.primary_rays(frame=1)
+    rays = torch.from_numpy(rays_np).cuda()
+    H.trace(g, rays, H.HRPP_CLOSEST_HIT, max_steps=2)
+    with pytest.raises(H.HrppError) as err:
+        g.check()
+    assert err.value.status == H.HRPP_ERR_TRAVERSAL_LIMIT
+    g.check()  # cleared
+    with pytest.raises(H.HrppError) as err:
+        H.trace(g, rays, H.HRPP_ANY_HIT, stats=True, max_steps=1)
+    assert err.value.status == H.HRPP_ERR_TRAVERSAL_LIMIT
+    g.check()
+    # a budget the rays never reach changes nothing
+    oh, ost = _oracle(s, rays_np, O.CLOSEST_HIT)
+    gh, gst = H.trace(g, rays, H.HRPP_CLOSEST_HIT, stats=True, max_steps=1_000_000)
+    torch.cuda.synchronize()
+    assert_same_hits(O.CLOSEST_HIT, gh.cpu().numpy(), oh)
+    assert_same_stats(gst, ost)
