@@ -23,6 +23,7 @@ _lib = None
 
 ANY_HIT, CLOSEST_HIT = 0, 1
 TWO_PHASE, SEQUENTIAL, UNBOUNDED = 0, 1, 2
+VERIFY_ROOT, VERIFY_BOTTOM_UP = 0, 1
 NO_HIT = 0xFFFFFFFF
 EMPTY_WORD = 0xFFFFFFFFFFFFFFFF
 TAG_BITS, LEAF_BITS = 36, 28
@@ -71,7 +72,7 @@ def _L():
                 "orc_ray_inverse": (None, [P, P, P]),
                 "orc_ray_box": (i32, [P, P, f32, f32, P, P, P]),
                 "orc_brute": (None, [P, u32, P, u32, i32, P, P]),
-                "orc_trace": (i32, [ctypes.POINTER(_Scene), P, u32, i32, ctypes.POINTER(_Table), P, P, P, P, P]),
+                "orc_trace": (i32, [ctypes.POINTER(_Scene), P, u32, i32, ctypes.POINTER(_Table), P, P, P, P, P, i32]),
                 "orc_unbounded_size": (None, [ctypes.POINTER(_Table), P, P]),
                 "orc_unbounded_free": (None, [ctypes.POINTER(_Table)]),
             }
@@ -206,10 +207,13 @@ class Table:
 # ---------------------------------------------------------------- trace --
 
 def trace(tris, nodes, prim_index, root, rays, mode: int, table: Table | None = None, per_ray: bool = False,
-          predicted=None):
+          predicted=None, verify: int = 0):
     """Plain traversal (table None) or HRPP against `table` (mutated).
     predicted: optional int32 [n] canonical node per ray whose subtree is
     traversed first (learned proposal; -1 = none).
+    verify: how closest-hit true positives are verified, VERIFY_ROOT (a
+    traversal from the root bounded by the predicted hit) or VERIFY_BOTTOM_UP
+    (a climb from the predicted hit's leaf through its ancestors' siblings).
 
     Returns (hits, stats dict[, outcome uint8[n], box_tests uint32[n]])."""
     tris = _f(tris).reshape(-1, 9)
@@ -227,7 +231,7 @@ def trace(tris, nodes, prim_index, root, rays, mode: int, table: Table | None = 
     tptr = ctypes.byref(table._c) if table is not None else None
     pred = None if predicted is None else np.ascontiguousarray(predicted, np.int32)
     rc = _L().orc_trace(ctypes.byref(sc), _p(rays), n, mode, tptr, _p(out), _p(stats), _p(outcome), _p(boxes),
-                        _p(pred))
+                        _p(pred), int(verify))
     if rc != 0:
         raise RuntimeError("orc_trace failed")
     sd = {k: int(stats[i]) for i, k in enumerate(STAT_NAMES)}

@@ -38,6 +38,11 @@
  *                                    on a true positive, else traverse and
  *                                    insert the leaf reached (Sec. 5: no
  *                                    duplicate nodes per entry).
+ *   verify_bottom_up                 exact verification of a closest-hit true
+ *                                    positive by climbing from the predicted
+ *                                    hit's leaf and traversing the siblings
+ *                                    met on the way (the alternative to a
+ *                                    bounded traversal from the root).
  */
 #include <math.h>
 #include <stdint.h>
@@ -62,6 +67,10 @@ typedef struct {
 
 enum { ORC_ANY = 0, ORC_CLOSEST = 1 };
 enum { ORC_TWO_PHASE = 0, ORC_SEQUENTIAL = 1, ORC_UNBOUNDED = 2 };
+/* how a closest-hit true positive is verified: a traversal from the root
+ * bounded by the predicted hit, or a climb from the predicted leaf testing
+ * the siblings on the way up */
+enum { ORC_VERIFY_ROOT = 0, ORC_VERIFY_BOTTOM_UP = 1 };
 
 typedef struct {
     uint64_t *words;  /* 2^log2_sets * 2^log2_ways table words (bounded modes) */
@@ -306,22 +315,52 @@ typedef struct {
 static const counter_set MAIN_COUNTERS = {S_INTERIOR, S_BOX_TESTS, S_LEAVES, S_TRI_TESTS};
 static const counter_set PRED_COUNTERS = {S_PRED_INTERIOR, S_PRED_BOX_TESTS, S_PRED_LEAVES, S_PRED_TRI_TESTS};
 
-/* Stack traversal of the subtree under `start` (the root for the main
- * traversal).  Interior nodes test each child's box with the current bound
- * (the ray's tmax, or the best hit so far in closest mode); children that are
- * hit are visited nearest first, ordered by (entry t, slot).  Returns 1 if
- * the best hit changed during this traversal. */
-static int traverse_from(const orc_scene *sc, uint32_t start, const float *ray, int mode, best_hit *b,
-                         workspace *ws, uint64_t *st, counter_set cs, uint32_t *box_tests_out)
+/* Tests the boxes of interior node n's children (all but the child `skip`;
+ * -1 skips none) against [tmin, tcur] and pushes the hit ones so that the
+ * nearest, by (entry t, slot), is popped first.  Returns the box tests made. */
+static uint32_t push_children(const orc_scene *sc, const orc_node *n, int32_t skip, const float *inv,
+                              const float *oinv, const float *ray, float tcur, workspace *ws, uint32_t *sp)
 {
-    float inv[3], oinv[3];
-    orc_ray_inverse(ray, inv, oinv);
-    uint32_t sp = 0;
-    ws->stack[sp++] = start;
-    int changed = 0;
+    float tn[4];
+    int slot[4], cnt = 0;
     uint32_t box_tests = 0;
-    while (sp > 0) {
-        const orc_node *n = &sc->nodes[ws->stack[--sp]];
+    for (int s = 0; s < 4; ++s) {
+        if (n->child[s] < 0 || n->child[s] == skip) continue;
+        const orc_node *c = &sc->nodes[n->child[s]];
+        box_tests += 1;
+        float t;
+        if (orc_ray_box(inv, oinv, ray[3], tcur, c->lo, c->hi, &t)) {
+            tn[cnt] = t;
+            slot[cnt] = s;
+            ++cnt;
+        }
+    }
+    /* insertion sort by (tn, slot); slots arrive ascending */
+    for (int i = 1; i < cnt; ++i) {
+        float kt = tn[i];
+        int ks = slot[i], j = i - 1;
+        while (j >= 0 && (tn[j] > kt || (tn[j] == kt && slot[j] > ks))) {
+            tn[j + 1] = tn[j];
+            slot[j + 1] = slot[j];
+            --j;
+        }
+        tn[j + 1] = kt;
+        slot[j + 1] = ks;
+    }
+    for (int i = cnt - 1; i >= 0; --i) ws->stack[(*sp)++] = (uint32_t)n->child[slot[i]];
+    return box_tests;
+}
+
+/* Runs the stack until it is empty (or an any-hit ray is answered): leaves
+ * test their triangles, interior nodes push their hit children with the
+ * current bound (the ray's tmax, or the best hit so far in closest mode).
+ * Returns 1 if the best hit changed. */
+static int run_stack(const orc_scene *sc, const float *ray, const float *inv, const float *oinv, int mode,
+                     best_hit *b, workspace *ws, uint32_t *sp, uint64_t *st, counter_set cs, uint32_t *box_tests)
+{
+    int changed = 0;
+    while (*sp > 0) {
+        const orc_node *n = &sc->nodes[ws->stack[--(*sp)]];
         if (n->count > 0) {
             st[cs.leaves] += 1;
             best_hit before = *b;
@@ -332,33 +371,22 @@ static int traverse_from(const orc_scene *sc, uint32_t start, const float *ray, 
         }
         st[cs.interior] += 1;
         float tcur = (mode == ORC_CLOSEST && b->found) ? b->t : ray[7];
-        float tn[4];
-        int slot[4], cnt = 0;
-        for (int s = 0; s < 4; ++s) {
-            if (n->child[s] < 0) continue;
-            const orc_node *c = &sc->nodes[n->child[s]];
-            box_tests += 1;
-            float t;
-            if (orc_ray_box(inv, oinv, ray[3], tcur, c->lo, c->hi, &t)) {
-                tn[cnt] = t;
-                slot[cnt] = s;
-                ++cnt;
-            }
-        }
-        /* insertion sort by (tn, slot); slots arrive ascending */
-        for (int i = 1; i < cnt; ++i) {
-            float kt = tn[i];
-            int ks = slot[i], j = i - 1;
-            while (j >= 0 && (tn[j] > kt || (tn[j] == kt && slot[j] > ks))) {
-                tn[j + 1] = tn[j];
-                slot[j + 1] = slot[j];
-                --j;
-            }
-            tn[j + 1] = kt;
-            slot[j + 1] = ks;
-        }
-        for (int i = cnt - 1; i >= 0; --i) ws->stack[sp++] = (uint32_t)n->child[slot[i]];
+        *box_tests += push_children(sc, n, -1, inv, oinv, ray, tcur, ws, sp);
     }
+    return changed;
+}
+
+/* Stack traversal of the subtree under `start` (the root for the main
+ * traversal), children that are hit visited nearest first, ordered by
+ * (entry t, slot).  Returns 1 if the best hit changed during this traversal. */
+static int traverse_from(const orc_scene *sc, uint32_t start, const float *ray, int mode, best_hit *b,
+                         workspace *ws, uint64_t *st, counter_set cs, uint32_t *box_tests_out)
+{
+    float inv[3], oinv[3];
+    orc_ray_inverse(ray, inv, oinv);
+    uint32_t sp = 0, box_tests = 0;
+    ws->stack[sp++] = start;
+    int changed = run_stack(sc, ray, inv, oinv, mode, b, ws, &sp, st, cs, &box_tests);
     st[cs.box_tests] += box_tests;
     if (box_tests_out) *box_tests_out = box_tests;
     return changed;
@@ -436,6 +464,36 @@ static int64_t predicted_node(const orc_scene *sc, const tree_info *t, uint32_t 
     n = t->parent[n];
     for (int g = 1; g < go_up && t->parent[n] >= 0; ++g) n = t->parent[n];
     return t->rank[n];
+}
+
+/* Bottom-up verification of a closest-hit true positive (the exact
+ * alternative to re-traversing from the root, Sec. 4.3 / Sec. 6.2): from the
+ * leaf holding the best hit so far, climb to the root; at each ancestor, test
+ * the boxes of its children other than the one the climb came from against
+ * [tmin, best t] and traverse the hit ones nearest first, as the main
+ * traversal would.  Every leaf but the starting one lies under exactly one
+ * of those siblings, so the final hit is the plain closest hit.  Counts the
+ * ancestors as interior nodes and their sibling boxes as box tests.  Returns
+ * 1 if the best hit changed. */
+static int verify_bottom_up(const orc_scene *sc, const tree_info *t, const float *ray, best_hit *b, workspace *ws,
+                            uint64_t *st, uint32_t *box_tests_out)
+{
+    float inv[3], oinv[3];
+    orc_ray_inverse(ray, inv, oinv);
+    int32_t from = t->leaf_at[b->leaf >> 2];
+    int32_t a = from >= 0 ? t->parent[from] : -1;
+    uint32_t sp = 0, box_tests = 0;
+    int changed = 0;
+    while (a >= 0) {
+        st[S_INTERIOR] += 1;
+        box_tests += push_children(sc, &sc->nodes[a], from, inv, oinv, ray, b->t, ws, &sp);
+        changed |= run_stack(sc, ray, inv, oinv, ORC_CLOSEST, b, ws, &sp, st, MAIN_COUNTERS, &box_tests);
+        from = a;
+        a = t->parent[a];
+    }
+    st[S_BOX_TESTS] += box_tests;
+    if (box_tests_out) *box_tests_out = box_tests;
+    return changed;
 }
 
 /* ------------------------------------------------------- unbounded map -- */
@@ -553,7 +611,7 @@ static const orc_node *find_leaf(const orc_scene *sc, uint32_t leaf)
  * each ray's traversal made.  Returns 0, or 1 on bad arguments / no memory.
  */
 int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode, orc_table *tab, void *out,
-              uint64_t *stats, uint8_t *outcome, uint32_t *ray_box_tests, const int32_t *predicted)
+              uint64_t *stats, uint8_t *outcome, uint32_t *ray_box_tests, const int32_t *predicted, int verify)
 {
     if (!sc || (!rays && n_rays) || (!out && n_rays) || !stats) return 1;
     workspace ws;
@@ -654,7 +712,11 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
         }
         if (run_traversal) {
             best_hit pred = b;
-            int changed = traverse(sc, ray, mode, &b, &ws, stats, ray_box_tests ? &ray_box_tests[i] : NULL);
+            int changed;
+            if (verify == ORC_VERIFY_BOTTOM_UP && mode == ORC_CLOSEST && oc == OUT_TRUE_POS)
+                changed = verify_bottom_up(sc, &ti, ray, &b, &ws, stats, ray_box_tests ? &ray_box_tests[i] : NULL);
+            else
+                changed = traverse(sc, ray, mode, &b, &ws, stats, ray_box_tests ? &ray_box_tests[i] : NULL);
             if (oc == OUT_TRUE_POS && changed && (b.prim != pred.prim || b.t != pred.t)) stats[S_TP_INEXACT] += 1;
             int64_t node = (tab && b.found) ? predicted_node(sc, &ti, b.leaf, go_up) : -1;
             if (node >= 0) {

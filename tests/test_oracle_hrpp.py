@@ -306,3 +306,132 @@ def test_predicted_leaf_of_the_hit_is_a_true_positive(small):
     bad = np.full(len(rays), len(small.nodes) + 5, np.int32)
     _, sb = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.ANY_HIT, predicted=bad)
     assert sb["positives"] == 0
+
+
+# ---------------------------------------------- bottom-up verification --
+
+def _tree(nodes, root):
+    """Parent and depth of every node under root, from a walk of the node
+    array written here (independent of the oracle's own tree walk)."""
+    parent, depth = {}, {int(root): 0}
+    stack = [int(root)]
+    while stack:
+        i = stack.pop()
+        for c in nodes[i]["child"]:
+            if c >= 0:
+                parent[int(c)] = i
+                depth[int(c)] = depth[i] + 1
+                stack.append(int(c))
+    return parent, depth
+
+
+def _leaf_nodes(nodes, prim_index):
+    m = {}
+    for i, n in enumerate(nodes):
+        if n["count"] > 0:
+            for j in range(int(n["count"])):
+                m[int(prim_index[n["first"] + j])] = i
+    return m
+
+
+_MOVED = ("interior_nodes", "box_tests", "leaves", "tri_tests")
+
+
+@pytest.mark.parametrize("scene", ["small", "small4"])
+def test_bottom_up_saves_exactly_the_climb_path(scene, request):
+    """With the leaf of each ray's closest hit predicted, root verification
+    and the climb visit the same sibling subtrees under the same bound: the
+    climb makes one box test fewer per ancestor of the leaf (the child it came
+    from), does not test the predicted leaf again, and visits the same
+    interior nodes."""
+    s = request.getfixturevalue(scene)
+    rays = s.primary_rays()[::7]
+    hp, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, O.CLOSEST_HIT)
+    leaf = _leaf_nodes(s.nodes, s.prim_index)
+    _, depth = _tree(s.nodes, s.root)
+    hit = np.nonzero(hp["prim"] != O.NO_HIT)[0]
+    assert len(hit) > 100
+    for k in hit[:160]:
+        lf = leaf[int(hp["prim"][k])]
+        pred = np.array([lf], np.int32)
+        r = rays[k:k + 1]
+        hr, sr = O.trace(s.tris, s.nodes, s.prim_index, s.root, r, O.CLOSEST_HIT, predicted=pred,
+                         verify=O.VERIFY_ROOT)
+        hb, sb = O.trace(s.tris, s.nodes, s.prim_index, s.root, r, O.CLOSEST_HIT, predicted=pred,
+                         verify=O.VERIFY_BOTTOM_UP)
+        assert hr.tobytes() == hb.tobytes() == hp[k:k + 1].tobytes()
+        assert sb["true_pos"] == sr["true_pos"] == 1 and sb["tp_inexact"] == sr["tp_inexact"] == 0
+        assert sr["interior_nodes"] == sb["interior_nodes"]
+        assert sr["box_tests"] - sb["box_tests"] == depth[lf]
+        assert sr["leaves"] - sb["leaves"] == 1
+        assert sr["tri_tests"] - sb["tri_tests"] == int(s.nodes[lf]["count"])
+        for key in sr:
+            if key not in _MOVED:
+                assert sr[key] == sb[key], key
+
+
+@pytest.mark.parametrize("scene", ["small", "small4"])
+@pytest.mark.parametrize("go_up", [0, 1])
+@pytest.mark.parametrize("ways", [1, 4])
+def test_bottom_up_keeps_results_and_table(scene, go_up, ways, request):
+    """Over frames with a table, the climb returns exactly the plain hits and
+    leaves the table and every predictor counter as root verification does
+    (inserts depend only on the final hit); only traversal work moves, and
+    it never grows."""
+    s = request.getfixturevalue(scene)
+    tr = O.Table(10, ways, 6, O.TWO_PHASE, go_up=go_up)
+    tb = O.Table(10, ways, 6, O.TWO_PHASE, go_up=go_up)
+    for frame in range(3):
+        rays = s.primary_rays(frame=frame)[::2]
+        hp, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, O.CLOSEST_HIT)
+        hr, sr = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, O.CLOSEST_HIT, tr, verify=O.VERIFY_ROOT)
+        hb, sb = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, O.CLOSEST_HIT, tb,
+                         verify=O.VERIFY_BOTTOM_UP)
+        assert hp.tobytes() == hr.tobytes() == hb.tobytes()
+        assert np.array_equal(tr.words, tb.words)
+        for key in sr:
+            if key not in _MOVED:
+                assert sr[key] == sb[key], (frame, key)
+        assert sb["box_tests"] <= sr["box_tests"]
+        if frame > 0:
+            assert sb["true_pos"] > 0 and sb["box_tests"] < sr["box_tests"]
+
+
+def test_bottom_up_finds_a_closer_hit(small):
+    """Predicting the leaf of a ray's second-nearest hit (a farther leaf):
+    the climb must still return the nearest hit, and counts the ray as an
+    inexact true positive, like root verification."""
+    s = small
+    rays = s.primary_rays()[::3]
+    h1, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, O.CLOSEST_HIT)
+    beyond = rays.copy()
+    beyond[:, 3] = h1["t"]                      # open interval: only hits past the first
+    h2, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, beyond, O.CLOSEST_HIT)
+    leaf = _leaf_nodes(s.nodes, s.prim_index)
+    two = (h1["prim"] != O.NO_HIT) & (h2["prim"] != O.NO_HIT)
+    pick = [k for k in np.nonzero(two)[0] if leaf[int(h1["prim"][k])] != leaf[int(h2["prim"][k])]]
+    assert len(pick) > 50
+    r = rays[pick]
+    pred = np.array([leaf[int(h2["prim"][k])] for k in pick], np.int32)
+    for verify in (O.VERIFY_ROOT, O.VERIFY_BOTTOM_UP):
+        hh, st = O.trace(s.tris, s.nodes, s.prim_index, s.root, r, O.CLOSEST_HIT, predicted=pred, verify=verify)
+        assert hh.tobytes() == h1[pick].tobytes()
+        assert st["true_pos"] == len(pick) and st["tp_inexact"] == len(pick)
+
+
+def test_bottom_up_on_a_root_leaf_scene():
+    """A tree that is one leaf has nothing to climb: the predicted leaf's
+    test is the whole answer."""
+    from paper_1910_01304_gb300 import scenes as S
+    tris = S.soup(3, 2, 0, 1, 0.5)
+    nodes, prim, root = S.build_bvh(tris)
+    assert nodes[root]["count"] > 0
+    rays = S.sphere_rays(300, 1, -0.5, 1.5)
+    hp, _ = O.trace(tris, nodes, prim, root, rays, O.CLOSEST_HIT)
+    pred = np.full(len(rays), root, np.int32)
+    hb, sb = O.trace(tris, nodes, prim, root, rays, O.CLOSEST_HIT, predicted=pred, verify=O.VERIFY_BOTTOM_UP)
+    assert hp.tobytes() == hb.tobytes()
+    n_hit = int((hp["prim"] != O.NO_HIT).sum())
+    assert n_hit > 0 and sb["true_pos"] == n_hit
+    assert sb["box_tests"] == 0 and sb["interior_nodes"] == 0
+    assert sb["leaves"] == len(rays) - n_hit      # only false positives traverse (the root leaf)
