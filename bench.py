@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--ways", type=int, default=2)
     ap.add_argument("--precision", type=int, default=6)
     ap.add_argument("--update", default="two_phase", choices=["two_phase", "online"])
+    ap.add_argument("--verify", default="root", choices=["root", "bottom_up"],
+                    help="how closest-hit true positives are verified")
     ap.add_argument("--quads", type=int, default=708)
     ap.add_argument("--spheres", type=int, default=64)
     ap.add_argument("--res", default="1920x1080")
@@ -585,6 +587,8 @@ def main():
         if pg is not None:
             pg.barrier()
 
+    verify = H.HRPP_VERIFY_BOTTOM_UP if args.verify == "bottom_up" else H.HRPP_VERIFY_ROOT
+
     def run(steps, warm, tables, events=None, offset=0):
         total = 0
         for k in range(steps):
@@ -592,7 +596,7 @@ def main():
             f = frames[fi]
             ev = events[k] if events is not None else (None, None)
             H.trace(g, f["prim"], H.HRPP_CLOSEST_HIT, tables[0], hits=out_c[fi],
-                    kernel_events=ev[0] if ev[0] else None)
+                    kernel_events=ev[0] if ev[0] else None, verify=verify)
             H.trace(g, f["ao"], H.HRPP_ANY_HIT, tables[1], hits=out_a[fi], kernel_events=ev[1] if ev[1] else None)
             total += rays_per_frame[fi]
         return total
@@ -649,7 +653,7 @@ def main():
 
     # --- counters for one frame (after the timed region: warm tables)
     f0 = frames[0]
-    _, sc = H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tab_c, stats=True)
+    _, sc = H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tab_c, stats=True, verify=verify)
     _, sa = H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tab_a, stats=True)
     _, pc = H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, None, stats=True)
     _, pa = H.trace(g, f0["ao"], H.HRPP_ANY_HIT, None, stats=True)
@@ -667,7 +671,7 @@ def main():
             host.append((hp, ha, oc, oa))
         def e2e_step(k):
             hp, ha, oc, oa = host[k % len(host)]
-            H.trace(g, hp, H.HRPP_CLOSEST_HIT, tab_c, hits=oc)
+            H.trace(g, hp, H.HRPP_CLOSEST_HIT, tab_c, hits=oc, verify=verify)
             H.trace(g, ha, H.HRPP_ANY_HIT, tab_a, hits=oa)
             return hp.shape[0] + ha.shape[0], hp.numel() * 4 + ha.numel() * 4, oc.numel() * 4 + oa.numel() * 4
         for k in range(args.warmup):
@@ -715,7 +719,7 @@ def main():
         "config": {"workload": WORKLOAD, "tris": int(sw.n_tris), "bvh_width": width,
                    "rays_per_step": float(np.mean(rays_per_frame)), "frames": args.frames,
                    "table": {"log2_entries": args.log2_entries, "ways": args.ways, "precision": args.precision,
-                             "update": args.update},
+                             "update": args.update, "verify": args.verify},
                    "l2": f"inputs larger than L2: {np.mean(rays_per_frame) * 32 / 1e6:.0f} MB of rays per step, "
                          f"{args.frames} frames cycled; scene resident"},
         "plain": {"value": p_value, "unit": "Mrays/s", "speedup_hrpp_over_plain": value / p_value,

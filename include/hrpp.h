@@ -152,10 +152,25 @@ typedef struct hrpp_scene_info {
  *                             error flag: the call returns
  *                             HRPP_ERR_TRAVERSAL_LIMIT when it synchronises
  *                             (host stats), else the next hrpp_scene_check
- *                             does.  For failure-detection tests. */
+ *                             does.  For failure-detection tests.
+ *   verify                    how a closest-hit true positive proves that no
+ *                             closer hit exists (Sec. 4.3 admits the
+ *                             unverified prediction can be wrong):
+ *                             HRPP_VERIFY_ROOT (default) traverses from the
+ *                             root bounded by the predicted hit;
+ *                             HRPP_VERIFY_BOTTOM_UP climbs from the predicted
+ *                             hit's leaf to the root, testing at each ancestor
+ *                             only the children off the climb's path and
+ *                             traversing those hit, bounded by the best hit.
+ *                             Both return exactly the plain closest hit and
+ *                             leave the same table; the climb skips one box
+ *                             test per level and the predicted leaf's
+ *                             re-test.  Other values: HRPP_ERR_INVALID_ARG. */
 #define HRPP_SCHEDULE_DEFAULT 0u
 #define HRPP_SCHEDULE_BATCH 1u
 #define HRPP_SCHEDULE_REFILL 2u
+#define HRPP_VERIFY_ROOT 0u
+#define HRPP_VERIFY_BOTTOM_UP 1u
 typedef struct hrpp_trace_opts {
     void *kernel_start, *kernel_stop;
     const int32_t *predicted_nodes;  /* device, one canonical node index per ray
@@ -166,7 +181,8 @@ typedef struct hrpp_trace_opts {
     uint32_t schedule;
     uint32_t refill_min;
     uint32_t max_steps;
-    uint32_t reserved[2];
+    uint32_t verify;
+    uint32_t reserved[1];
 } hrpp_trace_opts;
 
 typedef struct hrpp_scene hrpp_scene;

@@ -245,6 +245,19 @@ hrpp_status hrpp_scene_create(const float *tri_verts, uint32_t n_tris, const hrp
         if (n.count > 0) return (int32_t)~leaf_id(n);
         return dev_index[c];
     };
+    // parent links for the Go Up Level (Sec. 6.2) and bottom-up verification:
+    // interior node -> parent (also kept in the node's spare word), and a
+    // leaf's first prim_index slot -> the leaf's parent (-1 at the root)
+    std::vector<int32_t> h_parent(std::max<size_t>(1, v.order.size()), -1), h_leaf_parent(n_tris, -1);
+    for (uint32_t k = 0; k < v.order.size(); ++k) {
+        const hrpp_bvh_node &n = nodes[v.order[k]];
+        for (int q = 0; q < 4; ++q) {
+            const int32_t c = n.child[q];
+            if (c == -1) continue;
+            if (nodes[c].count > 0) h_leaf_parent[nodes[c].first] = (int32_t)k;
+            else h_parent[dev_index[c]] = (int32_t)k;
+        }
+    }
     const size_t f4_per_node = width == 2 ? 4 : 8;
     std::vector<float4> h_nodes(std::max<size_t>(1, v.order.size() * f4_per_node));
     for (uint32_t k = 0; k < v.order.size(); ++k) {
@@ -264,7 +277,7 @@ hrpp_status hrpp_scene_create(const float *tri_verts, uint32_t n_tris, const hrp
             d[0] = make_float4(b0->lo[0], b0->hi[0], b0->lo[1], b0->hi[1]);
             d[1] = make_float4(b1->lo[0], b1->hi[0], b1->lo[1], b1->hi[1]);
             d[2] = make_float4(b0->lo[2], b0->hi[2], b1->lo[2], b1->hi[2]);
-            int4 c = make_int4(refs[0], refs[1], 0, 0);
+            int4 c = make_int4(refs[0], refs[1], h_parent[k], 0);
             memcpy(&d[3], &c, sizeof c);
         } else {
             float lo[3][4], hi[3][4];
@@ -279,7 +292,8 @@ hrpp_status hrpp_scene_create(const float *tri_verts, uint32_t n_tris, const hrp
             }
             int4 c = make_int4(refs[0], refs[1], refs[2], refs[3]);
             memcpy(&d[6], &c, sizeof c);
-            d[7] = make_float4(0, 0, 0, 0);
+            int4 extra = make_int4(h_parent[k], 0, 0, 0);
+            memcpy(&d[7], &extra, sizeof extra);
         }
     }
     // canonical node -> device ref, for per-ray predicted nodes
@@ -291,18 +305,6 @@ hrpp_status hrpp_scene_create(const float *tri_verts, uint32_t n_tris, const hrp
             if (n.child[q] != -1 && nodes[n.child[q]].count > 0) h_canon[n.child[q]] = (int32_t)~leaf_id(nodes[n.child[q]]);
     }
     if (nodes[root].count > 0) h_canon[root] = (int32_t)~leaf_id(nodes[root]);
-    // parent links for the Go Up Level (Sec. 6.2): interior node -> parent,
-    // and a leaf's first prim_index slot -> the leaf's parent (-1 at the root)
-    std::vector<int32_t> h_parent(std::max<size_t>(1, v.order.size()), -1), h_leaf_parent(n_tris, -1);
-    for (uint32_t k = 0; k < v.order.size(); ++k) {
-        const hrpp_bvh_node &n = nodes[v.order[k]];
-        for (int q = 0; q < 4; ++q) {
-            const int32_t c = n.child[q];
-            if (c == -1) continue;
-            if (nodes[c].count > 0) h_leaf_parent[nodes[c].first] = (int32_t)k;
-            else h_parent[dev_index[c]] = (int32_t)k;
-        }
-    }
     // triangles in leaf (prim_index) order: v0 with the prim id, then the edges
     std::vector<float4> h_tris(3ull * n_tris);
     for (uint32_t k = 0; k < n_tris; ++k) {
@@ -546,6 +548,8 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         if (opts->refill_min > 32) return fail(HRPP_ERR_INVALID_ARG, "refill_min must be in [1, 32]");
         refill_min = opts->refill_min;
     }
+    if (opts && opts->verify != HRPP_VERIFY_ROOT && opts->verify != HRPP_VERIFY_BOTTOM_UP)
+        return fail(HRPP_ERR_INVALID_ARG, "unknown verify mode %u", opts->verify);
     if (table && table->device != sc->device) return fail(HRPP_ERR_INVALID_ARG, "table and scene on different devices");
     if (table && table->bound_scene && table->bound_scene != sc->id)
         return fail(HRPP_ERR_INVALID_ARG, "table is bound to another scene; reset it first");
@@ -609,6 +613,7 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         p.root_ref = sc->root_ref;
         p.max_steps = sc->n_interior + sc->n_leaves + 8u;
         if (opts && opts->max_steps > 0u && opts->max_steps < p.max_steps) p.max_steps = opts->max_steps;
+        p.verify = opts ? (int)opts->verify : 0;
         p.rays = reinterpret_cast<const float4 *>(d_rays);
         p.n_rays = n_rays;
         p.hits = d_hits;

@@ -72,6 +72,7 @@ struct TraceParams {
     const int32_t *predicted;    // per ray: canonical node whose subtree is traversed first (-1: none)
     const int32_t *canon_ref;    // canonical node -> device ref
     uint32_t n_nodes;            // canonical node count
+    int verify;                  // closest-hit true positives: 0 root traversal, 1 bottom-up climb
 };
 
 // ---------------------------------------------------------------- hashing --

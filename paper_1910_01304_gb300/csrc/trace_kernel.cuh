@@ -9,8 +9,10 @@
 //      touched); otherwise false positive.
 //   3. Traversal from the root unless an any-hit ray is done.  Closest-hit
 //      true positives traverse with the predicted hit as the initial bound,
-//      so the answer stays exact.  Children are visited nearest first, ties
-//      by slot; the stack lives in local memory (HRPP_MAX_STACK entries).
+//      so the answer stays exact; or (bottom-up verification) they climb from
+//      the predicted hit's leaf to the root and traverse only the siblings
+//      met on the way.  Children are visited nearest first, ties by slot; the
+//      stack lives in local memory (HRPP_MAX_STACK entries).
 //   4. A ray whose traversal produced its final hit inserts that hit's leaf:
 //      two-phase mode records it (atomicMax on the slot's winner + a record
 //      appended with one atomic per warp); online mode exchanges the word.
@@ -81,6 +83,8 @@ struct RayState {
     bool predicted_hit;
     uint32_t set;
     uint64_t tag;
+    int32_t from;      // bottom-up verification: the ref the climb is at (kDoneRef: not climbing)
+    bool climb_visit;  // the next interior visit is the climb's ancestor (then from moves up)
 };
 
 // Tests the triangles of one leaf.  Any-hit: returns true at the first valid
@@ -119,9 +123,11 @@ __device__ __forceinline__ int32_t pop(int32_t *stack, int &sp) { return sp > 0 
 // current bound and moves to the nearest hit child, pushing the others
 // (farthest deepest); with no hit child it pops.
 // PRED: the node belongs to a predicted subtree (Go Up Level > 0), counted
-// apart from the traversal from the root.
-template <int W, bool STATS, bool PRED = false>
-__device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s, int32_t *stack, Counters<STATS> &cnt)
+// apart from the traversal from the root.  SKIP: the child ref `skip` is
+// left out (the child a bottom-up climb came from).
+template <int W, bool STATS, bool PRED = false, bool SKIP = false>
+__device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s, int32_t *stack, Counters<STATS> &cnt,
+                                               int32_t skip = kDoneRef)
 {
     constexpr int kBoxStat = PRED ? ST_PRED_BOX_TESTS : ST_BOX_TESTS;
     cnt.add(PRED ? ST_PRED_INTERIOR : ST_INTERIOR);
@@ -131,10 +137,11 @@ __device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s
         const float4 a = __ldg(n), bb = __ldg(n + 1), c = __ldg(n + 2);
         const int4 e = __ldg(reinterpret_cast<const int4 *>(n + 3));
         float t0, t1;
-        const bool h0 = slab(s.ri, tmin, s.tcur, a.x, a.y, a.z, a.w, c.x, c.y, t0);
-        const bool v1 = e.y != kEmptyRef;
+        const bool v0 = !SKIP || e.x != skip;
+        const bool h0 = v0 && slab(s.ri, tmin, s.tcur, a.x, a.y, a.z, a.w, c.x, c.y, t0);
+        const bool v1 = e.y != kEmptyRef && (!SKIP || e.y != skip);
         const bool h1 = v1 && slab(s.ri, tmin, s.tcur, bb.x, bb.y, bb.z, bb.w, c.z, c.w, t1);
-        cnt.add(kBoxStat, 1u + (v1 ? 1u : 0u));
+        cnt.add(kBoxStat, (v0 ? 1u : 0u) + (v1 ? 1u : 0u));
         if (h0 && h1) {
             if (s.sp >= kStack) {
                 atomicOr(p.error, kErrStack);
@@ -161,10 +168,10 @@ __device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s
     float t0 = inf, t1 = inf, t2 = inf, t3 = inf, t;
     bool h0 = false, h1 = false, h2 = false, h3 = false;
     uint32_t nvalid = 0;
-    if (ch.x != kEmptyRef) { ++nvalid; if ((h0 = slab(s.ri, tmin, s.tcur, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, t))) t0 = t; }
-    if (ch.y != kEmptyRef) { ++nvalid; if ((h1 = slab(s.ri, tmin, s.tcur, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, t))) t1 = t; }
-    if (ch.z != kEmptyRef) { ++nvalid; if ((h2 = slab(s.ri, tmin, s.tcur, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, t))) t2 = t; }
-    if (ch.w != kEmptyRef) { ++nvalid; if ((h3 = slab(s.ri, tmin, s.tcur, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, t))) t3 = t; }
+    if (ch.x != kEmptyRef && (!SKIP || ch.x != skip)) { ++nvalid; if ((h0 = slab(s.ri, tmin, s.tcur, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, t))) t0 = t; }
+    if (ch.y != kEmptyRef && (!SKIP || ch.y != skip)) { ++nvalid; if ((h1 = slab(s.ri, tmin, s.tcur, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, t))) t1 = t; }
+    if (ch.z != kEmptyRef && (!SKIP || ch.z != skip)) { ++nvalid; if ((h2 = slab(s.ri, tmin, s.tcur, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, t))) t2 = t; }
+    if (ch.w != kEmptyRef && (!SKIP || ch.w != skip)) { ++nvalid; if ((h3 = slab(s.ri, tmin, s.tcur, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, t))) t3 = t; }
     cnt.add(kBoxStat, nvalid);
     const int nhit = (int)h0 + (int)h1 + (int)h2 + (int)h3;
     if (nhit == 0) {
@@ -214,6 +221,7 @@ __device__ __forceinline__ bool over_budget(const TraceParams &p, RayState &s)
     if (++s.steps > p.max_steps) {
         atomicOr(p.error, kErrSteps);
         s.ref = kDoneRef;
+        s.from = kDoneRef;
         return true;
     }
     return false;
@@ -223,7 +231,7 @@ __device__ __forceinline__ bool over_budget(const TraceParams &p, RayState &s)
 // tested; with Go Up Level > 0 each predicted interior node's subtree is
 // traversed (Sec. 6.2).  Returns true when the ray still has to traverse from
 // the root (then s.ref is the root).
-template <int W, bool CLOSEST, bool STATS>
+template <int W, bool CLOSEST, bool STATS, bool BU = false>
 __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayState &s, int32_t *stack,
                                           Counters<STATS> &cnt)
 {
@@ -236,6 +244,8 @@ __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayS
     s.b.found = s.b.from_trav = false;
     s.set = 0;
     s.tag = 0;
+    s.from = kDoneRef;
+    s.climb_visit = false;
     cnt.add(ST_RAYS);
     bool traverse = true, have_inverse = false;
     const bool learned = p.predicted != nullptr;
@@ -317,6 +327,11 @@ __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayS
         s.sp = 0;
         s.ref = p.root_ref;
         s.steps = 0;
+        if (BU && CLOSEST && s.b.found) {
+            // climb from the predicted hit's leaf (climb() visits the ancestors)
+            s.ref = kDoneRef;
+            s.from = (int32_t)~s.b.leaf;
+        }
     } else {
         s.ref = kDoneRef;
     }
@@ -396,23 +411,82 @@ __device__ __forceinline__ void append_records(const TraceParams &p, uint32_t la
     }
 }
 
-// The whole of one ray: lookup, traversal, result, insert decision.
-template <int W, bool CLOSEST, bool STATS>
+// Parent of interior node `node`, kept in the node's spare word.
+template <int W>
+__device__ __forceinline__ int32_t node_parent(const TraceParams &p, int32_t node)
+{
+    if (W == 2) return __ldg(reinterpret_cast<const int32_t *>(p.nodes + 4ull * (uint32_t)node + 3) + 2);
+    return __ldg(reinterpret_cast<const int32_t *>(p.nodes + 8ull * (uint32_t)node + 7));
+}
+
+// Bottom-up verification: once everything below the climb is traversed,
+// the ray moves to the parent of s.from; that visit (an ordinary interior
+// visit) tests only the children other than s.from and then the climb is at
+// the parent.  Returns false when the climb is over (past the root) or none
+// runs.
+template <int W>
+__device__ __forceinline__ bool climb(const TraceParams &p, RayState &s)
+{
+    if (s.from == kDoneRef) return false;
+    const int32_t up = s.from >= 0 ? node_parent<W>(p, s.from) : __ldg(p.leaf_parent + ((uint32_t)~s.from >> 2));
+    if (up < 0) {
+        s.from = kDoneRef;
+        return false;
+    }
+    s.ref = up;
+    s.climb_visit = true;
+    return true;
+}
+
+// One interior visit of the main traversal.  With bottom-up verification
+// (BU) the visit leaves out the child the climb came from; no other node has
+// that child, so passing it on every visit only matters at the climb's
+// ancestor.
+template <int W, bool BU, bool STATS>
+__device__ __forceinline__ void traverse_interior(const TraceParams &p, RayState &s, int32_t *stack,
+                                                  Counters<STATS> &cnt)
+{
+    if (!BU) {
+        visit_interior<W, STATS>(p, s, stack, cnt);
+        return;
+    }
+    const int32_t node = s.ref;
+    visit_interior<W, STATS, false, true>(p, s, stack, cnt, s.from);
+    if (s.climb_visit) {
+        s.from = node;
+        s.climb_visit = false;
+    }
+}
+
+// The whole of one ray: lookup, traversal, result, insert decision.  BU:
+// closest-hit true positives verify bottom-up; a lane whose stack runs dry
+// climbs within the same loop, without waiting for the rest of its warp.
+template <int W, bool CLOSEST, bool STATS, bool BU = false>
 __device__ __forceinline__ bool trace_one(const TraceParams &p, uint32_t i, int32_t *stack, Counters<STATS> &cnt,
                                           uint32_t &slot, uint64_t &word)
 {
+    static_assert(CLOSEST || !BU, "bottom-up verification is for closest-hit rays");
     RayState s;
-    if (start_ray<W, CLOSEST, STATS>(p, i, s, stack, cnt)) {
-        while (s.ref != kDoneRef) {
-            if (over_budget(p, s)) break;
-            if (s.ref >= 0) visit_interior<W, STATS>(p, s, stack, cnt);
-            else visit_leaf<CLOSEST, STATS>(p, s, stack, cnt);
+    if (start_ray<W, CLOSEST, STATS, BU>(p, i, s, stack, cnt)) {
+        if (!BU) {
+            while (s.ref != kDoneRef) {
+                if (over_budget(p, s)) break;
+                if (s.ref >= 0) visit_interior<W, STATS>(p, s, stack, cnt);
+                else visit_leaf<CLOSEST, STATS>(p, s, stack, cnt);
+            }
+        } else {
+            for (;;) {
+                if (s.ref == kDoneRef && !climb<W>(p, s)) break;
+                if (over_budget(p, s)) break;
+                if (s.ref >= 0) traverse_interior<W, BU, STATS>(p, s, stack, cnt);
+                else visit_leaf<CLOSEST, STATS>(p, s, stack, cnt);
+            }
         }
     }
     return finish_ray<CLOSEST, STATS>(p, i, s, cnt, slot, word);
 }
 
-template <int W, bool CLOSEST, bool STATS>
+template <int W, bool CLOSEST, bool STATS, bool BU = false>
 __global__ void __launch_bounds__(512) k_trace(const TraceParams p)
 {
     const uint32_t lane = threadIdx.x & 31u;
@@ -428,7 +502,7 @@ __global__ void __launch_bounds__(512) k_trace(const TraceParams p)
         bool want = false;
         uint32_t slot = 0;
         uint64_t word = 0;
-        if (i < p.n_rays) want = trace_one<W, CLOSEST, STATS>(p, i, stack, cnt, slot, word);
+        if (i < p.n_rays) want = trace_one<W, CLOSEST, STATS, BU>(p, i, stack, cnt, slot, word);
         append_records(p, lane, want, slot, i, word);
     }
     cnt.flush(p.ctl, lane);
@@ -500,7 +574,7 @@ cudaError_t launch_batch_width(bool stats, const BatchDesc &b, int block_threads
     return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(block_threads), args, 0, stream);
 }
 
-template <int W, bool CLOSEST, bool STATS>
+template <int W, bool CLOSEST, bool STATS, bool BU = false>
 __global__ void __launch_bounds__(512) k_trace_dyn(const TraceParams p)
 {
     const uint32_t lane = threadIdx.x & 31u;
@@ -523,7 +597,7 @@ __global__ void __launch_bounds__(512) k_trace_dyn(const TraceParams p)
                 const uint32_t mine = base + __popc(idle & lanemask_lt());
                 if (mine < p.n_rays) {
                     ray = mine;
-                    start_ray<W, CLOSEST, STATS>(p, ray, s, stack, cnt);
+                    start_ray<W, CLOSEST, STATS, BU>(p, ray, s, stack, cnt);
                 }
             }
         }
@@ -535,15 +609,17 @@ __global__ void __launch_bounds__(512) k_trace_dyn(const TraceParams p)
         if (ray != kNoRay && s.ref != kDoneRef) {
             while (s.ref >= 0) {
                 if (over_budget(p, s)) break;
-                visit_interior<W, STATS>(p, s, stack, cnt);
+                traverse_interior<W, BU, STATS>(p, s, stack, cnt);
             }
             if (s.ref != kDoneRef && !over_budget(p, s)) visit_leaf<CLOSEST, STATS>(p, s, stack, cnt);
         }
+        // a bottom-up verification with nothing left below moves up a level
+        if (BU && ray != kNoRay && s.ref == kDoneRef) climb<W>(p, s);
         // lanes whose ray is done write it out and free themselves
         bool want = false;
         uint32_t slot = 0;
         uint64_t word = 0;
-        const bool done = ray != kNoRay && s.ref == kDoneRef;
+        const bool done = ray != kNoRay && s.ref == kDoneRef && s.from == kDoneRef;
         if (done) want = finish_ray<CLOSEST, STATS>(p, ray, s, cnt, slot, word);
         append_records(p, lane, want, slot, ray, word);
         if (done) ray = kNoRay;
@@ -556,11 +632,14 @@ cudaError_t launch_width(bool closest, bool stats, int schedule, const TracePara
                          int blocks_per_sm_cap, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     const void *fn;
+    const bool bu = closest && p.verify == HRPP_VERIFY_BOTTOM_UP;
     if (schedule == 1) {
-        if (closest) fn = stats ? (const void *)k_trace_dyn<W, true, true> : (const void *)k_trace_dyn<W, true, false>;
+        if (bu) fn = stats ? (const void *)k_trace_dyn<W, true, true, true> : (const void *)k_trace_dyn<W, true, false, true>;
+        else if (closest) fn = stats ? (const void *)k_trace_dyn<W, true, true> : (const void *)k_trace_dyn<W, true, false>;
         else fn = stats ? (const void *)k_trace_dyn<W, false, true> : (const void *)k_trace_dyn<W, false, false>;
     } else {
-        if (closest) fn = stats ? (const void *)k_trace<W, true, true> : (const void *)k_trace<W, true, false>;
+        if (bu) fn = stats ? (const void *)k_trace<W, true, true, true> : (const void *)k_trace<W, true, false, true>;
+        else if (closest) fn = stats ? (const void *)k_trace<W, true, true> : (const void *)k_trace<W, true, false>;
         else fn = stats ? (const void *)k_trace<W, false, true> : (const void *)k_trace<W, false, false>;
     }
     int dev = 0, sms = 0, per_sm = 0;

@@ -46,10 +46,11 @@ class hrpp_trace_opts(ctypes.Structure):
     _fields_ = [("kernel_start", ctypes.c_void_p), ("kernel_stop", ctypes.c_void_p),
                 ("predicted_nodes", ctypes.c_void_p), ("block_threads", ctypes.c_uint32),
                 ("schedule", ctypes.c_uint32), ("refill_min", ctypes.c_uint32), ("max_steps", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 2)]
+                ("verify", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1)]
 
 
 HRPP_SCHEDULE_DEFAULT, HRPP_SCHEDULE_BATCH, HRPP_SCHEDULE_REFILL = 0, 1, 2
+HRPP_VERIFY_ROOT, HRPP_VERIFY_BOTTOM_UP = 0, 1
 
 
 class hrpp_batch_item(ctypes.Structure):
@@ -281,7 +282,7 @@ class Table:
 
 def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, stats: bool = False,
           stream=None, kernel_events=None, block_threads: int = 0, schedule: int = 0, refill_min: int = 0,
-          predicted=None, max_steps: int = 0):
+          predicted=None, max_steps: int = 0, verify: int = 0):
     """Traces rays ([n, 8] float32 torch tensor on the GPU, or a host numpy
     array / torch tensor).  Returns (hits, stats dict or None).
 
@@ -299,7 +300,8 @@ def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, 
             hits = torch.empty(shape, dtype=dtype, device=rays.device)
     st = hrpp_stats() if stats else None
     opts = None
-    if kernel_events is not None or block_threads or schedule or refill_min or max_steps or predicted is not None:
+    if (kernel_events is not None or block_threads or schedule or refill_min or max_steps or verify
+            or predicted is not None):
         opts = hrpp_trace_opts()
         if predicted is not None:
             opts.predicted_nodes = _ptr(predicted)
@@ -310,6 +312,7 @@ def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, 
         opts.schedule = schedule
         opts.refill_min = refill_min
         opts.max_steps = max_steps
+        opts.verify = verify
     check(hrpp_trace_ex(scene.handle, table.handle if table is not None else None, _ptr(rays), n, mode, _ptr(hits),
                         ctypes.byref(st) if st is not None else None, _stream_handle(stream),
                         ctypes.byref(opts) if opts is not None else None))

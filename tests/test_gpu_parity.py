@@ -295,6 +295,81 @@ def test_go_up_mid_terrain_bvh4(H):
         assert np.array_equal(tab.export(), otab.words)
 
 
+@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("go_up", [0, 1])
+@pytest.mark.parametrize("width_idx", [0, 1])
+def test_bottom_up_verification_matches_oracle(H, small_pair, go_up, width_idx, schedule):
+    """Closest-hit true positives verified by the bottom-up climb: hits,
+    every counter and the table words equal the oracle's, over three frames,
+    with both ray schedules."""
+    s, g = small_pair[width_idx]
+    tab = H.Table(12, 2, 6, go_up=go_up)
+    otab = O.Table(12, 2, 6, O.TWO_PHASE, go_up=go_up)
+    import torch
+    tp = 0
+    for frame in range(3):
+        rays = s.primary_rays(frame=frame)
+        oh, ost = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, O.CLOSEST_HIT, otab,
+                          verify=O.VERIFY_BOTTOM_UP)
+        gh, gst = H.trace(g, torch.from_numpy(rays).cuda(), H.HRPP_CLOSEST_HIT, tab, stats=True,
+                          schedule=schedule, verify=H.HRPP_VERIFY_BOTTOM_UP)
+        torch.cuda.synchronize()
+        assert_same_hits(O.CLOSEST_HIT, gh.cpu().numpy(), oh, f"frame {frame}")
+        assert_same_stats(gst, ost, msg=f"frame {frame}")
+        assert np.array_equal(tab.export(), otab.words)
+        tp += gst["true_pos"]
+    assert tp > 0
+
+
+@pytest.mark.parametrize("width", [2, 4])
+def test_bottom_up_with_predicted_treelets(H, width):
+    """Learned-style predictions (valid nodes, -1, out of range) verified by
+    the climb: hits and counters equal the oracle's."""
+    import torch
+    s = W.small_scene(width=width)
+    g = H.Scene.from_workload(s)
+    rays = s.primary_rays(frame=5)
+    rng = np.random.default_rng(11 + width)
+    pred = rng.integers(-1, len(s.nodes) + 3, len(rays)).astype(np.int32)
+    oh, ost = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, O.CLOSEST_HIT, predicted=pred,
+                      verify=O.VERIFY_BOTTOM_UP)
+    gh, gst = H.trace(g, torch.from_numpy(rays).cuda(), H.HRPP_CLOSEST_HIT, stats=True,
+                      predicted=torch.from_numpy(pred).cuda(), verify=H.HRPP_VERIFY_BOTTOM_UP)
+    torch.cuda.synchronize()
+    assert_same_hits(O.CLOSEST_HIT, gh.cpu().numpy(), oh)
+    assert_same_stats(gst, ost)
+    assert gst["true_pos"] > 0
+
+
+def test_bottom_up_mid_terrain_bvh4(H):
+    """A deeper 4-wide tree: two frames of jittered primaries through a
+    warm table, verified by the climb."""
+    import torch
+    s = W.terrain_scene(quads=64, n_spheres=4, subdiv=2, res=(160, 96))
+    g = H.Scene.from_workload(s)
+    tab = H.Table(14, 2, 6)
+    otab = O.Table(14, 2, 6, O.TWO_PHASE)
+    for frame in range(2):
+        rays = s.primary_rays(frame=frame)
+        oh, ost = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, O.CLOSEST_HIT, otab,
+                          verify=O.VERIFY_BOTTOM_UP)
+        gh, gst = H.trace(g, torch.from_numpy(rays).cuda(), H.HRPP_CLOSEST_HIT, tab, stats=True,
+                          verify=H.HRPP_VERIFY_BOTTOM_UP)
+        torch.cuda.synchronize()
+        assert_same_hits(O.CLOSEST_HIT, gh.cpu().numpy(), oh)
+        assert_same_stats(gst, ost)
+        assert np.array_equal(tab.export(), otab.words)
+
+
+def test_verify_mode_is_validated(H, small_pair):
+    import torch
+    s, g = small_pair[0]
+    rays = torch.from_numpy(s.primary_rays()[:64]).cuda()
+    with pytest.raises(H.HrppError) as err:
+        H.trace(g, rays, H.HRPP_CLOSEST_HIT, verify=2)
+    assert err.value.status == H.HRPP_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("width_idx", [0, 1])
 def test_step_budget_reports_traversal_limit(H, small_pair, width_idx):
     """Failure detection without a fault: a per-traversal step budget far
