@@ -11,9 +11,8 @@
 //      true positives traverse with the predicted hit as the initial bound,
 //      so the answer stays exact; or (bottom-up verification) they climb from
 //      the predicted hit's leaf to the root and traverse only the siblings
-//      met on the way.  Children are visited nearest first, ties by slot.
-//      The stack's top kShort entries live in shared memory, older ones
-//      spill to local memory (HRPP_MAX_STACK entries in all).
+//      met on the way.  Children are visited nearest first, ties by slot; the
+//      stack lives in local memory (HRPP_MAX_STACK entries).
 //   4. A ray whose traversal produced its final hit inserts that hit's leaf:
 //      two-phase mode records it (atomicMax on the slot's winner + a record
 //      appended with one atomic per warp); online mode exchanges the word.
@@ -78,8 +77,7 @@ struct RayState {
     RayInv ri;
     float tcur;
     Best b;
-    int sp;  // stack entries
-    int lo;  // entries [0, lo) spilled to local memory, [lo, sp) in shared memory
+    int sp;
     int32_t ref;
     uint32_t steps;
     bool predicted_hit;
@@ -119,57 +117,7 @@ __device__ __forceinline__ bool test_leaf(const TraceParams &p, uint32_t leaf, f
     return false;
 }
 
-// A ray's traversal stack.  The top kShort entries live in shared memory:
-// entry k in slot k mod kShort of this lane's column of its warp's block of
-// kShort x 32 words, so a warp's accesses fall in 32 distinct banks whatever
-// each lane's depth.  Entries below RayState::lo have been spilled to the
-// local-memory array `local`.
-constexpr int kShort = 8;
-static_assert(kShort > 0 && (kShort & (kShort - 1)) == 0, "short stack size");
-
-extern __shared__ int32_t short_stacks[];  // the block's short stacks (dynamic shared memory)
-
-struct Stack {
-    uint32_t col;    // this lane's column in short_stacks
-    int32_t *local;  // spilled entries
-    __device__ __forceinline__ int32_t &slot(int k) { return short_stacks[col + ((uint32_t)(k & (kShort - 1)) << 5)]; }
-};
-
-__device__ __forceinline__ void stack_init(Stack &st, int32_t *local)
-{
-    st.col = (threadIdx.x >> 5) * (kShort * 32) + (threadIdx.x & 31u);
-    st.local = local;
-}
-
-// dynamic shared memory the traversal kernels need per block
-__host__ __device__ constexpr size_t short_stack_bytes(int block_threads)
-{
-    return (size_t)kShort * sizeof(int32_t) * (size_t)block_threads;
-}
-
-__device__ __forceinline__ void stack_reset(RayState &s)
-{
-    s.sp = 0;
-    s.lo = 0;
-}
-
-// spills the oldest shared entries until n more fit in shared memory
-__device__ __forceinline__ void make_room(Stack &st, RayState &s, int n)
-{
-    while (s.sp + n - s.lo > kShort) {
-        st.local[s.lo] = st.slot(s.lo);
-        ++s.lo;
-    }
-}
-
-__device__ __forceinline__ int32_t pop(Stack &st, RayState &s)
-{
-    if (s.sp == 0) return kDoneRef;
-    --s.sp;
-    if (s.sp >= s.lo) return st.slot(s.sp);
-    s.lo = s.sp;  // the shared part was empty: the entry was spilled
-    return st.local[s.sp];
-}
+__device__ __forceinline__ int32_t pop(int32_t *stack, int &sp) { return sp > 0 ? stack[--sp] : kDoneRef; }
 
 // Visits the interior node s.ref: tests its children's boxes against the
 // current bound and moves to the nearest hit child, pushing the others
@@ -178,7 +126,7 @@ __device__ __forceinline__ int32_t pop(Stack &st, RayState &s)
 // apart from the traversal from the root.  SKIP: the child ref `skip` is
 // left out (the child a bottom-up climb came from).
 template <int W, bool STATS, bool PRED = false, bool SKIP = false>
-__device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s, Stack &stack, Counters<STATS> &cnt,
+__device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s, int32_t *stack, Counters<STATS> &cnt,
                                                int32_t skip = kDoneRef)
 {
     constexpr int kBoxStat = PRED ? ST_PRED_BOX_TESTS : ST_BOX_TESTS;
@@ -201,15 +149,14 @@ __device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s
                 return;
             }
             const bool swap = t1 < t0;
-            make_room(stack, s, 1);
-            stack.slot(s.sp++) = swap ? e.x : e.y;
+            stack[s.sp++] = swap ? e.x : e.y;
             s.ref = swap ? e.y : e.x;
         } else if (h0) {
             s.ref = e.x;
         } else if (h1) {
             s.ref = e.y;
         } else {
-            s.ref = pop(stack, s);
+            s.ref = pop(stack, s.sp);
         }
         return;
     }
@@ -228,7 +175,7 @@ __device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s
     cnt.add(kBoxStat, nvalid);
     const int nhit = (int)h0 + (int)h1 + (int)h2 + (int)h3;
     if (nhit == 0) {
-        s.ref = pop(stack, s);
+        s.ref = pop(stack, s.sp);
         return;
     }
     if (s.sp + nhit - 1 > kStack) {
@@ -246,20 +193,19 @@ __device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s
     c = t2 < t1; r1 += c; r2 += !c;
     c = t3 < t1; r1 += c; r3 += !c;
     c = t3 < t2; r2 += c; r3 += !c;
-    // rank 0 is visited next; rank k > 0 goes to stack entry sp + nhit - 1 - k
-    make_room(stack, s, nhit - 1);
+    // rank 0 is visited next; rank k > 0 goes to stack slot sp + nhit - 1 - k
     const int top = s.sp + nhit - 1;
-    if (h0) { if (r0 == 0) s.ref = ch.x; else stack.slot(top - r0) = ch.x; }
-    if (h1) { if (r1 == 0) s.ref = ch.y; else stack.slot(top - r1) = ch.y; }
-    if (h2) { if (r2 == 0) s.ref = ch.z; else stack.slot(top - r2) = ch.z; }
-    if (h3) { if (r3 == 0) s.ref = ch.w; else stack.slot(top - r3) = ch.w; }
+    if (h0) { if (r0 == 0) s.ref = ch.x; else stack[top - r0] = ch.x; }
+    if (h1) { if (r1 == 0) s.ref = ch.y; else stack[top - r1] = ch.y; }
+    if (h2) { if (r2 == 0) s.ref = ch.z; else stack[top - r2] = ch.z; }
+    if (h3) { if (r3 == 0) s.ref = ch.w; else stack[top - r3] = ch.w; }
     s.sp = top;
 }
 
 // Tests the leaf s.ref; any-hit rays end at the first valid hit, otherwise the
 // traversal pops the next node.
 template <bool CLOSEST, bool STATS, bool PRED = false>
-__device__ __forceinline__ void visit_leaf(const TraceParams &p, RayState &s, Stack &stack, Counters<STATS> &cnt)
+__device__ __forceinline__ void visit_leaf(const TraceParams &p, RayState &s, int32_t *stack, Counters<STATS> &cnt)
 {
     cnt.add(PRED ? ST_PRED_LEAVES : ST_LEAVES);
     if (test_leaf<CLOSEST, STATS>(p, ~(uint32_t)s.ref, s.o, s.d, s.b, s.tcur, !PRED, cnt,
@@ -267,7 +213,7 @@ __device__ __forceinline__ void visit_leaf(const TraceParams &p, RayState &s, St
         s.ref = kDoneRef;
         return;
     }
-    s.ref = pop(stack, s);
+    s.ref = pop(stack, s.sp);
 }
 
 __device__ __forceinline__ bool over_budget(const TraceParams &p, RayState &s)
@@ -286,7 +232,7 @@ __device__ __forceinline__ bool over_budget(const TraceParams &p, RayState &s)
 // traversed (Sec. 6.2).  Returns true when the ray still has to traverse from
 // the root (then s.ref is the root).
 template <int W, bool CLOSEST, bool STATS, bool BU = false>
-__device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayState &s, Stack &stack,
+__device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayState &s, int32_t *stack,
                                           Counters<STATS> &cnt)
 {
     s.o = __ldg(p.rays + 2ull * i);
@@ -316,7 +262,7 @@ __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayS
                 s.ri = ray_inverse(s.o, s.d);
                 have_inverse = true;
                 s.tcur = s.d.w;
-                stack_reset(s);
+                s.sp = 0;
                 s.ref = ref;
                 s.steps = 0;
                 while (s.ref != kDoneRef) {
@@ -351,7 +297,7 @@ __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayS
                     have_inverse = true;
                 }
                 s.tcur = (CLOSEST && s.b.found) ? s.b.t : s.d.w;
-                stack_reset(s);
+                s.sp = 0;
                 s.ref = (int32_t)node;
                 s.steps = 0;
                 while (s.ref != kDoneRef) {
@@ -378,7 +324,7 @@ __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayS
     if (traverse) {
         if (!have_inverse) s.ri = ray_inverse(s.o, s.d);
         s.tcur = (CLOSEST && s.b.found) ? s.b.t : s.d.w;
-        stack_reset(s);
+        s.sp = 0;
         s.ref = p.root_ref;
         s.steps = 0;
         if (BU && CLOSEST && s.b.found) {
@@ -497,7 +443,7 @@ __device__ __forceinline__ bool climb(const TraceParams &p, RayState &s)
 // that child, so passing it on every visit only matters at the climb's
 // ancestor.
 template <int W, bool BU, bool STATS>
-__device__ __forceinline__ void traverse_interior(const TraceParams &p, RayState &s, Stack &stack,
+__device__ __forceinline__ void traverse_interior(const TraceParams &p, RayState &s, int32_t *stack,
                                                   Counters<STATS> &cnt)
 {
     if (!BU) {
@@ -516,7 +462,7 @@ __device__ __forceinline__ void traverse_interior(const TraceParams &p, RayState
 // closest-hit true positives verify bottom-up; a lane whose stack runs dry
 // climbs within the same loop, without waiting for the rest of its warp.
 template <int W, bool CLOSEST, bool STATS, bool BU = false>
-__device__ __forceinline__ bool trace_one(const TraceParams &p, uint32_t i, Stack &stack, Counters<STATS> &cnt,
+__device__ __forceinline__ bool trace_one(const TraceParams &p, uint32_t i, int32_t *stack, Counters<STATS> &cnt,
                                           uint32_t &slot, uint64_t &word)
 {
     static_assert(CLOSEST || !BU, "bottom-up verification is for closest-hit rays");
@@ -546,9 +492,7 @@ __global__ void __launch_bounds__(512) k_trace(const TraceParams p)
     const uint32_t lane = threadIdx.x & 31u;
     Counters<STATS> cnt;
     cnt.init();
-    int32_t spilled[kStack];
-    Stack stack;
-    stack_init(stack, spilled);
+    int32_t stack[kStack];
     for (;;) {
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(&p.ctl->next_ray, 32u);
@@ -579,9 +523,7 @@ __global__ void __launch_bounds__(512) k_trace_batch(const BatchDesc b)
     TraceParams &p = item_params[warp];
     Counters<STATS> cnt;
     cnt.init();
-    int32_t spilled[kStack];
-    Stack stack;
-    stack_init(stack, spilled);
+    int32_t stack[kStack];
     uint32_t cur = 0xFFFFFFFFu;
     for (;;) {
         uint32_t chunk = 0;
@@ -621,7 +563,7 @@ cudaError_t launch_batch_width(bool stats, const BatchDesc &b, int block_threads
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block_threads, short_stack_bytes(block_threads));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block_threads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     const uint64_t warps_per_block = block_threads / 32;
@@ -629,8 +571,7 @@ cudaError_t launch_batch_width(bool stats, const BatchDesc &b, int block_threads
     if (blocks * warps_per_block > b.n_chunks) blocks = (b.n_chunks + warps_per_block - 1) / warps_per_block;
     if (blocks < 1) blocks = 1;
     void *args[] = {(void *)&b};
-    return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(block_threads), args, short_stack_bytes(block_threads),
-                            stream);
+    return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(block_threads), args, 0, stream);
 }
 
 template <int W, bool CLOSEST, bool STATS, bool BU = false>
@@ -639,9 +580,7 @@ __global__ void __launch_bounds__(512) k_trace_dyn(const TraceParams p)
     const uint32_t lane = threadIdx.x & 31u;
     Counters<STATS> cnt;
     cnt.init();
-    int32_t spilled[kStack];
-    Stack stack;
-    stack_init(stack, spilled);
+    int32_t stack[kStack];
     RayState s;
     uint32_t ray = kNoRay;
     bool pool_open = true;  // warp-uniform
@@ -708,7 +647,7 @@ cudaError_t launch_width(bool closest, bool stats, int schedule, const TracePara
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block_threads, short_stack_bytes(block_threads));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block_threads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (blocks_per_sm_cap > 0 && per_sm > blocks_per_sm_cap) per_sm = blocks_per_sm_cap;
@@ -720,8 +659,7 @@ cudaError_t launch_width(bool closest, bool stats, int schedule, const TracePara
     if (blocks < 1) blocks = 1;
     if (ev0) cudaEventRecord(ev0, stream);
     void *args[] = {(void *)&p};
-    e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(block_threads), args, short_stack_bytes(block_threads),
-                         stream);
+    e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(block_threads), args, 0, stream);
     if (ev1) cudaEventRecord(ev1, stream);
     return e;
 }
