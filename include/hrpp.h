@@ -129,8 +129,10 @@ typedef struct hrpp_scene_info {
     uint64_t device_bytes;
 } hrpp_scene_info;
 
-/* Per-call options of hrpp_trace_ex (all fields may be zero).  None of them
- * changes any result, counter or table word; they only change speed.
+/* Per-call options of hrpp_trace_ex (all fields may be zero).  Results and
+ * table words never depend on them, except that a max_steps budget a ray
+ * runs out of stops that ray early; verify changes node counters; the
+ * others change only speed.
  *   kernel_start/kernel_stop  cudaEvent_t (as void*) recorded on `stream`
  *                             immediately before and after the traversal
  *                             kernel, for timing it alone
@@ -243,6 +245,12 @@ hrpp_status hrpp_table_reset(hrpp_table *table, void *stream);
  * words' leaves: import only tables exported from the same scene. */
 hrpp_status hrpp_table_export(const hrpp_table *table, uint64_t *host_words, size_t n_words);
 hrpp_status hrpp_table_import(hrpp_table *table, const uint64_t *host_words, size_t n_words);
+/* Device-to-device copy of src's words into dst, asynchronous on `stream`
+ * (e.g. to restore a warm snapshot before each frame without a host round
+ * trip).  Both tables must be on the same device with the same
+ * log2_entries, ways, precision and Go Up Level, else HRPP_ERR_INVALID_ARG;
+ * dst takes src's scene binding.  The update mode of dst is unchanged. */
+hrpp_status hrpp_table_copy(hrpp_table *dst, const hrpp_table *src, void *stream);
 hrpp_status hrpp_table_get_config(const hrpp_table *table, int *log2_entries, int *ways, int *precision_bits,
                                   int *update_mode);
 void hrpp_table_destroy(hrpp_table *table);

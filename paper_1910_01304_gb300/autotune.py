@@ -12,6 +12,12 @@ with CUDA events on the current stream:
      and no self-prediction.
 It returns the fastest table (or none, when no table beats plain traversal)
 with the timings it measured.
+
+tune_batch does the same for a batched workload (one graph-replayed launch
+over many scenes): block size on plain traversal, then a table
+configuration for the closest-hit items and one for the any-hit items,
+each timed from tables warmed by other frames and restored before every
+replay.
 """
 from __future__ import annotations
 
@@ -84,6 +90,106 @@ def tune(scene: H.Scene, rays_warm, rays_eval, mode: int, table_grid: dict | Non
     return dict(mode="closest" if mode == H.HRPP_CLOSEST_HIT else "any", rays=n, launch=launch, plain_ms=plain_ms,
                 best_table=best["table"], best_ms=best["ms"], speedup_over_plain=plain_ms / best["ms"],
                 launch_times=[dict(c, ms=m) for m, c in launch_times], table_times=table_times)
+
+
+BATCH_TABLE_GRID = [None] + [dict(log2_entries=e, ways=w, precision=p) for e in (14, 16) for w in (1, 2)
+                              for p in (5, 6)]
+BATCH_BLOCK_GRID = (128, 256)
+
+
+class BatchSetup:
+    """One candidate configuration of a batched workload: a table per item
+    (or none), one graph-replayed Batch per frame, and device snapshots of the
+    tables after frames 1.. have warmed them.  step() restores the snapshots
+    and replays frame 0, so every step is the same work."""
+
+    def __init__(self, items, frames, cfg_closest, cfg_any, block_threads: int, stats: bool = False):
+        self.tables, self.snaps = [], []
+        for scene, mode in items:
+            cfg = cfg_closest if mode == H.HRPP_CLOSEST_HIT else cfg_any
+            if cfg is None:
+                self.tables.append(None)
+                continue
+            self.tables.append(H.Table(cfg["log2_entries"], cfg["ways"], cfg["precision"]))
+        self.batches = [H.Batch([(sc, t, rays, mode) for (sc, mode), t, rays in zip(items, self.tables, fr)],
+                                stats=stats and k == 0, block_threads=block_threads)
+                        for k, fr in enumerate(frames)]
+        for b in self.batches[1:]:
+            b.run()
+        for t in self.tables:
+            if t is None:
+                self.snaps.append(None)
+                continue
+            snap = H.Table(t.log2_entries, t.ways, t.precision)
+            snap.copy_from(t)
+            self.snaps.append(snap)
+
+    def step(self, stream=None):
+        for t, snap in zip(self.tables, self.snaps):
+            if t is not None:
+                t.copy_from(snap, stream)
+        self.batches[0].run(stream)
+
+    def hits(self):
+        return self.batches[0].hits
+
+    def close(self):
+        for b in self.batches:
+            b.close()
+        for t in self.tables + self.snaps:
+            if t is not None:
+                t.close()
+
+
+def _batch_digest(items, hits) -> str:
+    """Closest-hit results bit for bit; any-hit results as the occlusion
+    bit (the prim an any-hit ray reports may differ when a predicted leaf
+    answers it)."""
+    h = hashlib.sha1()
+    for (_, mode), out in zip(items, hits):
+        a = out.cpu().numpy()
+        h.update(a.tobytes() if mode == H.HRPP_CLOSEST_HIT else (a.view(np.uint32) != H.HRPP_NO_HIT).tobytes())
+    return h.hexdigest()
+
+
+def tune_batch(items, frames, table_grid=None, block_grid=None, reps: int = 3) -> dict:
+    """Tunes a batched workload.  items: [(Scene, mode)]; frames: per frame, a
+    list of ray tensors, one per item (frame 0 is the one timed, the others
+    warm the tables).  Picks the block size on plain traversal, then the
+    table configuration (or none) of the closest-hit items and of the any-hit
+    items in turn.  Every candidate must return the same results."""
+    grid = BATCH_TABLE_GRID if table_grid is None else table_grid
+    blocks = BATCH_BLOCK_GRID if block_grid is None else block_grid
+    reference = None
+
+    def measure(cfg_c, cfg_a, block):
+        nonlocal reference
+        setup = BatchSetup(items, frames, cfg_c, cfg_a, block)
+        ms = _time(setup.step, reps)
+        d = _batch_digest(items, setup.hits())
+        setup.close()
+        reference = reference or d
+        if d != reference:
+            raise AssertionError(f"configuration {cfg_c}, {cfg_a}, {block} changed the results")
+        return ms
+
+    tried = []
+    block_ms = [(measure(None, None, b), b) for b in blocks]
+    best_ms, block = min(block_ms)
+    tried += [dict(closest=None, any=None, block_threads=b, ms=m) for m, b in block_ms]
+    plain_ms = best_ms
+    choice = {"closest": None, "any": None}
+    for mode in ("closest", "any"):
+        for cfg in grid:
+            if cfg is None:
+                continue
+            trial = dict(choice, **{mode: cfg})
+            ms = measure(trial["closest"], trial["any"], block)
+            tried.append(dict(trial, block_threads=block, ms=ms))
+            if ms < best_ms:
+                best_ms, choice = ms, trial
+    return dict(closest=choice["closest"], any=choice["any"], block_threads=block, ms=best_ms, plain_ms=plain_ms,
+                tried=tried)
 
 
 def main():

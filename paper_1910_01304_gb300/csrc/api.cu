@@ -492,6 +492,23 @@ hrpp_status hrpp_table_import(hrpp_table *t, const uint64_t *host_words, size_t 
     return HRPP_OK;
 }
 
+hrpp_status hrpp_table_copy(hrpp_table *dst, const hrpp_table *src, void *stream)
+{
+    if (!dst || !src) return fail(HRPP_ERR_INVALID_ARG, "NULL argument");
+    if (dst == src) return HRPP_OK;
+    if (dst->device != src->device) return fail(HRPP_ERR_INVALID_ARG, "tables on different devices");
+    if (dst->log2_entries != src->log2_entries || dst->log2_ways != src->log2_ways ||
+        dst->precision != src->precision || dst->go_up != src->go_up)
+        return fail(HRPP_ERR_INVALID_ARG, "tables differ in size, ways, precision or Go Up Level");
+    DeviceGuard g(dst->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    const uint64_t n = 1ull << dst->log2_entries;
+    cudaError_t e = cudaMemcpyAsync(dst->d_words, src->d_words, n * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "table copy");
+    dst->bound_scene = src->bound_scene;
+    return HRPP_OK;
+}
+
 hrpp_status hrpp_table_get_config(const hrpp_table *t, int *log2_entries, int *ways, int *precision_bits,
                                   int *update_mode)
 {

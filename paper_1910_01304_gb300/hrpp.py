@@ -82,6 +82,7 @@ def _load():
         "hrpp_table_reset": (st, [P, P]),
         "hrpp_table_export": (st, [P, P, sz]),
         "hrpp_table_import": (st, [P, P, sz]),
+        "hrpp_table_copy": (st, [P, P, P]),
         "hrpp_table_get_config": (st, [P, P, P, P, P]),
         "hrpp_table_destroy": (None, [P]),
         "hrpp_trace": (st, [P, P, P, u32, i32, P, P, P]),
@@ -128,6 +129,7 @@ hrpp_table_set_go_up = _lib.hrpp_table_set_go_up
 hrpp_table_reset = _lib.hrpp_table_reset
 hrpp_table_export = _lib.hrpp_table_export
 hrpp_table_import = _lib.hrpp_table_import
+hrpp_table_copy = _lib.hrpp_table_copy
 hrpp_table_get_config = _lib.hrpp_table_get_config
 hrpp_table_destroy = _lib.hrpp_table_destroy
 hrpp_trace = _lib.hrpp_trace
@@ -267,6 +269,10 @@ class Table:
     def import_(self, words: np.ndarray):
         words = np.ascontiguousarray(words, np.uint64)
         check(hrpp_table_import(self.handle, _ptr(words), words.shape[0]))
+
+    def copy_from(self, src: "Table", stream=None):
+        """Device-to-device copy of src's words (hrpp_table_copy)."""
+        check(hrpp_table_copy(self.handle, src.handle, _stream_handle(stream)))
 
     def close(self):
         if getattr(self, "handle", None):

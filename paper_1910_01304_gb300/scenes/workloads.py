@@ -124,12 +124,23 @@ def batched_item(kind: str, n_tris: int, n_rays: int, seed: int, width: int = 4)
     n_cam = n_rays // 2
     w = max(1, int(np.ceil(np.sqrt(n_cam * 16 / 9))))
     h = max(1, int(np.ceil(n_cam / w)))
-    cam = pinhole_rays(eye, tgt, 60.0, w, h, seed=seed)[:n_cam]
-    rnd = sphere_rays(n_rays - n_cam, seed, float(lo.min()), float(hi.max()))
-    rays = np.ascontiguousarray(np.concatenate([cam, rnd]), np.float32)
     s = Scene(f"{kind}{seed}", tris, nodes, prim, root, width,
               dict(eye=eye, target=tgt, vfov=60.0, width=w, height=h, seed=seed))
-    return s, rays
+    return s, batched_rays(s, n_rays, 0)
+
+
+def batched_rays(scene: Scene, n_rays: int, frame: int) -> np.ndarray:
+    """The rays of a batched-workload scene for one frame: the camera half
+    at pixel centres (frame 0) or jittered (frame > 0), the random half drawn
+    from a stream of its own per frame."""
+    cam = scene.camera
+    _, _, lo, hi = _camera_for(scene.tris)
+    n_cam = n_rays // 2
+    c = pinhole_rays(cam["eye"], cam["target"], cam["vfov"], cam["width"], cam["height"], seed=cam["seed"],
+                     frame=frame)[:n_cam]
+    rseed = cam["seed"] if frame == 0 else cam["seed"] + 7919 * frame
+    rnd = sphere_rays(n_rays - n_cam, rseed, float(lo.min()), float(hi.max()))
+    return np.ascontiguousarray(np.concatenate([c, rnd]), np.float32)
 
 
 def batched_workload(n_scenes: int = 64, tris_range=(10_000, 2_000_000), rays_range=(4_096, 2_000_000),

@@ -24,3 +24,41 @@ def test_autotune_small_scene():
     assert len(r["table_times"]) == 16
     if r["best_table"] is not None:
         assert r["best_ms"] <= r["plain_ms"]
+
+
+def test_tune_batch_and_warm_snapshot_protocol():
+    """The batched autotuner on a small uneven batch: it returns a
+    configuration from its grid (every candidate gave identical results, or
+    it would have raised), and a BatchSetup step with the tuned tables
+    returns exactly the plain hits, step after step."""
+    import numpy as np
+    import torch
+    H = hrpp_mod()
+    from paper_1910_01304_gb300 import autotune
+    items, frames = [], [[], [], []]
+    for s, rays in W.batched_workload(n_scenes=6, tris_range=(2000, 20_000), rays_range=(2000, 20_000), seed=4):
+        g = H.Scene.from_workload(s)
+        half = len(rays) // 2
+        per_frame = [rays] + [W.batched_rays(s, len(rays), f) for f in (1, 2)]
+        for lo, hi, mode in ((0, half, H.HRPP_CLOSEST_HIT), (half, len(rays), H.HRPP_ANY_HIT)):
+            items.append((g, mode))
+            for f, r in enumerate(per_frame):
+                frames[f].append(torch.from_numpy(np.ascontiguousarray(r[lo:hi])).cuda())
+    grid = [None, dict(log2_entries=12, ways=1, precision=6), dict(log2_entries=14, ways=2, precision=5)]
+    r = autotune.tune_batch(items, frames, table_grid=grid, block_grid=(128,), reps=2)
+    assert r["block_threads"] == 128 and r["closest"] in grid and r["any"] in grid
+    assert len(r["tried"]) == 1 + 2 * 2
+    plain = autotune.BatchSetup(items, frames, None, None, 128)
+    plain.step()
+    cfg = grid[1]
+    tuned = autotune.BatchSetup(items, frames, cfg, cfg, 128)
+    for _ in range(2):
+        tuned.step()
+        torch.cuda.synchronize()
+        for (_, mode), a, b in zip(items, plain.hits(), tuned.hits()):
+            if mode == H.HRPP_CLOSEST_HIT:
+                assert torch.equal(a.view(torch.int32), b.view(torch.int32))
+            else:
+                assert torch.equal(a == -1, b == -1)
+    plain.close()
+    tuned.close()

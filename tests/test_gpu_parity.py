@@ -195,6 +195,37 @@ def test_table_bound_to_its_scene_and_roundtrip(H, small_pair):
     assert np.array_equal(tab.export(), words)
 
 
+def test_table_copy_restores_a_snapshot(H, small_pair):
+    """hrpp_table_copy: a device snapshot of a warm table, restored after the
+    table moved on, gives the words and the next batch's results, counters
+    and words that the oracle gives from the same snapshot."""
+    import torch
+    s, g = small_pair[1]
+    tab, snap = H.Table(12, 2, 6), H.Table(12, 2, 6)
+    for f in (1, 2):
+        H.trace(g, torch.from_numpy(s.primary_rays(frame=f)).cuda(), H.HRPP_CLOSEST_HIT, tab)
+    snap.copy_from(tab)
+    torch.cuda.synchronize()
+    words = snap.export()
+    assert np.array_equal(words, tab.export()) and (words != np.uint64(2**64 - 1)).any()
+    H.trace(g, torch.from_numpy(s.primary_rays(frame=3)).cuda(), H.HRPP_CLOSEST_HIT, tab)
+    assert not np.array_equal(tab.export(), words)
+    tab.copy_from(snap)
+    assert np.array_equal(tab.export(), words)
+    rays = s.primary_rays(frame=4)
+    otab = O.Table(12, 2, 6, O.TWO_PHASE)
+    otab.words[:] = words
+    oh, ost = _oracle(s, rays, O.CLOSEST_HIT, otab)
+    gh, gst = gpu_trace(H, g, rays, O.CLOSEST_HIT, tab)
+    assert_same_hits(O.CLOSEST_HIT, gh, oh)
+    assert_same_stats(gst, ost)
+    assert np.array_equal(tab.export(), otab.words)
+    for bad in (H.Table(12, 4, 6), H.Table(12, 2, 5), H.Table(13, 2, 6), H.Table(12, 2, 6, go_up=1)):
+        with pytest.raises(H.HrppError) as err:
+            bad.copy_from(snap)
+        assert err.value.status == H.HRPP_ERR_INVALID_ARG
+
+
 def test_block_sizes_give_identical_results(H, small_pair):
     s, g = small_pair[1]
     rays = s.primary_rays(frame=5)
