@@ -825,6 +825,8 @@ def main():
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                      "algorithmic_bytes_per_launch": bytes_launch,
+                     "node_tests_per_s": {"box": (st_dom["box_tests"] + st_dom["pred_box_tests"]) / (kt[dom] * 1e-3),
+                                          "triangle": (st_dom["tri_tests"] + st_dom["pred_tri_tests"]) / (kt[dom] * 1e-3)},
                      "traffic_source_hash": traffic_src, "kernel_source_hash": kernel_source_hash()},
         "cpu_baseline": cpu,
         "e2e": e2e,
