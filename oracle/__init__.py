@@ -24,6 +24,7 @@ _lib = None
 ANY_HIT, CLOSEST_HIT = 0, 1
 TWO_PHASE, SEQUENTIAL, UNBOUNDED = 0, 1, 2
 VERIFY_ROOT, VERIFY_BOTTOM_UP = 0, 1
+HASH_EXP_MSB, HASH_EXP_LSB = 0, 1
 NO_HIT = 0xFFFFFFFF
 EMPTY_WORD = 0xFFFFFFFFFFFFFFFF
 TAG_BITS, LEAF_BITS = 36, 28
@@ -54,7 +55,7 @@ class _Scene(ctypes.Structure):
 class _Table(ctypes.Structure):
     _fields_ = [("words", ctypes.c_void_p), ("log2_sets", ctypes.c_int), ("log2_ways", ctypes.c_int),
                 ("precision", ctypes.c_int), ("update_mode", ctypes.c_int), ("unbounded", ctypes.c_void_p),
-                ("go_up", ctypes.c_int)]
+                ("go_up", ctypes.c_int), ("hash_variant", ctypes.c_int)]
 
 
 def _L():
@@ -66,7 +67,9 @@ def _L():
             P, u32, u64, i32, f32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_float
             sig = {
                 "orc_hash_float": (u32, [f32, i32]),
+                "orc_hash_float_variant": (u32, [f32, i32, i32]),
                 "orc_ray_key": (u64, [P, i32]),
+                "orc_ray_key_variant": (u64, [P, i32, i32]),
                 "orc_mix48": (u64, [u64]),
                 "orc_ray_triangle": (i32, [P, P, P, P, P, P, P]),
                 "orc_ray_inverse": (None, [P, P, P]),
@@ -104,8 +107,14 @@ def hash_float(f: float, p: int) -> int:
     return int(_L().orc_hash_float(ctypes.c_float(f), p))
 
 
-def ray_key(ray, p: int) -> int:
+def ray_key(ray, p: int, variant: int = 0) -> int:
+    if variant:
+        return int(_L().orc_ray_key_variant(_p(_f(ray, 8)), p, variant))
     return int(_L().orc_ray_key(_p(_f(ray, 8)), p))
+
+
+def hash_float_variant(f: float, p: int, variant: int) -> int:
+    return int(_L().orc_hash_float_variant(ctypes.c_float(f), p, variant))
 
 
 def ray_keys(rays: np.ndarray, p: int) -> np.ndarray:
@@ -172,7 +181,7 @@ class Table:
     """Predictor table state held by the oracle (bounded modes: numpy words)."""
 
     def __init__(self, log2_entries: int, ways: int = 1, precision: int = 6, update_mode: int = TWO_PHASE,
-                 go_up: int = 0):
+                 go_up: int = 0, hash_variant: int = 0):
         log2_ways = {1: 0, 2: 1, 4: 2, 8: 3}[ways]
         if log2_entries - log2_ways < 0:
             raise ValueError("fewer entries than ways")
@@ -184,7 +193,9 @@ class Table:
         n_words = 1 << log2_entries if update_mode != UNBOUNDED else 1
         self.words = np.full(n_words, EMPTY_WORD, np.uint64)
         self.go_up = go_up
-        self._c = _Table(self.words.ctypes.data, self.log2_sets, self.log2_ways, precision, update_mode, None, go_up)
+        self.hash_variant = hash_variant
+        self._c = _Table(self.words.ctypes.data, self.log2_sets, self.log2_ways, precision, update_mode, None, go_up,
+                         hash_variant)
 
     def reset(self):
         self.words[:] = EMPTY_WORD

@@ -19,6 +19,9 @@
  *                                    hashes XORed with the swizzled direction
  *                                    hashes (ox^dz, oy^dy, oz^dx) and packed
  *                                    into at most 48 bits (16-bit fields).
+ *   orc_hash_float_variant           the same with the p least significant
+ *                                    exponent bits (a tuning variant, not
+ *                                    the paper's definition).
  *   orc_mix48, set/tag, way          the bounded table's index (the paper
  *                                    indexes an unbounded map by the key,
  *                                    Sec. 4.2; a bounded table needs a set
@@ -78,7 +81,13 @@ typedef struct {
     int update_mode;
     void *unbounded;  /* private state of the unbounded map */
     int go_up;        /* Sec. 6.2 Go Up Level: 0 = leaves, G > 0 = the ancestor G levels up */
+    int hash_variant; /* ORC_HASH_EXP_MSB (Sec. 5, the default) or ORC_HASH_EXP_LSB */
 } orc_table;
+
+/* Which exponent bits the per-float hash keeps: the p most significant ones
+ * (Sec. 5 as written) or, as a tuning variant, the p least significant ones,
+ * which tell neighbouring binades apart. */
+enum { ORC_HASH_EXP_MSB = 0, ORC_HASH_EXP_LSB = 1 };
 
 /* statistics counters, in this order */
 enum {
@@ -109,14 +118,29 @@ uint32_t orc_hash_float(float f, int p)
     return (sign << (2 * p)) | ((expo >> (8 - p)) << p) | (mant >> (23 - p));
 }
 
-/* Sec. 5: XOR origin hashes with swizzled direction hashes, pack to 48 bits. */
-uint64_t orc_ray_key(const float *ray, int p)
+/* The exponent-LSB variant: sign, then the p least significant exponent
+ * bits, then the p most significant mantissa bits (same field layout). */
+uint32_t orc_hash_float_variant(float f, int p, int variant)
 {
-    uint64_t h0 = orc_hash_float(ray[0], p) ^ orc_hash_float(ray[6], p);
-    uint64_t h1 = orc_hash_float(ray[1], p) ^ orc_hash_float(ray[5], p);
-    uint64_t h2 = orc_hash_float(ray[2], p) ^ orc_hash_float(ray[4], p);
+    if (variant != ORC_HASH_EXP_LSB) return orc_hash_float(f, p);
+    uint32_t b;
+    memcpy(&b, &f, sizeof b);
+    uint32_t sign = b >> 31;
+    uint32_t expo = (b >> 23) & 0xFFu;
+    uint32_t mant = b & 0x7FFFFFu;
+    return (sign << (2 * p)) | ((expo & ((1u << p) - 1u)) << p) | (mant >> (23 - p));
+}
+
+/* Sec. 5: XOR origin hashes with swizzled direction hashes, pack to 48 bits. */
+uint64_t orc_ray_key_variant(const float *ray, int p, int variant)
+{
+    uint64_t h0 = orc_hash_float_variant(ray[0], p, variant) ^ orc_hash_float_variant(ray[6], p, variant);
+    uint64_t h1 = orc_hash_float_variant(ray[1], p, variant) ^ orc_hash_float_variant(ray[5], p, variant);
+    uint64_t h2 = orc_hash_float_variant(ray[2], p, variant) ^ orc_hash_float_variant(ray[4], p, variant);
     return h0 | (h1 << 16) | (h2 << 32);
 }
+
+uint64_t orc_ray_key(const float *ray, int p) { return orc_ray_key_variant(ray, p, ORC_HASH_EXP_MSB); }
 
 /* Bijective 48-bit mixer (xorshift-multiply rounds, odd multipliers). */
 uint64_t orc_mix48(uint64_t k)
@@ -664,7 +688,7 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
             stats[S_LOOKUPS] += 1;
             if (!tab) {
                 /* learned proposal only */
-            } else if ((key = orc_ray_key(ray, tab->precision)), bounded) {
+            } else if ((key = orc_ray_key_variant(ray, tab->precision, tab->hash_variant)), bounded) {
                 uint64_t m = orc_mix48(key);
                 set = m & ((1ull << tab->log2_sets) - 1ull);
                 tag = (m >> tab->log2_sets) & ((1ull << TAG_BITS) - 1ull);

@@ -39,6 +39,32 @@ def test_hash_worked_values():
             assert O.hash_float(f, p) == int(row[1 + p]), (row, p)
 
 
+def test_hash_exponent_lsb_variant_worked_values():
+    """The tuning variant that keeps the exponent's least significant bits."""
+    rows = _rows("hash_lsb_worked_values.txt")
+    assert len(rows) == 6
+    for row in rows:
+        f = float(row[0])
+        assert _bits(f) == int(row[1], 16), row
+        for p in range(1, 8):
+            assert O.hash_float_variant(f, p, O.HASH_EXP_LSB) == int(row[1 + p]), (row, p)
+            assert O.hash_float_variant(f, p, O.HASH_EXP_MSB) == O.hash_float(f, p)
+
+
+def test_hash_variants_split_binades_differently():
+    """The Sec. 5 hash aliases neighbouring binades (1.0, 0.5, 0.25 share
+    their top exponent bits); the LSB variant separates them but aliases
+    binades 2^p apart instead."""
+    p = 3
+    msb = [O.hash_float(2.0 ** -k, p) for k in range(4)]
+    lsb = [O.hash_float_variant(2.0 ** -k, p, O.HASH_EXP_LSB) for k in range(4)]
+    assert len(set(msb)) == 1 and len(set(lsb)) == 4
+    assert O.hash_float_variant(1.0, p, O.HASH_EXP_LSB) == O.hash_float_variant(2.0 ** -8, p, O.HASH_EXP_LSB)
+    ray = [1.0, 0.5, 0.25, 0.0, 0.6, -0.8, 0.0, 1.0]
+    assert O.ray_key(ray, p, O.HASH_EXP_LSB) != O.ray_key(ray, p)
+    assert O.ray_key(ray, p, O.HASH_EXP_MSB) == O.ray_key(ray, p)
+
+
 def test_ray_key_worked_values():
     for row in _rows("ray_key_worked_values.txt"):
         ox, oy, oz, dx, dy, dz = map(float, row[:6])

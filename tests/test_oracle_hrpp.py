@@ -435,3 +435,20 @@ def test_bottom_up_on_a_root_leaf_scene():
     assert n_hit > 0 and sb["true_pos"] == n_hit
     assert sb["box_tests"] == 0 and sb["interior_nodes"] == 0
     assert sb["leaves"] == len(rays) - n_hit      # only false positives traverse (the root leaf)
+
+
+def test_exponent_lsb_hash_variant_keeps_results(small):
+    """The exponent-LSB hash variant files rays under other keys (so other
+    table words and predictions) but never changes a result."""
+    tm = O.Table(12, 2, 6, O.TWO_PHASE)
+    tl = O.Table(12, 2, 6, O.TWO_PHASE, hash_variant=O.HASH_EXP_LSB)
+    tp = 0
+    for frame in range(3):
+        rays = small.primary_rays(frame=frame)[::2]
+        hp, _ = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.CLOSEST_HIT)
+        hm, sm = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.CLOSEST_HIT, tm)
+        hl, sl = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.CLOSEST_HIT, tl)
+        assert hp.tobytes() == hm.tobytes() == hl.tobytes()
+        tp += sl["true_pos"]
+        _check_identities(sl, len(rays))
+    assert tp > 0 and not np.array_equal(tm.words, tl.words)
