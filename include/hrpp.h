@@ -236,6 +236,16 @@ hrpp_status hrpp_table_configure(hrpp_table *table, int precision_bits, int upda
  * Scenes whose root is a leaf store nothing for G > 0.  Changing G makes the
  * stored words meaningless: reset the table with it. */
 hrpp_status hrpp_table_set_go_up(hrpp_table *table, int go_up_level);
+/* Which exponent bits the ray hash keeps (a tuning knob; results never
+ * depend on it): HRPP_HASH_EXP_MSB (default) takes the p most significant
+ * exponent bits, as Sec. 5 defines the hash; HRPP_HASH_EXP_LSB takes the p
+ * least significant ones, which separates neighbouring binades (1.0, 0.5,
+ * 0.25 ...) that the Sec. 5 hash files under one key.  Sign and mantissa
+ * bits are as in Sec. 5.  Changing it makes the stored words meaningless:
+ * reset the table with it.  Other values: HRPP_ERR_INVALID_ARG. */
+#define HRPP_HASH_EXP_MSB 0
+#define HRPP_HASH_EXP_LSB 1
+hrpp_status hrpp_table_set_hash(hrpp_table *table, int hash_variant);
 /* Empties the table (asynchronous on stream) and unbinds it from its scene.
  * A table binds to the first scene it is traced with; tracing it with
  * another scene returns INVALID_ARG until it is reset. */
@@ -248,7 +258,8 @@ hrpp_status hrpp_table_import(hrpp_table *table, const uint64_t *host_words, siz
 /* Device-to-device copy of src's words into dst, asynchronous on `stream`
  * (e.g. to restore a warm snapshot before each frame without a host round
  * trip).  Both tables must be on the same device with the same
- * log2_entries, ways, precision and Go Up Level, else HRPP_ERR_INVALID_ARG;
+ * log2_entries, ways, precision, Go Up Level and hash variant, else
+ * HRPP_ERR_INVALID_ARG;
  * dst takes src's scene binding.  The update mode of dst is unchanged. */
 hrpp_status hrpp_table_copy(hrpp_table *dst, const hrpp_table *src, void *stream);
 hrpp_status hrpp_table_get_config(const hrpp_table *table, int *log2_entries, int *ways, int *precision_bits,

@@ -1,12 +1,16 @@
 """Autotuner for HRPP launch and predictor-table parameters.
 
 Nothing it picks can change a result: every candidate traces the same rays
-and the tuner checks that all of them return bit-identical hits.  It times,
-with CUDA events on the current stream:
+and the tuner checks that all of them return the same results.  Closest-hit
+hits are compared bit for bit; any-hit results by their occlusion bit, the only
+part of them that is defined (a ray answered by a predicted node may report
+another occluder than plain traversal finds first).  It times, with CUDA
+events on the current stream:
   1. the traversal launch shape (threads per block, ray schedule) on plain
      traversal;
   2. predictor tables over a grid of sizes, associativities, hash precisions
-     (Sec. 5.1's tight-vs-loose trade-off) and Go Up Levels (Sec. 6.2): each
+     (Sec. 5.1's tight-vs-loose trade-off; p = 1..7), the exponent bits the
+     hash keeps (most or least significant) and Go Up Levels (Sec. 6.2): each
      table is warmed on one ray set (a previous frame) and then frozen while
      a second ray set is timed, so the timing sees realistic prediction rates
      and no self-prediction.
@@ -31,7 +35,8 @@ from . import hrpp as H
 
 LAUNCH_GRID = [dict(block_threads=b, schedule=s) for b in (64, 128, 256)
                for s in (H.HRPP_SCHEDULE_BATCH, H.HRPP_SCHEDULE_REFILL)]
-TABLE_GRID = dict(log2_entries=(14, 16, 18, 20), ways=(1, 2, 4), precision=(4, 5, 6, 7), go_up=(0, 1))
+TABLE_GRID = dict(log2_entries=(14, 16, 18, 20), ways=(1, 2, 4), precision=(1, 2, 3, 4, 5, 6, 7), go_up=(0, 1),
+                  hash=(H.HRPP_HASH_EXP_MSB, H.HRPP_HASH_EXP_LSB))
 
 
 def _time(fn, reps: int) -> float:
@@ -48,8 +53,13 @@ def _time(fn, reps: int) -> float:
     return float(np.median(ts))
 
 
-def _digest(t) -> str:
-    return hashlib.sha1(t.cpu().numpy().tobytes()).hexdigest()
+def _digest(t, mode: int) -> str:
+    """Closest-hit results bit for bit; any-hit results as the occlusion bit
+    (a ray answered by a predicted node may report another occluder)."""
+    a = t.cpu().numpy()
+    if mode != H.HRPP_CLOSEST_HIT:
+        a = a.view(np.uint32) != H.HRPP_NO_HIT
+    return hashlib.sha1(a.tobytes()).hexdigest()
 
 
 def tune(scene: H.Scene, rays_warm, rays_eval, mode: int, table_grid: dict | None = None, reps: int = 5,
@@ -66,7 +76,7 @@ def tune(scene: H.Scene, rays_warm, rays_eval, mode: int, table_grid: dict | Non
     launch_times = []
     for cfg in launches:
         ms = _time(lambda: H.trace(scene, rays_eval, mode, None, hits=out, **cfg), reps)
-        d = _digest(out)
+        d = _digest(out, mode)
         reference = reference or d
         if d != reference:
             raise AssertionError(f"launch shape {cfg} changed the result")
@@ -77,11 +87,12 @@ def tune(scene: H.Scene, rays_warm, rays_eval, mode: int, table_grid: dict | Non
     keys = list(grid)
     for values in itertools.product(*(grid[k] for k in keys)):
         tc = dict(zip(keys, values))
-        t = H.Table(tc["log2_entries"], tc["ways"], tc["precision"], H.HRPP_UPDATE_TWO_PHASE, go_up=tc["go_up"])
+        t = H.Table(tc["log2_entries"], tc["ways"], tc["precision"], H.HRPP_UPDATE_TWO_PHASE, go_up=tc.get("go_up", 0),
+                    hash_variant=tc.get("hash", H.HRPP_HASH_EXP_MSB))
         H.trace(scene, rays_warm, mode, t, **launch)
         t.configure(tc["precision"], H.HRPP_UPDATE_FROZEN)
         ms = _time(lambda: H.trace(scene, rays_eval, mode, t, hits=out, **launch), reps)
-        if _digest(out) != reference:
+        if _digest(out, mode) != reference:
             raise AssertionError(f"table {tc} changed the result")
         table_times.append(dict(tc, ms=ms))
         if ms < best["ms"]:
@@ -92,8 +103,8 @@ def tune(scene: H.Scene, rays_warm, rays_eval, mode: int, table_grid: dict | Non
                 launch_times=[dict(c, ms=m) for m, c in launch_times], table_times=table_times)
 
 
-BATCH_TABLE_GRID = [None] + [dict(log2_entries=e, ways=w, precision=p) for e in (14, 16) for w in (1, 2)
-                              for p in (5, 6)]
+BATCH_TABLE_GRID = [None] + [dict(log2_entries=e, ways=w, precision=p, hash=h) for e in (14, 16) for w in (1, 2)
+                              for p in (5, 6) for h in (H.HRPP_HASH_EXP_MSB, H.HRPP_HASH_EXP_LSB)]
 BATCH_BLOCK_GRID = (128, 256)
 
 
@@ -110,7 +121,8 @@ class BatchSetup:
             if cfg is None:
                 self.tables.append(None)
                 continue
-            self.tables.append(H.Table(cfg["log2_entries"], cfg["ways"], cfg["precision"]))
+            self.tables.append(H.Table(cfg["log2_entries"], cfg["ways"], cfg["precision"],
+                                       hash_variant=cfg.get("hash", H.HRPP_HASH_EXP_MSB)))
         self.batches = [H.Batch([(sc, t, rays, mode) for (sc, mode), t, rays in zip(items, self.tables, fr)],
                                 stats=stats and k == 0, block_threads=block_threads)
                         for k, fr in enumerate(frames)]
@@ -120,7 +132,7 @@ class BatchSetup:
             if t is None:
                 self.snaps.append(None)
                 continue
-            snap = H.Table(t.log2_entries, t.ways, t.precision)
+            snap = H.Table(t.log2_entries, t.ways, t.precision, hash_variant=t.hash_variant)
             snap.copy_from(t)
             self.snaps.append(snap)
 

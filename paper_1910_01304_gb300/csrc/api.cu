@@ -453,6 +453,15 @@ hrpp_status hrpp_table_set_go_up(hrpp_table *t, int go_up_level)
     return HRPP_OK;
 }
 
+hrpp_status hrpp_table_set_hash(hrpp_table *t, int hash_variant)
+{
+    if (!t) return fail(HRPP_ERR_INVALID_ARG, "table is NULL");
+    if (hash_variant != HRPP_HASH_EXP_MSB && hash_variant != HRPP_HASH_EXP_LSB)
+        return fail(HRPP_ERR_INVALID_ARG, "unknown hash variant %d", hash_variant);
+    t->hash_variant = hash_variant;
+    return HRPP_OK;
+}
+
 hrpp_status hrpp_table_reset(hrpp_table *t, void *stream)
 {
     if (!t) return fail(HRPP_ERR_INVALID_ARG, "table is NULL");
@@ -498,8 +507,8 @@ hrpp_status hrpp_table_copy(hrpp_table *dst, const hrpp_table *src, void *stream
     if (dst == src) return HRPP_OK;
     if (dst->device != src->device) return fail(HRPP_ERR_INVALID_ARG, "tables on different devices");
     if (dst->log2_entries != src->log2_entries || dst->log2_ways != src->log2_ways ||
-        dst->precision != src->precision || dst->go_up != src->go_up)
-        return fail(HRPP_ERR_INVALID_ARG, "tables differ in size, ways, precision or Go Up Level");
+        dst->precision != src->precision || dst->go_up != src->go_up || dst->hash_variant != src->hash_variant)
+        return fail(HRPP_ERR_INVALID_ARG, "tables differ in size, ways, precision, Go Up Level or hash variant");
     DeviceGuard g(dst->device);
     if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
     const uint64_t n = 1ull << dst->log2_entries;
@@ -652,6 +661,7 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
             p.precision = table->precision;
             p.update_mode = table->update_mode;
             p.go_up = table->go_up;
+            p.hash_variant = table->hash_variant;
         }
         cudaEvent_t ev0 = opts ? (cudaEvent_t)opts->kernel_start : nullptr;
         cudaEvent_t ev1 = opts ? (cudaEvent_t)opts->kernel_stop : nullptr;

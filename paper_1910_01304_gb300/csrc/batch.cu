@@ -170,6 +170,7 @@ hrpp_status hrpp_batch_create(const hrpp_batch_item *items, uint32_t n_items, in
                 p.precision = it.table->precision;
                 p.update_mode = it.table->update_mode;
                 p.go_up = it.table->go_up;
+                p.hash_variant = it.table->hash_variant;
                 if (it.table->update_mode == HRPP_UPDATE_TWO_PHASE) {
                     p.records = b->d_records + rec_off;
                     rec_off += it.n_rays;

@@ -73,28 +73,31 @@ struct TraceParams {
     const int32_t *canon_ref;    // canonical node -> device ref
     uint32_t n_nodes;            // canonical node count
     int verify;                  // closest-hit true positives: 0 root traversal, 1 bottom-up climb
+    int hash_variant;            // 0: exponent MSBs (Sec. 5), 1: exponent LSBs
 };
 
 // ---------------------------------------------------------------- hashing --
 
 // Sec. 5: sign bit, then the p most significant exponent bits, then the p most
-// significant mantissa bits of the float's IEEE-754 encoding.
-__device__ __forceinline__ uint32_t hash_float(float f, int p)
+// significant mantissa bits of the float's IEEE-754 encoding.  lsb: the
+// tuning variant that keeps the p least significant exponent bits instead.
+__device__ __forceinline__ uint32_t hash_float(float f, int p, bool lsb)
 {
     const uint32_t b = __float_as_uint(f);
     const uint32_t sign = b >> 31;
     const uint32_t expo = (b >> 23) & 0xFFu;
     const uint32_t mant = b & 0x7FFFFFu;
-    return (sign << (2 * p)) | ((expo >> (8 - p)) << p) | (mant >> (23 - p));
+    const uint32_t e = lsb ? (expo & ((1u << p) - 1u)) : (expo >> (8 - p));
+    return (sign << (2 * p)) | (e << p) | (mant >> (23 - p));
 }
 
 // Sec. 5: origin hashes XOR the swizzled direction hashes (o.x^d.z, o.y^d.y,
 // o.z^d.x), packed into 16-bit fields of a 48-bit key.
-__device__ __forceinline__ uint64_t ray_key(float4 o, float4 d, int p)
+__device__ __forceinline__ uint64_t ray_key(float4 o, float4 d, int p, bool lsb = false)
 {
-    const uint64_t h0 = hash_float(o.x, p) ^ hash_float(d.z, p);
-    const uint64_t h1 = hash_float(o.y, p) ^ hash_float(d.y, p);
-    const uint64_t h2 = hash_float(o.z, p) ^ hash_float(d.x, p);
+    const uint64_t h0 = hash_float(o.x, p, lsb) ^ hash_float(d.z, p, lsb);
+    const uint64_t h1 = hash_float(o.y, p, lsb) ^ hash_float(d.y, p, lsb);
+    const uint64_t h2 = hash_float(o.z, p, lsb) ^ hash_float(d.x, p, lsb);
     return h0 | (h1 << 16) | (h2 << 32);
 }
 

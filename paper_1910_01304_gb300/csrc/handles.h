@@ -29,6 +29,7 @@ struct hrpp_table {
     int log2_entries, log2_ways, log2_sets;
     int precision, update_mode;
     int go_up;
+    int hash_variant;  // HRPP_HASH_EXP_MSB or HRPP_HASH_EXP_LSB
     uint64_t *d_words;
     uint32_t *d_winner;
     uint64_t bound_scene;

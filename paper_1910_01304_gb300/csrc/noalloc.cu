@@ -161,6 +161,7 @@ extern "C" hrpp_status hrpp_trace_noalloc(const hrpp_scene *sc, hrpp_table *tabl
             p.precision = table->precision;
             p.update_mode = table->update_mode;
             p.go_up = table->go_up;
+            p.hash_variant = table->hash_variant;
         }
         e = sc->width == 2 ? launch_trace_w2(closest, out_stats != nullptr, 0, p, 128, 0, stream, nullptr, nullptr)
                            : launch_trace_w4(closest, out_stats != nullptr, 0, p, 128, 0, stream, nullptr, nullptr);

@@ -276,7 +276,7 @@ __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayS
         const uint32_t ways = p.table ? (1u << p.log2_ways) : 0u;
         const uint64_t *set = nullptr;
         if (p.table) {
-            const uint64_t m = mix48(ray_key(s.o, s.d, p.precision));
+            const uint64_t m = mix48(ray_key(s.o, s.d, p.precision, p.hash_variant == HRPP_HASH_EXP_LSB));
             s.set = (uint32_t)(m & ((1ull << p.log2_sets) - 1ull));
             s.tag = (m >> p.log2_sets) & kTagMask;
             set = p.table + ((uint64_t)s.set << p.log2_ways);

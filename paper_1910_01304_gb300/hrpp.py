@@ -51,6 +51,7 @@ class hrpp_trace_opts(ctypes.Structure):
 
 HRPP_SCHEDULE_DEFAULT, HRPP_SCHEDULE_BATCH, HRPP_SCHEDULE_REFILL = 0, 1, 2
 HRPP_VERIFY_ROOT, HRPP_VERIFY_BOTTOM_UP = 0, 1
+HRPP_HASH_EXP_MSB, HRPP_HASH_EXP_LSB = 0, 1
 
 
 class hrpp_batch_item(ctypes.Structure):
@@ -79,6 +80,7 @@ def _load():
         "hrpp_table_create": (st, [i32, i32, P]),
         "hrpp_table_configure": (st, [P, i32, i32]),
         "hrpp_table_set_go_up": (st, [P, i32]),
+        "hrpp_table_set_hash": (st, [P, i32]),
         "hrpp_table_reset": (st, [P, P]),
         "hrpp_table_export": (st, [P, P, sz]),
         "hrpp_table_import": (st, [P, P, sz]),
@@ -126,6 +128,7 @@ hrpp_scene_destroy = _lib.hrpp_scene_destroy
 hrpp_table_create = _lib.hrpp_table_create
 hrpp_table_configure = _lib.hrpp_table_configure
 hrpp_table_set_go_up = _lib.hrpp_table_set_go_up
+hrpp_table_set_hash = _lib.hrpp_table_set_hash
 hrpp_table_reset = _lib.hrpp_table_reset
 hrpp_table_export = _lib.hrpp_table_export
 hrpp_table_import = _lib.hrpp_table_import
@@ -240,7 +243,7 @@ class Table:
     """Predictor table (hrpp_table_create / hrpp_table_configure)."""
 
     def __init__(self, log2_entries: int, ways: int = 1, precision: int = 6, update_mode: int = HRPP_UPDATE_TWO_PHASE,
-                 go_up: int = 0):
+                 go_up: int = 0, hash_variant: int = HRPP_HASH_EXP_MSB):
         h = ctypes.c_void_p()
         check(hrpp_table_create(log2_entries, ways, ctypes.byref(h)))
         self.handle = h
@@ -248,10 +251,15 @@ class Table:
         self.ways = ways
         self.configure(precision, update_mode)
         self.set_go_up(go_up)
+        self.set_hash(hash_variant)
 
     def set_go_up(self, go_up: int):
         check(hrpp_table_set_go_up(self.handle, go_up))
         self.go_up = go_up
+
+    def set_hash(self, hash_variant: int):
+        check(hrpp_table_set_hash(self.handle, hash_variant))
+        self.hash_variant = hash_variant
 
     def configure(self, precision: int, update_mode: int):
         check(hrpp_table_configure(self.handle, precision, update_mode))

@@ -195,6 +195,33 @@ def test_table_bound_to_its_scene_and_roundtrip(H, small_pair):
     assert np.array_equal(tab.export(), words)
 
 
+@pytest.mark.parametrize("width_idx", [0, 1])
+def test_exponent_lsb_hash_matches_oracle(H, small_pair, width_idx):
+    """The exponent-LSB hash variant: hits, counters and table words equal
+    the oracle's over three frames of both query modes, at p = 3 (where the
+    variants file rays differently)."""
+    s, g = small_pair[width_idx]
+    tabs = {m: H.Table(12, 2, 3, hash_variant=H.HRPP_HASH_EXP_LSB) for m in (O.CLOSEST_HIT, O.ANY_HIT)}
+    otabs = {m: O.Table(12, 2, 3, O.TWO_PHASE, hash_variant=O.HASH_EXP_LSB) for m in (O.CLOSEST_HIT, O.ANY_HIT)}
+    msb = O.Table(12, 2, 3, O.TWO_PHASE)
+    for frame in range(3):
+        prim = s.primary_rays(frame=frame)
+        ph, _ = _oracle(s, prim, O.CLOSEST_HIT)
+        shadow, _ = W.secondary_shadow(s, prim, ph["t"], ph["prim"])
+        _oracle(s, prim, O.CLOSEST_HIT, msb)
+        for mode, rays in ((O.CLOSEST_HIT, prim), (O.ANY_HIT, shadow)):
+            oh, ost = _oracle(s, rays, mode, otabs[mode])
+            gh, gst = gpu_trace(H, g, rays, mode, tabs[mode])
+            assert_same_hits(mode, gh, oh, f"frame {frame}")
+            assert_same_stats(gst, ost, msg=f"frame {frame}")
+            assert np.array_equal(tabs[mode].export(), otabs[mode].words)
+    assert not np.array_equal(otabs[O.CLOSEST_HIT].words, msb.words)
+    with pytest.raises(H.HrppError):
+        tabs[O.CLOSEST_HIT].set_hash(2)
+    with pytest.raises(H.HrppError):
+        H.Table(12, 2, 3).copy_from(tabs[O.CLOSEST_HIT])
+
+
 def test_table_copy_restores_a_snapshot(H, small_pair):
     """hrpp_table_copy: a device snapshot of a warm table, restored after the
     table moved on, gives the words and the next batch's results, counters
