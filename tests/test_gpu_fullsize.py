@@ -86,3 +86,80 @@ def test_full_batched_workload_sampled():
         oh, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays[idx], O.CLOSEST_HIT)
         gh = batch.hits[k].cpu().numpy()[idx]
         assert np.array_equal(as_words(gh), as_words(oh)), f"item {k}"
+
+
+def test_full_pathtrace_sampled():
+    """Config 5 at full size: 4,281,344 triangles, 1280x720 x 4 spp x 5
+    diffuse bounces plus a shadow ray per bounce (36.9M rays), traced through
+    HRPP with one 2^18 x 2-way table per query mode shared by all bounces, as
+    bench.py times it.  Each batch is checked on a random sample against the
+    oracle's plain traversal: closest hits bit for bit, shadow rays by their
+    occlusion bit (and the GPU's plain any-hit prim bit for bit)."""
+    import torch
+    H = hrpp_mod()
+    s = W.pathtrace_scene()
+    assert s.n_tris == 4_281_344
+    g = H.Scene.from_workload(s)
+    rng = np.random.default_rng(2)
+
+    def gpu_closest(rays):
+        hits, _ = H.trace(g, torch.from_numpy(np.ascontiguousarray(rays)).cuda(), H.HRPP_CLOSEST_HIT)
+        h = hits.cpu().numpy()
+        return h[:, 0].copy(), h[:, 1].view(np.uint32).copy()
+
+    bounces = W.path_bounces(s, W.path_primary(s, spp=4, frame=0), gpu_closest, bounces=5, frame=0)
+    assert len(bounces) == 5 and sum(len(c) + len(sh) for c, sh in bounces) > 30_000_000
+    tabs = {O.CLOSEST_HIT: H.Table(18, 2, 6), O.ANY_HIT: H.Table(18, 2, 6)}
+    for b, (closest, shadow) in enumerate(bounces):
+        for mode, rays in ((O.CLOSEST_HIT, closest), (O.ANY_HIT, shadow)):
+            d = torch.from_numpy(rays).cuda()
+            gh, gst = H.trace(g, d, mode, tabs[mode], stats=True)
+            torch.cuda.synchronize()
+            g.check()
+            assert gst["rays"] == len(rays)
+            idx = np.sort(rng.choice(len(rays), 800, replace=False))
+            oh, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays[idx], mode)
+            gh = gh.cpu().numpy()[idx]
+            if mode == O.CLOSEST_HIT:
+                assert np.array_equal(as_words(gh), as_words(oh)), f"bounce {b}"
+            else:
+                assert np.array_equal(any_prims(gh) == O.NO_HIT, oh == O.NO_HIT), f"bounce {b}"
+                gp, _ = H.trace(g, d, H.HRPP_ANY_HIT)
+                assert np.array_equal(any_prims(gp.cpu().numpy()[idx]), oh), f"bounce {b} plain"
+
+
+def test_full_learned_proposal_sampled():
+    """Config 4 at full size: the closest-hit proposal trained as bench.py
+    trains it (jittered frames of the small scene's camera until ~30M
+    traces).  On a held-out frame, predictions sampled across the batch are
+    an argmax of the oracle's logits under the trained weights, and traversal
+    with every prediction returns exactly the plain hits."""
+    import torch
+    from oracle import proposal as P
+    H = hrpp_mod()
+    s = W.small_scene()
+    g = H.Scene.from_workload(s)
+    prop = H.Proposal.for_workload(g, s, seed=1)
+    traces, f = 0, 0
+    while traces < 30_000_000:
+        f += 1
+        rays = torch.from_numpy(s.primary_rays(frame=f)).cuda()
+        hits, _ = H.trace(g, rays, H.HRPP_CLOSEST_HIT)
+        prop.train(rays, prop.labels(hits), lr=1e-3)
+        traces += int(rays.shape[0])
+    test_np = s.primary_rays(frame=100_000)
+    test = torch.from_numpy(test_np).cuda()
+    nodes, classes = prop.predict(test)
+    plain, _ = H.trace(g, test, H.HRPP_CLOSEST_HIT)
+    learned, st = H.trace(g, test, H.HRPP_CLOSEST_HIT, stats=True, predicted=nodes)
+    torch.cuda.synchronize()
+    assert torch.equal(plain.view(torch.int32), learned.view(torch.int32))
+    assert st["true_pos"] > 0.4 * st["rays"]
+    rows = np.sort(np.random.default_rng(3).choice(len(test_np), 1500, replace=False))
+    root = s.nodes[s.root]
+    w = P.Weights.from_flat(prop.get_weights())
+    _, _, z = P.forward(w, P.features(test_np[rows], root["lo"], root["hi"]))
+    picked = z[np.arange(len(rows)), classes.cpu().numpy()[rows]]
+    span = z.max(axis=1) - z.min(axis=1)
+    assert np.all(z.max(axis=1) - picked <= 0.02 * span)
+    assert np.mean(classes.cpu().numpy()[rows] == np.argmax(z, axis=1)) > 0.97
