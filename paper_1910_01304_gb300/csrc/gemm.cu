@@ -82,6 +82,25 @@ cudaError_t launch(const void *a, const void *b, const umma::GemmArgs &g, int sp
 
 }  // namespace
 
+cudaError_t softmax_xent(const void *h2, const void *w3, const umma::SoftmaxArgs &g, cudaStream_t s)
+{
+    static bool configured = false;
+    const size_t smem = umma::softmax_smem_bytes<>();
+    if (!configured) {
+        cudaError_t e =
+            cudaFuncSetAttribute(umma::k_softmax_xent<>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    if (g.npad <= 0 || g.npad % umma::BM != 0 || ((uintptr_t)h2 & 15u) || ((uintptr_t)w3 & 15u)) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    cudaError_t e = make_map(&ma, h2, (uint64_t)g.npad, umma::SX_K, umma::BM);
+    if (e == cudaSuccess) e = make_map(&mb, w3, umma::SX_CLASSES, umma::SX_K, umma::SX_BN);
+    if (e != cudaSuccess) return e;
+    umma::k_softmax_xent<><<<g.npad / umma::BM, umma::SX_THREADS, smem, s>>>(ma, mb, g);
+    return cudaGetLastError();
+}
+
 bool gemm_shape_ok(int m, int n, int k, int bn)
 {
     return m > 0 && n > 0 && k > 0 && m % umma::BM == 0 && n % bn == 0 && k % umma::BK == 0;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "umma.cuh"
+#include "umma_softmax.cuh"
 
 namespace hrpp {
 bool gemm_shape_ok(int m, int n, int k, int bn);
@@ -11,4 +12,8 @@ bool gemm_shape_ok(int m, int n, int k, int bn);
 // width bn (128 or 256); splits > 1 divides K across CTAs (EPI_F32_ATOMIC).
 cudaError_t gemm_bf16(const void *a, const void *b, int epi, int bn, const umma::GemmArgs &g, int splits,
                       cudaStream_t s);
+// Fused output layer + softmax cross-entropy (umma_softmax.cuh): h2 [npad,
+// 256] and w3 [4096, 256] bf16, K-major; writes dZ (both layouts), adds the
+// loss and the labelled-row count.
+cudaError_t softmax_xent(const void *h2, const void *w3, const umma::SoftmaxArgs &g, cudaStream_t s);
 }  // namespace hrpp

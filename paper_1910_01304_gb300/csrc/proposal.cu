@@ -146,86 +146,6 @@ __global__ void __launch_bounds__(kFeatRows) k_featurize(const float4 *rays, uin
     }
 }
 
-// Softmax cross-entropy over 16 rows per block (8 warps, two rows each for
-// the row statistics): the loss of every labelled row is summed into
-// loss_sum and the row counted; dZ = softmax - onehot (zero for unlabelled
-// rows) is written in bf16 row-major and, through a shared-memory transpose,
-// column-major, both with 16-byte stores.
-constexpr int kSmRows = 16;
-constexpr int kSmCols = 128;  // columns per transposed chunk
-
-__global__ void __launch_bounds__(256) k_softmax_ce(const float *logits, const int32_t *labels, uint32_t n,
-                                                    uint32_t npad, __nv_bfloat16 *dz, __nv_bfloat16 *dzt,
-                                                    float *loss_sum, unsigned int *count)
-{
-    __shared__ float row_m[kSmRows], row_inv[kSmRows];
-    __shared__ int row_lab[kSmRows];
-    __shared__ __align__(16) __nv_bfloat16 tileT[kSmCols * (kSmRows + 8)];
-    const uint32_t r0 = blockIdx.x * kSmRows;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (int k = 0; k < kSmRows / 8; ++k) {
-        const int lr = warp * (kSmRows / 8) + k;
-        const uint32_t r = r0 + lr;
-        int lab = r < n ? labels[r] : -1;
-        if (lab >= kCls) lab = -1;
-        float m = 0.0f, inv = 0.0f;
-        if (lab >= 0) {
-            const float4 *z = reinterpret_cast<const float4 *>(logits + (size_t)r * kCls);
-            m = -INFINITY;
-            for (int c = lane; c < kCls / 4; c += 32) {
-                const float4 v = z[c];
-                m = fmaxf(m, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
-            }
-            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
-            float sum = 0.0f;
-            for (int c = lane; c < kCls / 4; c += 32) {
-                const float4 v = z[c];
-                sum += expf(v.x - m) + expf(v.y - m) + expf(v.z - m) + expf(v.w - m);
-            }
-            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-            inv = 1.0f / sum;
-            if (lane == 0) {
-                atomicAdd(loss_sum, logf(sum) - (logits[(size_t)r * kCls + lab] - m));
-                atomicAdd(count, 1u);
-            }
-        }
-        if (lane == 0) {
-            row_m[lr] = m;
-            row_inv[lr] = inv;
-            row_lab[lr] = lab;
-        }
-    }
-    __syncthreads();
-    const int lr = t >> 4, cg = (t & 15) * 8;  // this thread's row and 8 columns within a chunk
-    const uint32_t r = r0 + lr;
-    const float m = row_m[lr], inv = row_inv[lr];
-    const int lab = row_lab[lr];
-    for (int c0 = 0; c0 < kCls; c0 += kSmCols) {
-        __align__(16) __nv_bfloat16 g[8];
-        if (lab >= 0) {
-            const float4 *z = reinterpret_cast<const float4 *>(logits + (size_t)r * kCls + c0 + cg);
-            const float4 a = z[0], b = z[1];
-            const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                g[j] = __float2bfloat16_rn(expf(v[j] - m) * inv - (c0 + cg + j == lab ? 1.0f : 0.0f));
-        } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) g[j] = __float2bfloat16_rn(0.0f);
-        }
-        *reinterpret_cast<uint4 *>(dz + (size_t)r * kCls + c0 + cg) = *reinterpret_cast<const uint4 *>(g);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) tileT[(cg + j) * (kSmRows + 8) + lr] = g[j];
-        __syncthreads();
-        {
-            const int cc = t >> 1, h = (t & 1) * 8;  // column and half of the 16 rows
-            *reinterpret_cast<uint4 *>(dzt + (size_t)(c0 + cc) * npad + r0 + h) =
-                *reinterpret_cast<const uint4 *>(tileT + cc * (kSmRows + 8) + h);
-        }
-        __syncthreads();
-    }
-}
-
 // out[i] = sum over the row i of a bf16 [rows, cols] matrix (256 threads per row)
 __global__ void __launch_bounds__(256) k_rowsum(const __nv_bfloat16 *a, uint32_t cols, float *out)
 {
@@ -313,7 +233,7 @@ struct hrpp_proposal {
     __nv_bfloat16 *w1h, *w2h, *w3h, *w2t, *w3t;
     int step;
     __nv_bfloat16 *X, *XT, *H1, *H1T, *H2, *H2T, *dZ3, *dZ3T, *dZ2, *dZ2T, *dZ1T;
-    float *logits, *loss_sum;
+    float *loss_sum;
     unsigned int *count, *err;
     float *call_loss;           // loss and labelled rows summed over one train call
     unsigned int *call_count;
@@ -331,7 +251,7 @@ void proposal_free(hrpp_proposal *p)
     if (!p) return;
     void *ptrs[] = {p->sin_t, p->class_node, p->prim_class, p->master, p->grad, p->m, p->v, p->w1h, p->w2h,
                     p->w3h, p->w2t, p->w3t, p->X, p->XT, p->H1, p->H1T, p->H2, p->H2T, p->dZ3, p->dZ3T,
-                    p->dZ2, p->dZ2T, p->dZ1T, p->logits, p->loss_sum, p->count, p->err, p->call_loss, p->call_count,
+                    p->dZ2, p->dZ2T, p->dZ1T, p->loss_sum, p->count, p->err, p->call_loss, p->call_count,
                     p->lab, p->amax, p->Xi, p->H1i, p->H2i, p->amaxi};
     for (void *q : ptrs) cudaFree(q);
     delete p;
@@ -424,16 +344,25 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
         if ((e = cudaMemsetAsync(amax, 0, sizeof(unsigned long long) * npad, s)) != cudaSuccess) return e;
         return gemm_bf16(H2, p->w3h, umma::EPI_ARGMAX, tile_n((int)npad, kCls), g, 1, s);
     }
-    g.c32 = p->logits;
-    if ((e = gemm_bf16(H2, p->w3h, umma::EPI_F32, 256, g, 1, s)) != cudaSuccess) return e;
-    if (!train) return cudaSuccess;
+    if (!train) return cudaErrorInvalidValue;  // forward passes end in the argmax above
     if ((e = cudaMemcpyAsync(p->lab, labels, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->loss_sum, 0, sizeof(float), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->count, 0, sizeof(unsigned int), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->grad, 0, sizeof(float) * kMaster, s)) != cudaSuccess)
         return e;
-    k_softmax_ce<<<npad / kSmRows, 256, 0, s>>>(p->logits, p->lab, n, npad, p->dZ3, p->dZ3T, p->loss_sum, p->count);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // logits, softmax cross-entropy and dZ3 in one tensor-core pass (the
+    // logits never reach memory)
+    umma::SoftmaxArgs sx = {};
+    sx.bias = p->master + ob3;
+    sx.labels = p->lab;
+    sx.n = (int)n;
+    sx.npad = (int)npad;
+    sx.dz = p->dZ3;
+    sx.dzt = p->dZ3T;
+    sx.loss_sum = p->loss_sum;
+    sx.count = p->count;
+    sx.error = p->err;
+    if ((e = softmax_xent(H2, p->w3h, sx, s)) != cudaSuccess) return e;
     // dW3 = dZ3^T H2
     g = args(kCls, kHid, (int)npad, p);
     g.c32 = p->grad + oW3;
@@ -618,7 +547,6 @@ hrpp_status hrpp_proposal_create(const hrpp_scene *sc, const hrpp_bvh_node *node
     alloc(&p->dZ2, rows * kHid * 2);
     alloc(&p->dZ2T, rows * kHid * 2);
     alloc(&p->dZ1T, rows * kHid * 2);
-    alloc(&p->logits, rows * kCls * 4);
     alloc(&p->loss_sum, 4);
     alloc(&p->count, 4);
     alloc(&p->err, 4);

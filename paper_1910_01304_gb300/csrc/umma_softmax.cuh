@@ -1,0 +1,281 @@
+// Fused output layer and softmax cross-entropy of the learned proposal's
+// training step, on the tensor cores (tcgen05):
+//
+//   Z    = H2 W3^T + b3            [rows, 4096], never written to memory
+//   loss = log sum_j exp(Z_rj) - Z_r,label        per labelled row
+//   dZ   = softmax(Z_r) - onehot(label)           bf16, row-major and transposed
+//
+// One CTA owns 128 rows and computes all 16 column tiles of 256 twice.  The
+// first pass keeps each row's running maximum and sum of exponentials; the
+// second recomputes each tile and writes the gradient.  The CTA's 128 x 256
+// tile of H2 stays in shared memory; W3 streams from L2 in 256 x 64 blocks
+// through a 4-stage ring.  Two TMEM accumulators of 256 columns let the
+// epilogue of one tile overlap the MMAs of the next.
+//   warps 0-15 epilogue: warp w reads TMEM lanes 32(w%4).. (rows) and the
+//              64-column slice w/4 of every tile; the four partial row
+//              statistics of a row are combined in shared memory after pass 1
+//   warp 16    TMA producer (one lane)
+//   warp 17    MMA issuer (one lane)
+// Every mbarrier wait is bounded; a wait that gives up sets the error flag,
+// the CTA drains its outstanding copies and MMAs (bounded again), frees its
+// TMEM and returns.
+#pragma once
+
+#include "umma.cuh"
+
+namespace hrpp {
+namespace umma {
+
+constexpr int SX_CLASSES = 4096;
+constexpr int SX_K = 256;                       // hidden width
+constexpr int SX_BN = 256;                      // columns per tile (one TMEM accumulator)
+constexpr int SX_TILES = SX_CLASSES / SX_BN;    // 16 per pass
+constexpr int SX_KB = SX_K / BK;                // 4 K blocks per tile
+constexpr int SX_NST = 4;                       // W3 ring stages
+constexpr uint32_t SX_A_BLOCK = BM * BK * 2;    // 16 KB
+constexpr uint32_t SX_A_BYTES = SX_KB * SX_A_BLOCK;
+constexpr uint32_t SX_B_BYTES = SX_BN * BK * 2; // 32 KB per stage
+constexpr int SX_EPI_WARPS = 16;                // 4 row groups x 4 column slices
+constexpr int SX_SLICE = SX_BN / 4;             // columns of a tile per epilogue warp
+constexpr int SX_THREADS = (SX_EPI_WARPS + 2) * 32;
+constexpr int SX_PITCH = 24;                    // bf16 per staged row: 16 + 8 (16-byte aligned, bank-staggered)
+constexpr uint32_t SX_STAGE_BYTES = SX_EPI_WARPS * 32 * SX_PITCH * 2;
+
+template <int NST = SX_NST>
+constexpr size_t softmax_smem_bytes()
+{
+    return (size_t)SX_A_BYTES + (size_t)NST * SX_B_BYTES + SX_STAGE_BYTES + 1024;
+}
+
+struct SoftmaxArgs {
+    const float *bias;      // b3 [4096]
+    const int32_t *labels;  // [npad]: class, or -1 for no target (read for rows < n)
+    int n;                  // rows >= n are padding (no target)
+    int npad;               // rows, a multiple of 128
+    __nv_bfloat16 *dz;      // [npad, 4096]
+    __nv_bfloat16 *dzt;     // [4096, npad]
+    float *loss_sum;        // += loss of every labelled row
+    unsigned int *count;    // += labelled rows
+    unsigned int *error;    // set to 1 when a bounded wait gives up
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// NST: stages of the W3 ring (a template so that every file that includes
+// this header shares one instance)
+template <int NST = SX_NST>
+__global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_constant__ CUtensorMap tma_a,
+                                                         const __grid_constant__ CUtensorMap tma_b,
+                                                         const SoftmaxArgs g)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t a_full, full_bar[NST], empty_bar[NST], acc_full[2], acc_empty[2], drain;
+    __shared__ uint32_t tmem_base;
+    __shared__ float part_m[4][BM], part_s[4][BM], zl[BM];  // per column slice and row
+    __shared__ int any_failed;
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *a_s = smem;
+    unsigned char *b_s = smem + SX_A_BYTES;
+    __nv_bfloat16 *stage = reinterpret_cast<__nv_bfloat16 *>(b_s + NST * SX_B_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM;
+    constexpr int kTiles = 2 * SX_TILES;
+
+    if (threadIdx.x == 0) {
+        any_failed = 0;
+        mbar_init(&a_full, 1);
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], SX_EPI_WARPS);  // one arrival per epilogue warp
+        }
+        mbar_init(&drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(2u * SX_BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    bool failed = false;
+
+    if (warp == SX_EPI_WARPS) {
+        if (lane == 0) {
+            // H2 tile (4 K blocks, 64 KB), then W3 blocks for both passes
+            mbar_expect_tx(&a_full, SX_A_BYTES);
+            for (int kb = 0; kb < SX_KB; ++kb) tma_load_2d(a_s + kb * SX_A_BLOCK, &tma_a, kb * BK, m0, &a_full);
+            int issued = 0;
+            for (int i = 0; i < kTiles * SX_KB; ++i) {
+                const int t = i / SX_KB, kb = i % SX_KB, s = i % NST;
+                if (!mbar_wait(&empty_bar[s], ((uint32_t)(i / NST) & 1u) ^ 1u)) {
+                    failed = true;
+                    break;
+                }
+                mbar_expect_tx(&full_bar[s], SX_B_BYTES);
+                tma_load_2d(b_s + s * SX_B_BYTES, &tma_b, kb * BK, (t % SX_TILES) * SX_BN, &full_bar[s]);
+                ++issued;
+            }
+            // copies still in flight after a timeout land before the CTA exits
+            mbar_wait(&a_full, 0);
+            if (failed)
+                for (int i = (issued > NST ? issued - NST : 0); i < issued; ++i)
+                    mbar_wait(&full_bar[i % NST], (uint32_t)(i / NST) & 1u);
+        }
+    } else if (warp == SX_EPI_WARPS + 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = instr_desc(BM, SX_BN);
+            if (!mbar_wait(&a_full, 0)) failed = true;
+            int i = 0;
+            for (int t = 0; t < kTiles && !failed; ++t) {
+                const int b = t & 1;
+                if (!mbar_wait(&acc_empty[b], ((uint32_t)(t >> 1) & 1u) ^ 1u)) {
+                    failed = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(b * SX_BN);
+                for (int kb = 0; kb < SX_KB; ++kb, ++i) {
+                    const int s = i % NST;
+                    if (!mbar_wait(&full_bar[s], (uint32_t)(i / NST) & 1u)) {
+                        failed = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem_u32(a_s + kb * SX_A_BLOCK), b0 = smem_u32(b_s + s * SX_B_BYTES);
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k)
+                        mma_bf16(d, smem_desc(a0 + 32u * k), smem_desc(b0 + 32u * k), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                    mma_commit(&empty_bar[s]);
+                }
+                if (failed) break;
+                mma_commit(&acc_full[b]);
+            }
+            // every MMA issued above completes before the CTA frees TMEM
+            mma_commit(&drain);
+            mbar_wait(&drain, 0);
+        }
+    } else {
+        // epilogue: row group q (TMEM lanes 32q..), column slice cs of each tile
+        const int q = warp & 3, cs = warp >> 2;
+        const int r = q * 32 + lane;
+        const int row = m0 + r;
+        int lab = row < g.n ? g.labels[row] : -1;
+        if (lab >= SX_CLASSES) lab = -1;
+        float m = -__int_as_float(0x7F800000), ssum = 0.0f, inv = 0.0f;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        __nv_bfloat16 *st = stage + warp * 32 * SX_PITCH;
+        // pass 1: running maximum and sum of exponentials over this slice
+        for (int t = 0; t < SX_TILES; ++t) {
+            const int b = t & 1;
+            bool ok = mbar_wait(&acc_full[b], (uint32_t)(t >> 1) & 1u);
+            // tcgen05.ld is warp-collective: a warp reads TMEM only if all its lanes may
+            ok = __all_sync(0xFFFFFFFFu, ok);
+            if (!ok) {
+                failed = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t taddr = tmem + lane_base + (uint32_t)(b * SX_BN + cs * SX_SLICE);
+            const int col0 = t * SX_BN + cs * SX_SLICE;
+#pragma unroll 1
+            for (int c0 = 0; c0 < SX_SLICE; c0 += 16) {
+                float v[16];
+                tmem_ld16(taddr + (uint32_t)c0, v);
+                float cm = m;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    v[j] += g.bias[col0 + c0 + j];
+                    cm = fmaxf(cm, v[j]);
+                    if (col0 + c0 + j == lab) zl[r] = v[j];
+                }
+                float acc = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc += __expf(v[j] - cm);
+                ssum = ssum * __expf(m - cm) + acc;
+                m = cm;
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
+        // combine the four slices' statistics of each row; every epilogue warp
+        // reaches this barrier once, also after a failed wait
+        part_m[cs][r] = m;
+        part_s[cs][r] = ssum;
+        if (failed) any_failed = 1;
+        asm volatile("bar.sync 1, %0;" ::"n"(SX_EPI_WARPS * 32) : "memory");
+        if (any_failed) failed = true;
+        if (!failed) {
+            m = fmaxf(fmaxf(part_m[0][r], part_m[1][r]), fmaxf(part_m[2][r], part_m[3][r]));
+            ssum = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) ssum += part_s[k][r] * __expf(part_m[k][r] - m);
+            inv = lab >= 0 ? 1.0f / ssum : 0.0f;
+            if (cs == 0 && lab >= 0) {
+                atomicAdd(g.loss_sum, logf(ssum) + m - zl[r]);
+                atomicAdd(g.count, 1u);
+            }
+        }
+        // pass 2: dZ = softmax - onehot (zero for rows without a target)
+        for (int t = SX_TILES; t < kTiles && !failed; ++t) {
+            const int b = t & 1;
+            bool ok = mbar_wait(&acc_full[b], (uint32_t)(t >> 1) & 1u);
+            ok = __all_sync(0xFFFFFFFFu, ok);
+            if (!ok) {
+                failed = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t taddr = tmem + lane_base + (uint32_t)(b * SX_BN + cs * SX_SLICE);
+            const int col0 = (t - SX_TILES) * SX_BN + cs * SX_SLICE;
+#pragma unroll 1
+            for (int c0 = 0; c0 < SX_SLICE; c0 += 16) {
+                float v[16];
+                tmem_ld16(taddr + (uint32_t)c0, v);
+                __align__(16) __nv_bfloat16 qv[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = col0 + c0 + j;
+                    const float p =
+                        lab >= 0 ? __expf(v[j] + g.bias[col] - m) * inv - (col == lab ? 1.0f : 0.0f) : 0.0f;
+                    qv[j] = __float2bfloat16_rn(p);
+                    g.dzt[(size_t)col * g.npad + row] = qv[j];
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(st + lane * SX_PITCH);
+                dst[0] = *reinterpret_cast<const uint4 *>(qv);
+                dst[1] = *reinterpret_cast<const uint4 *>(qv + 8);
+                __syncwarp();
+                // the warp's 32 rows x 16 columns: 2 lanes per 32-byte row segment
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int idx = lane + 32 * k, rr = idx >> 1, hh = idx & 1;
+                    const uint4 val = *reinterpret_cast<const uint4 *>(st + rr * SX_PITCH + hh * 8);
+                    *reinterpret_cast<uint4 *>(g.dz + (size_t)(m0 + q * 32 + rr) * SX_CLASSES + col0 + c0 + hh * 8) =
+                        val;
+                }
+                __syncwarp();
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
+    }
+    if (failed && g.error) atomicExch(g.error, 1u);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * SX_BN) : "memory");
+}
+
+}  // namespace umma
+}  // namespace hrpp
