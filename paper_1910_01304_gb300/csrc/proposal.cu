@@ -111,22 +111,26 @@ __global__ void __launch_bounds__(kFeatRows) k_featurize(const float4 *rays, uin
     }
     __nv_bfloat16 *row = tile + t * kFeatPitch;
     const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-    for (int c = 0; c < kIn; ++c) {
-        __nv_bfloat16 v = zero;
-        if (live) {
-            if (c < 5) {
-                v = __float2bfloat16_rn(__fsub_rn(__fmul_rn((float)q[c], 1.0f / 32768.0f), 1.0f));
-            } else if (c < 95) {
-                const int i = (c - 5) / 18, k = ((c - 5) % 18) >> 1;
-                uint32_t ph = (q[i] << k) & 0xFFFFu;
-                if ((c - 5) & 1) ph = (ph + 16384u) & 0xFFFFu;
-                v = sin_t[ph];
-            } else if (c == 95) {
-                v = __float2bfloat16_rn(1.0f);
+    if (live) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            row[i] = __float2bfloat16_rn(__fsub_rn(__fmul_rn((float)q[i], 1.0f / 32768.0f), 1.0f));
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const uint32_t ph = (q[i] << k) & 0xFFFFu;
+                row[5 + 18 * i + 2 * k] = sin_t[ph];                          // sine
+                row[6 + 18 * i + 2 * k] = sin_t[(ph + 16384u) & 0xFFFFu];     // cosine
             }
         }
-        row[c] = v;
+        row[95] = __float2bfloat16_rn(1.0f);
+    } else {
+#pragma unroll
+        for (int c = 0; c < kFeat; ++c) row[c] = zero;
     }
+    // padding columns 96..127
+    const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int c = kFeat; c < kIn; c += 8) *reinterpret_cast<uint4 *>(row + c) = z4;
     __syncthreads();
     // row-major: the tile's rows are consecutive in X
     const uint32_t rows_here = npad - r0 < (uint32_t)kFeatRows ? npad - r0 : (uint32_t)kFeatRows;
@@ -163,14 +167,18 @@ __global__ void __launch_bounds__(256) k_rowsum(const __nv_bfloat16 *a, uint32_t
     }
 }
 
-// Adam on a [rows, cols] parameter (cols = 1 for biases); optional bf16
-// copies in [rows, cols] and [cols, rows] layouts
-__global__ void __launch_bounds__(256) k_adam(float *w, const float *g, float *m, float *v, uint32_t rows,
-                                              uint32_t cols, float lr, float bc1, float bc2, const unsigned int *count,
-                                              __nv_bfloat16 *wh, __nv_bfloat16 *wt)
+// Adam on every parameter in one launch (masters laid out W1 | b1 | W2 | b2 |
+// W3 | b3, weights [rows, cols] row-major); the weights' bf16 copies are
+// refreshed, row-major and (W2, W3) transposed.
+struct AdamOut {
+    __nv_bfloat16 *w1h, *w2h, *w2t, *w3h, *w3t;
+};
+
+__global__ void __launch_bounds__(256) k_adam(float *w, const float *g, float *m, float *v, float lr, float bc1,
+                                              float bc2, const unsigned int *count, AdamOut out)
 {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows * cols) return;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kMaster) return;
     const float scale = 1.0f / (float)(*count > 0u ? *count : 1u);
     const float gi = g[i] * scale;
     const float mi = 0.9f * m[i] + 0.1f * gi;
@@ -180,8 +188,17 @@ __global__ void __launch_bounds__(256) k_adam(float *w, const float *g, float *m
     const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
     w[i] = wi;
     const __nv_bfloat16 h = __float2bfloat16_rn(wi);
-    if (wh) wh[i] = h;
-    if (wt) wt[(size_t)(i % cols) * rows + i / cols] = h;
+    if (i < ob1) {
+        out.w1h[i - oW1] = h;
+    } else if (i >= oW2 && i < ob2) {
+        const size_t k = i - oW2;
+        out.w2h[k] = h;
+        out.w2t[(k % kHid) * kHid + k / kHid] = h;
+    } else if (i >= oW3 && i < ob3) {
+        const size_t k = i - oW3;
+        out.w3h[k] = h;
+        out.w3t[(k % kHid) * kCls + k / kHid] = h;
+    }
 }
 
 // adds one minibatch's loss total and labelled-row count to the call's
@@ -402,17 +419,9 @@ cudaError_t adam(hrpp_proposal *p, float lr, cudaStream_t s)
 {
     p->step += 1;
     const float bc1 = 1.0f - std::pow(0.9f, (float)p->step), bc2 = 1.0f - std::pow(0.999f, (float)p->step);
-    auto run = [&](size_t off, uint32_t rows, uint32_t cols, __nv_bfloat16 *wh, __nv_bfloat16 *wt) {
-        const uint32_t n = rows * cols;
-        k_adam<<<(n + 255) / 256, 256, 0, s>>>(p->master + off, p->grad + off, p->m + off, p->v + off, rows, cols, lr,
-                                                bc1, bc2, p->count, wh, wt);
-    };
-    run(oW1, kHid, kIn, p->w1h, nullptr);
-    run(ob1, kHid, 1, nullptr, nullptr);
-    run(oW2, kHid, kHid, p->w2h, p->w2t);
-    run(ob2, kHid, 1, nullptr, nullptr);
-    run(oW3, kCls, kHid, p->w3h, p->w3t);
-    run(ob3, kCls, 1, nullptr, nullptr);
+    const AdamOut out = {p->w1h, p->w2h, p->w2t, p->w3h, p->w3t};
+    k_adam<<<(unsigned)((kMaster + 255) / 256), 256, 0, s>>>(p->master, p->grad, p->m, p->v, lr, bc1, bc2, p->count,
+                                                             out);
     return cudaGetLastError();
 }
 
