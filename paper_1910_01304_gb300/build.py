@@ -59,7 +59,7 @@ def build(verbose_ptxas: bool = False, force: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        r = subprocess.run([_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
+        r = subprocess.run([_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-ldl"], capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, LIB)

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -17,6 +18,31 @@
 #include "hrpp.h"
 
 using namespace hrpp;
+
+cudaError_t hrpp::device_malloc(void **ptr, size_t bytes)
+{
+    static std::mutex mu;
+    static std::string seen;
+    static long long made = 0;
+    const char *v = std::getenv("HRPP_FAIL_ALLOC_AFTER");
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!v || !*v) {
+            seen.clear();  // unset: the next value counts from zero
+        } else {
+            if (seen != v) {
+                seen = v;
+                made = 0;
+            }
+            if (made++ >= std::atoll(v)) {
+                *ptr = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+        }
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
 
 namespace {
 
@@ -336,10 +362,10 @@ hrpp_status hrpp_scene_create(const float *tri_verts, uint32_t n_tris, const hrp
     const size_t cb = h_canon.size() * sizeof(int32_t);
     sc->n_nodes = n_nodes;
     sc->bytes = nb + tb + pb + lb + cb + sizeof(uint32_t);
-    if ((e = cudaMalloc(&sc->d_nodes, nb)) != cudaSuccess || (e = cudaMalloc(&sc->d_tris, tb)) != cudaSuccess ||
-        (e = cudaMalloc(&sc->d_error, sizeof(uint32_t))) != cudaSuccess ||
-        (e = cudaMalloc(&sc->d_parent, pb)) != cudaSuccess || (e = cudaMalloc(&sc->d_leaf_parent, lb)) != cudaSuccess ||
-        (e = cudaMalloc(&sc->d_canon_ref, cb)) != cudaSuccess ||
+    if ((e = device_malloc((void **)&sc->d_nodes, nb)) != cudaSuccess || (e = device_malloc((void **)&sc->d_tris, tb)) != cudaSuccess ||
+        (e = device_malloc((void **)&sc->d_error, sizeof(uint32_t))) != cudaSuccess ||
+        (e = device_malloc((void **)&sc->d_parent, pb)) != cudaSuccess || (e = device_malloc((void **)&sc->d_leaf_parent, lb)) != cudaSuccess ||
+        (e = device_malloc((void **)&sc->d_canon_ref, cb)) != cudaSuccess ||
         (e = cudaMemcpy(sc->d_canon_ref, h_canon.data(), cb, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(sc->d_nodes, h_nodes.data(), nb, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(sc->d_tris, h_tris.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -424,7 +450,7 @@ hrpp_status hrpp_table_create(int log2_entries, int ways, hrpp_table **out)
     t->precision = 6;
     t->update_mode = HRPP_UPDATE_TWO_PHASE;
     const uint64_t n = 1ull << log2_entries;
-    if ((e = cudaMalloc(&t->d_words, n * 8)) != cudaSuccess || (e = cudaMalloc(&t->d_winner, n * 4)) != cudaSuccess ||
+    if ((e = device_malloc((void **)&t->d_words, n * 8)) != cudaSuccess || (e = device_malloc((void **)&t->d_winner, n * 4)) != cudaSuccess ||
         (e = cudaMemset(t->d_words, 0xFF, n * 8)) != cudaSuccess || (e = cudaMemset(t->d_winner, 0, n * 4)) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess) {
         hrpp_table_destroy(t);
@@ -548,6 +574,7 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
                           hrpp_mode mode, void *out_hits, hrpp_stats *out_stats, void *stream_,
                           const hrpp_trace_opts *opts)
 {
+    hrpp::NvtxRange nvtx_range("hrpp_trace");
     if (!sc) return fail(HRPP_ERR_INVALID_ARG, "scene is NULL");
     if (mode != HRPP_ANY_HIT && mode != HRPP_CLOSEST_HIT) return fail(HRPP_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
     const bool closest = mode == HRPP_CLOSEST_HIT;

@@ -127,11 +127,11 @@ hrpp_status hrpp_batch_create(const hrpp_batch_item *items, uint32_t n_items, in
     b->ctl_bytes = 256ull * (n_items + 1);
     hrpp_status status = HRPP_OK;
     do {
-        if ((e = cudaMalloc(&b->d_items, sizeof(TraceParams) * n_items)) != cudaSuccess ||
-            (e = cudaMalloc(&b->d_ctl, b->ctl_bytes)) != cudaSuccess ||
-            (e = cudaMalloc(&b->d_records, sizeof(Record) * (total_records ? total_records : 1))) != cudaSuccess ||
-            (e = cudaMalloc(&b->d_chunk_item, sizeof(uint32_t) * (total_chunks ? total_chunks : 1))) != cudaSuccess ||
-            (e = cudaMalloc(&b->d_chunk_first, sizeof(uint32_t) * (total_chunks ? total_chunks : 1))) != cudaSuccess) {
+        if ((e = hrpp::device_malloc((void **)&b->d_items, sizeof(TraceParams) * n_items)) != cudaSuccess ||
+            (e = hrpp::device_malloc((void **)&b->d_ctl, b->ctl_bytes)) != cudaSuccess ||
+            (e = hrpp::device_malloc((void **)&b->d_records, sizeof(Record) * (total_records ? total_records : 1))) != cudaSuccess ||
+            (e = hrpp::device_malloc((void **)&b->d_chunk_item, sizeof(uint32_t) * (total_chunks ? total_chunks : 1))) != cudaSuccess ||
+            (e = hrpp::device_malloc((void **)&b->d_chunk_first, sizeof(uint32_t) * (total_chunks ? total_chunks : 1))) != cudaSuccess) {
             status = bfail(e == cudaErrorMemoryAllocation ? HRPP_ERR_OOM : HRPP_ERR_CUDA, "batch allocation: %s",
                            cudaGetErrorString(e));
             break;
@@ -231,6 +231,7 @@ hrpp_status hrpp_batch_create(const hrpp_batch_item *items, uint32_t n_items, in
 
 hrpp_status hrpp_batch_run(hrpp_batch *b, void *stream)
 {
+    hrpp::NvtxRange nvtx_range("hrpp_batch_run");
     if (!b) return bfail(HRPP_ERR_INVALID_ARG, "batch is NULL");
     int prev = -1;
     cudaError_t e = cudaGetDevice(&prev);

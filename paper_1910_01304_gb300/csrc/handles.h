@@ -3,10 +3,28 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 
 #include "hrpp.h"
+
+namespace hrpp {
+// cudaMalloc with host-side fault injection for tests: while the environment
+// holds HRPP_FAIL_ALLOC_AFTER=N, the allocations after the first N made since
+// that value was set fail with cudaErrorMemoryAllocation (nothing is
+// allocated).  Every object-creating entry point allocates through it.
+cudaError_t device_malloc(void **ptr, size_t bytes);
+
+// Names an entry point's host-side span in profiler timelines (NVTX; a no-op
+// unless a profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace hrpp
 
 struct hrpp_scene {
     int device;

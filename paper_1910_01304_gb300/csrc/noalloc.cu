@@ -78,6 +78,7 @@ extern "C" hrpp_status hrpp_trace_noalloc(const hrpp_scene *sc, hrpp_table *tabl
                                           uint32_t n_rays, hrpp_mode mode, void *out_hits, hrpp_stats *out_stats,
                                           void *stream_)
 {
+    hrpp::NvtxRange nvtx_range("hrpp_trace_noalloc");
     if (!sc) return noalloc_fail(HRPP_ERR_INVALID_ARG, "scene is NULL");
     if (mode != HRPP_ANY_HIT && mode != HRPP_CLOSEST_HIT) return noalloc_fail(HRPP_ERR_INVALID_ARG, "unknown mode");
     const bool closest = mode == HRPP_CLOSEST_HIT;

@@ -531,7 +531,7 @@ hrpp_status hrpp_proposal_create(const hrpp_scene *sc, const hrpp_bvh_node *node
     const size_t rows = kBmax;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](auto **ptr, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMalloc((void **)ptr, bytes);
+        if (e == cudaSuccess) e = hrpp::device_malloc((void **)ptr, bytes);
     };
     alloc(&p->sin_t, 65536 * 2);
     alloc(&p->class_node, kCls * 4);
@@ -610,6 +610,7 @@ hrpp_status hrpp_proposal_labels(hrpp_proposal *p, const hrpp_hit *hits, uint32_
 hrpp_status hrpp_proposal_train(hrpp_proposal *p, const hrpp_ray *rays, const int32_t *labels, uint32_t n, float lr,
                                 float *out_mean_loss, void *stream)
 {
+    hrpp::NvtxRange nvtx_range("hrpp_proposal_train");
     if (!p || (n && (!rays || !labels))) return pfail(HRPP_ERR_INVALID_ARG, "NULL argument");
     if (!(lr > 0.0f)) return pfail(HRPP_ERR_INVALID_ARG, "lr must be positive");
     Dev dv(p->device);
@@ -667,16 +668,23 @@ hrpp_status hrpp_proposal_gradients(hrpp_proposal *p, const hrpp_ray *rays, cons
 hrpp_status hrpp_proposal_predict(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, int32_t *out_nodes,
                                   int32_t *out_classes, void *stream)
 {
+    hrpp::NvtxRange nvtx_range("hrpp_proposal_predict");
     if (!p || (n && (!rays || (!out_nodes && !out_classes)))) return pfail(HRPP_ERR_INVALID_ARG, "NULL argument");
     Dev dv(p->device);
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
     if (!p->Xi) {
-        if ((e = cudaMalloc(&p->Xi, (size_t)kBinfer * kIn * 2)) != cudaSuccess ||
-            (e = cudaMalloc(&p->H1i, (size_t)kBinfer * kHid * 2)) != cudaSuccess ||
-            (e = cudaMalloc(&p->H2i, (size_t)kBinfer * kHid * 2)) != cudaSuccess ||
-            (e = cudaMalloc(&p->amaxi, (size_t)kBinfer * 8)) != cudaSuccess)
-            return pfail(HRPP_ERR_OOM, "predict buffers: %s", cudaGetErrorString(e));
+        if ((e = hrpp::device_malloc((void **)&p->Xi, (size_t)kBinfer * kIn * 2)) != cudaSuccess ||
+            (e = hrpp::device_malloc((void **)&p->H1i, (size_t)kBinfer * kHid * 2)) != cudaSuccess ||
+            (e = hrpp::device_malloc((void **)&p->H2i, (size_t)kBinfer * kHid * 2)) != cudaSuccess ||
+            (e = hrpp::device_malloc((void **)&p->amaxi, (size_t)kBinfer * 8)) != cudaSuccess) {
+            void *bufs[] = {p->Xi, p->H1i, p->H2i, p->amaxi};
+            for (void *q : bufs) cudaFree(q);
+            p->Xi = p->H1i = p->H2i = nullptr;
+            p->amaxi = nullptr;
+            return pfail(e == cudaErrorMemoryAllocation ? HRPP_ERR_OOM : HRPP_ERR_CUDA, "predict buffers: %s",
+                         cudaGetErrorString(e));
+        }
     }
     for (uint32_t off = 0; off < n && e == cudaSuccess; off += kBinfer) {
         const uint32_t b = n - off < kBinfer ? n - off : kBinfer;

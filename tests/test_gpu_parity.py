@@ -454,3 +454,44 @@ def test_step_budget_reports_traversal_limit(H, small_pair, width_idx):
     torch.cuda.synchronize()
     assert_same_hits(O.CLOSEST_HIT, gh.cpu().numpy(), oh)
     assert_same_stats(gst, ost)
+
+
+def test_injected_allocation_failures_return_oom(H, small_pair, monkeypatch):
+    """Host-side fault injection (HRPP_FAIL_ALLOC_AFTER=N fails the device
+    allocations after the first N): every creating entry point reports
+    HRPP_ERR_OOM at each of its allocations, cleans up, and works again once
+    the variable is gone."""
+    import torch
+    s, g = small_pair[0]
+    rays = torch.from_numpy(s.primary_rays()[:256]).cuda()
+    makers = {
+        "scene": (6, lambda: H.Scene.from_workload(s)),
+        "table": (2, lambda: H.Table(10, 2, 6)),
+        "batch": (5, lambda: H.Batch([(g, None, rays, H.HRPP_CLOSEST_HIT)])),
+    }
+    for name, (n_allocs, make) in makers.items():
+        for k in range(n_allocs):
+            monkeypatch.setenv("HRPP_FAIL_ALLOC_AFTER", str(k))
+            with pytest.raises(H.HrppError) as err:
+                make()
+            assert err.value.status == H.HRPP_ERR_OOM, (name, k)
+            monkeypatch.delenv("HRPP_FAIL_ALLOC_AFTER")
+        obj = make()  # nothing left behind: the next creation works
+        obj.close()
+    for k in (0, 7, 20):
+        monkeypatch.setenv("HRPP_FAIL_ALLOC_AFTER", str(k))
+        with pytest.raises(H.HrppError) as err:
+            H.Proposal.for_workload(g, s, seed=1)
+        assert err.value.status == H.HRPP_ERR_OOM
+        monkeypatch.delenv("HRPP_FAIL_ALLOC_AFTER")
+    prop = H.Proposal.for_workload(g, s, seed=1)
+    monkeypatch.setenv("HRPP_FAIL_ALLOC_AFTER", "2")
+    with pytest.raises(H.HrppError) as err:
+        prop.predict(rays)
+    assert err.value.status == H.HRPP_ERR_OOM
+    monkeypatch.delenv("HRPP_FAIL_ALLOC_AFTER")
+    nodes, _ = prop.predict(rays)  # the half-made buffers were released
+    traced, _ = H.trace(g, rays, H.HRPP_CLOSEST_HIT, predicted=nodes)
+    plain, _ = H.trace(g, rays, H.HRPP_CLOSEST_HIT)
+    torch.cuda.synchronize()
+    assert torch.equal(traced.view(torch.int32), plain.view(torch.int32))

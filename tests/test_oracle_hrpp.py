@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from paper_1910_01304_gb300.scenes import workloads as W
 
 
 def _leaf_of_prim(nodes, prim_index):
@@ -452,3 +453,49 @@ def test_exponent_lsb_hash_variant_keeps_results(small):
         tp += sl["true_pos"]
         _check_identities(sl, len(rays))
     assert tp > 0 and not np.array_equal(tm.words, tl.words)
+
+
+# ------------------------------------------- qualitative trends (Sec. 5-6) --
+
+def _unbounded_run(s, p, mode, warm_frames=3):
+    """Warm an unbounded (limit-study) table with a few frames, then trace one
+    more; returns (distinct keys, stored leaves, stats of the last frame)."""
+    t = O.Table(12, 1, p, O.UNBOUNDED)
+
+    def rays_of(f):
+        pr = s.primary_rays(frame=f)[::2]
+        if mode == O.CLOSEST_HIT:
+            return pr
+        ph, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, pr, O.CLOSEST_HIT)
+        sh, _ = W.secondary_shadow(s, pr, ph["t"], ph["prim"])
+        return sh
+
+    for f in range(warm_frames):
+        O.trace(s.tris, s.nodes, s.prim_index, s.root, rays_of(f), mode, t)
+    keys, leaves = t.unbounded_size()
+    _, st = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays_of(warm_frames), mode, t)
+    return keys, leaves, st
+
+
+@pytest.mark.parametrize("mode", [O.CLOSEST_HIT, O.ANY_HIT])
+def test_precision_trades_keys_for_false_positives(small, mode):
+    """Sec. 5.1 / 6.1: looser hashing (fewer bits) files more rays under one
+    key, so entries hold more leaves and predictions miss more often; tighter
+    hashing needs more keys and more stored leaves."""
+    runs = {p: _unbounded_run(small, p, mode) for p in (2, 4, 6)}
+    keys = [runs[p][0] for p in (2, 4, 6)]
+    leaves = [runs[p][1] for p in (2, 4, 6)]
+    per_key = [l / k for k, l in zip(keys, leaves)]
+    fps = [runs[p][2]["false_pos"] for p in (2, 4, 6)]
+    assert keys[0] < keys[1] < keys[2]
+    assert leaves[0] < leaves[1] < leaves[2]
+    assert per_key[0] > per_key[1] > per_key[2]
+    assert fps[0] > fps[1] > fps[2]
+
+
+def test_hit_all_locality_exceeds_hit_any(small):
+    """Sec. 6.1: closest-hit (hit-all) rays are predicted far more often than
+    shadow (hit-any) rays with the same hash."""
+    _, _, sc = _unbounded_run(small, 6, O.CLOSEST_HIT)
+    _, _, sa = _unbounded_run(small, 6, O.ANY_HIT)
+    assert sc["true_pos"] / sc["rays"] > 5 * sa["true_pos"] / sa["rays"]
