@@ -82,13 +82,16 @@ cudaError_t launch(const void *a, const void *b, const umma::GemmArgs &g, int sp
 
 }  // namespace
 
-cudaError_t softmax_xent(const void *h2, const void *w3, const umma::SoftmaxArgs &g, cudaStream_t s)
+namespace {
+
+template <bool PREDICT>
+cudaError_t launch_output_layer(const void *h2, const void *w3, const umma::SoftmaxArgs &g, cudaStream_t s)
 {
-    static bool configured = false;
+    static bool configured = false;  // per instance; attribute setting is idempotent
     const size_t smem = umma::softmax_smem_bytes<>();
     if (!configured) {
-        cudaError_t e =
-            cudaFuncSetAttribute(umma::k_softmax_xent<>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(umma::k_softmax_xent<umma::SX_NST, PREDICT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
@@ -97,8 +100,20 @@ cudaError_t softmax_xent(const void *h2, const void *w3, const umma::SoftmaxArgs
     cudaError_t e = make_map(&ma, h2, (uint64_t)g.npad, umma::SX_K, umma::BM);
     if (e == cudaSuccess) e = make_map(&mb, w3, umma::SX_CLASSES, umma::SX_K, umma::SX_BN);
     if (e != cudaSuccess) return e;
-    umma::k_softmax_xent<><<<g.npad / umma::BM, umma::SX_THREADS, smem, s>>>(ma, mb, g);
+    umma::k_softmax_xent<umma::SX_NST, PREDICT><<<g.npad / umma::BM, umma::SX_THREADS, smem, s>>>(ma, mb, g);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t softmax_xent(const void *h2, const void *w3, const umma::SoftmaxArgs &g, cudaStream_t s)
+{
+    return launch_output_layer<false>(h2, w3, g, s);
+}
+
+cudaError_t softmax_argmax(const void *h2, const void *w3, const umma::SoftmaxArgs &g, cudaStream_t s)
+{
+    return launch_output_layer<true>(h2, w3, g, s);
 }
 
 bool gemm_shape_ok(int m, int n, int k, int bn)
@@ -126,8 +141,6 @@ cudaError_t gemm_bf16(const void *a, const void *b, int epi, int bn, const umma:
     HRPP_GEMM_CASE(128, umma::EPI_BIAS_RELU)
     HRPP_GEMM_CASE(256, umma::EPI_RELU_GRAD)
     HRPP_GEMM_CASE(128, umma::EPI_RELU_GRAD)
-    HRPP_GEMM_CASE(128, umma::EPI_ARGMAX)
-    HRPP_GEMM_CASE(256, umma::EPI_ARGMAX)
 #undef HRPP_GEMM_CASE
     return cudaErrorInvalidValue;
 }

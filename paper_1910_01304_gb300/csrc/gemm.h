@@ -16,4 +16,7 @@ cudaError_t gemm_bf16(const void *a, const void *b, int epi, int bn, const umma:
 // 256] and w3 [4096, 256] bf16, K-major; writes dZ (both layouts), adds the
 // loss and the labelled-row count.
 cudaError_t softmax_xent(const void *h2, const void *w3, const umma::SoftmaxArgs &g, cudaStream_t s);
+// The same kernel in prediction mode: per row, the first argmax of the output
+// layer and its treelet node (g.out_classes / g.out_nodes, rows < g.n).
+cudaError_t softmax_argmax(const void *h2, const void *w3, const umma::SoftmaxArgs &g, cudaStream_t s);
 }  // namespace hrpp

@@ -218,17 +218,6 @@ __global__ void k_to_bf16(const float *w, uint32_t rows, uint32_t cols, __nv_bfl
     if (wt) wt[(size_t)(i % cols) * rows + i / cols] = h;
 }
 
-__global__ void k_argmax_finish(const unsigned long long *amax, uint32_t n, const int32_t *class_node,
-                                int32_t *nodes, int32_t *classes)
-{
-    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const uint32_t cls = 0xFFFFFFFFu - (uint32_t)(amax[r] & 0xFFFFFFFFull);
-    const uint32_t c = cls < (uint32_t)kCls ? cls : 0u;
-    if (nodes) nodes[r] = class_node[c];
-    if (classes) classes[r] = (int32_t)c;
-}
-
 __global__ void k_labels(const float4 *hits, uint32_t n, const int32_t *prim_class, uint32_t n_tris, int32_t *out)
 {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -255,10 +244,8 @@ struct hrpp_proposal {
     float *call_loss;           // loss and labelled rows summed over one train call
     unsigned int *call_count;
     int32_t *lab;
-    unsigned long long *amax;
     // inference chunk buffers (allocated on the first prediction)
     __nv_bfloat16 *Xi, *H1i, *H2i;
-    unsigned long long *amaxi;
 };
 
 namespace {
@@ -269,7 +256,7 @@ void proposal_free(hrpp_proposal *p)
     void *ptrs[] = {p->sin_t, p->class_node, p->prim_class, p->master, p->grad, p->m, p->v, p->w1h, p->w2h,
                     p->w3h, p->w2t, p->w3t, p->X, p->XT, p->H1, p->H1T, p->H2, p->H2T, p->dZ3, p->dZ3T,
                     p->dZ2, p->dZ2T, p->dZ1T, p->loss_sum, p->count, p->err, p->call_loss, p->call_count,
-                    p->lab, p->amax, p->Xi, p->H1i, p->H2i, p->amaxi};
+                    p->lab, p->Xi, p->H1i, p->H2i};
     for (void *q : ptrs) cudaFree(q);
     delete p;
 }
@@ -333,12 +320,11 @@ int splits_for(int m_tiles, int k)
 // forward (and, when train, the backward into p->grad) on rows [0, n) of
 // rays, padded to npad rows; labels (device) when train
 cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const int32_t *labels, bool train,
-                      bool argmax, cudaStream_t s)
+                      bool argmax, cudaStream_t s, int32_t *out_nodes = nullptr, int32_t *out_classes = nullptr)
 {
     const uint32_t npad = pad128(n);
     cudaError_t e;
     __nv_bfloat16 *X = argmax ? p->Xi : p->X, *H1 = argmax ? p->H1i : p->H1, *H2 = argmax ? p->H2i : p->H2;
-    unsigned long long *amax = argmax ? p->amaxi : p->amax;
     k_featurize<<<npad / kFeatRows, kFeatRows, 0, s>>>(reinterpret_cast<const float4 *>(rays), n, npad, p->lo[0],
                                                     p->lo[1], p->lo[2], p->scale[0], p->scale[1], p->scale[2],
                                                     p->sin_t, X, train ? p->XT : nullptr);
@@ -353,13 +339,17 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     g.c16 = H2;
     g.c16t = train ? p->H2T : nullptr;
     if ((e = gemm_bf16(H1, p->w2h, umma::EPI_BIAS_RELU, tile_n((int)npad, kHid), g, 1, s)) != cudaSuccess) return e;
-    g = args((int)npad, kCls, kHid, p);
-    g.bias = p->master + ob3;
     if (argmax) {
-        g.argmax = amax;
-        g.m_valid = (int)n;
-        if ((e = cudaMemsetAsync(amax, 0, sizeof(unsigned long long) * npad, s)) != cudaSuccess) return e;
-        return gemm_bf16(H2, p->w3h, umma::EPI_ARGMAX, tile_n((int)npad, kCls), g, 1, s);
+        // output layer and first argmax in one tensor-core pass
+        umma::SoftmaxArgs sx = {};
+        sx.bias = p->master + ob3;
+        sx.n = (int)n;
+        sx.npad = (int)npad;
+        sx.out_classes = out_classes;
+        sx.out_nodes = out_nodes;
+        sx.class_node = p->class_node;
+        sx.error = p->err;
+        return softmax_argmax(H2, p->w3h, sx, s);
     }
     if (!train) return cudaErrorInvalidValue;  // forward passes end in the argmax above
     if ((e = cudaMemcpyAsync(p->lab, labels, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
@@ -562,7 +552,6 @@ hrpp_status hrpp_proposal_create(const hrpp_scene *sc, const hrpp_bvh_node *node
     alloc(&p->call_loss, 4);
     alloc(&p->call_count, 4);
     alloc(&p->lab, rows * 4);
-    alloc(&p->amax, rows * 8);
     if (e == cudaSuccess) e = cudaMemcpy(p->sin_t, sin_h.data(), 65536 * 2, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->class_node, p->h_class_node.data(), kCls * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->prim_class, prim_class.data(), (size_t)sc->n_tris * 4, cudaMemcpyHostToDevice);
@@ -676,24 +665,18 @@ hrpp_status hrpp_proposal_predict(hrpp_proposal *p, const hrpp_ray *rays, uint32
     if (!p->Xi) {
         if ((e = hrpp::device_malloc((void **)&p->Xi, (size_t)kBinfer * kIn * 2)) != cudaSuccess ||
             (e = hrpp::device_malloc((void **)&p->H1i, (size_t)kBinfer * kHid * 2)) != cudaSuccess ||
-            (e = hrpp::device_malloc((void **)&p->H2i, (size_t)kBinfer * kHid * 2)) != cudaSuccess ||
-            (e = hrpp::device_malloc((void **)&p->amaxi, (size_t)kBinfer * 8)) != cudaSuccess) {
-            void *bufs[] = {p->Xi, p->H1i, p->H2i, p->amaxi};
+            (e = hrpp::device_malloc((void **)&p->H2i, (size_t)kBinfer * kHid * 2)) != cudaSuccess) {
+            void *bufs[] = {p->Xi, p->H1i, p->H2i};
             for (void *q : bufs) cudaFree(q);
             p->Xi = p->H1i = p->H2i = nullptr;
-            p->amaxi = nullptr;
             return pfail(e == cudaErrorMemoryAllocation ? HRPP_ERR_OOM : HRPP_ERR_CUDA, "predict buffers: %s",
                          cudaGetErrorString(e));
         }
     }
     for (uint32_t off = 0; off < n && e == cudaSuccess; off += kBinfer) {
         const uint32_t b = n - off < kBinfer ? n - off : kBinfer;
-        e = run_batch(p, rays + off, b, nullptr, false, true, s);
-        if (e == cudaSuccess) {
-            k_argmax_finish<<<(b + 255) / 256, 256, 0, s>>>(p->amaxi, b, p->class_node, out_nodes ? out_nodes + off : nullptr,
-                                                            out_classes ? out_classes + off : nullptr);
-            e = cudaGetLastError();
-        }
+        e = run_batch(p, rays + off, b, nullptr, false, true, s, out_nodes ? out_nodes + off : nullptr,
+                      out_classes ? out_classes + off : nullptr);
     }
     if (e != cudaSuccess) return pfail(HRPP_ERR_CUDA, "predict: %s", cudaGetErrorString(e));
     return HRPP_OK;

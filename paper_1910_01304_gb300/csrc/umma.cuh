@@ -36,8 +36,7 @@ enum Epilogue : int {
     EPI_F32 = 0,        // C (+ bias per column) -> fp32 row-major
     EPI_F32_ATOMIC = 1, // split-K: atomicAdd into fp32 row-major
     EPI_BIAS_RELU = 2,  // relu(C + bias) -> bf16 row-major and bf16 transposed
-    EPI_RELU_GRAD = 3,  // C * (act > 0) -> bf16 row-major and bf16 transposed
-    EPI_ARGMAX = 4      // per row: max over columns of C + bias -> packed atomicMax
+    EPI_RELU_GRAD = 3   // C * (act > 0) -> bf16 row-major and bf16 transposed
 };
 
 struct GemmArgs {
@@ -48,8 +47,7 @@ struct GemmArgs {
     __nv_bfloat16 *c16t;     // bf16 transposed output [N, M] (may be null)
     const float *bias;       // per column (may be null)
     const __nv_bfloat16 *act;   // EPI_RELU_GRAD: activation [M, N] whose > 0 mask is applied
-    unsigned long long *argmax; // EPI_ARGMAX: per row (ordered max << 32) | ~column
-    int m_valid;             // rows >= m_valid are padding: not written (argmax / stores)
+    int m_valid;             // rows >= m_valid are padding: not written
     unsigned int *error;     // set to 1 when a bounded wait gives up
 };
 
@@ -142,12 +140,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ uint32_t ordered_f32(float f)
-{
-    const uint32_t b = __float_as_uint(f);
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
 template <int BN, int NST = STAGES>
@@ -244,8 +236,6 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
     const int row = m0 + warp * 32 + lane;
     if (ready) {
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-        float best = -__int_as_float(0x7F800000);
-        int best_col = 0;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float v[16];
@@ -287,21 +277,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
 #pragma unroll
                     for (int j = 0; j < 16; ++j) g.c16t[(size_t)(col0 + j) * g.M + row] = h[j];
                 }
-            } else if (EPI == EPI_ARGMAX) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float x = v[j] + (g.bias ? g.bias[col0 + j] : 0.0f);
-                    if (x > best) {
-                        best = x;
-                        best_col = col0 + j;
-                    }
-                }
             }
-        }
-        if (EPI == EPI_ARGMAX && row < g.m_valid) {
-            const unsigned long long key =
-                ((unsigned long long)ordered_f32(best) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)best_col);
-            atomicMax(g.argmax + row, key);
         }
     }
     if (failed && g.error) atomicExch(g.error, 1u);

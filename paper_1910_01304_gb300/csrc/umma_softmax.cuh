@@ -16,6 +16,8 @@
 //              statistics of a row are combined in shared memory after pass 1
 //   warp 16    TMA producer (one lane)
 //   warp 17    MMA issuer (one lane)
+// The prediction mode makes one pass and keeps each row's first maximum
+// (argmax over the 4096 classes of Z), writing the class and its treelet node.
 // Every mbarrier wait is bounded; a wait that gives up sets the error flag,
 // the CTA drains its outstanding copies and MMAs (bounded again), frees its
 // TMEM and returns.
@@ -49,6 +51,10 @@ constexpr size_t softmax_smem_bytes()
 
 struct SoftmaxArgs {
     const float *bias;      // b3 [4096]
+    // prediction (PREDICT = true): first argmax per row, and its treelet node
+    int32_t *out_classes;   // [n] (may be null)
+    int32_t *out_nodes;     // [n] (may be null)
+    const int32_t *class_node;  // [4096]
     const int32_t *labels;  // [npad]: class, or -1 for no target (read for rows < n)
     int n;                  // rows >= n are padding (no target)
     int npad;               // rows, a multiple of 128
@@ -65,8 +71,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 }
 
 // NST: stages of the W3 ring (a template so that every file that includes
-// this header shares one instance)
-template <int NST = SX_NST>
+// this header shares one instance).  PREDICT: one pass that keeps each row's
+// first maximum instead of the two training passes.
+template <int NST = SX_NST, bool PREDICT = false>
 __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_constant__ CUtensorMap tma_a,
                                                          const __grid_constant__ CUtensorMap tma_b,
                                                          const SoftmaxArgs g)
@@ -82,7 +89,7 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
     __nv_bfloat16 *stage = reinterpret_cast<__nv_bfloat16 *>(b_s + NST * SX_B_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM;
-    constexpr int kTiles = 2 * SX_TILES;
+    constexpr int kTiles = PREDICT ? SX_TILES : 2 * SX_TILES;
 
     if (threadIdx.x == 0) {
         any_failed = 0;
@@ -169,9 +176,10 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
         const int q = warp & 3, cs = warp >> 2;
         const int r = q * 32 + lane;
         const int row = m0 + r;
-        int lab = row < g.n ? g.labels[row] : -1;
+        int lab = (!PREDICT && row < g.n) ? g.labels[row] : -1;
         if (lab >= SX_CLASSES) lab = -1;
         float m = -__int_as_float(0x7F800000), ssum = 0.0f, inv = 0.0f;
+        int best = 0;  // PREDICT: this slice's first maximum
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         __nv_bfloat16 *st = stage + warp * 32 * SX_PITCH;
         // pass 1: running maximum and sum of exponentials over this slice
@@ -191,6 +199,18 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
             for (int c0 = 0; c0 < SX_SLICE; c0 += 16) {
                 float v[16];
                 tmem_ld16(taddr + (uint32_t)c0, v);
+                if (PREDICT) {
+                    // first maximum: columns arrive in ascending order
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float z = v[j] + g.bias[col0 + c0 + j];
+                        if (z > m) {
+                            m = z;
+                            best = col0 + c0 + j;
+                        }
+                    }
+                    continue;
+                }
                 float cm = m;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -211,11 +231,28 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
         // combine the four slices' statistics of each row; every epilogue warp
         // reaches this barrier once, also after a failed wait
         part_m[cs][r] = m;
-        part_s[cs][r] = ssum;
+        part_s[cs][r] = PREDICT ? __int_as_float(best) : ssum;
         if (failed) any_failed = 1;
         asm volatile("bar.sync 1, %0;" ::"n"(SX_EPI_WARPS * 32) : "memory");
         if (any_failed) failed = true;
-        if (!failed) {
+        if (PREDICT) {
+            // the row's first maximum: slices hold ascending column ranges
+            if (!failed && cs == 0 && row < g.n) {
+                float bm = part_m[0][r];
+                int bc = __float_as_int(part_s[0][r]);
+#pragma unroll
+                for (int k = 1; k < 4; ++k) {
+                    const float z = part_m[k][r];
+                    const int c = __float_as_int(part_s[k][r]);
+                    if (z > bm || (z == bm && c < bc)) {
+                        bm = z;
+                        bc = c;
+                    }
+                }
+                if (g.out_classes) g.out_classes[row] = bc;
+                if (g.out_nodes) g.out_nodes[row] = g.class_node[bc];
+            }
+        } else if (!failed) {
             m = fmaxf(fmaxf(part_m[0][r], part_m[1][r]), fmaxf(part_m[2][r], part_m[3][r]));
             ssum = 0.0f;
 #pragma unroll
@@ -227,7 +264,7 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
             }
         }
         // pass 2: dZ = softmax - onehot (zero for rows without a target)
-        for (int t = SX_TILES; t < kTiles && !failed; ++t) {
+        for (int t = SX_TILES; !PREDICT && t < kTiles && !failed; ++t) {
             const int b = t & 1;
             bool ok = mbar_wait(&acc_full[b], (uint32_t)(t >> 1) & 1u);
             ok = __all_sync(0xFFFFFFFFu, ok);
