@@ -183,6 +183,16 @@ def recorded_traffic(kernel: str):
     return None, None
 
 
+def table_occupancy(words: np.ndarray, ways: int) -> dict:
+    """Fill of a bounded table after a step: the share of valid words and the
+    mean number of nodes per used set (the paper's leaves per entry)."""
+    valid = words != np.uint64(0xFFFFFFFFFFFFFFFF)
+    per_set = valid.reshape(-1, ways).sum(axis=1)
+    used = per_set > 0
+    return {"valid_words": int(valid.sum()), "words": int(words.size), "fill": float(valid.mean()),
+            "nodes_per_used_set": float(per_set[used].mean()) if used.any() else 0.0}
+
+
 def algorithmic_bytes(st: dict, mode_closest: bool, width: int, ways: int) -> float:
     """Bytes the method must move for one batch: rays, results, table sets,
     interior nodes, triangles (traversal and predicted leaves), insert records."""
@@ -764,6 +774,7 @@ def main():
     restore((tab_c, tab_a))
     _, sc = H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tab_c, stats=True, verify=verify)
     _, sa = H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tab_a, stats=True)
+    occupancy = {name: table_occupancy(t.export(), args.ways) for name, t in (("closest", tab_c), ("any", tab_a))}
     _, pc = H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, None, stats=True)
     _, pa = H.trace(g, f0["ao"], H.HRPP_ANY_HIT, None, stats=True)
     g.check()
@@ -831,6 +842,7 @@ def main():
         "plain": {"value": p_value, "unit": "Mrays/s", "speedup_hrpp_over_plain": value / p_value,
                   "kernel_ms": p_kt},
         "per_mode_kernel_ms": kt,
+        "table_occupancy": occupancy,
         "skipped": {"closest": skipped(sc, pc), "any": skipped(sa, pa),
                     "paper_context": "paper Table 1 (PBRT limit study, no hardware stated): 30-69% hit-all, "
                                      "<1-48% hit-any savings"},
