@@ -770,13 +770,26 @@ def main():
     p_rays, p_ms, p_kt = timed((None, None), True)
     p_value = sum_over_ranks(p_rays) / (max_over_ranks(p_ms) * 1e-3) / 1e6
 
-    # --- counters of one step (from the restored warm tables)
+    # --- counters of one step (from the restored warm tables), with per-ray
+    # outcomes of HRPP and per-ray box tests of plain traversal
     restore((tab_c, tab_a))
-    _, sc = H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tab_c, stats=True, verify=verify)
-    _, sa = H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tab_a, stats=True)
+    per_ray = {}
+    for name, key in (("closest", "prim"), ("any", "ao")):
+        n = int(f0[key].shape[0])
+        per_ray[name] = (torch.empty(n, dtype=torch.uint8, device="cuda"), torch.empty(n, dtype=torch.int32, device="cuda"))
+    _, sc = H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tab_c, stats=True, verify=verify,
+                    ray_outcome=per_ray["closest"][0])
+    _, sa = H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tab_a, stats=True, ray_outcome=per_ray["any"][0])
     occupancy = {name: table_occupancy(t.export(), args.ways) for name, t in (("closest", tab_c), ("any", tab_a))}
-    _, pc = H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, None, stats=True)
-    _, pa = H.trace(g, f0["ao"], H.HRPP_ANY_HIT, None, stats=True)
+    _, pc = H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, None, stats=True, ray_box_tests=per_ray["closest"][1])
+    _, pa = H.trace(g, f0["ao"], H.HRPP_ANY_HIT, None, stats=True, ray_box_tests=per_ray["any"][1])
+
+    def skipped_limit(name):
+        # the paper's semantics (its true positives skip traversal): the share
+        # of plain box tests that belong to rays HRPP predicted correctly
+        oc, bx = per_ray[name]
+        bx = bx.double()
+        return float(bx[oc == H.HRPP_OUTCOME_TRUE_POS].sum() / bx.sum().clamp(min=1))
     g.check()
 
     # --- end to end through the C ABI with host buffers
@@ -818,9 +831,10 @@ def main():
     kname = f"k_trace<{width}, {'closest' if dom == 'closest' else 'any'}, hrpp>"
     traffic, traffic_src = recorded_traffic(f"bvh{width}_{dom}")
 
-    def skipped(h, p):
+    def skipped(h, p, limit):
         return {"prediction_ratio": h["true_pos"] / max(1, h["rays"]),
                 "skipped_exact_box_tests": 1.0 - h["box_tests"] / max(1, p["box_tests"]),
+                "skipped_limit_box_tests": limit,
                 "skipped_exact_interior_nodes": 1.0 - h["interior_nodes"] / max(1, p["interior_nodes"]),
                 "positives": h["positives"], "true_pos": h["true_pos"], "false_pos": h["false_pos"],
                 "tp_inexact": h["tp_inexact"], "rays": h["rays"]}
@@ -843,7 +857,8 @@ def main():
                   "kernel_ms": p_kt},
         "per_mode_kernel_ms": kt,
         "table_occupancy": occupancy,
-        "skipped": {"closest": skipped(sc, pc), "any": skipped(sa, pa),
+        "skipped": {"closest": skipped(sc, pc, skipped_limit("closest")),
+                    "any": skipped(sa, pa, skipped_limit("any")),
                     "paper_context": "paper Table 1 (PBRT limit study, no hardware stated): 30-69% hit-all, "
                                      "<1-48% hit-any savings"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",

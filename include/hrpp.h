@@ -185,7 +185,18 @@ typedef struct hrpp_trace_opts {
     uint32_t max_steps;
     uint32_t verify;
     uint32_t reserved[1];
+    uint8_t *ray_outcome;     /* device, one per ray, or NULL: HRPP_OUTCOME_* */
+    uint32_t *ray_box_tests;  /* device, one per ray, or NULL: box tests of the
+                                 ray's traversal from the root (0 for an
+                                 any-hit true positive; predicted subtrees
+                                 not included) */
 } hrpp_trace_opts;
+/* Per-ray outcome codes (Sec. 4.3).  The per-ray outputs above are filled
+ * only when the call also collects statistics (out_stats != NULL). */
+#define HRPP_OUTCOME_PLAIN 0      /* no lookup (no table, no prediction) */
+#define HRPP_OUTCOME_NEGATIVE 1   /* nothing predicted */
+#define HRPP_OUTCOME_FALSE_POS 2  /* predicted nodes held no valid hit */
+#define HRPP_OUTCOME_TRUE_POS 3   /* a predicted node held a valid hit */
 
 typedef struct hrpp_scene hrpp_scene;
 typedef struct hrpp_table hrpp_table;

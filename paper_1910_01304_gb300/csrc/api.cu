@@ -667,6 +667,10 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         p.max_steps = sc->n_interior + sc->n_leaves + 8u;
         if (opts && opts->max_steps > 0u && opts->max_steps < p.max_steps) p.max_steps = opts->max_steps;
         p.verify = opts ? (int)opts->verify : 0;
+        if (opts && out_stats) {
+            p.ray_outcome = opts->ray_outcome;
+            p.ray_box_tests = opts->ray_box_tests;
+        }
         p.rays = reinterpret_cast<const float4 *>(d_rays);
         p.n_rays = n_rays;
         p.hits = d_hits;

@@ -74,6 +74,8 @@ struct TraceParams {
     uint32_t n_nodes;            // canonical node count
     int verify;                  // closest-hit true positives: 0 root traversal, 1 bottom-up climb
     int hash_variant;            // 0: exponent MSBs (Sec. 5), 1: exponent LSBs
+    uint8_t *ray_outcome;        // per ray (statistics launches only; may be null)
+    uint32_t *ray_box_tests;     // per ray (statistics launches only; may be null)
 };
 
 // ---------------------------------------------------------------- hashing --

@@ -85,6 +85,8 @@ struct RayState {
     uint64_t tag;
     int32_t from;      // bottom-up verification: the ref the climb is at (kDoneRef: not climbing)
     bool climb_visit;  // the next interior visit is the climb's ancestor (then from moves up)
+    uint8_t outcome;   // HRPP_OUTCOME_* (written out by statistics launches)
+    uint32_t box0;     // the lane's box-test counter when this ray's traversal began
 };
 
 // Tests triangle j of a leaf (triangles from tr).  Any-hit: returns true at a
@@ -270,6 +272,7 @@ __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayS
     s.tag = 0;
     s.from = kDoneRef;
     s.climb_visit = false;
+    s.outcome = HRPP_OUTCOME_PLAIN;
     cnt.add(ST_RAYS);
     bool traverse = true, have_inverse = false;
     const bool learned = p.predicted != nullptr;
@@ -334,17 +337,21 @@ __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayS
         }
         if (!positive) {
             cnt.add(ST_NEGATIVES);
+            s.outcome = HRPP_OUTCOME_NEGATIVE;
         } else {
             cnt.add(ST_POSITIVES);
             if (s.b.found) {
                 cnt.add(ST_TRUE_POS);
+                s.outcome = HRPP_OUTCOME_TRUE_POS;
                 if (!CLOSEST) traverse = false;
             } else {
                 cnt.add(ST_FALSE_POS);
+                s.outcome = HRPP_OUTCOME_FALSE_POS;
             }
         }
     }
     s.predicted_hit = s.b.found;
+    if (STATS) s.box0 = cnt.c[ST_BOX_TESTS];
     if (traverse) {
         if (!have_inverse) s.ri = ray_inverse(s.o, s.d);
         s.tcur = (CLOSEST && s.b.found) ? s.b.t : s.d.w;
@@ -407,6 +414,10 @@ __device__ __forceinline__ bool finish_ray(const TraceParams &p, uint32_t i, con
         }
     }
     if (s.b.found) cnt.add(ST_HITS);
+    if (STATS) {
+        if (p.ray_outcome) p.ray_outcome[i] = s.outcome;
+        if (p.ray_box_tests) p.ray_box_tests[i] = cnt.c[ST_BOX_TESTS] - s.box0;
+    }
     if (CLOSEST) {
         reinterpret_cast<float4 *>(p.hits)[i] = make_float4(s.b.t, __uint_as_float(s.b.prim), s.b.u, s.b.v);
     } else {

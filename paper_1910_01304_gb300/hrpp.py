@@ -46,12 +46,14 @@ class hrpp_trace_opts(ctypes.Structure):
     _fields_ = [("kernel_start", ctypes.c_void_p), ("kernel_stop", ctypes.c_void_p),
                 ("predicted_nodes", ctypes.c_void_p), ("block_threads", ctypes.c_uint32),
                 ("schedule", ctypes.c_uint32), ("refill_min", ctypes.c_uint32), ("max_steps", ctypes.c_uint32),
-                ("verify", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1)]
+                ("verify", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1),
+                ("ray_outcome", ctypes.c_void_p), ("ray_box_tests", ctypes.c_void_p)]
 
 
 HRPP_SCHEDULE_DEFAULT, HRPP_SCHEDULE_BATCH, HRPP_SCHEDULE_REFILL = 0, 1, 2
 HRPP_VERIFY_ROOT, HRPP_VERIFY_BOTTOM_UP = 0, 1
 HRPP_HASH_EXP_MSB, HRPP_HASH_EXP_LSB = 0, 1
+HRPP_OUTCOME_PLAIN, HRPP_OUTCOME_NEGATIVE, HRPP_OUTCOME_FALSE_POS, HRPP_OUTCOME_TRUE_POS = 0, 1, 2, 3
 
 
 class hrpp_batch_item(ctypes.Structure):
@@ -296,7 +298,7 @@ class Table:
 
 def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, stats: bool = False,
           stream=None, kernel_events=None, block_threads: int = 0, schedule: int = 0, refill_min: int = 0,
-          predicted=None, max_steps: int = 0, verify: int = 0):
+          predicted=None, max_steps: int = 0, verify: int = 0, ray_outcome=None, ray_box_tests=None):
     """Traces rays ([n, 8] float32 torch tensor on the GPU, or a host numpy
     array / torch tensor).  Returns (hits, stats dict or None).
 
@@ -315,7 +317,7 @@ def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, 
     st = hrpp_stats() if stats else None
     opts = None
     if (kernel_events is not None or block_threads or schedule or refill_min or max_steps or verify
-            or predicted is not None):
+            or predicted is not None or ray_outcome is not None or ray_box_tests is not None):
         opts = hrpp_trace_opts()
         if predicted is not None:
             opts.predicted_nodes = _ptr(predicted)
@@ -327,6 +329,10 @@ def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, 
         opts.refill_min = refill_min
         opts.max_steps = max_steps
         opts.verify = verify
+        if ray_outcome is not None:
+            opts.ray_outcome = _ptr(ray_outcome)
+        if ray_box_tests is not None:
+            opts.ray_box_tests = _ptr(ray_box_tests)
     check(hrpp_trace_ex(scene.handle, table.handle if table is not None else None, _ptr(rays), n, mode, _ptr(hits),
                         ctypes.byref(st) if st is not None else None, _stream_handle(stream),
                         ctypes.byref(opts) if opts is not None else None))

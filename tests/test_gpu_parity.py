@@ -495,3 +495,39 @@ def test_injected_allocation_failures_return_oom(H, small_pair, monkeypatch):
     plain, _ = H.trace(g, rays, H.HRPP_CLOSEST_HIT)
     torch.cuda.synchronize()
     assert torch.equal(traced.view(torch.int32), plain.view(torch.int32))
+
+
+@pytest.mark.parametrize("go_up", [0, 1])
+@pytest.mark.parametrize("width_idx", [0, 1])
+def test_per_ray_outcomes_and_box_tests_match_oracle(H, small_pair, go_up, width_idx):
+    """Per-ray outputs of a statistics launch: the outcome class (Sec. 4.3)
+    and the box tests of the traversal from the root, ray by ray, equal the
+    oracle's, for plain traversal and for HRPP over three frames."""
+    import torch
+    s, g = small_pair[width_idx]
+    tab = H.Table(12, 2, 6, go_up=go_up)
+    otab = O.Table(12, 2, 6, O.TWO_PHASE, go_up=go_up)
+    for frame in range(3):
+        prim = s.primary_rays(frame=frame)
+        ph, _ = _oracle(s, prim, O.CLOSEST_HIT)
+        shadow, _ = W.secondary_shadow(s, prim, ph["t"], ph["prim"])
+        for mode, rays in ((O.CLOSEST_HIT, prim), (O.ANY_HIT, shadow)):
+            for use_table in (False, True):
+                if use_table and mode == O.ANY_HIT:
+                    continue  # one table, fed by the closest-hit rays
+                d = torch.from_numpy(rays).cuda()
+                oc = torch.full((len(rays),), 255, dtype=torch.uint8, device="cuda")
+                bx = torch.zeros(len(rays), dtype=torch.int32, device="cuda")
+                _, ost, ooc, obx = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, mode,
+                                           otab if use_table else None, per_ray=True)
+                _, gst = H.trace(g, d, mode, tab if use_table else None, stats=True, ray_outcome=oc,
+                                 ray_box_tests=bx)
+                torch.cuda.synchronize()
+                assert_same_stats(gst, ost)
+                assert np.array_equal(oc.cpu().numpy(), ooc), (frame, mode, use_table)
+                assert np.array_equal(bx.cpu().numpy().view(np.uint32), obx), (frame, mode, use_table)
+    # without statistics the per-ray buffers are left alone
+    oc = torch.full((len(prim),), 255, dtype=torch.uint8, device="cuda")
+    H.trace(g, torch.from_numpy(prim).cuda(), H.HRPP_CLOSEST_HIT, tab, ray_outcome=oc)
+    torch.cuda.synchronize()
+    assert bool((oc == 255).all())
