@@ -23,7 +23,7 @@ _lib = None
 
 ANY_HIT, CLOSEST_HIT = 0, 1
 TWO_PHASE, SEQUENTIAL, UNBOUNDED = 0, 1, 2
-VERIFY_ROOT, VERIFY_BOTTOM_UP = 0, 1
+VERIFY_ROOT, VERIFY_BOTTOM_UP, VERIFY_NONE = 0, 1, 2
 HASH_EXP_MSB, HASH_EXP_LSB = 0, 1
 NO_HIT = 0xFFFFFFFF
 EMPTY_WORD = 0xFFFFFFFFFFFFFFFF
@@ -223,8 +223,9 @@ def trace(tris, nodes, prim_index, root, rays, mode: int, table: Table | None = 
     predicted: optional int32 [n] canonical node per ray whose subtree is
     traversed first (learned proposal; -1 = none).
     verify: how closest-hit true positives are verified, VERIFY_ROOT (a
-    traversal from the root bounded by the predicted hit) or VERIFY_BOTTOM_UP
-    (a climb from the predicted hit's leaf through its ancestors' siblings).
+    traversal from the root bounded by the predicted hit), VERIFY_BOTTOM_UP
+    (a climb from the predicted hit's leaf through its ancestors' siblings) or
+    VERIFY_NONE (the paper's semantics: the predicted hit is returned).
 
     Returns (hits, stats dict[, outcome uint8[n], box_tests uint32[n]])."""
     tris = _f(tris).reshape(-1, 9)

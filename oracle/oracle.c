@@ -71,9 +71,10 @@ typedef struct {
 enum { ORC_ANY = 0, ORC_CLOSEST = 1 };
 enum { ORC_TWO_PHASE = 0, ORC_SEQUENTIAL = 1, ORC_UNBOUNDED = 2 };
 /* how a closest-hit true positive is verified: a traversal from the root
- * bounded by the predicted hit, or a climb from the predicted leaf testing
- * the siblings on the way up */
-enum { ORC_VERIFY_ROOT = 0, ORC_VERIFY_BOTTOM_UP = 1 };
+ * bounded by the predicted hit, a climb from the predicted leaf testing the
+ * siblings on the way up, or not at all (the paper's semantics, Sec. 4.3:
+ * the predicted hit is returned as it is, and may not be the closest) */
+enum { ORC_VERIFY_ROOT = 0, ORC_VERIFY_BOTTOM_UP = 1, ORC_VERIFY_NONE = 2 };
 
 typedef struct {
     uint64_t *words;  /* 2^log2_sets * 2^log2_ways table words (bounded modes) */
@@ -727,7 +728,7 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
                 if (b.found) {
                     oc = OUT_TRUE_POS;
                     stats[S_TRUE_POS] += 1;
-                    if (mode == ORC_ANY) run_traversal = 0;
+                    if (mode == ORC_ANY || verify == ORC_VERIFY_NONE) run_traversal = 0;
                 } else {
                     oc = OUT_FALSE_POS;
                     stats[S_FALSE_POS] += 1;

@@ -499,3 +499,36 @@ def test_hit_all_locality_exceeds_hit_any(small):
     _, _, sc = _unbounded_run(small, 6, O.CLOSEST_HIT)
     _, _, sa = _unbounded_run(small, 6, O.ANY_HIT)
     assert sc["true_pos"] / sc["rays"] > 5 * sa["true_pos"] / sa["rays"]
+
+
+# ------------------------------------ the paper's semantics (no verification) --
+
+def test_unverified_true_positives_follow_the_paper(small):
+    """VERIFY_NONE (Sec. 4.3 as the paper runs it): a closest-hit true
+    positive returns the best hit among its predicted leaves and does no
+    traversal and no insert; every other ray is exactly as with verification.
+    Results can then differ from plain traversal only on true positives, and
+    where they do, the returned hit is still a real hit of that ray."""
+    s = small
+    tv = O.Table(12, 2, 6, O.TWO_PHASE)
+    tn = O.Table(12, 2, 6, O.TWO_PHASE)
+    wrong_total = 0
+    for frame in range(4):
+        rays = s.primary_rays(frame=frame)[::2]
+        hp, sp, _, bxp = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, O.CLOSEST_HIT, per_ray=True)
+        hv, sv = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, O.CLOSEST_HIT, tv)
+        hn, sn, ocn, bxn = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, O.CLOSEST_HIT, tn, per_ray=True,
+                                   verify=O.VERIFY_NONE)
+        assert hp.tobytes() == hv.tobytes()
+        tp = ocn == 3
+        assert np.all(bxn[tp] == 0) and sn["tp_inexact"] == 0
+        # every other ray is answered and counted exactly as plain traversal
+        assert hn[~tp].tobytes() == hp[~tp].tobytes() and np.array_equal(bxn[~tp], bxp[~tp])
+        wrong = np.nonzero(hn["prim"] != hp["prim"])[0]
+        assert np.all(tp[wrong])
+        wrong_total += len(wrong)
+        for k in wrong[:20]:   # a real hit of that ray, never closer than the true closest
+            tri = np.asarray(s.tris, np.float32).reshape(-1, 9)[hn["prim"][k]]
+            hit, t, _, _ = O.ray_triangle(rays[k], tri[0:3], tri[3:6], tri[6:9])
+            assert hit and t == hn["t"][k] and hn["t"][k] >= hp["t"][k]
+    assert wrong_total > 0
