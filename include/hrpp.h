@@ -167,12 +167,17 @@ typedef struct hrpp_scene_info {
  *                             Both return exactly the plain closest hit and
  *                             leave the same table; the climb skips one box
  *                             test per level and the predicted leaf's
- *                             re-test.  Other values: HRPP_ERR_INVALID_ARG. */
+ *                             re-test.  HRPP_VERIFY_NONE is the paper's own
+ *                             semantics and NOT exact: a true positive
+ *                             returns its predicted hit, which may not be the
+ *                             closest, and does no traversal and no insert.
+ *                             Other values: HRPP_ERR_INVALID_ARG. */
 #define HRPP_SCHEDULE_DEFAULT 0u
 #define HRPP_SCHEDULE_BATCH 1u
 #define HRPP_SCHEDULE_REFILL 2u
 #define HRPP_VERIFY_ROOT 0u
 #define HRPP_VERIFY_BOTTOM_UP 1u
+#define HRPP_VERIFY_NONE 2u
 typedef struct hrpp_trace_opts {
     void *kernel_start, *kernel_stop;
     const int32_t *predicted_nodes;  /* device, one canonical node index per ray

@@ -601,7 +601,8 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         if (opts->refill_min > 32) return fail(HRPP_ERR_INVALID_ARG, "refill_min must be in [1, 32]");
         refill_min = opts->refill_min;
     }
-    if (opts && opts->verify != HRPP_VERIFY_ROOT && opts->verify != HRPP_VERIFY_BOTTOM_UP)
+    if (opts && opts->verify != HRPP_VERIFY_ROOT && opts->verify != HRPP_VERIFY_BOTTOM_UP &&
+        opts->verify != HRPP_VERIFY_NONE)
         return fail(HRPP_ERR_INVALID_ARG, "unknown verify mode %u", opts->verify);
     if (table && table->device != sc->device) return fail(HRPP_ERR_INVALID_ARG, "table and scene on different devices");
     if (table && table->bound_scene && table->bound_scene != sc->id)

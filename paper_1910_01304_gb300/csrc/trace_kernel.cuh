@@ -343,7 +343,9 @@ __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayS
             if (s.b.found) {
                 cnt.add(ST_TRUE_POS);
                 s.outcome = HRPP_OUTCOME_TRUE_POS;
-                if (!CLOSEST) traverse = false;
+                // any-hit: answered; closest-hit without verification (the
+                // paper's semantics, not exact): the predicted hit stands
+                if (!CLOSEST || p.verify == HRPP_VERIFY_NONE) traverse = false;
             } else {
                 cnt.add(ST_FALSE_POS);
                 s.outcome = HRPP_OUTCOME_FALSE_POS;
@@ -379,8 +381,9 @@ __device__ __forceinline__ bool finish_ray(const TraceParams &p, uint32_t i, con
     if (CLOSEST && s.predicted_hit && s.b.from_trav) cnt.add(ST_TP_INEXACT);
     // Sec. 5: a ray that traversed inserts the node of its final hit (the leaf,
     // or its ancestor go_up levels up, Sec. 6.2) unless its entry holds it
-    // already.  Any-hit true positives were answered by the predictor.
-    const bool traversed = CLOSEST || !s.predicted_hit;
+    // already.  Any-hit true positives (and closest-hit ones left unverified)
+    // were answered by the predictor.
+    const bool traversed = !s.predicted_hit || (CLOSEST && p.verify != HRPP_VERIFY_NONE);
     if (p.table && traversed && s.b.found && p.update_mode != HRPP_UPDATE_FROZEN) {
         uint32_t node = s.b.leaf;
         bool storable = true;

@@ -51,7 +51,7 @@ class hrpp_trace_opts(ctypes.Structure):
 
 
 HRPP_SCHEDULE_DEFAULT, HRPP_SCHEDULE_BATCH, HRPP_SCHEDULE_REFILL = 0, 1, 2
-HRPP_VERIFY_ROOT, HRPP_VERIFY_BOTTOM_UP = 0, 1
+HRPP_VERIFY_ROOT, HRPP_VERIFY_BOTTOM_UP, HRPP_VERIFY_NONE = 0, 1, 2
 HRPP_HASH_EXP_MSB, HRPP_HASH_EXP_LSB = 0, 1
 HRPP_OUTCOME_PLAIN, HRPP_OUTCOME_NEGATIVE, HRPP_OUTCOME_FALSE_POS, HRPP_OUTCOME_TRUE_POS = 0, 1, 2, 3
 

@@ -419,12 +419,37 @@ def test_bottom_up_mid_terrain_bvh4(H):
         assert np.array_equal(tab.export(), otab.words)
 
 
+@pytest.mark.parametrize("go_up", [0, 1])
+@pytest.mark.parametrize("width_idx", [0, 1])
+def test_unverified_mode_matches_oracle(H, small_pair, go_up, width_idx):
+    """HRPP_VERIFY_NONE (the paper's semantics, not exact): hits, counters
+    and table words equal the oracle's VERIFY_NONE over three frames, and
+    some true positives do return another hit than plain traversal."""
+    import torch
+    s, g = small_pair[width_idx]
+    tab = H.Table(12, 2, 6, go_up=go_up)
+    otab = O.Table(12, 2, 6, O.TWO_PHASE, go_up=go_up)
+    differ = 0
+    for frame in range(3):
+        rays = s.primary_rays(frame=frame)
+        oh, ost = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, O.CLOSEST_HIT, otab, verify=O.VERIFY_NONE)
+        gh, gst = H.trace(g, torch.from_numpy(rays).cuda(), H.HRPP_CLOSEST_HIT, tab, stats=True,
+                          verify=H.HRPP_VERIFY_NONE)
+        torch.cuda.synchronize()
+        assert_same_hits(O.CLOSEST_HIT, gh.cpu().numpy(), oh, f"frame {frame}")
+        assert_same_stats(gst, ost, msg=f"frame {frame}")
+        assert np.array_equal(tab.export(), otab.words)
+        ph, _ = _oracle(s, rays, O.CLOSEST_HIT)
+        differ += int((as_words(oh) != as_words(ph)).any(axis=1).sum())
+    assert differ > 0
+
+
 def test_verify_mode_is_validated(H, small_pair):
     import torch
     s, g = small_pair[0]
     rays = torch.from_numpy(s.primary_rays()[:64]).cuda()
     with pytest.raises(H.HrppError) as err:
-        H.trace(g, rays, H.HRPP_CLOSEST_HIT, verify=2)
+        H.trace(g, rays, H.HRPP_CLOSEST_HIT, verify=3)
     assert err.value.status == H.HRPP_ERR_INVALID_ARG
 
 
