@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--traces", type=int, default=50_000_000, help="learned workload: training traces")
-    ap.add_argument("--workload", default="terrain", choices=["terrain", "batched", "pathtrace", "learned"],
+    ap.add_argument("--workload", default="terrain", choices=["terrain", "small", "batched", "pathtrace", "learned"],
                     help="terrain: the headline step; batched: the 64-scene uneven mix in one graph-replayed launch")
     ap.add_argument("--scenes", type=int, default=64)
     ap.add_argument("--no-learned", action="store_true", help="pathtrace: skip the learned proposal")
@@ -409,6 +409,105 @@ def run_batched(args):
     return 0
 
 
+def run_small(args):
+    """Config 1: the small scene (1,792 tris, binary BVH), 256x256 primary
+    closest-hit rays and one shadow any-hit ray per hit, 2^12-entry
+    direct-mapped tables.  Each step restores the tables warmed by the other
+    frames and traces frame 0; the step is captured into a CUDA graph (these
+    launches are latency-bound) and replayed."""
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1910_01304_gb300 import hrpp as H
+    from paper_1910_01304_gb300.scenes import workloads as W
+    s = W.small_scene()
+    g = H.Scene.from_workload(s)
+    frames = []
+    for f in range(max(2, args.frames)):
+        prim = s.primary_rays(frame=frame_index(f, rank))
+        hits, _ = H.trace(g, torch.from_numpy(prim).cuda(), H.HRPP_CLOSEST_HIT)
+        hh = hits.cpu().numpy()
+        shadow, _ = W.secondary_shadow(s, prim, hh[:, 0], hh[:, 1].view(np.uint32))
+        frames.append((torch.from_numpy(prim).cuda(), torch.from_numpy(shadow).cuda()))
+    tab_c, tab_a = H.Table(12, 1, 6), H.Table(12, 1, 6)
+    for prim, shadow in frames[1:]:
+        H.trace(g, prim, H.HRPP_CLOSEST_HIT, tab_c)
+        H.trace(g, shadow, H.HRPP_ANY_HIT, tab_a)
+    snap_c, snap_a = H.Table(12, 1, 6), H.Table(12, 1, 6)
+    snap_c.copy_from(tab_c)
+    snap_a.copy_from(tab_a)
+    prim, shadow = frames[0]
+    out_c = torch.empty((prim.shape[0], 4), dtype=torch.float32, device="cuda")
+    out_a = torch.empty((shadow.shape[0],), dtype=torch.int32, device="cuda")
+    n_rays = int(prim.shape[0] + shadow.shape[0])
+
+    def step(tables):
+        if tables[0] is not None:
+            tables[0].copy_from(snap_c)
+            tables[1].copy_from(snap_a)
+        H.trace(g, prim, H.HRPP_CLOSEST_HIT, tables[0], hits=out_c)
+        H.trace(g, shadow, H.HRPP_ANY_HIT, tables[1], hits=out_a)
+
+    def timed(tables):
+        graph, replay = None, lambda: step(tables)
+        try:
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                for _ in range(3):
+                    step(tables)
+            torch.cuda.current_stream().wait_stream(side)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                step(tables)
+            replay = graph.replay
+        except Exception as exc:  # capture unsupported: time plain launches
+            print(f"CUDA graph capture failed ({exc}); timing launches", file=sys.stderr)
+            graph = None
+        for _ in range(args.warmup):
+            replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps, graph is not None
+
+    ms, graphed = timed((tab_c, tab_a))
+    p_ms, p_graphed = timed((None, None))
+    tab_c.copy_from(snap_c)
+    tab_a.copy_from(snap_a)
+    _, sc = H.trace(g, prim, H.HRPP_CLOSEST_HIT, tab_c, stats=True)
+    _, sa = H.trace(g, shadow, H.HRPP_ANY_HIT, tab_a, stats=True)
+    _, pc = H.trace(g, prim, H.HRPP_CLOSEST_HIT, None, stats=True)
+    _, pa = H.trace(g, shadow, H.HRPP_ANY_HIT, None, stats=True)
+    g.check()
+
+    def skipped(h, p):
+        return {"prediction_ratio": h["true_pos"] / max(1, h["rays"]),
+                "skipped_exact_box_tests": 1.0 - h["box_tests"] / max(1, p["box_tests"]), "rays": h["rays"]}
+
+    value = job_mrays_per_s(n_rays, ms)
+    line = {"metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "small scene: icosphere (1,280 tris) on a 16x16-quad ground (512 tris), binary "
+                                   "BVH; 256x256 primary closest-hit rays + 1 shadow any-hit ray per hit",
+                       "rays_per_step": n_rays, "frames": max(2, args.frames),
+                       "table": {"log2_entries": 12, "ways": 1, "precision": 6},
+                       "protocol": "each step: restore the tables warmed by the other frames, trace frame 0",
+                       "cuda_graph": graphed and p_graphed},
+            "plain": {"value": job_mrays_per_s(n_rays, p_ms), "ms_per_step": p_ms, "speedup_hrpp_over_plain": p_ms / ms},
+            "skipped": {"closest": skipped(sc, pc), "any": skipped(sa, pa)},
+            "gpu_launches": 4 * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_pathtrace(args):
     """Config 5: 1280x720 x 4 spp x 5 diffuse bounces (+ one shadow ray per
     bounce) on the 4.28M-triangle closed terrain, HRPP vs plain per bounce."""
@@ -657,6 +756,8 @@ def main():
         return run_pathtrace(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "small":
+        return run_small(args)
     rank, world, local = dist_env()
     import torch
     if not torch.cuda.is_available():
