@@ -145,7 +145,7 @@ typedef struct hrpp_scene_info {
  *                             ray is done take new rays while the rest of
  *                             the warp keeps traversing)
  *   refill_min                REFILL: idle lanes needed before a warp refills,
- *                             1..32 (0 = default)
+ *                             1..32 (0 = default, 24)
  *   max_steps                 node visits allowed per traversal (0 = the
  *                             default, interior nodes + leaves + 8, which a
  *                             traversal of a valid tree never reaches; larger

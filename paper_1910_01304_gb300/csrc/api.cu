@@ -49,7 +49,7 @@ namespace {
 // launch defaults (measured on GB300, see bench.py / the autotuner)
 constexpr uint32_t kDefaultBlockThreads = 128;
 constexpr uint32_t kDefaultSchedule = HRPP_SCHEDULE_BATCH;
-constexpr uint32_t kDefaultRefillMin = 16;
+constexpr uint32_t kDefaultRefillMin = 24;
 
 thread_local std::string g_last_error;
 std::atomic<uint64_t> g_next_scene_id{1};

@@ -21,8 +21,9 @@
 //   k_trace      a warp takes 32 rays, traces them to completion, repeats.
 //   k_trace_dyn  lanes whose ray finished take new rays (one atomic per warp
 //                for all of them) once refill_min lanes are idle, while the
-//                other lanes keep traversing; each round a lane descends
-//                interior nodes until a leaf is due, then tests that leaf.
+//                other lanes keep traversing; every iteration each lane visits
+//                one node, as in k_trace, between two warp votes (refill,
+//                finished rays).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -643,24 +644,24 @@ __global__ void __launch_bounds__(512) k_trace_dyn(const TraceParams p)
             if (!pool_open) break;
             continue;
         }
-        // one round: descend interior nodes until a leaf is due, then test it
-        if (ray != kNoRay && s.ref != kDoneRef) {
-            while (s.ref >= 0) {
-                if (over_budget(p, s)) break;
-                traverse_interior<W, BU, STATS>(p, s, stack, cnt);
+        // one node per lane per iteration, as the batch schedule does
+        if (ray != kNoRay) {
+            if (s.ref == kDoneRef) {
+                if (BU) climb<W>(p, s);
+            } else if (!over_budget(p, s)) {
+                if (s.ref >= 0) traverse_interior<W, BU, STATS>(p, s, stack, cnt);
+                else visit_leaf<CLOSEST, STATS>(p, s, stack, cnt);
             }
-            if (s.ref != kDoneRef && !over_budget(p, s)) visit_leaf<CLOSEST, STATS>(p, s, stack, cnt);
         }
-        // a bottom-up verification with nothing left below moves up a level
-        if (BU && ray != kNoRay && s.ref == kDoneRef) climb<W>(p, s);
-        // lanes whose ray is done write it out and free themselves
-        bool want = false;
-        uint32_t slot = 0;
-        uint64_t word = 0;
         const bool done = ray != kNoRay && s.ref == kDoneRef && s.from == kDoneRef;
-        if (done) want = finish_ray<CLOSEST, STATS>(p, ray, s, cnt, slot, word);
-        append_records(p, lane, want, slot, ray, word);
-        if (done) ray = kNoRay;
+        if (__any_sync(0xFFFFFFFFu, done)) {
+            bool want = false;
+            uint32_t slot = 0;
+            uint64_t word = 0;
+            if (done) want = finish_ray<CLOSEST, STATS>(p, ray, s, cnt, slot, word);
+            append_records(p, lane, want, slot, ray, word);
+            if (done) ray = kNoRay;
+        }
     }
     cnt.flush(p.ctl, lane);
 }
