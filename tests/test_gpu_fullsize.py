@@ -163,3 +163,40 @@ def test_full_learned_proposal_sampled():
     span = z.max(axis=1) - z.min(axis=1)
     assert np.all(z.max(axis=1) - picked <= 0.02 * span)
     assert np.mean(classes.cpu().numpy()[rows] == np.argmax(z, axis=1)) > 0.97
+
+
+def test_maximum_table_and_ray_counts():
+    """The size limits: tables at both ends of the allowed range (2^28
+    entries in 8-way sets, a single 8-way set, a single entry) match the
+    oracle word for word, and one call with 2^28 + 3 rays (8.6 GB of rays:
+    copies of one frame) returns the single-frame answer for every copy."""
+    import torch
+    H = hrpp_mod()
+    s = W.small_scene()
+    g = H.Scene.from_workload(s)
+    for log2_entries, ways in ((28, 8), (3, 8), (0, 1)):
+        tab = H.Table(log2_entries, ways, 6)
+        otab = O.Table(log2_entries, ways, 6, O.TWO_PHASE)
+        for frame in range(2):
+            rays = s.primary_rays(frame=frame)
+            oh, ost = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, O.CLOSEST_HIT, otab)
+            gh, gst = gpu_trace(H, g, rays, O.CLOSEST_HIT, tab)
+            assert_same_hits(O.CLOSEST_HIT, gh, oh, f"2^{log2_entries} x {ways}")
+            assert_same_stats(gst, ost, msg=f"2^{log2_entries} x {ways}")
+        assert np.array_equal(tab.export(), otab.words)
+        tab.close()
+        del otab
+    frame_np = s.primary_rays(frame=3)
+    base = torch.from_numpy(frame_np).cuda()
+    n = (1 << 28) + 3
+    big = base.repeat(n // base.shape[0] + 1, 1)[:n].contiguous()
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    H.trace(g, big, H.HRPP_ANY_HIT, hits=out)
+    ref, _ = H.trace(g, base, H.HRPP_ANY_HIT)
+    torch.cuda.synchronize()
+    g.check()
+    copies = out[: (n // base.shape[0]) * base.shape[0]].view(-1, base.shape[0])
+    assert bool((copies == ref.unsqueeze(0)).all())
+    assert torch.equal(out[-3:], ref[:3])
+    oh, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, frame_np[:4000], O.ANY_HIT)
+    assert np.array_equal(any_prims(ref[:4000].cpu().numpy()), oh)
