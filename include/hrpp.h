@@ -22,6 +22,11 @@
  *     host array it is given; the caller keeps ownership of its buffers.
  *   - Objects live on the CUDA device that was current when they were made;
  *     calls switch to that device and restore the caller's afterwards.
+ *   - Concurrency: a scene may be traced by any number of calls at once (it
+ *     is read-only on the GPU, but its error flag is shared).  A table, a
+ *     batch or a proposal must not be used by two calls whose GPU work
+ *     overlaps (two streams, or two host threads): order them on one stream
+ *     or with events.  Host-side calls are thread-safe otherwise.
  */
 #ifndef HRPP_H
 #define HRPP_H
