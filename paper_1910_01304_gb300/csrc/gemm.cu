@@ -55,14 +55,11 @@ cudaError_t make_map(CUtensorMap *map, const void *ptr, uint64_t rows, uint64_t 
 template <int BN, int EPI, int NST>
 cudaError_t launch_stages(const void *a, const void *b, const umma::GemmArgs &g, int splits, cudaStream_t s)
 {
-    static bool configured = false;  // per template instance; attribute setting is idempotent
     const size_t smem = umma::gemm_smem_bytes<BN, NST>();
-    if (!configured) {
-        cudaError_t e =
-            cudaFuncSetAttribute(umma::k_gemm<BN, EPI, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    // once per template instance (thread-safe static initialisation)
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(umma::k_gemm<BN, EPI, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
     CUtensorMap ma, mb;
     cudaError_t e = make_map(&ma, a, (uint64_t)g.M, (uint64_t)g.K, umma::BM);
     if (e == cudaSuccess) e = make_map(&mb, b, (uint64_t)g.N, (uint64_t)g.K, BN);
@@ -87,14 +84,11 @@ namespace {
 template <bool PREDICT>
 cudaError_t launch_output_layer(const void *h2, const void *w3, const umma::SoftmaxArgs &g, cudaStream_t s)
 {
-    static bool configured = false;  // per instance; attribute setting is idempotent
     const size_t smem = umma::softmax_smem_bytes<>();
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(umma::k_softmax_xent<umma::SX_NST, PREDICT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    // once per instance (thread-safe static initialisation)
+    static const cudaError_t attr = cudaFuncSetAttribute(umma::k_softmax_xent<umma::SX_NST, PREDICT>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
     if (g.npad <= 0 || g.npad % umma::BM != 0 || ((uintptr_t)h2 & 15u) || ((uintptr_t)w3 & 15u)) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     cudaError_t e = make_map(&ma, h2, (uint64_t)g.npad, umma::SX_K, umma::BM);
