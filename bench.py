@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--quads", type=int, default=708)
     ap.add_argument("--spheres", type=int, default=64)
     ap.add_argument("--res", default="1920x1080")
+    ap.add_argument("--l2", default="none", choices=["none", "table", "nodes"],
+                    help="terrain: persisting-L2 window of the timed HRPP traces (with a set-aside)")
+    ap.add_argument("--l2-set-aside-mb", type=int, default=64)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -228,6 +231,53 @@ def make_frames(args, rank, scene_w, H, g, torch):
     return frames
 
 
+def host_threads():
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OracleThreads:
+    """The oracle's trace, unchanged, run ray-parallel across the host cores.
+    Thread i takes rays i, i+k, i+2k, ... of each batch (a static
+    partition that spreads sky and terrain rays evenly) and, for HRPP, its own
+    pair of tables; the ctypes call releases the interpreter lock, so the k
+    calls run concurrently.  Chunk copies and result gathering sit outside
+    the timed calls."""
+
+    def __init__(self, O, sw, k: int, table_args=None):
+        from concurrent.futures import ThreadPoolExecutor
+        self.O, self.sw, self.k = O, sw, k
+        self.pool = ThreadPoolExecutor(k)
+        self.tables = None
+        if table_args is not None:
+            self.tables = {m: [O.Table(*table_args) for _ in range(k)] for m in (O.CLOSEST_HIT, O.ANY_HIT)}
+
+    def split(self, rays):
+        return [np.ascontiguousarray(rays[i::self.k]) for i in range(self.k)]
+
+    def trace(self, chunks, mode):
+        """Traces prepared chunks; returns (per-chunk hits, seconds)."""
+        O, sw = self.O, self.sw
+        tabs = self.tables[mode] if self.tables is not None else [None] * self.k
+        t0 = time.perf_counter()
+        futs = [self.pool.submit(O.trace, sw.tris, sw.nodes, sw.prim_index, sw.root, c, mode, tb)
+                for c, tb in zip(chunks, tabs) if len(c)]
+        res = [f.result()[0] for f in futs]
+        return res, time.perf_counter() - t0
+
+    def gather(self, res, n, dtype):
+        out = np.empty(n, dtype)
+        for i, r in enumerate(res):
+            out[i::self.k] = r
+        return out
+
+    def close(self):
+        self.pool.shutdown()
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -237,50 +287,84 @@ def run_reference(args):
     w, h = map(int, args.res.split("x"))
     sw = W.terrain_scene(quads=args.quads, n_spheres=args.spheres, res=(w, h))
     prim = sw.primary_rays(frame=1)
-    tc = O.Table(args.log2_entries, args.ways, args.precision, O.TWO_PHASE)
-    ta = O.Table(args.log2_entries, args.ways, args.precision, O.TWO_PHASE)
-    # each step: a bounded sample of the step's work: 16 whole image rows spread
-    # evenly down the frame (each row's rays in order, coherent as the GPU's
-    # batches; sky and near terrain in the frame's proportions), traced as
-    # primary closest-hit rays, then the AO any-hit rays of their hits
-    n_rows = 16
+    k = host_threads()
+    ot = OracleThreads(O, sw, k, (args.log2_entries, args.ways, args.precision, O.TWO_PHASE))
+    # each step: a bounded sample of the step's work: 16 whole image rows per
+    # host thread, spread evenly down the frame (sky and near terrain in the
+    # frame's proportions), traced as primary closest-hit rays, then the AO
+    # any-hit rays of their hits; each thread keeps its own tables across
+    # steps
+    n_rows = min(h, 16 * k)
     band = n_rows * w
 
-    def step(k):
+    def step(j):
         """Returns (rays traced, seconds spent tracing)."""
-        rows = [(k + j * (h // n_rows)) % h for j in range(n_rows)]
+        rows = [(j + r * (h // n_rows)) % h for r in range(n_rows)]
         sp = np.ascontiguousarray(np.concatenate([prim[r * w:(r + 1) * w] for r in rows]))
-        t0 = time.perf_counter()
-        ph, _ = O.trace(sw.tris, sw.nodes, sw.prim_index, sw.root, sp, O.CLOSEST_HIT, tc)
-        t1 = time.perf_counter()
+        res, t_p = ot.trace(ot.split(sp), O.CLOSEST_HIT)
+        ph = ot.gather(res, len(sp), O.HIT_DTYPE)
         sa, _ = W.secondary_ao(sw, sp, ph["t"], ph["prim"], frame=1)
-        t2 = time.perf_counter()
-        O.trace(sw.tris, sw.nodes, sw.prim_index, sw.root, sa, O.ANY_HIT, ta)
-        t3 = time.perf_counter()
-        return len(sp) + len(sa), (t1 - t0) + (t3 - t2)
+        _, t_a = ot.trace(ot.split(sa), O.ANY_HIT)
+        return len(sp) + len(sa), t_p + t_a
 
-    for k in range(args.warmup):
-        step(k * 7)
+    for j in range(args.warmup):
+        step(j * 7)
     rays, dt = 0, 0.0
-    for k in range(args.steps):
-        r, t = step((args.warmup + k) * 7)
+    for j in range(args.steps):
+        r, t = step((args.warmup + j) * 7)
         rays += r
         dt += t
+    ot.close()
     v = rays / dt / 1e6
     sample = (f"per step: {n_rows} whole rows spread evenly down a {w}x{h} frame ({band} primary closest-hit rays) and "
-              "the AO any-hit rays of their hits, oracle HRPP two-phase; the AO generation between the two traces "
-              "is not timed")
+              f"the AO any-hit rays of their hits, oracle HRPP two-phase on {k} host threads (thread i takes rays "
+              "i, i+k, ... with its own tables); the AO generation between the two traces is not timed")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mrays/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": v, "unit": "Mrays/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "Mrays/s", "cores": k, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def cpu_baseline(args, sw, frames):
+    """The oracle, as it stands, on the host cores.
+
+    value: HRPP (two-phase) over all of frame 0 on every host core, each
+    thread with its own tables warmed by its share of the other frames (the
+    GPU step's protocol, per thread); plain: the same rays without tables;
+    single_core: HRPP on one core over a sample of frame 0 with cold tables."""
+    import oracle as O
+    k = host_threads()
+    ta = (args.log2_entries, args.ways, args.precision, O.TWO_PHASE)
+    ot = OracleThreads(O, sw, k, ta)
+    for f in range(1, len(frames)):
+        ot.trace(ot.split(frames[f]["prim_h"]), O.CLOSEST_HIT)
+        ot.trace(ot.split(frames[f]["ao_h"]), O.ANY_HIT)
+    cp, ca = ot.split(frames[0]["prim_h"]), ot.split(frames[0]["ao_h"])
+    n0 = len(frames[0]["prim_h"]) + len(frames[0]["ao_h"])
+    _, t_p = ot.trace(cp, O.CLOSEST_HIT)
+    _, t_a = ot.trace(ca, O.ANY_HIT)
+    ot.close()
+    v_hrpp = n0 / (t_p + t_a) / 1e6
+    plain = OracleThreads(O, sw, k)
+    _, u_p = plain.trace(cp, O.CLOSEST_HIT)
+    _, u_a = plain.trace(ca, O.ANY_HIT)
+    plain.close()
+    v_plain = n0 / (u_p + u_a) / 1e6
+    single = cpu_single_core(args, sw, frames)
+    return {"value": v_hrpp, "unit": "Mrays/s", "cores": k, "kind": "oracle",
+            "sample": f"all of frame 0 ({len(frames[0]['prim_h'])} primary closest-hit + {len(frames[0]['ao_h'])} "
+                      f"AO any-hit rays), oracle HRPP two-phase on {k} host threads (thread i takes rays i, i+k, ... "
+                      f"with its own tables, warmed by its share of {len(frames) - 1} other frames), "
+                      f"{t_p + t_a:.2f} s",
+            "plain": {"value": v_plain, "unit": "Mrays/s", "cores": k, "seconds": u_p + u_a},
+            "single_core": single}
+
+
+def cpu_single_core(args, sw, frames):
     """The oracle, as it stands, on a bounded sample of frame 0 (one core)."""
     import oracle as O
     prim = frames[0]["prim_h"]
@@ -791,6 +875,10 @@ def main():
             pg.barrier()
 
     verify = H.HRPP_VERIFY_BOTTOM_UP if args.verify == "bottom_up" else H.HRPP_VERIFY_ROOT
+    l2_kinds = {"none": H.HRPP_L2_NONE, "table": H.HRPP_L2_TABLE, "nodes": H.HRPP_L2_NODES}
+    l2_kind = [l2_kinds[args.l2]]
+    if args.l2 != "none":
+        H.l2_set_aside(args.l2_set_aside_mb << 20)
 
     # Warm tables: the other frames (1 .. F-1) go through HRPP once; device
     # snapshots of the tables they leave are restored at the start of every
@@ -816,8 +904,9 @@ def main():
             ev = events[k] if events is not None else (None, None)
             restore(tables)
             H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tables[0], hits=out_c,
-                    kernel_events=ev[0] if ev[0] else None, verify=verify)
-            H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tables[1], hits=out_a, kernel_events=ev[1] if ev[1] else None)
+                    kernel_events=ev[0] if ev[0] else None, verify=verify, l2_persist=l2_kind[0])
+            H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tables[1], hits=out_a, kernel_events=ev[1] if ev[1] else None,
+                    l2_persist=l2_kind[0])
             total += rays_per_frame[0]
         return total
 
@@ -870,6 +959,24 @@ def main():
     # --- plain traversal on the same rays
     p_rays, p_ms, p_kt = timed((None, None), True)
     p_value = sum_over_ranks(p_rays) / (max_over_ranks(p_ms) * 1e-3) / 1e6
+
+    # --- the same HRPP step with a persisting-L2 window over the table words
+    # or over the interior nodes (a set-aside only for these runs)
+    l2_variants = None
+    if args.l2 == "none":
+        try:
+            granted = H.l2_set_aside(args.l2_set_aside_mb << 20)
+        except H.HrppError:
+            granted = 0
+        if granted:
+            l2_variants = {"set_aside_bytes": granted}
+            for name in ("table", "nodes"):
+                l2_kind[0] = l2_kinds[name]
+                v_rays, v_ms, v_kt = timed((tab_c, tab_a), True)
+                l2_variants[name] = {"value": sum_over_ranks(v_rays) / (max_over_ranks(v_ms) * 1e-3) / 1e6,
+                                     "kernel_ms": v_kt}
+            l2_kind[0] = H.HRPP_L2_NONE
+            H.l2_set_aside(0)
 
     # --- counters of one step (from the restored warm tables), with per-ray
     # outcomes of HRPP and per-ray box tests of plain traversal
@@ -976,12 +1083,13 @@ def main():
                    "protocol": f"each step: restore the tables warmed by {args.frames - 1} other jittered frames, "
                                "then trace frame 0 (closest-hit primaries, then AO) with two-phase updates",
                    "table": {"log2_entries": args.log2_entries, "ways": args.ways, "precision": args.precision,
-                             "update": args.update, "verify": args.verify},
+                             "update": args.update, "verify": args.verify, "l2_window": args.l2},
                    "l2": f"inputs larger than L2: {rays_per_frame[0] * 32 / 1e6:.0f} MB of rays per step; "
                          "scene resident"},
         "plain": {"value": p_value, "unit": "Mrays/s", "speedup_hrpp_over_plain": value / p_value,
                   "kernel_ms": p_kt},
         "per_mode_kernel_ms": kt,
+        "l2_persist": l2_variants,
         "table_occupancy": occupancy,
         "paper_semantics": paper_semantics,
         "skipped": {"closest": skipped(sc, pc, skipped_limit("closest")),

@@ -176,13 +176,27 @@ typedef struct hrpp_scene_info {
  *                             semantics and NOT exact: a true positive
  *                             returns its predicted hit, which may not be the
  *                             closest, and does no traversal and no insert.
- *                             Other values: HRPP_ERR_INVALID_ARG. */
+ *                             Other values: HRPP_ERR_INVALID_ARG.
+ *   l2_persist                which device range the traversal launch marks
+ *                             persisting in L2 (an access-policy window on
+ *                             the launch): HRPP_L2_NONE (default),
+ *                             HRPP_L2_TABLE (the table's words; nothing
+ *                             without a table) or HRPP_L2_NODES (the scene's
+ *                             interior nodes).  It takes effect only while
+ *                             the context has a persisting-L2 set-aside
+ *                             (hrpp_l2_set_aside); the window is clipped to
+ *                             the device's maximum and its hit ratio is
+ *                             set-aside / window bytes (at most 1).  Other
+ *                             values: HRPP_ERR_INVALID_ARG. */
 #define HRPP_SCHEDULE_DEFAULT 0u
 #define HRPP_SCHEDULE_BATCH 1u
 #define HRPP_SCHEDULE_REFILL 2u
 #define HRPP_VERIFY_ROOT 0u
 #define HRPP_VERIFY_BOTTOM_UP 1u
 #define HRPP_VERIFY_NONE 2u
+#define HRPP_L2_NONE 0u
+#define HRPP_L2_TABLE 1u
+#define HRPP_L2_NODES 2u
 typedef struct hrpp_trace_opts {
     void *kernel_start, *kernel_stop;
     const int32_t *predicted_nodes;  /* device, one canonical node index per ray
@@ -194,7 +208,7 @@ typedef struct hrpp_trace_opts {
     uint32_t refill_min;
     uint32_t max_steps;
     uint32_t verify;
-    uint32_t reserved[1];
+    uint32_t l2_persist;
     uint8_t *ray_outcome;     /* device, one per ray, or NULL: HRPP_OUTCOME_* */
     uint32_t *ray_box_tests;  /* device, one per ray, or NULL: box tests of the
                                  ray's traversal from the root (0 for an
@@ -308,6 +322,16 @@ hrpp_status hrpp_trace(const hrpp_scene *scene, hrpp_table *table, const hrpp_ra
 hrpp_status hrpp_trace_ex(const hrpp_scene *scene, hrpp_table *table, const hrpp_ray *rays, uint32_t n_rays,
                           hrpp_mode mode, void *out_hits, hrpp_stats *out_stats, void *stream,
                           const hrpp_trace_opts *opts);
+
+/* Sets the current device's persisting-L2 set-aside (the part of L2 that
+ * lines from an hrpp_trace_opts.l2_persist window may keep) to `bytes`,
+ * clipped to the device's maximum, and writes the size in force to *granted
+ * (may be NULL).  bytes == 0 releases it and returns lines already marked
+ * persisting to normal.  The setting belongs to this process's CUDA context
+ * on the current device: it applies to every kernel of the process that
+ * uses an access-policy window and ends with the context.  Returns
+ * HRPP_ERR_CUDA when the device has no persisting L2. */
+hrpp_status hrpp_l2_set_aside(size_t bytes, size_t *granted);
 
 /* hrpp_trace for callers that must not allocate device memory.  The paper
  * has no counterpart; this is a library-usage entry point.  hrpp_trace takes

@@ -604,6 +604,8 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
     if (opts && opts->verify != HRPP_VERIFY_ROOT && opts->verify != HRPP_VERIFY_BOTTOM_UP &&
         opts->verify != HRPP_VERIFY_NONE)
         return fail(HRPP_ERR_INVALID_ARG, "unknown verify mode %u", opts->verify);
+    if (opts && opts->l2_persist > HRPP_L2_NODES)
+        return fail(HRPP_ERR_INVALID_ARG, "unknown l2_persist value %u", opts->l2_persist);
     if (table && table->device != sc->device) return fail(HRPP_ERR_INVALID_ARG, "table and scene on different devices");
     if (table && table->bound_scene && table->bound_scene != sc->id)
         return fail(HRPP_ERR_INVALID_ARG, "table is bound to another scene; reset it first");
@@ -698,8 +700,13 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         cudaEvent_t ev0 = opts ? (cudaEvent_t)opts->kernel_start : nullptr;
         cudaEvent_t ev1 = opts ? (cudaEvent_t)opts->kernel_stop : nullptr;
         const int sched = schedule == HRPP_SCHEDULE_REFILL ? 1 : 0;
-        e = sc->width == 2 ? launch_trace_w2(closest, out_stats != nullptr, sched, p, (int)block_threads, 0, stream, ev0, ev1)
-                           : launch_trace_w4(closest, out_stats != nullptr, sched, p, (int)block_threads, 0, stream, ev0, ev1);
+        L2Window l2{nullptr, 0};
+        if (opts && opts->l2_persist == HRPP_L2_TABLE && table)
+            l2 = L2Window{table->d_words, sizeof(uint64_t) << table->log2_entries};
+        else if (opts && opts->l2_persist == HRPP_L2_NODES)
+            l2 = L2Window{sc->d_nodes, (size_t)sc->n_interior * (sc->width == 2 ? 64u : 128u)};
+        e = sc->width == 2 ? launch_trace_w2(closest, out_stats != nullptr, sched, p, (int)block_threads, 0, stream, ev0, ev1, &l2)
+                           : launch_trace_w4(closest, out_stats != nullptr, sched, p, (int)block_threads, 0, stream, ev0, ev1, &l2);
         if (e != cudaSuccess) { status = cuda_fail(e, "trace launch"); break; }
         if (two_phase && (e = launch_table_apply(table->d_words, table->d_winner, p.records, ctl, n_rays, stream)) != cudaSuccess) {
             status = cuda_fail(e, "table update launch");
@@ -728,6 +735,28 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
             cudaMemset(sc->d_error, 0, sizeof(uint32_t));
             return fail(HRPP_ERR_TRAVERSAL_LIMIT, "a ray was stopped early (flag %u)", flag);
         }
+    }
+    return HRPP_OK;
+}
+
+hrpp_status hrpp_l2_set_aside(size_t bytes, size_t *granted)
+{
+    int dev = 0, max_persist = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if ((e = cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev)) != cudaSuccess)
+        return cuda_fail(e, "persisting L2 size");
+    if (max_persist <= 0) return fail(HRPP_ERR_CUDA, "device %d has no persisting L2", dev);
+    if (bytes > (size_t)max_persist) bytes = (size_t)max_persist;
+    if (bytes == 0 && (e = cudaCtxResetPersistingL2Cache()) != cudaSuccess)
+        return cuda_fail(e, "cudaCtxResetPersistingL2Cache");
+    if ((e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, bytes)) != cudaSuccess)
+        return cuda_fail(e, "cudaDeviceSetLimit(persisting L2)");
+    if (granted) {
+        size_t now = 0;
+        if ((e = cudaDeviceGetLimit(&now, cudaLimitPersistingL2CacheSize)) != cudaSuccess)
+            return cuda_fail(e, "cudaDeviceGetLimit(persisting L2)");
+        *granted = now;
     }
     return HRPP_OK;
 }

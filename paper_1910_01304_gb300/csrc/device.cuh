@@ -208,13 +208,23 @@ __device__ __forceinline__ bool tri_test(float4 o, float4 d, float4 v0, float4 e
     return true;
 }
 
+// A device range whose L2 hits the traversal launch marks persisting (an
+// access-policy window on the launch; it takes effect only while the context
+// has a persisting-L2 set-aside).
+struct L2Window {
+    const void *base;
+    size_t bytes;
+};
+
 // host launchers (trace_bvh2.cu, trace_bvh4.cu, table.cu)
 // schedule: 0 = each warp traces 32 rays to completion before taking the next
 // 32; 1 = lanes that finish take new rays while the others keep traversing
 cudaError_t launch_trace_w2(bool closest, bool stats, int schedule, const TraceParams &p, int block_threads,
-                            int blocks_per_sm_cap, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1);
+                            int blocks_per_sm_cap, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1,
+                            const L2Window *l2 = nullptr);
 cudaError_t launch_trace_w4(bool closest, bool stats, int schedule, const TraceParams &p, int block_threads,
-                            int blocks_per_sm_cap, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1);
+                            int blocks_per_sm_cap, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1,
+                            const L2Window *l2 = nullptr);
 cudaError_t launch_table_apply(uint64_t *table, uint32_t *winner, const Record *records, Ctl *ctl,
                                uint32_t max_records, cudaStream_t stream);
 // batched launches (batch.cu): every item of one BVH width in one kernel, then

@@ -4,9 +4,9 @@
 namespace hrpp {
 
 cudaError_t launch_trace_w4(bool closest, bool stats, int schedule, const TraceParams &p, int block_threads, int blocks_per_sm_cap,
-                            cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1)
+                            cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1, const L2Window *l2)
 {
-    return launch_width<4>(closest, stats, schedule, p, block_threads, blocks_per_sm_cap, stream, ev0, ev1);
+    return launch_width<4>(closest, stats, schedule, p, block_threads, blocks_per_sm_cap, stream, ev0, ev1, l2);
 }
 
 cudaError_t launch_batch_w4(bool stats, const BatchDesc &b, int block_threads, cudaStream_t stream)

@@ -28,6 +28,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "device.cuh"
 
 namespace hrpp {
@@ -668,7 +670,8 @@ __global__ void __launch_bounds__(512) k_trace_dyn(const TraceParams p)
 
 template <int W>
 cudaError_t launch_width(bool closest, bool stats, int schedule, const TraceParams &p, int block_threads,
-                         int blocks_per_sm_cap, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1)
+                         int blocks_per_sm_cap, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1,
+                         const L2Window *l2 = nullptr)
 {
     const void *fn;
     const bool bu = closest && p.verify == HRPP_VERIFY_BOTTOM_UP;
@@ -696,9 +699,43 @@ cudaError_t launch_width(bool closest, bool stats, int schedule, const TracePara
     const uint64_t warps_per_block = block_threads / 32;
     if (blocks * warps_per_block > warps_needed) blocks = (warps_needed + warps_per_block - 1) / warps_per_block;
     if (blocks < 1) blocks = 1;
+    // persisting-L2 window: only while the context has a set-aside, and no
+    // larger than the device allows
+    cudaLaunchAttribute attr;
+    unsigned n_attr = 0;
+    if (l2 && l2->base && l2->bytes) {
+        size_t set_aside = 0;
+        int max_window = 0;
+        if ((e = cudaDeviceGetLimit(&set_aside, cudaLimitPersistingL2CacheSize)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev)) != cudaSuccess)
+            return e;
+        if (set_aside > 0 && max_window > 0) {
+            const size_t bytes = l2->bytes < (size_t)max_window ? l2->bytes : (size_t)max_window;
+            memset(&attr, 0, sizeof attr);
+            attr.id = cudaLaunchAttributeAccessPolicyWindow;
+            attr.val.accessPolicyWindow.base_ptr = const_cast<void *>(l2->base);
+            attr.val.accessPolicyWindow.num_bytes = bytes;
+            attr.val.accessPolicyWindow.hitRatio = set_aside >= bytes ? 1.0f : (float)((double)set_aside / bytes);
+            attr.val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+            attr.val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+            n_attr = 1;
+        }
+    }
     if (ev0) cudaEventRecord(ev0, stream);
     void *args[] = {(void *)&p};
-    e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(block_threads), args, 0, stream);
+    if (n_attr) {
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof cfg);
+        cfg.gridDim = dim3((unsigned)blocks);
+        cfg.blockDim = dim3(block_threads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = stream;
+        cfg.attrs = &attr;
+        cfg.numAttrs = n_attr;
+        e = cudaLaunchKernelExC(&cfg, fn, args);
+    } else {
+        e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(block_threads), args, 0, stream);
+    }
     if (ev1) cudaEventRecord(ev1, stream);
     return e;
 }

@@ -46,13 +46,14 @@ class hrpp_trace_opts(ctypes.Structure):
     _fields_ = [("kernel_start", ctypes.c_void_p), ("kernel_stop", ctypes.c_void_p),
                 ("predicted_nodes", ctypes.c_void_p), ("block_threads", ctypes.c_uint32),
                 ("schedule", ctypes.c_uint32), ("refill_min", ctypes.c_uint32), ("max_steps", ctypes.c_uint32),
-                ("verify", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 1),
+                ("verify", ctypes.c_uint32), ("l2_persist", ctypes.c_uint32),
                 ("ray_outcome", ctypes.c_void_p), ("ray_box_tests", ctypes.c_void_p)]
 
 
 HRPP_SCHEDULE_DEFAULT, HRPP_SCHEDULE_BATCH, HRPP_SCHEDULE_REFILL = 0, 1, 2
 HRPP_VERIFY_ROOT, HRPP_VERIFY_BOTTOM_UP, HRPP_VERIFY_NONE = 0, 1, 2
 HRPP_HASH_EXP_MSB, HRPP_HASH_EXP_LSB = 0, 1
+HRPP_L2_NONE, HRPP_L2_TABLE, HRPP_L2_NODES = 0, 1, 2
 HRPP_OUTCOME_PLAIN, HRPP_OUTCOME_NEGATIVE, HRPP_OUTCOME_FALSE_POS, HRPP_OUTCOME_TRUE_POS = 0, 1, 2, 3
 
 
@@ -92,6 +93,7 @@ def _load():
         "hrpp_trace": (st, [P, P, P, u32, i32, P, P, P]),
         "hrpp_trace_ex": (st, [P, P, P, u32, i32, P, P, P, P]),
         "hrpp_trace_noalloc": (st, [P, P, P, u32, i32, P, P, P]),
+        "hrpp_l2_set_aside": (st, [sz, P]),
         "hrpp_batch_create": (st, [P, u32, i32, u32, P]),
         "hrpp_batch_run": (st, [P, P]),
         "hrpp_batch_get_stats": (st, [P, u32, P]),
@@ -140,6 +142,7 @@ hrpp_table_destroy = _lib.hrpp_table_destroy
 hrpp_trace = _lib.hrpp_trace
 hrpp_trace_ex = _lib.hrpp_trace_ex
 hrpp_trace_noalloc = _lib.hrpp_trace_noalloc
+hrpp_l2_set_aside = _lib.hrpp_l2_set_aside
 hrpp_batch_create = _lib.hrpp_batch_create
 hrpp_batch_run = _lib.hrpp_batch_run
 hrpp_batch_get_stats = _lib.hrpp_batch_get_stats
@@ -298,7 +301,8 @@ class Table:
 
 def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, stats: bool = False,
           stream=None, kernel_events=None, block_threads: int = 0, schedule: int = 0, refill_min: int = 0,
-          predicted=None, max_steps: int = 0, verify: int = 0, ray_outcome=None, ray_box_tests=None):
+          predicted=None, max_steps: int = 0, verify: int = 0, ray_outcome=None, ray_box_tests=None,
+          l2_persist: int = 0):
     """Traces rays ([n, 8] float32 torch tensor on the GPU, or a host numpy
     array / torch tensor).  Returns (hits, stats dict or None).
 
@@ -316,7 +320,7 @@ def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, 
             hits = torch.empty(shape, dtype=dtype, device=rays.device)
     st = hrpp_stats() if stats else None
     opts = None
-    if (kernel_events is not None or block_threads or schedule or refill_min or max_steps or verify
+    if (kernel_events is not None or block_threads or schedule or refill_min or max_steps or verify or l2_persist
             or predicted is not None or ray_outcome is not None or ray_box_tests is not None):
         opts = hrpp_trace_opts()
         if predicted is not None:
@@ -329,6 +333,7 @@ def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, 
         opts.refill_min = refill_min
         opts.max_steps = max_steps
         opts.verify = verify
+        opts.l2_persist = l2_persist
         if ray_outcome is not None:
             opts.ray_outcome = _ptr(ray_outcome)
         if ray_box_tests is not None:
@@ -337,6 +342,14 @@ def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, 
                         ctypes.byref(st) if st is not None else None, _stream_handle(stream),
                         ctypes.byref(opts) if opts is not None else None))
     return hits, (st.as_dict() if st is not None else None)
+
+
+def l2_set_aside(nbytes: int) -> int:
+    """Sets the current device's persisting-L2 set-aside (0 releases it);
+    returns the size in force."""
+    got = ctypes.c_size_t(0)
+    check(hrpp_l2_set_aside(int(nbytes), ctypes.byref(got)))
+    return int(got.value)
 
 
 def closest_fields(hits):

@@ -454,6 +454,43 @@ def test_verify_mode_is_validated(H, small_pair):
 
 
 @pytest.mark.parametrize("width_idx", [0, 1])
+def test_l2_persisting_window_changes_nothing(H, small_pair, width_idx):
+    """An L2 access-policy window over the table or the interior nodes, with
+    a persisting set-aside in force, leaves hits, counters and table words
+    exactly as without it; an unknown window kind is rejected; releasing the
+    set-aside leaves none."""
+    import torch
+    s, g = small_pair[width_idx]
+    frames = [torch.from_numpy(s.primary_rays(frame=f)).cuda() for f in (1, 2)]
+    try:
+        granted = H.l2_set_aside(4 << 20)
+    except H.HrppError as err:  # a device without persisting L2: the window is a no-op
+        assert err.status == H.HRPP_ERR_CUDA
+        granted = 0
+    try:
+        ref = H.Table(10, ways=2, precision=6)
+        want = []
+        for r in frames:
+            h, st = H.trace(g, r, H.HRPP_CLOSEST_HIT, ref, stats=True)
+            want.append((h.view(torch.int32).cpu(), st))
+        for kind in (H.HRPP_L2_TABLE, H.HRPP_L2_NODES):
+            t = H.Table(10, ways=2, precision=6)
+            for r, (wh, wst) in zip(frames, want):
+                h, st = H.trace(g, r, H.HRPP_CLOSEST_HIT, t, stats=True, l2_persist=kind)
+                assert torch.equal(h.view(torch.int32).cpu(), wh) and st == wst
+            assert np.array_equal(t.export(), ref.export())
+            hp, _ = H.trace(g, frames[0], H.HRPP_ANY_HIT, None, l2_persist=kind)
+            hq, _ = H.trace(g, frames[0], H.HRPP_ANY_HIT, None)
+            assert torch.equal(hp, hq)
+        with pytest.raises(H.HrppError) as err:
+            H.trace(g, frames[0], H.HRPP_CLOSEST_HIT, ref, l2_persist=3)
+        assert err.value.status == H.HRPP_ERR_INVALID_ARG
+    finally:
+        if granted:
+            assert H.l2_set_aside(0) == 0
+
+
+@pytest.mark.parametrize("width_idx", [0, 1])
 def test_step_budget_reports_traversal_limit(H, small_pair, width_idx):
     """Failure detection without a fault: a per-traversal step budget far
     below what the rays need stops them early.  The kernel's bounded loop sets
