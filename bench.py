@@ -9,9 +9,11 @@ of 708x708 quads plus 64 icospheres, 2,313,248 triangles, 4-wide BVH.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hrpp|reference]
 
 Prints one JSON line (rank 0).  `value` is HRPP Mrays/s over all ranks with
-the rays already resident on the GPU; `e2e` is the same through the C ABI with
-host buffers (upload and download inside the timed region); `plain` gives the
-same library with no table on the same rays.  The reference arm times the CPU
+the rays already resident on the GPU; `e2e` is the same from pinned host
+memory, every step's rays uploaded and hits downloaded inside the timed region
+(a double-buffered frame loop whose copies overlap the traces; `e2e.staged`
+is hrpp_trace on host buffers, one stream); `plain` gives the same library
+with no table on the same rays.  The reference arm times the CPU
 oracle on a bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -169,9 +171,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source."""
+def recorded_traffic(kernel: str, what: str = "traffic"):
+    """A per-launch ncu figure from the committed summary ("traffic": DRAM
+    bytes, "inst": warp instructions), if it was taken on the current kernel
+    source.  Returns (value or None, source hash of the record)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None, None
@@ -179,7 +182,7 @@ def recorded_traffic(kernel: str):
     with open(path) as fh:
         for line in fh:
             parts = line.split()
-            if len(parts) >= 4 and parts[0] == "traffic" and parts[1] == kernel:
+            if len(parts) >= 4 and parts[0] == what and parts[1] == kernel:
                 if parts[3] == src:
                     return float(parts[2]), parts[3]
                 return None, parts[3]
@@ -1025,31 +1028,95 @@ def main():
         return float(bx[oc == H.HRPP_OUTCOME_TRUE_POS].sum() / bx.sum().clamp(min=1))
     g.check()
 
-    # --- end to end through the C ABI with host buffers
+    # --- end to end from pinned host memory, every step's rays uploaded and
+    # its hits downloaded inside the timed region
     e2e = None
     if not args.no_e2e:
         hp = torch.from_numpy(f0["prim_h"]).pin_memory()
         ha = torch.from_numpy(f0["ao_h"]).pin_memory()
+        n_step = hp.shape[0] + ha.shape[0]
+        h2d, d2h = hp.numel() * 4 + ha.numel() * 4, out_c.numel() * 4 + out_a.numel() * 4
+
+        def timed_loop(step):
+            for k in range(args.warmup):
+                step(k)
+            barrier()
+            t0 = time.perf_counter()
+            for k in range(args.steps):
+                step(args.warmup + k)
+            barrier()
+            return max_over_ranks(time.perf_counter() - t0)
+
+        # (1) the plainest use: hrpp_trace on host buffers, which stages the
+        # rays and hits through device memory and returns with the hits in
+        # host memory (one stream, no overlap)
         oc = torch.empty((hp.shape[0], 4), dtype=torch.float32).pin_memory()
         oa = torch.empty((ha.shape[0],), dtype=torch.int32).pin_memory()
 
-        def e2e_step(k):
+        def staged_step(k):
             restore((tab_c, tab_a))
             H.trace(g, hp, H.HRPP_CLOSEST_HIT, tab_c, hits=oc, verify=verify)
             H.trace(g, ha, H.HRPP_ANY_HIT, tab_a, hits=oa)
-            return hp.shape[0] + ha.shape[0], hp.numel() * 4 + ha.numel() * 4, oc.numel() * 4 + oa.numel() * 4
-        for k in range(args.warmup):
-            e2e_step(k)
-        barrier()
-        t0 = time.perf_counter()
-        er, hb, db = 0, 0, 0
-        for k in range(args.steps):
-            a, b, c = e2e_step(args.warmup + k)
-            er, hb, db = er + a, hb + b, db + c
-        barrier()
-        dt = max_over_ranks(time.perf_counter() - t0)
-        e2e = {"value": sum_over_ranks(er) / dt / 1e6, "unit": "Mrays/s", "h2d_bytes_per_step": hb // args.steps,
-               "d2h_bytes_per_step": db // args.steps}
+        dt_staged = timed_loop(staged_step)
+
+        # (2) a frame loop as a renderer would run it: hrpp_trace on device
+        # buffers, double-buffered, with uploads on one copy stream and
+        # downloads on another, so that copies overlap the traces (the AO
+        # upload under the primary trace, the next step's uploads under this
+        # step's AO trace, the downloads under the next step)
+        comp = torch.cuda.current_stream()
+        up, down = torch.cuda.Stream(), torch.cuda.Stream()
+        dp = [torch.empty_like(f0["prim"]) for _ in range(2)]
+        da = [torch.empty_like(f0["ao"]) for _ in range(2)]
+        dhc = [torch.empty_like(out_c) for _ in range(2)]
+        dha = [torch.empty_like(out_a) for _ in range(2)]
+        hoc = [torch.empty(tuple(out_c.shape), dtype=torch.float32).pin_memory() for _ in range(2)]
+        hoa = [torch.empty(tuple(out_a.shape), dtype=torch.int32).pin_memory() for _ in range(2)]
+        consumed, downloaded = [None, None], [None, None]
+
+        def event(stream):
+            e = torch.cuda.Event()
+            e.record(stream)
+            return e
+
+        def pipe_step(k):
+            b = k % 2
+            with torch.cuda.stream(up):
+                if consumed[b] is not None:      # step k-2's traces are done with these buffers
+                    up.wait_event(consumed[b])
+                dp[b].copy_(hp, non_blocking=True)
+                up_p = event(up)
+                da[b].copy_(ha, non_blocking=True)
+                up_a = event(up)
+            if downloaded[b] is not None:        # step k-2's hits have left these buffers
+                comp.wait_event(downloaded[b])
+            restore((tab_c, tab_a))
+            comp.wait_event(up_p)
+            H.trace(g, dp[b], H.HRPP_CLOSEST_HIT, tab_c, hits=dhc[b], verify=verify)
+            done_c = event(comp)
+            comp.wait_event(up_a)
+            H.trace(g, da[b], H.HRPP_ANY_HIT, tab_a, hits=dha[b])
+            done_a = event(comp)
+            consumed[b] = done_a
+            with torch.cuda.stream(down):
+                down.wait_event(done_c)
+                hoc[b].copy_(dhc[b], non_blocking=True)
+                down.wait_event(done_a)
+                hoa[b].copy_(dha[b], non_blocking=True)
+                downloaded[b] = event(down)
+        dt_pipe = timed_loop(pipe_step)
+        last = (args.warmup + args.steps - 1) % 2
+        # closest hits bit for bit against plain traversal; any-hit rays by
+        # whether they are occluded (any valid hit may be reported)
+        same = bool(torch.equal(hoc[last].view(torch.int32), out_plain.cpu().view(torch.int32))
+                    and torch.equal(hoa[last] == -1, out_a.cpu() == -1))
+        e2e = {"value": sum_over_ranks(n_step * args.steps) / dt_pipe / 1e6, "unit": "Mrays/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "how": "hrpp_trace on double-buffered device buffers; pinned-host uploads and downloads on two copy "
+                      "streams, overlapping the traces",
+               "hits_checked": same,
+               "staged": {"value": sum_over_ranks(n_step * args.steps) / dt_staged / 1e6, "unit": "Mrays/s",
+                          "how": "hrpp_trace on host buffers: staged through device memory, one stream, no overlap"}}
 
     if rank != 0:
         return 0
@@ -1063,6 +1130,18 @@ def main():
     achieved = bytes_launch / (kt[dom] * 1e-3) / 1e9
     kname = f"k_trace<{width}, {'closest' if dom == 'closest' else 'any'}, hrpp>"
     traffic, traffic_src = recorded_traffic(f"bvh{width}_{dom}")
+    # issue slots: the launch's warp instructions (ncu, same kernel source)
+    # against one warp instruction per cycle per SM sub-partition
+    inst, _ = recorded_traffic(f"bvh{width}_{dom}", "inst")
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_hz = (clk.get("sm_mhz") or 0) * 1e6
+    issue = None
+    if inst is not None and sm_hz > 0:
+        peak_issue = n_sm * 4 * sm_hz
+        issue = {"warp_inst_per_launch": inst, "achieved": inst / (kt[dom] * 1e-3), "peak": peak_issue,
+                 "unit": "warp inst/s", "frac": inst / (kt[dom] * 1e-3) / peak_issue,
+                 "peak_basis": f"{n_sm} SMs x 4 sub-partitions x 1 warp instruction per cycle at the sampled "
+                               f"{sm_hz / 1e6:.0f} MHz"}
 
     def skipped(h, p, limit):
         return {"prediction_ratio": h["true_pos"] / max(1, h["rays"]),
@@ -1101,7 +1180,8 @@ def main():
                      "algorithmic_bytes_per_launch": bytes_launch,
                      "node_tests_per_s": {"box": (st_dom["box_tests"] + st_dom["pred_box_tests"]) / (kt[dom] * 1e-3),
                                           "triangle": (st_dom["tri_tests"] + st_dom["pred_tri_tests"]) / (kt[dom] * 1e-3)},
-                     "traffic_source_hash": traffic_src, "kernel_source_hash": kernel_source_hash()},
+                     "traffic_source_hash": traffic_src, "kernel_source_hash": kernel_source_hash(),
+                     "issue": issue},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
