@@ -90,6 +90,9 @@ cudaError_t launch_output_layer(const void *h2, const void *w3, const umma::Soft
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr != cudaSuccess) return attr;
     if (g.npad <= 0 || g.npad % umma::BM != 0 || ((uintptr_t)h2 & 15u) || ((uintptr_t)w3 & 15u)) return cudaErrorInvalidValue;
+    // the epilogue reads the bias and writes dZ rows 16 bytes at a time
+    if (!g.bias || ((uintptr_t)g.bias & 15u) || (!PREDICT && (!g.dz || !g.dzt || ((uintptr_t)g.dz & 15u))))
+        return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     cudaError_t e = make_map(&ma, h2, (uint64_t)g.npad, umma::SX_K, umma::BM);
     if (e == cudaSuccess) e = make_map(&mb, w3, umma::SX_CLASSES, umma::SX_K, umma::SX_BN);

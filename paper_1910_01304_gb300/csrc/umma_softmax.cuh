@@ -40,13 +40,11 @@ constexpr uint32_t SX_B_BYTES = SX_BN * BK * 2; // 32 KB per stage
 constexpr int SX_EPI_WARPS = 16;                // 4 row groups x 4 column slices
 constexpr int SX_SLICE = SX_BN / 4;             // columns of a tile per epilogue warp
 constexpr int SX_THREADS = (SX_EPI_WARPS + 2) * 32;
-constexpr int SX_PITCH = 24;                    // bf16 per staged row: 16 + 8 (16-byte aligned, bank-staggered)
-constexpr uint32_t SX_STAGE_BYTES = SX_EPI_WARPS * 32 * SX_PITCH * 2;
 
 template <int NST = SX_NST>
 constexpr size_t softmax_smem_bytes()
 {
-    return (size_t)SX_A_BYTES + (size_t)NST * SX_B_BYTES + SX_STAGE_BYTES + 1024;
+    return (size_t)SX_A_BYTES + (size_t)NST * SX_B_BYTES + 1024;
 }
 
 struct SoftmaxArgs {
@@ -70,6 +68,29 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// three-input maximum (one instruction); equals fmaxf twice for non-NaN inputs
+__device__ __forceinline__ float max3(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// v[j] += bias[j] for 32 columns; bias is 16-byte aligned and the same for
+// every lane (a broadcast load)
+__device__ __forceinline__ void add_bias32(float (&v)[32], const float *bias)
+{
+    const float4 *b4 = reinterpret_cast<const float4 *>(bias);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float4 b = __ldg(b4 + j);
+        v[4 * j] += b.x;
+        v[4 * j + 1] += b.y;
+        v[4 * j + 2] += b.z;
+        v[4 * j + 3] += b.w;
+    }
+}
+
 // NST: stages of the W3 ring (a template so that every file that includes
 // this header shares one instance).  PREDICT: one pass that keeps each row's
 // first maximum instead of the two training passes.
@@ -86,7 +107,6 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *a_s = smem;
     unsigned char *b_s = smem + SX_A_BYTES;
-    __nv_bfloat16 *stage = reinterpret_cast<__nv_bfloat16 *>(b_s + NST * SX_B_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM;
     constexpr int kTiles = PREDICT ? SX_TILES : 2 * SX_TILES;
@@ -181,7 +201,6 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
         float m = -__int_as_float(0x7F800000), ssum = 0.0f, inv = 0.0f;
         int best = 0;  // PREDICT: this slice's first maximum
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        __nv_bfloat16 *st = stage + warp * 32 * SX_PITCH;
         // pass 1: running maximum and sum of exponentials over this slice
         for (int t = 0; t < SX_TILES; ++t) {
             const int b = t & 1;
@@ -196,31 +215,34 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
             const uint32_t taddr = tmem + lane_base + (uint32_t)(b * SX_BN + cs * SX_SLICE);
             const int col0 = t * SX_BN + cs * SX_SLICE;
 #pragma unroll 1
-            for (int c0 = 0; c0 < SX_SLICE; c0 += 16) {
-                float v[16];
-                tmem_ld16(taddr + (uint32_t)c0, v);
+            for (int c0 = 0; c0 < SX_SLICE; c0 += 32) {
+                float v[32];
+                tmem_ld32(taddr + (uint32_t)c0, v);
+                add_bias32(v, g.bias + col0 + c0);
                 if (PREDICT) {
                     // first maximum: columns arrive in ascending order
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float z = v[j] + g.bias[col0 + c0 + j];
-                        if (z > m) {
-                            m = z;
+                    for (int j = 0; j < 32; ++j) {
+                        if (v[j] > m) {
+                            m = v[j];
                             best = col0 + c0 + j;
                         }
                     }
                     continue;
                 }
+                // the row's label logit, when its column is in this chunk
+                const uint32_t off = (uint32_t)(lab - (col0 + c0));
+                if (off < 32u) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if ((uint32_t)j == off) zl[r] = v[j];
+                }
                 float cm = m;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    v[j] += g.bias[col0 + c0 + j];
-                    cm = fmaxf(cm, v[j]);
-                    if (col0 + c0 + j == lab) zl[r] = v[j];
-                }
+                for (int j = 0; j < 32; j += 2) cm = max3(cm, v[j], v[j + 1]);
                 float acc = 0.0f;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) acc += __expf(v[j] - cm);
+                for (int j = 0; j < 32; ++j) acc += __expf(v[j] - cm);
                 ssum = ssum * __expf(m - cm) + acc;
                 m = cm;
             }
@@ -276,31 +298,35 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
             const uint32_t taddr = tmem + lane_base + (uint32_t)(b * SX_BN + cs * SX_SLICE);
             const int col0 = (t - SX_TILES) * SX_BN + cs * SX_SLICE;
 #pragma unroll 1
-            for (int c0 = 0; c0 < SX_SLICE; c0 += 16) {
-                float v[16];
-                tmem_ld16(taddr + (uint32_t)c0, v);
-                __align__(16) __nv_bfloat16 qv[16];
+            for (int c0 = 0; c0 < SX_SLICE; c0 += 32) {
+                float v[32];
+                tmem_ld32(taddr + (uint32_t)c0, v);
+                add_bias32(v, g.bias + col0 + c0);
+                // softmax (zero for rows without a target: inv = 0), minus
+                // the one-hot of the label when its column is in this chunk
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = __expf(v[j] - m) * inv;
+                const uint32_t off = (uint32_t)(lab - (col0 + c0));
+                if (off < 32u) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if ((uint32_t)j == off) v[j] -= 1.0f;
+                }
+                __align__(16) __nv_bfloat162 q2[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) q2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                // dZ: the lane's row, 64 contiguous bytes
+                uint4 *dst = reinterpret_cast<uint4 *>(g.dz + (size_t)row * SX_CLASSES + col0 + c0);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) dst[k] = reinterpret_cast<const uint4 *>(q2)[k];
+                // dZ^T: column j of the chunk is row col0 + c0 + j; the warp's
+                // 32 lanes write 64 contiguous bytes of it
+                __nv_bfloat16 *dt = g.dzt + (size_t)(col0 + c0) * g.npad + row;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int col = col0 + c0 + j;
-                    const float p =
-                        lab >= 0 ? __expf(v[j] + g.bias[col] - m) * inv - (col == lab ? 1.0f : 0.0f) : 0.0f;
-                    qv[j] = __float2bfloat16_rn(p);
-                    g.dzt[(size_t)col * g.npad + row] = qv[j];
+                    dt[(size_t)(2 * j) * g.npad] = __low2bfloat16(q2[j]);
+                    dt[(size_t)(2 * j + 1) * g.npad] = __high2bfloat16(q2[j]);
                 }
-                uint4 *dst = reinterpret_cast<uint4 *>(st + lane * SX_PITCH);
-                dst[0] = *reinterpret_cast<const uint4 *>(qv);
-                dst[1] = *reinterpret_cast<const uint4 *>(qv + 8);
-                __syncwarp();
-                // the warp's 32 rows x 16 columns: 2 lanes per 32-byte row segment
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const int idx = lane + 32 * k, rr = idx >> 1, hh = idx & 1;
-                    const uint4 val = *reinterpret_cast<const uint4 *>(st + rr * SX_PITCH + hh * 8);
-                    *reinterpret_cast<uint4 *>(g.dz + (size_t)(m0 + q * 32 + rr) * SX_CLASSES + col0 + c0 + hh * 8) =
-                        val;
-                }
-                __syncwarp();
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
