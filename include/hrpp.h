@@ -457,6 +457,16 @@ void hrpp_proposal_destroy(hrpp_proposal *p);
  * must be multiples of 128 and k of 64 (INVALID_ARG otherwise).  Waits for
  * the result. */
 hrpp_status hrpp_gemm_bf16(const void *a, const void *b, float *c, int m, int n, int k, void *stream);
+/* hrpp_gemm_bf16 with operand layouts (layout 0 is hrpp_gemm_bf16):
+ *   HRPP_GEMM_A_MN_MAJOR  A is stored [k, m] (m contiguous), i.e. the
+ *                         product uses its transpose without copying it
+ *   HRPP_GEMM_B_MN_MAJOR  B is stored [k, n] (n contiguous)
+ * Other bits: INVALID_ARG.  The learned proposal's weight gradients
+ * (dW = dZ^T H over the rows of a minibatch) take both operands MN-major. */
+#define HRPP_GEMM_A_MN_MAJOR 1
+#define HRPP_GEMM_B_MN_MAJOR 2
+hrpp_status hrpp_gemm_bf16_ex(const void *a, const void *b, float *c, int m, int n, int k, int layout,
+                              void *stream);
 
 const char *hrpp_last_error(void);
 const char *hrpp_status_string(hrpp_status status);

@@ -52,29 +52,48 @@ cudaError_t make_map(CUtensorMap *map, const void *ptr, uint64_t rows, uint64_t 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int BN, int EPI, int NST>
+// MN-major bf16 matrix stored [k, mn] (mn contiguous) as a TMA map with
+// 64 x 64 boxes (64 mn elements = one 128-byte swizzle row, 64 K rows).
+cudaError_t make_map_mn(CUtensorMap *map, const void *ptr, uint64_t k, uint64_t mn)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 encode;
+    cudaError_t e = encoder(&encode);
+    if (e != cudaSuccess) return e;
+    cuuint64_t dims[2] = {mn, k};
+    cuuint64_t strides[1] = {mn * 2};
+    cuuint32_t box[2] = {64u, (cuuint32_t)umma::BK};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int BN, int EPI, int NST, bool AMN, bool BMN>
 cudaError_t launch_stages(const void *a, const void *b, const umma::GemmArgs &g, int splits, cudaStream_t s)
 {
     const size_t smem = umma::gemm_smem_bytes<BN, NST>();
     // once per template instance (thread-safe static initialisation)
-    static const cudaError_t attr =
-        cudaFuncSetAttribute(umma::k_gemm<BN, EPI, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static const cudaError_t attr = cudaFuncSetAttribute(umma::k_gemm<BN, EPI, NST, AMN, BMN>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr != cudaSuccess) return attr;
     CUtensorMap ma, mb;
-    cudaError_t e = make_map(&ma, a, (uint64_t)g.M, (uint64_t)g.K, umma::BM);
-    if (e == cudaSuccess) e = make_map(&mb, b, (uint64_t)g.N, (uint64_t)g.K, BN);
+    cudaError_t e = AMN ? make_map_mn(&ma, a, (uint64_t)g.K, (uint64_t)g.M)
+                        : make_map(&ma, a, (uint64_t)g.M, (uint64_t)g.K, umma::BM);
+    if (e == cudaSuccess)
+        e = BMN ? make_map_mn(&mb, b, (uint64_t)g.K, (uint64_t)g.N) : make_map(&mb, b, (uint64_t)g.N, (uint64_t)g.K, BN);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)(g.N / BN), (unsigned)(g.M / umma::BM), (unsigned)splits);
-    umma::k_gemm<BN, EPI, NST><<<grid, 128, smem, s>>>(ma, mb, g);
+    umma::k_gemm<BN, EPI, NST, AMN, BMN><<<grid, 128, smem, s>>>(ma, mb, g);
     return cudaGetLastError();
 }
 
 // short K ranges (at most 4 K blocks per CTA) take the 2-stage variant
-template <int BN, int EPI>
+template <int BN, int EPI, bool AMN = false, bool BMN = false>
 cudaError_t launch(const void *a, const void *b, const umma::GemmArgs &g, int splits, cudaStream_t s)
 {
-    if (g.k_blocks_per_split <= 4) return launch_stages<BN, EPI, 2>(a, b, g, splits, s);
-    return launch_stages<BN, EPI, umma::STAGES>(a, b, g, splits, s);
+    if (g.k_blocks_per_split <= 4) return launch_stages<BN, EPI, 2, AMN, BMN>(a, b, g, splits, s);
+    return launch_stages<BN, EPI, umma::STAGES, AMN, BMN>(a, b, g, splits, s);
 }
 
 }  // namespace
@@ -91,7 +110,7 @@ cudaError_t launch_output_layer(const void *h2, const void *w3, const umma::Soft
     if (attr != cudaSuccess) return attr;
     if (g.npad <= 0 || g.npad % umma::BM != 0 || ((uintptr_t)h2 & 15u) || ((uintptr_t)w3 & 15u)) return cudaErrorInvalidValue;
     // the epilogue reads the bias and writes dZ rows 16 bytes at a time
-    if (!g.bias || ((uintptr_t)g.bias & 15u) || (!PREDICT && (!g.dz || !g.dzt || ((uintptr_t)g.dz & 15u))))
+    if (!g.bias || ((uintptr_t)g.bias & 15u) || (!PREDICT && (!g.dz || ((uintptr_t)g.dz & 15u))))
         return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     cudaError_t e = make_map(&ma, h2, (uint64_t)g.npad, umma::SX_K, umma::BM);
@@ -119,7 +138,7 @@ bool gemm_shape_ok(int m, int n, int k, int bn)
 }
 
 cudaError_t gemm_bf16(const void *a, const void *b, int epi, int bn, const umma::GemmArgs &g0, int splits,
-                      cudaStream_t s)
+                      cudaStream_t s, int layout)
 {
     umma::GemmArgs g = g0;
     const int kb = g.K / umma::BK;
@@ -128,6 +147,23 @@ cudaError_t gemm_bf16(const void *a, const void *b, int epi, int bn, const umma:
     g.k_blocks_per_split = (kb + splits - 1) / splits;
     splits = (kb + g.k_blocks_per_split - 1) / g.k_blocks_per_split;
     if (((uintptr_t)a & 15u) || ((uintptr_t)b & 15u)) return cudaErrorInvalidValue;
+    if (layout != 0) {
+        // MN-major operands: the weight gradients of the training step
+        // (split-K atomics) and the utility entry point (plain fp32)
+#define HRPP_GEMM_MN(BN_, EPI_, L_)                                                                   \
+    if (bn == BN_ && epi == EPI_ && layout == L_)                                                     \
+        return launch<BN_, EPI_, (L_ & GEMM_A_MN) != 0, (L_ & GEMM_B_MN) != 0>(a, b, g, splits, s);
+        HRPP_GEMM_MN(128, umma::EPI_F32, 1)
+        HRPP_GEMM_MN(128, umma::EPI_F32, 2)
+        HRPP_GEMM_MN(128, umma::EPI_F32, 3)
+        HRPP_GEMM_MN(256, umma::EPI_F32, 1)
+        HRPP_GEMM_MN(256, umma::EPI_F32, 2)
+        HRPP_GEMM_MN(256, umma::EPI_F32, 3)
+        HRPP_GEMM_MN(128, umma::EPI_F32_ATOMIC, 3)
+        HRPP_GEMM_MN(256, umma::EPI_F32_ATOMIC, 3)
+#undef HRPP_GEMM_MN
+        return cudaErrorInvalidValue;
+    }
 #define HRPP_GEMM_CASE(BN_, EPI_) \
     if (bn == BN_ && epi == EPI_) return launch<BN_, EPI_>(a, b, g, splits, s);
     HRPP_GEMM_CASE(128, umma::EPI_F32)
@@ -146,8 +182,16 @@ cudaError_t gemm_bf16(const void *a, const void *b, int epi, int bn, const umma:
 
 extern "C" hrpp_status hrpp_gemm_bf16(const void *a, const void *b, float *c, int m, int n, int k, void *stream)
 {
+    return hrpp_gemm_bf16_ex(a, b, c, m, n, k, 0, stream);
+}
+
+extern "C" hrpp_status hrpp_gemm_bf16_ex(const void *a, const void *b, float *c, int m, int n, int k, int layout,
+                                         void *stream)
+{
     char msg[160];
     if (!a || !b || !c) return hrpp::report(HRPP_ERR_INVALID_ARG, "NULL matrix");
+    if (layout < 0 || layout > (HRPP_GEMM_A_MN_MAJOR | HRPP_GEMM_B_MN_MAJOR))
+        return hrpp::report(HRPP_ERR_INVALID_ARG, "unknown layout flags");
     const int bn = (n % 256 == 0) ? 256 : 128;
     if (!hrpp::gemm_shape_ok(m, n, k, bn)) {
         snprintf(msg, sizeof msg, "shape %d x %d x %d: M must be a multiple of 128, N of 128, K of 64", m, n, k);
@@ -164,7 +208,7 @@ extern "C" hrpp_status hrpp_gemm_bf16(const void *a, const void *b, float *c, in
         g.c32 = c;
         g.m_valid = m;
         g.error = err;
-        e = hrpp::gemm_bf16(a, b, hrpp::umma::EPI_F32, bn, g, 1, (cudaStream_t)stream);
+        e = hrpp::gemm_bf16(a, b, hrpp::umma::EPI_F32, bn, g, 1, (cudaStream_t)stream, layout);
     }
     unsigned int flag = 0;
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);

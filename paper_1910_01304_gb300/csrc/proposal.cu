@@ -3,16 +3,18 @@
 // ray the root of a BVH treelet to traverse first.
 //
 // Training step on a minibatch of rows padded to a multiple of 128:
-//   X  = features(rays)                      bf16 [B, 128] and [128, B]
-//   H1 = relu(X W1^T + b1), H2 = relu(H1 W2^T + b2)   bf16, both layouts
-//   Z  = H2 W3^T + b3                        fp32 [B, 4096]
-//   dZ = softmax(Z) - onehot(label)          bf16 [B, 4096] and [4096, B]
+//   X  = features(rays)                      bf16 [B, 128]
+//   H1 = relu(X W1^T + b1), H2 = relu(H1 W2^T + b2)   bf16 [B, 256]
+//   Z  = H2 W3^T + b3                        fp32, never stored
+//   dZ = softmax(Z) - onehot(label)          bf16 [B, 4096]
 //   dW3 = dZ^T H2, dZ2 = (dZ W3) * (H2 > 0), dW2 = dZ2^T H1,
 //   dZ1 = (dZ2 W2) * (H1 > 0), dW1 = dZ1^T X, db = column sums
 //   Adam on fp32 master weights, scaled by 1 / (labelled rows); bf16 copies
 //   refreshed in the [out, in] and [in, out] layouts the GEMMs read.
-// Every GEMM is C = A B^T with K-major operands, so activations and
-// gradients are written in both layouts by the producing epilogue.
+// Every GEMM is C = A B^T.  The forward and dZ GEMMs read K-major operands;
+// the weight gradients reduce over the rows of the minibatch and read the
+// row-major activations and gradients as MN-major operands, so nothing is
+// stored transposed.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -79,15 +81,13 @@ __device__ __forceinline__ uint32_t quantise16(float u)
 
 // Features of 128 rows per block.  Each thread builds its row's 128 bf16
 // inputs in shared memory; the block then writes the tile row-major (one
-// contiguous 32 KB span of X) and, when XT is given, column-major (256
-// contiguous bytes per feature), both with 16-byte stores.
+// contiguous 32 KB span of X) with 16-byte stores.
 constexpr int kFeatRows = 128;
 constexpr int kFeatPitch = kIn + 8;  // bf16 elements per shared row (16-byte aligned, staggers banks)
 
 __global__ void __launch_bounds__(kFeatRows) k_featurize(const float4 *rays, uint32_t n, uint32_t npad, float lox,
                                                          float loy, float loz, float sx, float sy, float sz,
-                                                         const __nv_bfloat16 *sin_t, __nv_bfloat16 *X,
-                                                         __nv_bfloat16 *XT)
+                                                         const __nv_bfloat16 *sin_t, __nv_bfloat16 *X)
 {
     __shared__ __align__(16) __nv_bfloat16 tile[kFeatRows * kFeatPitch];
     const uint32_t t = threadIdx.x, r0 = blockIdx.x * kFeatRows, r = r0 + t;
@@ -139,32 +139,51 @@ __global__ void __launch_bounds__(kFeatRows) k_featurize(const float4 *rays, uin
         const uint32_t rr = k / (kIn / 8), cc = (k % (kIn / 8)) * 8;
         dst[k] = *reinterpret_cast<const uint4 *>(tile + rr * kFeatPitch + cc);
     }
-    if (!XT) return;
-    // column-major: feature c of rows r0.. is contiguous in XT
-    for (uint32_t k = t; k < kIn * (rows_here / 8); k += kFeatRows) {
-        const uint32_t c = k / (rows_here / 8), rr = (k % (rows_here / 8)) * 8;
-        __align__(16) __nv_bfloat16 v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = tile[(rr + j) * kFeatPitch + c];
-        *reinterpret_cast<uint4 *>(XT + (size_t)c * npad + r0 + rr) = *reinterpret_cast<const uint4 *>(v);
-    }
 }
 
-// out[i] = sum over the row i of a bf16 [rows, cols] matrix (256 threads per row)
-__global__ void __launch_bounds__(256) k_rowsum(const __nv_bfloat16 *a, uint32_t cols, float *out)
+// out[c] += sum over rows of a bf16 [rows, cols] row-major matrix (the bias
+// gradients; cols a multiple of 256).  A block of 32 x 8 threads covers 256
+// columns and kColsumRows rows: thread (x, y) sums the 8 adjacent columns of
+// group x (one 16-byte load per row) over rows y, y + 8, ..., so each warp
+// reads 512 contiguous bytes per row; the 8 partial sums of a column meet in
+// shared memory and the block adds them with one atomic per column.
+constexpr uint32_t kColsumRows = 256;
+
+__global__ void __launch_bounds__(256) k_colsum(const __nv_bfloat16 *a, uint32_t rows, uint32_t cols, float *out)
 {
-    __shared__ float red[8];
-    const __nv_bfloat16 *row = a + (size_t)blockIdx.x * cols;
-    float s = 0.0f;
-    for (uint32_t c = threadIdx.x; c < cols; c += 256) s += __bfloat162float(row[c]);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float tot = 0.0f;
-        for (int w = 0; w < 8; ++w) tot += red[w];
-        out[blockIdx.x] = tot;
+    __shared__ float part[8][32 * 8 + 4];
+    const uint32_t x = threadIdx.x, y = threadIdx.y;
+    const uint32_t c = 8u * (blockIdx.x * 32u + x);
+    const uint32_t r0 = blockIdx.y * kColsumRows;
+    const uint32_t r1 = r0 + kColsumRows < rows ? r0 + kColsumRows : rows;
+    float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    const __nv_bfloat16 *p = a + (size_t)(r0 + y) * cols + c;
+#pragma unroll 8
+    for (uint32_t r = r0 + y; r < r1; r += 8u, p += 8ull * cols) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 f = __bfloat1622float2(h[j]);
+            acc[2 * j] += f.x;
+            acc[2 * j + 1] += f.y;
+        }
     }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) part[y][8 * x + j] = acc[j];
+    __syncthreads();
+    // thread (x, y) now adds column 8x' + j' of the block for one (x', j')
+    const uint32_t t = y * 32u + x;  // 0..255: one column of the block each
+    float sum = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += part[k][t];
+    atomicAdd(out + 8u * blockIdx.x * 32u + t, sum);
+}
+
+void colsum(const __nv_bfloat16 *a, uint32_t rows, uint32_t cols, float *out, cudaStream_t s)
+{
+    const dim3 grid(cols / 256u, (rows + kColsumRows - 1) / kColsumRows);
+    k_colsum<<<grid, dim3(32, 8), 0, s>>>(a, rows, cols, out);
 }
 
 // Adam on every parameter in one launch (masters laid out W1 | b1 | W2 | b2 |
@@ -238,7 +257,7 @@ struct hrpp_proposal {
     float *master, *grad, *m, *v;
     __nv_bfloat16 *w1h, *w2h, *w3h, *w2t, *w3t;
     int step;
-    __nv_bfloat16 *X, *XT, *H1, *H1T, *H2, *H2T, *dZ3, *dZ3T, *dZ2, *dZ2T, *dZ1T;
+    __nv_bfloat16 *X, *H1, *H2, *dZ3, *dZ2, *dZ1;
     float *loss_sum;
     unsigned int *count, *err;
     float *call_loss;           // loss and labelled rows summed over one train call
@@ -254,8 +273,7 @@ void proposal_free(hrpp_proposal *p)
 {
     if (!p) return;
     void *ptrs[] = {p->sin_t, p->class_node, p->prim_class, p->master, p->grad, p->m, p->v, p->w1h, p->w2h,
-                    p->w3h, p->w2t, p->w3t, p->X, p->XT, p->H1, p->H1T, p->H2, p->H2T, p->dZ3, p->dZ3T,
-                    p->dZ2, p->dZ2T, p->dZ1T, p->loss_sum, p->count, p->err, p->call_loss, p->call_count,
+                    p->w3h, p->w2t, p->w3t, p->X, p->H1, p->H2, p->dZ3, p->dZ2, p->dZ1, p->loss_sum, p->count, p->err, p->call_loss, p->call_count,
                     p->lab, p->Xi, p->H1i, p->H2i};
     for (void *q : ptrs) cudaFree(q);
     delete p;
@@ -327,17 +345,15 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     __nv_bfloat16 *X = argmax ? p->Xi : p->X, *H1 = argmax ? p->H1i : p->H1, *H2 = argmax ? p->H2i : p->H2;
     k_featurize<<<npad / kFeatRows, kFeatRows, 0, s>>>(reinterpret_cast<const float4 *>(rays), n, npad, p->lo[0],
                                                     p->lo[1], p->lo[2], p->scale[0], p->scale[1], p->scale[2],
-                                                    p->sin_t, X, train ? p->XT : nullptr);
+                                                    p->sin_t, X);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     umma::GemmArgs g = args((int)npad, kHid, kIn, p);
     g.bias = p->master + ob1;
     g.c16 = H1;
-    g.c16t = train ? p->H1T : nullptr;
     if ((e = gemm_bf16(X, p->w1h, umma::EPI_BIAS_RELU, tile_n((int)npad, kHid), g, 1, s)) != cudaSuccess) return e;
     g = args((int)npad, kHid, kHid, p);
     g.bias = p->master + ob2;
     g.c16 = H2;
-    g.c16t = train ? p->H2T : nullptr;
     if ((e = gemm_bf16(H1, p->w2h, umma::EPI_BIAS_RELU, tile_n((int)npad, kHid), g, 1, s)) != cudaSuccess) return e;
     if (argmax) {
         // output layer and first argmax in one tensor-core pass
@@ -365,43 +381,43 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     sx.n = (int)n;
     sx.npad = (int)npad;
     sx.dz = p->dZ3;
-    sx.dzt = p->dZ3T;
     sx.loss_sum = p->loss_sum;
     sx.count = p->count;
     sx.error = p->err;
     if ((e = softmax_xent(H2, p->w3h, sx, s)) != cudaSuccess) return e;
+    // the weight gradients reduce over rows: both operands MN-major
+    constexpr int kMN = GEMM_A_MN | GEMM_B_MN;
     // dW3 = dZ3^T H2
     g = args(kCls, kHid, (int)npad, p);
     g.c32 = p->grad + oW3;
-    if ((e = gemm_bf16(p->dZ3T, p->H2T, umma::EPI_F32_ATOMIC, 256, g, splits_for(kCls / 128, (int)npad), s)) !=
+    if ((e = gemm_bf16(p->dZ3, p->H2, umma::EPI_F32_ATOMIC, 256, g, splits_for(kCls / 128, (int)npad), s, kMN)) !=
         cudaSuccess)
         return e;
     // dZ2 = (dZ3 W3) * (H2 > 0)
     g = args((int)npad, kHid, kCls, p);
     g.act = p->H2;
     g.c16 = p->dZ2;
-    g.c16t = p->dZ2T;
     if ((e = gemm_bf16(p->dZ3, p->w3t, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid), g, 1, s)) != cudaSuccess) return e;
     // dW2 = dZ2^T H1
     g = args(kHid, kHid, (int)npad, p);
     g.c32 = p->grad + oW2;
-    if ((e = gemm_bf16(p->dZ2T, p->H1T, umma::EPI_F32_ATOMIC, 256, g, splits_for(kHid / 128, (int)npad), s)) !=
+    if ((e = gemm_bf16(p->dZ2, p->H1, umma::EPI_F32_ATOMIC, 256, g, splits_for(kHid / 128, (int)npad), s, kMN)) !=
         cudaSuccess)
         return e;
-    // dZ1 = (dZ2 W2) * (H1 > 0), transposed only
+    // dZ1 = (dZ2 W2) * (H1 > 0)
     g = args((int)npad, kHid, kHid, p);
     g.act = p->H1;
-    g.c16t = p->dZ1T;
+    g.c16 = p->dZ1;
     if ((e = gemm_bf16(p->dZ2, p->w2t, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid), g, 1, s)) != cudaSuccess) return e;
     // dW1 = dZ1^T X
     g = args(kHid, kIn, (int)npad, p);
     g.c32 = p->grad + oW1;
-    if ((e = gemm_bf16(p->dZ1T, p->XT, umma::EPI_F32_ATOMIC, 128, g, splits_for(kHid / 128, (int)npad), s)) !=
+    if ((e = gemm_bf16(p->dZ1, p->X, umma::EPI_F32_ATOMIC, 128, g, splits_for(kHid / 128, (int)npad), s, kMN)) !=
         cudaSuccess)
         return e;
-    k_rowsum<<<kCls, 256, 0, s>>>(p->dZ3T, npad, p->grad + ob3);
-    k_rowsum<<<kHid, 256, 0, s>>>(p->dZ2T, npad, p->grad + ob2);
-    k_rowsum<<<kHid, 256, 0, s>>>(p->dZ1T, npad, p->grad + ob1);
+    colsum(p->dZ3, npad, kCls, p->grad + ob3, s);
+    colsum(p->dZ2, npad, kHid, p->grad + ob2, s);
+    colsum(p->dZ1, npad, kHid, p->grad + ob1, s);
     return cudaGetLastError();
 }
 
@@ -536,16 +552,11 @@ hrpp_status hrpp_proposal_create(const hrpp_scene *sc, const hrpp_bvh_node *node
     alloc(&p->w2t, (size_t)kHid * kHid * 2);
     alloc(&p->w3t, (size_t)kCls * kHid * 2);
     alloc(&p->X, rows * kIn * 2);
-    alloc(&p->XT, rows * kIn * 2);
     alloc(&p->H1, rows * kHid * 2);
-    alloc(&p->H1T, rows * kHid * 2);
     alloc(&p->H2, rows * kHid * 2);
-    alloc(&p->H2T, rows * kHid * 2);
     alloc(&p->dZ3, rows * kCls * 2);
-    alloc(&p->dZ3T, rows * kCls * 2);
     alloc(&p->dZ2, rows * kHid * 2);
-    alloc(&p->dZ2T, rows * kHid * 2);
-    alloc(&p->dZ1T, rows * kHid * 2);
+    alloc(&p->dZ1, rows * kHid * 2);
     alloc(&p->loss_sum, 4);
     alloc(&p->count, 4);
     alloc(&p->err, 4);
@@ -578,7 +589,7 @@ hrpp_status hrpp_proposal_features(hrpp_proposal *p, const hrpp_ray *rays, uint3
     if (n == 0) return HRPP_OK;
     k_featurize<<<(n + kFeatRows - 1) / kFeatRows, kFeatRows, 0, (cudaStream_t)stream>>>(
         reinterpret_cast<const float4 *>(rays), n, n, p->lo[0], p->lo[1], p->lo[2], p->scale[0], p->scale[1],
-        p->scale[2], p->sin_t, static_cast<__nv_bfloat16 *>(out_bf16), nullptr);
+        p->scale[2], p->sin_t, static_cast<__nv_bfloat16 *>(out_bf16));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return pfail(HRPP_ERR_CUDA, "features: %s", cudaGetErrorString(e));
     return HRPP_OK;

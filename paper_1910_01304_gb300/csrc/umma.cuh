@@ -1,13 +1,17 @@
 // Tensor-core GEMM for sm_103a: tcgen05.mma with the accumulator in tensor
 // memory (TMEM), operands staged in shared memory by TMA.
 //
-//   C[M, N] = A[M, K] * B[N, K]^T        A, B: bf16, K-major (rows of K)
-//                                         accumulation: fp32 in TMEM
+//   C[M, N] = A[M, K] * B[N, K]^T        A, B: bf16; accumulation fp32 in TMEM
+//
+// Each operand is K-major (stored [M or N][K], rows of K) or MN-major (stored
+// [K][M or N]: the row-major activations and gradients of the training step,
+// whose weight gradients reduce over rows), chosen per operand at compile time.
 //
 // One CTA computes a 128 x BN tile of C (BN = 128 or 256) over a K range:
 //   warp 0 lane 0   TMA producer: per 64-wide K block, one 128 x 64 A tile
 //                   and one BN x 64 B tile (128-byte swizzle) into a 4-stage
-//                   ring guarded by full/empty mbarriers
+//                   ring guarded by full/empty mbarriers; an MN-major tile is
+//                   loaded as 64-wide slices of 64 K rows, 8 KB apart
 //   warp 1 lane 0   MMA issuer: 4 x tcgen05.mma (K = 16 each) per K block,
 //                   tcgen05.commit frees the stage; a last commit signals the
 //                   accumulator
@@ -35,16 +39,15 @@ constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait rounds before giving up
 enum Epilogue : int {
     EPI_F32 = 0,        // C (+ bias per column) -> fp32 row-major
     EPI_F32_ATOMIC = 1, // split-K: atomicAdd into fp32 row-major
-    EPI_BIAS_RELU = 2,  // relu(C + bias) -> bf16 row-major and bf16 transposed
-    EPI_RELU_GRAD = 3   // C * (act > 0) -> bf16 row-major and bf16 transposed
+    EPI_BIAS_RELU = 2,  // relu(C + bias) -> bf16 row-major
+    EPI_RELU_GRAD = 3   // C * (act > 0) -> bf16 row-major
 };
 
 struct GemmArgs {
     int M, N, K;             // full problem (M, N multiples of 128/BN; K of 64)
     int k_blocks_per_split;  // K blocks handled by one CTA (gridDim.z splits)
     float *c32;              // EPI_F32 / EPI_F32_ATOMIC output [M, N]
-    __nv_bfloat16 *c16;      // bf16 output [M, N] (may be null)
-    __nv_bfloat16 *c16t;     // bf16 transposed output [N, M] (may be null)
+    __nv_bfloat16 *c16;      // bf16 output [M, N]
     const float *bias;       // per column (may be null)
     const __nv_bfloat16 *act;   // EPI_RELU_GRAD: activation [M, N] whose > 0 mask is applied
     int m_valid;             // rows >= m_valid are padding: not written
@@ -91,24 +94,37 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row core groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
+// Shared-memory matrix descriptor, 128-byte swizzle.  K-major: rows of 128
+// bytes (64 K elements), 8-row core groups 1024 bytes apart (the leading
+// offset is unused).  MN-major: rows of 128 bytes hold 64 M (or N) elements
+// of one K index; 8-row groups along K are 1024 bytes apart (stride offset)
+// and 64-element slices along M (N) are kMnSliceBytes apart (leading offset).
+constexpr uint32_t kMnSliceBytes = BK * 128;  // one 64 x 64 slice: 64 K rows of 128 bytes
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, bool mn_major = false)
 {
     uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-    d |= (uint64_t)(16u >> 4) << 16;           // leading byte offset (unused when swizzled K-major)
-    d |= (uint64_t)(1024u >> 4) << 32;         // stride byte offset between 8-row groups
-    d |= (uint64_t)1u << 46;                   // descriptor version
-    d |= (uint64_t)2u << 61;                   // 128-byte swizzle
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);                          // start address
+    d |= (uint64_t)((mn_major ? kMnSliceBytes : 16u) >> 4) << 16;      // leading byte offset
+    d |= (uint64_t)(1024u >> 4) << 32;                                 // stride byte offset
+    d |= (uint64_t)1u << 46;                                           // descriptor version
+    d |= (uint64_t)2u << 61;                                           // 128-byte swizzle
     return d;
 }
 
-// Instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, both
-// K-major, M x N tile.
-__host__ __device__ constexpr uint32_t instr_desc(int m, int n)
+// Instruction descriptor, kind::f16: fp32 accumulator, bf16 A and B, M x N
+// tile; a_mn / b_mn mark an MN-major operand (the transpose bits).
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n, bool a_mn = false, bool b_mn = false)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// Byte offset of the k-th 16-deep K step inside one stage's operand tile:
+// 32 bytes along a K-major row, two 8-row groups down an MN-major slice.
+__host__ __device__ constexpr uint32_t kstep_offset(int k, bool mn_major)
+{
+    return mn_major ? 2048u * (uint32_t)k : 32u * (uint32_t)k;
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -168,7 +184,8 @@ constexpr size_t gemm_smem_bytes()
 // NST pipeline stages: 4 for long K; 2 for short K, which halves the shared
 // memory so two CTAs share an SM (their TMEM accumulators fit its 512
 // columns) and one CTA's epilogue overlaps the other's loads
-template <int BN, int EPI, int NST = STAGES>
+// AMN / BMN: A / B is MN-major (its tensor map is [K][M or N], 64 x 64 boxes).
+template <int BN, int EPI, int NST = STAGES, bool AMN = false, bool BMN = false>
 __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtensorMap tma_a,
                                                  const __grid_constant__ CUtensorMap tma_b, const GemmArgs g)
 {
@@ -218,13 +235,26 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
                 break;
             }
             mbar_expect_tx(&full_bar[s], kABytes + kBBytes);
-            tma_load_2d(a_s + s * kABytes, &tma_a, (kb0 + i) * BK, m0, &full_bar[s]);
-            tma_load_2d(b_s + s * kBBytes, &tma_b, (kb0 + i) * BK, n0, &full_bar[s]);
+            const int k0 = (kb0 + i) * BK;
+            if (AMN) {
+#pragma unroll
+                for (int j = 0; j < BM / 64; ++j)
+                    tma_load_2d(a_s + s * kABytes + j * kMnSliceBytes, &tma_a, m0 + 64 * j, k0, &full_bar[s]);
+            } else {
+                tma_load_2d(a_s + s * kABytes, &tma_a, k0, m0, &full_bar[s]);
+            }
+            if (BMN) {
+#pragma unroll
+                for (int j = 0; j < BN / 64; ++j)
+                    tma_load_2d(b_s + s * kBBytes + j * kMnSliceBytes, &tma_b, n0 + 64 * j, k0, &full_bar[s]);
+            } else {
+                tma_load_2d(b_s + s * kBBytes, &tma_b, k0, n0, &full_bar[s]);
+            }
             ++issued;
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        constexpr uint32_t idesc = instr_desc(BM, BN);
+        constexpr uint32_t idesc = instr_desc(BM, BN, AMN, BMN);
         for (int i = 0; i < n_kb; ++i) {
             const int s = i % NST;
             const uint32_t ph = (uint32_t)(i / NST) & 1u;
@@ -236,7 +266,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
             const uint32_t a0 = smem_u32(a_s + s * kABytes), b0 = smem_u32(b_s + s * kBBytes);
 #pragma unroll
             for (int k = 0; k < BK / 16; ++k)
-                mma_bf16(tmem, smem_desc(a0 + 32u * k), smem_desc(b0 + 32u * k), idesc, (i > 0 || k > 0) ? 1u : 0u);
+                mma_bf16(tmem, smem_desc(a0 + kstep_offset(k, AMN), AMN), smem_desc(b0 + kstep_offset(k, BMN), BMN),
+                         idesc, (i > 0 || k > 0) ? 1u : 0u);
             mma_commit(&empty_bar[s]);
         }
         // tracks every MMA issued above, even after a timeout
@@ -285,15 +316,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
                     for (int j = 0; j < 16; ++j)
                         h[j] = __float2bfloat16_rn(fmaxf(v[j] + (g.bias ? g.bias[col0 + j] : 0.0f), 0.0f));
                 }
-                if (g.c16) {
-                    uint4 *dst = reinterpret_cast<uint4 *>(g.c16 + (size_t)row * g.N + col0);
-                    dst[0] = *reinterpret_cast<const uint4 *>(h);
-                    dst[1] = *reinterpret_cast<const uint4 *>(h + 8);
-                }
-                if (g.c16t) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) g.c16t[(size_t)(col0 + j) * g.M + row] = h[j];
-                }
+                uint4 *dst = reinterpret_cast<uint4 *>(g.c16 + (size_t)row * g.N + col0);
+                dst[0] = *reinterpret_cast<const uint4 *>(h);
+                dst[1] = *reinterpret_cast<const uint4 *>(h + 8);
             }
         }
     }

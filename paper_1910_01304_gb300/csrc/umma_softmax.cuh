@@ -3,14 +3,15 @@
 //
 //   Z    = H2 W3^T + b3            [rows, 4096], never written to memory
 //   loss = log sum_j exp(Z_rj) - Z_r,label        per labelled row
-//   dZ   = softmax(Z_r) - onehot(label)           bf16, row-major and transposed
+//   dZ   = softmax(Z_r) - onehot(label)           bf16, row-major
 //
 // One CTA owns 128 rows and computes all 16 column tiles of 256 twice.  The
 // first pass keeps each row's running maximum and sum of exponentials; the
 // second recomputes each tile and writes the gradient.  The CTA's 128 x 256
 // tile of H2 stays in shared memory; W3 streams from L2 in 256 x 64 blocks
-// through a 4-stage ring.  Two TMEM accumulators of 256 columns let the
-// epilogue of one tile overlap the MMAs of the next.
+// through a 4-stage ring; b3 is copied to shared memory once.  Two TMEM
+// accumulators of 256 columns let the epilogue of one tile overlap the MMAs
+// of the next.
 //   warps 0-15 epilogue: warp w reads TMEM lanes 32(w%4).. (rows) and the
 //              64-column slice w/4 of every tile; the four partial row
 //              statistics of a row are combined in shared memory after pass 1
@@ -44,7 +45,7 @@ constexpr int SX_THREADS = (SX_EPI_WARPS + 2) * 32;
 template <int NST = SX_NST>
 constexpr size_t softmax_smem_bytes()
 {
-    return (size_t)SX_A_BYTES + (size_t)NST * SX_B_BYTES + 1024;
+    return (size_t)SX_A_BYTES + (size_t)NST * SX_B_BYTES + SX_CLASSES * sizeof(float) + 1024;
 }
 
 struct SoftmaxArgs {
@@ -57,7 +58,6 @@ struct SoftmaxArgs {
     int n;                  // rows >= n are padding (no target)
     int npad;               // rows, a multiple of 128
     __nv_bfloat16 *dz;      // [npad, 4096]
-    __nv_bfloat16 *dzt;     // [4096, npad]
     float *loss_sum;        // += loss of every labelled row
     unsigned int *count;    // += labelled rows
     unsigned int *error;    // set to 1 when a bounded wait gives up
@@ -76,14 +76,14 @@ __device__ __forceinline__ float max3(float a, float b, float c)
     return r;
 }
 
-// v[j] += bias[j] for 32 columns; bias is 16-byte aligned and the same for
-// every lane (a broadcast load)
+// v[j] += bias[j] for 32 columns; bias is in shared memory, 16-byte aligned
+// and the same for every lane (a broadcast read)
 __device__ __forceinline__ void add_bias32(float (&v)[32], const float *bias)
 {
     const float4 *b4 = reinterpret_cast<const float4 *>(bias);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const float4 b = __ldg(b4 + j);
+        const float4 b = b4[j];
         v[4 * j] += b.x;
         v[4 * j + 1] += b.y;
         v[4 * j + 2] += b.z;
@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *a_s = smem;
     unsigned char *b_s = smem + SX_A_BYTES;
+    float *bias_s = reinterpret_cast<float *>(b_s + NST * SX_B_BYTES);  // b3, read by every epilogue warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM;
     constexpr int kTiles = PREDICT ? SX_TILES : 2 * SX_TILES;
@@ -125,6 +126,8 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
         mbar_init(&drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    for (int i = threadIdx.x; i < SX_CLASSES / 4; i += SX_THREADS)
+        reinterpret_cast<float4 *>(bias_s)[i] = __ldg(reinterpret_cast<const float4 *>(g.bias) + i);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                      "r"(2u * SX_BN)
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
             for (int c0 = 0; c0 < SX_SLICE; c0 += 32) {
                 float v[32];
                 tmem_ld32(taddr + (uint32_t)c0, v);
-                add_bias32(v, g.bias + col0 + c0);
+                add_bias32(v, bias_s + col0 + c0);
                 if (PREDICT) {
                     // first maximum: columns arrive in ascending order
 #pragma unroll
@@ -301,7 +304,7 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
             for (int c0 = 0; c0 < SX_SLICE; c0 += 32) {
                 float v[32];
                 tmem_ld32(taddr + (uint32_t)c0, v);
-                add_bias32(v, g.bias + col0 + c0);
+                add_bias32(v, bias_s + col0 + c0);
                 // softmax (zero for rows without a target: inv = 0), minus
                 // the one-hot of the label when its column is in this chunk
 #pragma unroll
@@ -319,14 +322,6 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
                 uint4 *dst = reinterpret_cast<uint4 *>(g.dz + (size_t)row * SX_CLASSES + col0 + c0);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) dst[k] = reinterpret_cast<const uint4 *>(q2)[k];
-                // dZ^T: column j of the chunk is row col0 + c0 + j; the warp's
-                // 32 lanes write 64 contiguous bytes of it
-                __nv_bfloat16 *dt = g.dzt + (size_t)(col0 + c0) * g.npad + row;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    dt[(size_t)(2 * j) * g.npad] = __low2bfloat16(q2[j]);
-                    dt[(size_t)(2 * j + 1) * g.npad] = __high2bfloat16(q2[j]);
-                }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();

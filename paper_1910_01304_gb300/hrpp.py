@@ -53,6 +53,7 @@ class hrpp_trace_opts(ctypes.Structure):
 HRPP_SCHEDULE_DEFAULT, HRPP_SCHEDULE_BATCH, HRPP_SCHEDULE_REFILL = 0, 1, 2
 HRPP_VERIFY_ROOT, HRPP_VERIFY_BOTTOM_UP, HRPP_VERIFY_NONE = 0, 1, 2
 HRPP_HASH_EXP_MSB, HRPP_HASH_EXP_LSB = 0, 1
+HRPP_GEMM_A_MN_MAJOR, HRPP_GEMM_B_MN_MAJOR = 1, 2
 HRPP_L2_NONE, HRPP_L2_TABLE, HRPP_L2_NODES = 0, 1, 2
 HRPP_OUTCOME_PLAIN, HRPP_OUTCOME_NEGATIVE, HRPP_OUTCOME_FALSE_POS, HRPP_OUTCOME_TRUE_POS = 0, 1, 2, 3
 
@@ -99,6 +100,7 @@ def _load():
         "hrpp_batch_get_stats": (st, [P, u32, P]),
         "hrpp_batch_destroy": (None, [P]),
         "hrpp_gemm_bf16": (st, [P, P, P, i32, i32, i32, P]),
+        "hrpp_gemm_bf16_ex": (st, [P, P, P, i32, i32, i32, i32, P]),
         "hrpp_proposal_create": (st, [P, P, u32, u32, P, u32, ctypes.c_uint64, P]),
         "hrpp_proposal_features": (st, [P, P, u32, P, P]),
         "hrpp_proposal_labels": (st, [P, P, u32, P, P]),
@@ -148,6 +150,7 @@ hrpp_batch_run = _lib.hrpp_batch_run
 hrpp_batch_get_stats = _lib.hrpp_batch_get_stats
 hrpp_batch_destroy = _lib.hrpp_batch_destroy
 hrpp_gemm_bf16 = _lib.hrpp_gemm_bf16
+hrpp_gemm_bf16_ex = _lib.hrpp_gemm_bf16_ex
 hrpp_proposal_create = _lib.hrpp_proposal_create
 hrpp_proposal_features = _lib.hrpp_proposal_features
 hrpp_proposal_labels = _lib.hrpp_proposal_labels
