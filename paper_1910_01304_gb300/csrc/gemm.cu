@@ -35,6 +35,29 @@ cudaError_t encoder(PFN_cuTensorMapEncodeTiled_v12000 *out)
     return cudaSuccess;
 }
 
+// Raises a kernel's dynamic shared-memory limit once per device (the
+// attribute belongs to the current device).  A failure is not remembered, so
+// a later call retries.
+class SmemAttr {
+  public:
+    cudaError_t set(const void *fn, size_t smem)
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        std::lock_guard<std::mutex> lk(mu_);
+        if ((done_ >> dev) & 1u) return cudaSuccess;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) done_ |= 1ull << dev;
+        return e;
+    }
+
+  private:
+    std::mutex mu_;
+    uint64_t done_ = 0;
+};
+
 // K-major bf16 matrix [rows, k] as a TMA map with 64 x box_rows boxes and
 // 128-byte swizzle (the layout the tcgen05 shared-memory descriptor expects).
 cudaError_t make_map(CUtensorMap *map, const void *ptr, uint64_t rows, uint64_t k, uint32_t box_rows)
@@ -73,12 +96,11 @@ template <int BN, int EPI, int NST, bool AMN, bool BMN>
 cudaError_t launch_stages(const void *a, const void *b, const umma::GemmArgs &g, int splits, cudaStream_t s)
 {
     const size_t smem = umma::gemm_smem_bytes<BN, NST>();
-    // once per template instance (thread-safe static initialisation)
-    static const cudaError_t attr = cudaFuncSetAttribute(umma::k_gemm<BN, EPI, NST, AMN, BMN>,
-                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (attr != cudaSuccess) return attr;
+    static SmemAttr attr;  // one per template instance
+    cudaError_t e = attr.set((const void *)umma::k_gemm<BN, EPI, NST, AMN, BMN>, smem);
+    if (e != cudaSuccess) return e;
     CUtensorMap ma, mb;
-    cudaError_t e = AMN ? make_map_mn(&ma, a, (uint64_t)g.K, (uint64_t)g.M)
+    e = AMN ? make_map_mn(&ma, a, (uint64_t)g.K, (uint64_t)g.M)
                         : make_map(&ma, a, (uint64_t)g.M, (uint64_t)g.K, umma::BM);
     if (e == cudaSuccess)
         e = BMN ? make_map_mn(&mb, b, (uint64_t)g.K, (uint64_t)g.N) : make_map(&mb, b, (uint64_t)g.N, (uint64_t)g.K, BN);
@@ -104,16 +126,15 @@ template <bool PREDICT>
 cudaError_t launch_output_layer(const void *h2, const void *w3, const umma::SoftmaxArgs &g, cudaStream_t s)
 {
     const size_t smem = umma::softmax_smem_bytes<>();
-    // once per instance (thread-safe static initialisation)
-    static const cudaError_t attr = cudaFuncSetAttribute(umma::k_softmax_xent<umma::SX_NST, PREDICT>,
-                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (attr != cudaSuccess) return attr;
+    static SmemAttr attr;  // one per instance
+    cudaError_t e = attr.set((const void *)umma::k_softmax_xent<umma::SX_NST, PREDICT>, smem);
+    if (e != cudaSuccess) return e;
     if (g.npad <= 0 || g.npad % umma::BM != 0 || ((uintptr_t)h2 & 15u) || ((uintptr_t)w3 & 15u)) return cudaErrorInvalidValue;
     // the epilogue reads the bias and writes dZ rows 16 bytes at a time
     if (!g.bias || ((uintptr_t)g.bias & 15u) || (!PREDICT && (!g.dz || ((uintptr_t)g.dz & 15u))))
         return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    cudaError_t e = make_map(&ma, h2, (uint64_t)g.npad, umma::SX_K, umma::BM);
+    e = make_map(&ma, h2, (uint64_t)g.npad, umma::SX_K, umma::BM);
     if (e == cudaSuccess) e = make_map(&mb, w3, umma::SX_CLASSES, umma::SX_K, umma::SX_BN);
     if (e != cudaSuccess) return e;
     umma::k_softmax_xent<umma::SX_NST, PREDICT><<<g.npad / umma::BM, umma::SX_THREADS, smem, s>>>(ma, mb, g);
