@@ -462,6 +462,18 @@ def run_batched(args):
     stats = [setup.batches[0].stats(k) for k in range(len(items))]
     setup.close()
 
+    # the same frame-0 rays with one plain hrpp_trace launch per item, for
+    # comparison with the single persistent launch
+    outs = [torch.empty((r.shape[0], 4) if mode == H.HRPP_CLOSEST_HIT else (r.shape[0],),
+                        dtype=torch.float32 if mode == H.HRPP_CLOSEST_HIT else torch.int32, device="cuda")
+            for (g, mode), r in zip(items, frames[0])]
+
+    class PerItem:
+        def step(self):
+            for (g, mode), r, o in zip(items, frames[0], outs):
+                H.trace(g, r, mode, None, hits=o, block_threads=tuned["block_threads"])
+    per_item_ms = timed(PerItem())
+
     def ways_of(mode):
         cfg = tuned["closest"] if mode == H.HRPP_CLOSEST_HIT else tuned["any"]
         return cfg["ways"] if cfg else 0
@@ -487,7 +499,9 @@ def run_batched(args):
                          "seconds": tune_s, "items_with_a_table": n_tables},
             "plain": {"value": n_rays / (res["plain"] * 1e-3) / 1e6, "ms_per_step": res["plain"],
                       "speedup_hrpp_over_plain": res["plain"] / res["hrpp"]},
-            "roofline": {"bound": "hbm", "kernel": "k_trace_batch<4> + k_apply_batch (graph)",
+            "plain_per_item_launches": {"value": n_rays / (per_item_ms * 1e-3) / 1e6, "ms_per_step": per_item_ms,
+                                        "launches": len(items)},
+            "roofline": {"bound": "hbm", "kernel": "k_trace_batch<4, closest> || k_trace_batch<4, any> + k_apply_batch (graph)",
                          "achieved": hb / (res["hrpp"] * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": hb / (res["hrpp"] * 1e-3) / 1e9 / peak, "peak_kind": peak_kind, "traffic": None},
             "true_pos": tp, "lookups": lookups,

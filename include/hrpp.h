@@ -360,8 +360,9 @@ hrpp_status hrpp_trace_noalloc(const hrpp_scene *scene, hrpp_table *table, const
                                hrpp_mode mode, void *out_hits, hrpp_stats *out_stats, void *stream);
 
 /* Batched traces: many (scene, table, rays) items -- scenes of different
- * sizes, batches of uneven lengths -- traced by ONE persistent kernel launch
- * (plus one launch applying every two-phase table's inserts), recorded once
+ * sizes, batches of uneven lengths -- traced by one persistent kernel launch
+ * per query mode (the closest-hit and any-hit launches run side by side),
+ * plus one launch applying every two-phase table's inserts, recorded once
  * into a CUDA graph and replayed by hrpp_batch_run.  Per item the results,
  * counters and table updates are exactly those of hrpp_trace on that item.
  *   scene, table  as for hrpp_trace; all scenes of a batch share one device

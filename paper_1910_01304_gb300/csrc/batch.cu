@@ -1,5 +1,6 @@
-// Batched traces: many (scene, table, rays) items in one persistent launch,
-// captured once into a CUDA graph and replayed by hrpp_batch_run.
+// Batched traces: many (scene, table, rays) items in one persistent launch
+// per query mode (the two launches run side by side), captured once into a
+// CUDA graph and replayed by hrpp_batch_run.
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -20,12 +21,13 @@ struct hrpp_batch {
     bool stats;
     uint32_t block_threads;
     TraceParams *d_items;
-    unsigned char *d_ctl;       // [cursor: 256 B][item 0 Ctl: 256 B]...[item n-1 Ctl]
+    unsigned char *d_ctl;       // [cursors: 256 B][item 0 Ctl: 256 B]...[item n-1 Ctl]
     size_t ctl_bytes;
     Record *d_records;
     uint32_t *d_chunk_item, *d_chunk_first;
     uint32_t n_chunks;
-    cudaStream_t capture_stream;
+    uint32_t n_closest_chunks;  // chunks of closest-hit items come first
+    cudaStream_t capture_stream, side_stream;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     cudaStream_t last_stream;
@@ -59,6 +61,7 @@ void release(hrpp_batch *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    if (b->side_stream) cudaStreamDestroy(b->side_stream);
     cudaFree(b->d_items);
     cudaFree(b->d_ctl);
     cudaFree(b->d_records);
@@ -142,6 +145,7 @@ hrpp_status hrpp_batch_create(const hrpp_batch_item *items, uint32_t n_items, in
         chunk_first.reserve(total_chunks);
         uint64_t rec_off = 0;
         uint32_t max_n = 0;
+        std::vector<uint32_t> any_item, any_first;  // appended after the closest-hit chunks
         for (uint32_t k = 0; k < n_items; ++k) {
             const hrpp_batch_item &it = items[k];
             const hrpp_scene *sc = it.scene;
@@ -179,10 +183,13 @@ hrpp_status hrpp_batch_create(const hrpp_batch_item *items, uint32_t n_items, in
             }
             if (it.n_rays > max_n) max_n = it.n_rays;
             for (uint32_t c = 0; c < (it.n_rays + 31u) / 32u; ++c) {
-                chunk_item.push_back(k);
-                chunk_first.push_back(32u * c);
+                (p.closest ? chunk_item : any_item).push_back(k);
+                (p.closest ? chunk_first : any_first).push_back(32u * c);
             }
         }
+        b->n_closest_chunks = (uint32_t)chunk_item.size();
+        chunk_item.insert(chunk_item.end(), any_item.begin(), any_item.end());
+        chunk_first.insert(chunk_first.end(), any_first.begin(), any_first.end());
         if ((e = cudaMemcpy(b->d_items, h.data(), sizeof(TraceParams) * n_items, cudaMemcpyHostToDevice)) != cudaSuccess ||
             (total_chunks &&
              ((e = cudaMemcpy(b->d_chunk_item, chunk_item.data(), 4 * total_chunks, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -191,25 +198,47 @@ hrpp_status hrpp_batch_create(const hrpp_batch_item *items, uint32_t n_items, in
             status = bfail(HRPP_ERR_CUDA, "batch upload: %s", cudaGetErrorString(e));
             break;
         }
-        // capture: zero the cursor and item control blocks, trace every item,
-        // apply every two-phase table's inserts
+        // capture: zero the cursors and item control blocks; trace the
+        // closest-hit items on the capture stream and the any-hit items on a
+        // side stream, so the two launches overlap; then apply every
+        // two-phase table's inserts
         if ((e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&b->side_stream, cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
             status = bfail(HRPP_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
             break;
         }
-        BatchDesc d;
-        d.items = b->d_items;
-        d.chunk_item = b->d_chunk_item;
-        d.chunk_first = b->d_chunk_first;
-        d.n_chunks = b->n_chunks;
-        d.cursor = reinterpret_cast<unsigned int *>(b->d_ctl);
-        cudaError_t ec = cudaMemsetAsync(b->d_ctl, 0, b->ctl_bytes, b->capture_stream);
-        if (ec == cudaSuccess && b->n_chunks)
-            ec = b->width == 2 ? launch_batch_w2(b->stats, d, (int)block_threads, b->capture_stream)
-                               : launch_batch_w4(b->stats, d, (int)block_threads, b->capture_stream);
+        const uint32_t n_any = b->n_chunks - b->n_closest_chunks;
+        BatchDesc dc, da;
+        dc.items = da.items = b->d_items;
+        dc.chunk_item = b->d_chunk_item;
+        dc.chunk_first = b->d_chunk_first;
+        dc.n_chunks = b->n_closest_chunks;
+        dc.cursor = reinterpret_cast<unsigned int *>(b->d_ctl);
+        da.chunk_item = b->d_chunk_item + b->n_closest_chunks;
+        da.chunk_first = b->d_chunk_first + b->n_closest_chunks;
+        da.n_chunks = n_any;
+        da.cursor = reinterpret_cast<unsigned int *>(b->d_ctl) + 1;
+        cudaEvent_t fork = nullptr, join = nullptr;
+        cudaError_t ec = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (ec == cudaSuccess) ec = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+        if (ec == cudaSuccess) ec = cudaMemsetAsync(b->d_ctl, 0, b->ctl_bytes, b->capture_stream);
+        const bool both = dc.n_chunks && da.n_chunks;
+        if (ec == cudaSuccess && both) ec = cudaEventRecord(fork, b->capture_stream);
+        if (ec == cudaSuccess && both) ec = cudaStreamWaitEvent(b->side_stream, fork, 0);
+        if (ec == cudaSuccess && dc.n_chunks)
+            ec = b->width == 2 ? launch_batch_w2(true, b->stats, dc, (int)block_threads, b->capture_stream)
+                               : launch_batch_w4(true, b->stats, dc, (int)block_threads, b->capture_stream);
+        cudaStream_t any_stream = both ? b->side_stream : b->capture_stream;
+        if (ec == cudaSuccess && da.n_chunks)
+            ec = b->width == 2 ? launch_batch_w2(false, b->stats, da, (int)block_threads, any_stream)
+                               : launch_batch_w4(false, b->stats, da, (int)block_threads, any_stream);
+        if (ec == cudaSuccess && both) ec = cudaEventRecord(join, b->side_stream);
+        if (ec == cudaSuccess && both) ec = cudaStreamWaitEvent(b->capture_stream, join, 0);
         if (ec == cudaSuccess && total_records) ec = launch_table_apply_batch(b->d_items, n_items, max_n, b->capture_stream);
         e = cudaStreamEndCapture(b->capture_stream, &b->graph);
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
         if (ec != cudaSuccess || e != cudaSuccess) {
             status = bfail(HRPP_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec != cudaSuccess ? ec : e));
             break;

@@ -238,8 +238,9 @@ struct BatchDesc {
 };
 
 
-cudaError_t launch_batch_w2(bool stats, const BatchDesc &b, int block_threads, cudaStream_t stream);
-cudaError_t launch_batch_w4(bool stats, const BatchDesc &b, int block_threads, cudaStream_t stream);
+// one launch per query mode: every chunk of b belongs to items of that mode
+cudaError_t launch_batch_w2(bool closest, bool stats, const BatchDesc &b, int block_threads, cudaStream_t stream);
+cudaError_t launch_batch_w4(bool closest, bool stats, const BatchDesc &b, int block_threads, cudaStream_t stream);
 cudaError_t launch_table_apply_batch(const TraceParams *items, uint32_t n_items, uint32_t max_records,
                                      cudaStream_t stream);
 cudaError_t launch_table_fill(uint64_t *words, uint64_t n_words, cudaStream_t stream);

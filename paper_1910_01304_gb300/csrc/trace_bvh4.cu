@@ -9,9 +9,9 @@ cudaError_t launch_trace_w4(bool closest, bool stats, int schedule, const TraceP
     return launch_width<4>(closest, stats, schedule, p, block_threads, blocks_per_sm_cap, stream, ev0, ev1, l2);
 }
 
-cudaError_t launch_batch_w4(bool stats, const BatchDesc &b, int block_threads, cudaStream_t stream)
+cudaError_t launch_batch_w4(bool closest, bool stats, const BatchDesc &b, int block_threads, cudaStream_t stream)
 {
-    return launch_batch_width<4>(stats, b, block_threads, stream);
+    return launch_batch_width<4>(closest, stats, b, block_threads, stream);
 }
 
 }  // namespace hrpp

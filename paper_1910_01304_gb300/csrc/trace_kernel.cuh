@@ -549,14 +549,15 @@ __global__ void __launch_bounds__(512) k_trace(const TraceParams p)
     cnt.flush(p.ctl, lane);
 }
 
-// Many (scene, table, rays) items in one persistent launch.  The rays of all
-// items are cut into 32-ray chunks (a chunk never spans two items); a warp
-// takes the next chunk from the batch cursor, copies that item's parameters
-// into shared memory when the item changes, traces the chunk exactly as
-// k_trace would, and adds its counters to the item's own control block.
+// Many (scene, table, rays) items of one query mode in one persistent
+// launch (a batch runs one launch per mode).  The rays of all items are cut
+// into 32-ray chunks (a chunk never spans two items); a warp takes the next
+// chunk from the launch's cursor, copies that item's parameters into shared
+// memory when the item changes, traces the chunk exactly as k_trace would,
+// and adds its counters to the item's own control block.
 constexpr int kBatchMaxWarps = 16;  // up to 512 threads per block
 
-template <int W, bool STATS>
+template <int W, bool CLOSEST, bool STATS>
 __global__ void __launch_bounds__(512) k_trace_batch(const BatchDesc b)
 {
     __shared__ TraceParams item_params[kBatchMaxWarps];
@@ -586,19 +587,17 @@ __global__ void __launch_bounds__(512) k_trace_batch(const BatchDesc b)
         bool want = false;
         uint32_t slot = 0;
         uint64_t word = 0;
-        if (i < p.n_rays) {
-            if (p.closest) want = trace_one<W, true, STATS>(p, i, stack, cnt, slot, word);
-            else want = trace_one<W, false, STATS>(p, i, stack, cnt, slot, word);
-        }
+        if (i < p.n_rays) want = trace_one<W, CLOSEST, STATS>(p, i, stack, cnt, slot, word);
         append_records(p, lane, want, slot, i, word);
     }
     if (cur != 0xFFFFFFFFu) cnt.flush(p.ctl, lane);
 }
 
 template <int W>
-cudaError_t launch_batch_width(bool stats, const BatchDesc &b, int block_threads, cudaStream_t stream)
+cudaError_t launch_batch_width(bool closest, bool stats, const BatchDesc &b, int block_threads, cudaStream_t stream)
 {
-    const void *fn = stats ? (const void *)k_trace_batch<W, true> : (const void *)k_trace_batch<W, false>;
+    const void *fn = closest ? (stats ? (const void *)k_trace_batch<W, true, true> : (const void *)k_trace_batch<W, true, false>)
+                             : (stats ? (const void *)k_trace_batch<W, false, true> : (const void *)k_trace_batch<W, false, false>);
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
