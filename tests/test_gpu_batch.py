@@ -66,17 +66,24 @@ def test_batch_matches_oracle_per_item(H, width):
                 assert np.array_equal(tables[k].export(), otables[k].words), f"item {k} table"
 
 
-def test_batch_equals_single_calls(H):
+@pytest.mark.parametrize("modes", ["closest", "any", "mixed"])
+def test_batch_equals_single_calls(H, modes):
+    """Batches of one query mode (one launch) and of both (two launches side
+    by side) give exactly the hits of one hrpp_trace per item."""
     import torch
     items = list(W.batched_workload(n_scenes=4, tris_range=(1000, 8000), rays_range=(500, 3000), seed=8))
     gs = [H.Scene.from_workload(s) for s, _ in items]
     rs = [torch.from_numpy(r).cuda() for _, r in items]
-    batch = H.Batch([(g, None, r, H.HRPP_CLOSEST_HIT) for g, r in zip(gs, rs)])
-    batch.run()
-    for k in range(len(items)):
-        single, _ = H.trace(gs[k], rs[k], H.HRPP_CLOSEST_HIT)
-        torch.cuda.synchronize()
-        assert torch.equal(single.view(torch.int32), batch.hits[k].view(torch.int32))
+    pick = {"closest": lambda k: H.HRPP_CLOSEST_HIT, "any": lambda k: H.HRPP_ANY_HIT,
+            "mixed": lambda k: H.HRPP_ANY_HIT if k % 2 else H.HRPP_CLOSEST_HIT}[modes]
+    ms = [pick(k) for k in range(len(items))]
+    batch = H.Batch([(g, None, r, m) for g, r, m in zip(gs, rs, ms)])
+    for _ in range(2):
+        batch.run()
+        for k in range(len(items)):
+            single, _ = H.trace(gs[k], rs[k], ms[k])
+            torch.cuda.synchronize()
+            assert torch.equal(single.view(torch.int32), batch.hits[k].view(torch.int32)), (modes, k)
 
 
 def test_batch_rejects_mixed_widths_and_shared_tables(H):
