@@ -414,8 +414,7 @@ __device__ __forceinline__ bool finish_ray(const TraceParams &p, uint32_t i, con
                 if (old == word) cnt.add(ST_DUP_INSERTS);
                 else if (old != HRPP_EMPTY_WORD) cnt.add(ST_EVICTIONS);
             } else {
-                atomicMax(p.winner + slot, i + 1u);
-                want_record = true;
+                want_record = true;  // append_records claims the slot
             }
         }
     }
@@ -432,13 +431,27 @@ __device__ __forceinline__ bool finish_ray(const TraceParams &p, uint32_t i, con
     return want_record;
 }
 
-// Appends the two-phase insert records of the lanes that want one (all 32
-// lanes must call this together): one atomic per warp.
+// Two-phase inserts of the lanes that want one (all 32 lanes call this
+// together).  A slot goes to the highest ray index aimed at it.  LANE_ORDERED
+// (the warp's rays rise with the lane): of the lanes aimed at one slot only
+// the highest lane can win, so the others are counted as lost inserts here
+// (k_apply counts the rest) and leave no record.  The remaining lanes claim
+// their slots (atomicMax of ray + 1) and append their records with one atomic
+// per warp.
+template <bool LANE_ORDERED, bool STATS>
 __device__ __forceinline__ void append_records(const TraceParams &p, uint32_t lane, bool want, uint32_t slot,
-                                               uint32_t ray, uint64_t word)
+                                               uint32_t ray, uint64_t word, Counters<STATS> &cnt)
 {
+    if (!__any_sync(0xFFFFFFFFu, want)) return;
+    if (LANE_ORDERED) {
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, want ? slot : 0xFFFFFFFFu);
+        if (want && lane != 31u - (uint32_t)__clz(peers)) {
+            cnt.add(ST_DUP_INSERTS);
+            want = false;
+        }
+    }
+    if (want) atomicMax(p.winner + slot, ray + 1u);
     const uint32_t m = __ballot_sync(0xFFFFFFFFu, want);
-    if (!m) return;
     const uint32_t leader = __ffs(m) - 1;
     uint32_t rb = 0;
     if (lane == leader) rb = atomicAdd(&p.ctl->n_records, (uint32_t)__popc(m));
@@ -544,7 +557,7 @@ __global__ void __launch_bounds__(512) k_trace(const TraceParams p)
         uint32_t slot = 0;
         uint64_t word = 0;
         if (i < p.n_rays) want = trace_one<W, CLOSEST, STATS, BU>(p, i, stack, cnt, slot, word);
-        append_records(p, lane, want, slot, i, word);
+        append_records<true>(p, lane, want, slot, i, word, cnt);
     }
     cnt.flush(p.ctl, lane);
 }
@@ -588,7 +601,7 @@ __global__ void __launch_bounds__(512) k_trace_batch(const BatchDesc b)
         uint32_t slot = 0;
         uint64_t word = 0;
         if (i < p.n_rays) want = trace_one<W, CLOSEST, STATS>(p, i, stack, cnt, slot, word);
-        append_records(p, lane, want, slot, i, word);
+        append_records<true>(p, lane, want, slot, i, word, cnt);
     }
     if (cur != 0xFFFFFFFFu) cnt.flush(p.ctl, lane);
 }
@@ -670,7 +683,7 @@ __global__ void __launch_bounds__(512) k_trace_dyn(const TraceParams p)
             uint32_t slot = 0;
             uint64_t word = 0;
             if (done) want = finish_ray<CLOSEST, STATS>(p, ray, s, cnt, slot, word);
-            append_records(p, lane, want, slot, ray, word);
+            append_records<false>(p, lane, want, slot, ray, word, cnt);
             if (done) ray = kNoRay;
         }
     }
