@@ -58,8 +58,9 @@ cudaError_t launch_table_apply(uint64_t *table, uint32_t *winner, const Record *
                                uint32_t max_records, cudaStream_t stream)
 {
     int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
     uint32_t blocks = (max_records + 255u) / 256u;
     if (blocks > (uint32_t)sms * 4u) blocks = (uint32_t)sms * 4u;
     if (blocks < 1) blocks = 1;
@@ -80,8 +81,9 @@ cudaError_t launch_table_apply_batch(const TraceParams *items, uint32_t n_items,
 cudaError_t launch_table_fill(uint64_t *words, uint64_t n_words, cudaStream_t stream)
 {
     int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
     uint64_t blocks = (n_words + 255u) / 256u;
     if (blocks > (uint64_t)sms * 8u) blocks = (uint64_t)sms * 8u;
     if (blocks < 1) blocks = 1;
