@@ -309,9 +309,12 @@ cudaError_t refresh_bf16(hrpp_proposal *p, cudaStream_t s)
 uint32_t pad128(uint32_t n) { return (n + 127u) & ~127u; }
 
 // 256-wide tiles unless that leaves fewer than two CTAs per SM (152 SMs)
-int tile_n(int m, int n)
+// Tile width: 256 when there are tiles for two waves, or when K is long
+// enough (>= 2048) that one wave of wide tiles streams A once instead of
+// splitting it over a partial second wave.
+int tile_n(int m, int n, int k)
 {
-    const bool wide_ok = n % 256 == 0 && (m / 128) * (n / 256) >= 2 * 152;
+    const bool wide_ok = n % 256 == 0 && ((m / 128) * (n / 256) >= 2 * 152 || k >= 2048);
     return wide_ok ? 256 : 128;
 }
 
@@ -350,11 +353,11 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     umma::GemmArgs g = args((int)npad, kHid, kIn, p);
     g.bias = p->master + ob1;
     g.c16 = H1;
-    if ((e = gemm_bf16(X, p->w1h, umma::EPI_BIAS_RELU, tile_n((int)npad, kHid), g, 1, s)) != cudaSuccess) return e;
+    if ((e = gemm_bf16(X, p->w1h, umma::EPI_BIAS_RELU, tile_n((int)npad, kHid, kIn), g, 1, s)) != cudaSuccess) return e;
     g = args((int)npad, kHid, kHid, p);
     g.bias = p->master + ob2;
     g.c16 = H2;
-    if ((e = gemm_bf16(H1, p->w2h, umma::EPI_BIAS_RELU, tile_n((int)npad, kHid), g, 1, s)) != cudaSuccess) return e;
+    if ((e = gemm_bf16(H1, p->w2h, umma::EPI_BIAS_RELU, tile_n((int)npad, kHid, kHid), g, 1, s)) != cudaSuccess) return e;
     if (argmax) {
         // output layer and first argmax in one tensor-core pass
         umma::SoftmaxArgs sx = {};
@@ -397,7 +400,7 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     g = args((int)npad, kHid, kCls, p);
     g.act = p->H2;
     g.c16 = p->dZ2;
-    if ((e = gemm_bf16(p->dZ3, p->w3t, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid), g, 1, s)) != cudaSuccess) return e;
+    if ((e = gemm_bf16(p->dZ3, p->w3t, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid, kCls), g, 1, s)) != cudaSuccess) return e;
     // dW2 = dZ2^T H1
     g = args(kHid, kHid, (int)npad, p);
     g.c32 = p->grad + oW2;
@@ -408,7 +411,7 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     g = args((int)npad, kHid, kHid, p);
     g.act = p->H1;
     g.c16 = p->dZ1;
-    if ((e = gemm_bf16(p->dZ2, p->w2t, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid), g, 1, s)) != cudaSuccess) return e;
+    if ((e = gemm_bf16(p->dZ2, p->w2t, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid, kHid), g, 1, s)) != cudaSuccess) return e;
     // dW1 = dZ1^T X
     g = args(kHid, kIn, (int)npad, p);
     g.c32 = p->grad + oW1;
