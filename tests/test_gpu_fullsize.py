@@ -66,7 +66,8 @@ def test_full_terrain_primary_and_ao(full):
 
 
 def test_full_batched_workload_sampled():
-    """The 64-scene uneven batch at full size in one graph-replayed launch:
+    """The 64-scene uneven batch at full size, graph-replayed (one launch per
+    query mode, side by side):
     every item checked against the oracle on a random sample of its rays."""
     import torch
     H = hrpp_mod()
