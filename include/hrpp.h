@@ -454,9 +454,9 @@ void hrpp_proposal_destroy(hrpp_proposal *p);
  * building block, exposed for testing): C[m, n] = A[m, k] * B[n, k]^T on the
  * tensor cores (tcgen05.mma, fp32 accumulation in tensor memory, operands
  * loaded by TMA).  A, B: bf16, row-major with k contiguous (K-major), device
- * memory, 16-byte aligned; C: fp32 row-major [m, n], device memory.  m and n
- * must be multiples of 128 and k of 64 (INVALID_ARG otherwise).  Waits for
- * the result. */
+ * memory, 16-byte aligned; C: fp32 row-major [m, n], device memory, 32-byte
+ * aligned.  m and n must be multiples of 128 and k of 64 (INVALID_ARG
+ * otherwise, and for misaligned pointers).  Waits for the result. */
 hrpp_status hrpp_gemm_bf16(const void *a, const void *b, float *c, int m, int n, int k, void *stream);
 /* hrpp_gemm_bf16 with operand layouts (layout 0 is hrpp_gemm_bf16):
  *   HRPP_GEMM_A_MN_MAJOR  A is stored [k, m] (m contiguous), i.e. the

@@ -130,8 +130,8 @@ cudaError_t launch_output_layer(const void *h2, const void *w3, const umma::Soft
     cudaError_t e = attr.set((const void *)umma::k_softmax_xent<umma::SX_NST, PREDICT>, smem);
     if (e != cudaSuccess) return e;
     if (g.npad <= 0 || g.npad % umma::BM != 0 || ((uintptr_t)h2 & 15u) || ((uintptr_t)w3 & 15u)) return cudaErrorInvalidValue;
-    // the epilogue reads the bias and writes dZ rows 16 bytes at a time
-    if (!g.bias || ((uintptr_t)g.bias & 15u) || (!PREDICT && (!g.dz || ((uintptr_t)g.dz & 15u))))
+    // the epilogue reads the bias 16 bytes and writes dZ rows 32 bytes at a time
+    if (!g.bias || ((uintptr_t)g.bias & 15u) || (!PREDICT && (!g.dz || ((uintptr_t)g.dz & 31u))))
         return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     e = make_map(&ma, h2, (uint64_t)g.npad, umma::SX_K, umma::BM);
@@ -168,6 +168,11 @@ cudaError_t gemm_bf16(const void *a, const void *b, int epi, int bn, const umma:
     g.k_blocks_per_split = (kb + splits - 1) / splits;
     splits = (kb + g.k_blocks_per_split - 1) / g.k_blocks_per_split;
     if (((uintptr_t)a & 15u) || ((uintptr_t)b & 15u)) return cudaErrorInvalidValue;
+    // epilogue stores: 32 bytes per lane (plain fp32 and bf16 outputs), 16
+    // bytes per atomic
+    if ((epi == umma::EPI_F32 && ((uintptr_t)g.c32 & 31u)) || (epi == umma::EPI_F32_ATOMIC && ((uintptr_t)g.c32 & 15u)) ||
+        ((epi == umma::EPI_BIAS_RELU || epi == umma::EPI_RELU_GRAD) && ((uintptr_t)g.c16 & 31u)))
+        return cudaErrorInvalidValue;
     if (layout != 0) {
         // MN-major operands: the weight gradients of the training step
         // (split-K atomics) and the utility entry point (plain fp32)
@@ -213,6 +218,8 @@ extern "C" hrpp_status hrpp_gemm_bf16_ex(const void *a, const void *b, float *c,
     if (!a || !b || !c) return hrpp::report(HRPP_ERR_INVALID_ARG, "NULL matrix");
     if (layout < 0 || layout > (HRPP_GEMM_A_MN_MAJOR | HRPP_GEMM_B_MN_MAJOR))
         return hrpp::report(HRPP_ERR_INVALID_ARG, "unknown layout flags");
+    if (((uintptr_t)a & 15u) || ((uintptr_t)b & 15u) || ((uintptr_t)c & 31u))
+        return hrpp::report(HRPP_ERR_INVALID_ARG, "A and B must be 16-byte aligned, C 32-byte aligned");
     const int bn = (n % 256 == 0) ? 256 : 128;
     if (!hrpp::gemm_shape_ok(m, n, k, bn)) {
         snprintf(msg, sizeof msg, "shape %d x %d x %d: M must be a multiple of 128, N of 128, K of 64", m, n, k);

@@ -138,6 +138,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
         : "memory");
 }
 
+// One 32-byte global store (dst 32-byte aligned).  A lane's 32 bytes fill a
+// whole sector, and a warp's store with each lane on its own row costs one L2
+// request per row instead of two.
+__device__ __forceinline__ void st_global_32b(void *dst, const uint32_t (&w)[8])
+{
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "r"(w[0]), "r"(w[1]),
+                 "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -156,23 +166,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 32 consecutive TMEM columns of the warp's 32 lanes (one row per lane)
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
-{
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 template <int BN, int NST = STAGES>
@@ -296,11 +289,19 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
 #pragma unroll
                     for (int j = 0; j < 16; ++j) v[j] += g.bias[col0 + j];
                 }
+                if (EPI == EPI_F32) {
+                    // two 32-byte stores: each a full sector of the lane's row
 #pragma unroll
-                for (int j = 0; j < 16; j += 4) {
-                    const float4 x = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                    if (EPI == EPI_F32) *reinterpret_cast<float4 *>(dst + j) = x;
-                    else atomicAdd(reinterpret_cast<float4 *>(dst + j), x);
+                    for (int j = 0; j < 16; j += 8) {
+                        uint32_t w[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) w[q] = __float_as_uint(v[j + q]);
+                        st_global_32b(dst + j, w);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        atomicAdd(reinterpret_cast<float4 *>(dst + j), make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]));
                 }
             } else if (EPI == EPI_BIAS_RELU || EPI == EPI_RELU_GRAD) {
                 __align__(16) __nv_bfloat16 h[16];
@@ -316,9 +317,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
                     for (int j = 0; j < 16; ++j)
                         h[j] = __float2bfloat16_rn(fmaxf(v[j] + (g.bias ? g.bias[col0 + j] : 0.0f), 0.0f));
                 }
-                uint4 *dst = reinterpret_cast<uint4 *>(g.c16 + (size_t)row * g.N + col0);
-                dst[0] = *reinterpret_cast<const uint4 *>(h);
-                dst[1] = *reinterpret_cast<const uint4 *>(h + 8);
+                st_global_32b(g.c16 + (size_t)row * g.N + col0, *reinterpret_cast<const uint32_t(*)[8]>(h));
             }
         }
     }

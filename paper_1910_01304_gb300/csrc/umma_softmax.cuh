@@ -76,18 +76,62 @@ __device__ __forceinline__ float max3(float a, float b, float c)
     return r;
 }
 
-// v[j] += bias[j] for 32 columns; bias is in shared memory, 16-byte aligned
-// and the same for every lane (a broadcast read)
-__device__ __forceinline__ void add_bias32(float (&v)[32], const float *bias)
+// v[j] = column j of a 16-column TMEM chunk + bias[j]; bias is in shared
+// memory, 16-byte aligned and the same for every lane (a broadcast read)
+__device__ __forceinline__ void chunk_plus_bias(const uint32_t (&r)[16], const float *bias, float (&v)[16])
 {
     const float4 *b4 = reinterpret_cast<const float4 *>(bias);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < 4; ++j) {
         const float4 b = b4[j];
-        v[4 * j] += b.x;
-        v[4 * j + 1] += b.y;
-        v[4 * j + 2] += b.z;
-        v[4 * j + 3] += b.w;
+        v[4 * j] = __uint_as_float(r[4 * j]) + b.x;
+        v[4 * j + 1] = __uint_as_float(r[4 * j + 1]) + b.y;
+        v[4 * j + 2] = __uint_as_float(r[4 * j + 2]) + b.z;
+        v[4 * j + 3] = __uint_as_float(r[4 * j + 3]) + b.w;
+    }
+}
+
+// Issues a 16-column TMEM load of the warp's 32 lanes without waiting for it.
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+// Waits for the thread's TMEM loads.  r passes through the instruction, so no
+// read of the loaded registers can be scheduled above the wait.
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+}
+
+// Calls f(chunk, c0) on the 16-column chunks of a warp's column slice, in
+// ascending order, loading chunk k + 1 while f works on chunk k.
+template <typename F>
+__device__ __forceinline__ void for_each_chunk(uint32_t taddr, F &&f)
+{
+    constexpr int kChunks = SX_SLICE / 16;
+    static_assert(kChunks % 2 == 0, "chunks go in pairs");
+    uint32_t ra[16], rb[16];
+    tmem_ld16_issue(taddr, ra);
+    tmem_wait16(ra);
+#pragma unroll
+    for (int k = 0; k < kChunks; k += 2) {
+        tmem_ld16_issue(taddr + 16u * (uint32_t)(k + 1), rb);
+        f(ra, 16 * k);
+        tmem_wait16(rb);
+        if (k + 2 < kChunks) tmem_ld16_issue(taddr + 16u * (uint32_t)(k + 2), ra);
+        f(rb, 16 * (k + 1));
+        if (k + 2 < kChunks) tmem_wait16(ra);
     }
 }
 
@@ -217,38 +261,36 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t taddr = tmem + lane_base + (uint32_t)(b * SX_BN + cs * SX_SLICE);
             const int col0 = t * SX_BN + cs * SX_SLICE;
-#pragma unroll 1
-            for (int c0 = 0; c0 < SX_SLICE; c0 += 32) {
-                float v[32];
-                tmem_ld32(taddr + (uint32_t)c0, v);
-                add_bias32(v, bias_s + col0 + c0);
+            for_each_chunk(taddr, [&](const uint32_t(&rc)[16], int c0) {
+                float v[16];
+                chunk_plus_bias(rc, bias_s + col0 + c0, v);
                 if (PREDICT) {
                     // first maximum: columns arrive in ascending order
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
+                    for (int j = 0; j < 16; ++j) {
                         if (v[j] > m) {
                             m = v[j];
                             best = col0 + c0 + j;
                         }
                     }
-                    continue;
+                    return;
                 }
                 // the row's label logit, when its column is in this chunk
                 const uint32_t off = (uint32_t)(lab - (col0 + c0));
-                if (off < 32u) {
+                if (off < 16u) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
+                    for (int j = 0; j < 16; ++j)
                         if ((uint32_t)j == off) zl[r] = v[j];
                 }
                 float cm = m;
 #pragma unroll
-                for (int j = 0; j < 32; j += 2) cm = max3(cm, v[j], v[j + 1]);
+                for (int j = 0; j < 16; j += 2) cm = max3(cm, v[j], v[j + 1]);
                 float acc = 0.0f;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) acc += __expf(v[j] - cm);
+                for (int j = 0; j < 16; ++j) acc += __expf(v[j] - cm);
                 ssum = ssum * __expf(m - cm) + acc;
                 m = cm;
-            }
+            });
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);
@@ -300,29 +342,28 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t taddr = tmem + lane_base + (uint32_t)(b * SX_BN + cs * SX_SLICE);
             const int col0 = (t - SX_TILES) * SX_BN + cs * SX_SLICE;
-#pragma unroll 1
-            for (int c0 = 0; c0 < SX_SLICE; c0 += 32) {
-                float v[32];
-                tmem_ld32(taddr + (uint32_t)c0, v);
-                add_bias32(v, bias_s + col0 + c0);
+            for_each_chunk(taddr, [&](const uint32_t(&rc)[16], int c0) {
+                float v[16];
+                chunk_plus_bias(rc, bias_s + col0 + c0, v);
                 // softmax (zero for rows without a target: inv = 0), minus
                 // the one-hot of the label when its column is in this chunk
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = __expf(v[j] - m) * inv;
+                for (int j = 0; j < 16; ++j) v[j] = __expf(v[j] - m) * inv;
                 const uint32_t off = (uint32_t)(lab - (col0 + c0));
-                if (off < 32u) {
+                if (off < 16u) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
+                    for (int j = 0; j < 16; ++j)
                         if ((uint32_t)j == off) v[j] -= 1.0f;
                 }
-                __align__(16) __nv_bfloat162 q2[16];
+                uint32_t w[8];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) q2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                // dZ: the lane's row, 64 contiguous bytes
-                uint4 *dst = reinterpret_cast<uint4 *>(g.dz + (size_t)row * SX_CLASSES + col0 + c0);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) dst[k] = reinterpret_cast<const uint4 *>(q2)[k];
-            }
+                for (int j = 0; j < 8; ++j) {
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                    w[j] = *reinterpret_cast<const uint32_t *>(&h);
+                }
+                // dZ: the lane's row, one 32-byte store (one full sector)
+                st_global_32b(g.dz + (size_t)row * SX_CLASSES + col0 + c0, w);
+            });
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[b]);

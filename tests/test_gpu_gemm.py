@@ -64,3 +64,7 @@ def test_gemm_rejects_bad_shapes():
     assert H.hrpp_gemm_bf16(x.data_ptr(), x.data_ptr(), c.data_ptr(), 100, 128, 64, None) == H.HRPP_ERR_INVALID_ARG
     assert H.hrpp_gemm_bf16_ex(x.data_ptr(), x.data_ptr(), c.data_ptr(), 128, 128, 64, 4, None) == \
         H.HRPP_ERR_INVALID_ARG
+    # the epilogue writes C 32 bytes at a time: a 16-byte offset is rejected
+    c2 = torch.zeros(128 * 128 + 8, device="cuda")
+    assert H.hrpp_gemm_bf16(x.data_ptr(), x.data_ptr(), c2.data_ptr() + 16, 128, 128, 64, None) == \
+        H.HRPP_ERR_INVALID_ARG
