@@ -175,7 +175,8 @@ cudaError_t gemm_bf16(const void *a, const void *b, int epi, int bn, const umma:
         return cudaErrorInvalidValue;
     if (layout != 0) {
         // MN-major operands: the weight gradients of the training step
-        // (split-K atomics) and the utility entry point (plain fp32)
+        // (split-K atomics, both MN-major), its dZ GEMMs (the weights as B,
+        // MN-major) and the utility entry point (plain fp32)
 #define HRPP_GEMM_MN(BN_, EPI_, L_)                                                                   \
     if (bn == BN_ && epi == EPI_ && layout == L_)                                                     \
         return launch<BN_, EPI_, (L_ & GEMM_A_MN) != 0, (L_ & GEMM_B_MN) != 0>(a, b, g, splits, s);
@@ -187,6 +188,8 @@ cudaError_t gemm_bf16(const void *a, const void *b, int epi, int bn, const umma:
         HRPP_GEMM_MN(256, umma::EPI_F32, 3)
         HRPP_GEMM_MN(128, umma::EPI_F32_ATOMIC, 3)
         HRPP_GEMM_MN(256, umma::EPI_F32_ATOMIC, 3)
+        HRPP_GEMM_MN(128, umma::EPI_RELU_GRAD, 2)
+        HRPP_GEMM_MN(256, umma::EPI_RELU_GRAD, 2)
 #undef HRPP_GEMM_MN
         return cudaErrorInvalidValue;
     }

@@ -13,8 +13,9 @@ bool gemm_shape_ok(int m, int n, int k, int bn);
 constexpr int GEMM_A_MN = 1, GEMM_B_MN = 2;
 // C = A[M, K] * B[N, K]^T with the given epilogue (umma::Epilogue) and tile
 // width bn (128 or 256); splits > 1 divides K across CTAs (EPI_F32_ATOMIC).
-// layout 0: both operands K-major; MN-major layouts exist for EPI_F32 and,
-// with both operands MN-major, EPI_F32_ATOMIC.
+// layout 0: both operands K-major; MN-major layouts exist for EPI_F32, for
+// EPI_F32_ATOMIC with both operands MN-major and for EPI_RELU_GRAD with B
+// MN-major.
 cudaError_t gemm_bf16(const void *a, const void *b, int epi, int bn, const umma::GemmArgs &g, int splits,
                       cudaStream_t s, int layout = 0);
 // Fused output layer + softmax cross-entropy (umma_softmax.cuh): h2 [npad,

@@ -10,11 +10,11 @@
 //   dW3 = dZ^T H2, dZ2 = (dZ W3) * (H2 > 0), dW2 = dZ2^T H1,
 //   dZ1 = (dZ2 W2) * (H1 > 0), dW1 = dZ1^T X, db = column sums
 //   Adam on fp32 master weights, scaled by 1 / (labelled rows); bf16 copies
-//   refreshed in the [out, in] and [in, out] layouts the GEMMs read.
-// Every GEMM is C = A B^T.  The forward and dZ GEMMs read K-major operands;
-// the weight gradients reduce over the rows of the minibatch and read the
-// row-major activations and gradients as MN-major operands, so nothing is
-// stored transposed.
+//   refreshed, row-major ([out, in]).
+// Every GEMM is C = A B^T.  The forward GEMMs read K-major operands; the dZ
+// GEMMs read the weights [out, in] as MN-major B; the weight gradients reduce
+// over the rows of the minibatch and read the row-major activations and
+// gradients as MN-major operands.  Nothing is stored transposed.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -188,9 +188,9 @@ void colsum(const __nv_bfloat16 *a, uint32_t rows, uint32_t cols, float *out, cu
 
 // Adam on every parameter in one launch (masters laid out W1 | b1 | W2 | b2 |
 // W3 | b3, weights [rows, cols] row-major); the weights' bf16 copies are
-// refreshed, row-major and (W2, W3) transposed.
+// refreshed, row-major (the dZ GEMMs read W2 and W3 as MN-major operands).
 struct AdamOut {
-    __nv_bfloat16 *w1h, *w2h, *w2t, *w3h, *w3t;
+    __nv_bfloat16 *w1h, *w2h, *w3h;
 };
 
 __global__ void __launch_bounds__(256) k_adam(float *w, const float *g, float *m, float *v, float lr, float bc1,
@@ -210,13 +210,9 @@ __global__ void __launch_bounds__(256) k_adam(float *w, const float *g, float *m
     if (i < ob1) {
         out.w1h[i - oW1] = h;
     } else if (i >= oW2 && i < ob2) {
-        const size_t k = i - oW2;
-        out.w2h[k] = h;
-        out.w2t[(k % kHid) * kHid + k / kHid] = h;
+        out.w2h[i - oW2] = h;
     } else if (i >= oW3 && i < ob3) {
-        const size_t k = i - oW3;
-        out.w3h[k] = h;
-        out.w3t[(k % kHid) * kCls + k / kHid] = h;
+        out.w3h[i - oW3] = h;
     }
 }
 
@@ -228,13 +224,10 @@ __global__ void k_accumulate_loss(const float *loss_sum, const unsigned int *cou
     *call_count += *count;
 }
 
-__global__ void k_to_bf16(const float *w, uint32_t rows, uint32_t cols, __nv_bfloat16 *wh, __nv_bfloat16 *wt)
+__global__ void k_to_bf16(const float *w, uint32_t n, __nv_bfloat16 *wh)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= rows * cols) return;
-    const __nv_bfloat16 h = __float2bfloat16_rn(w[i]);
-    if (wh) wh[i] = h;
-    if (wt) wt[(size_t)(i % cols) * rows + i / cols] = h;
+    if (i < n) wh[i] = __float2bfloat16_rn(w[i]);
 }
 
 __global__ void k_labels(const float4 *hits, uint32_t n, const int32_t *prim_class, uint32_t n_tris, int32_t *out)
@@ -255,7 +248,7 @@ struct hrpp_proposal {
     int32_t *class_node, *prim_class;
     std::vector<int32_t> h_class_node;
     float *master, *grad, *m, *v;
-    __nv_bfloat16 *w1h, *w2h, *w3h, *w2t, *w3t;
+    __nv_bfloat16 *w1h, *w2h, *w3h;
     int step;
     __nv_bfloat16 *X, *H1, *H2, *dZ3, *dZ2, *dZ1;
     float *loss_sum;
@@ -273,7 +266,7 @@ void proposal_free(hrpp_proposal *p)
 {
     if (!p) return;
     void *ptrs[] = {p->sin_t, p->class_node, p->prim_class, p->master, p->grad, p->m, p->v, p->w1h, p->w2h,
-                    p->w3h, p->w2t, p->w3t, p->X, p->H1, p->H2, p->dZ3, p->dZ2, p->dZ1, p->loss_sum, p->count, p->err, p->call_loss, p->call_count,
+                    p->w3h, p->X, p->H1, p->H2, p->dZ3, p->dZ2, p->dZ1, p->loss_sum, p->count, p->err, p->call_loss, p->call_count,
                     p->lab, p->Xi, p->H1i, p->H2i};
     for (void *q : ptrs) cudaFree(q);
     delete p;
@@ -296,13 +289,13 @@ struct Dev {
 
 cudaError_t refresh_bf16(hrpp_proposal *p, cudaStream_t s)
 {
-    auto run = [&](size_t off, uint32_t rows, uint32_t cols, __nv_bfloat16 *wh, __nv_bfloat16 *wt) {
+    auto run = [&](size_t off, uint32_t rows, uint32_t cols, __nv_bfloat16 *wh) {
         const uint32_t n = rows * cols;
-        k_to_bf16<<<(n + 255) / 256, 256, 0, s>>>(p->master + off, rows, cols, wh, wt);
+        k_to_bf16<<<(n + 255) / 256, 256, 0, s>>>(p->master + off, n, wh);
     };
-    run(oW1, kHid, kIn, p->w1h, nullptr);
-    run(oW2, kHid, kHid, p->w2h, p->w2t);
-    run(oW3, kCls, kHid, p->w3h, p->w3t);
+    run(oW1, kHid, kIn, p->w1h);
+    run(oW2, kHid, kHid, p->w2h);
+    run(oW3, kCls, kHid, p->w3h);
     return cudaGetLastError();
 }
 
@@ -400,7 +393,10 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     g = args((int)npad, kHid, kCls, p);
     g.act = p->H2;
     g.c16 = p->dZ2;
-    if ((e = gemm_bf16(p->dZ3, p->w3t, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid, kCls), g, 1, s)) != cudaSuccess) return e;
+    // B = W3 stored [4096, 256]: read MN-major
+    if ((e = gemm_bf16(p->dZ3, p->w3h, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid, kCls), g, 1, s, GEMM_B_MN)) !=
+        cudaSuccess)
+        return e;
     // dW2 = dZ2^T H1
     g = args(kHid, kHid, (int)npad, p);
     g.c32 = p->grad + oW2;
@@ -411,7 +407,9 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     g = args((int)npad, kHid, kHid, p);
     g.act = p->H1;
     g.c16 = p->dZ1;
-    if ((e = gemm_bf16(p->dZ2, p->w2t, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid, kHid), g, 1, s)) != cudaSuccess) return e;
+    if ((e = gemm_bf16(p->dZ2, p->w2h, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid, kHid), g, 1, s, GEMM_B_MN)) !=
+        cudaSuccess)
+        return e;
     // dW1 = dZ1^T X
     g = args(kHid, kIn, (int)npad, p);
     g.c32 = p->grad + oW1;
@@ -428,7 +426,7 @@ cudaError_t adam(hrpp_proposal *p, float lr, cudaStream_t s)
 {
     p->step += 1;
     const float bc1 = 1.0f - std::pow(0.9f, (float)p->step), bc2 = 1.0f - std::pow(0.999f, (float)p->step);
-    const AdamOut out = {p->w1h, p->w2h, p->w2t, p->w3h, p->w3t};
+    const AdamOut out = {p->w1h, p->w2h, p->w3h};
     k_adam<<<(unsigned)((kMaster + 255) / 256), 256, 0, s>>>(p->master, p->grad, p->m, p->v, lr, bc1, bc2, p->count,
                                                              out);
     return cudaGetLastError();
@@ -552,8 +550,6 @@ hrpp_status hrpp_proposal_create(const hrpp_scene *sc, const hrpp_bvh_node *node
     alloc(&p->w1h, (size_t)kHid * kIn * 2);
     alloc(&p->w2h, (size_t)kHid * kHid * 2);
     alloc(&p->w3h, (size_t)kCls * kHid * 2);
-    alloc(&p->w2t, (size_t)kHid * kHid * 2);
-    alloc(&p->w3t, (size_t)kCls * kHid * 2);
     alloc(&p->X, rows * kIn * 2);
     alloc(&p->H1, rows * kHid * 2);
     alloc(&p->H2, rows * kHid * 2);
