@@ -381,6 +381,8 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     sx.count = p->count;
     sx.error = p->err;
     if ((e = softmax_xent(H2, p->w3h, sx, s)) != cudaSuccess) return e;
+    // db3 while part of the 134 MB dZ3 is still in L2
+    colsum(p->dZ3, npad, kCls, p->grad + ob3, s);
     // the weight gradients reduce over rows: both operands MN-major
     constexpr int kMN = GEMM_A_MN | GEMM_B_MN;
     // dW3 = dZ3^T H2
@@ -416,7 +418,6 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     if ((e = gemm_bf16(p->dZ1, p->X, umma::EPI_F32_ATOMIC, 128, g, splits_for(kHid / 128, (int)npad), s, kMN)) !=
         cudaSuccess)
         return e;
-    colsum(p->dZ3, npad, kCls, p->grad + ob3, s);
     colsum(p->dZ2, npad, kHid, p->grad + ob2, s);
     colsum(p->dZ1, npad, kHid, p->grad + ob1, s);
     return cudaGetLastError();
