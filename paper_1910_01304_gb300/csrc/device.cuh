@@ -78,6 +78,16 @@ struct TraceParams {
     uint32_t *ray_box_tests;     // per ray (statistics launches only; may be null)
 };
 
+// 32 bytes through the read-only data path in one load (p 32-byte aligned):
+// a BVH node arrives in 4 (4-wide) or 2 (binary) loads per lane instead of 8
+// or 4 16-byte ones.
+__device__ __forceinline__ void ldg32(const float4 *p, float4 &a, float4 &b)
+{
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
 // ---------------------------------------------------------------- hashing --
 
 // Sec. 5: sign bit, then the p most significant exponent bits, then the p most

@@ -159,8 +159,10 @@ __device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s
     const float tmin = s.o.w;
     if (W == 2) {
         const float4 *n = p.nodes + 4ull * (uint32_t)s.ref;
-        const float4 a = __ldg(n), bb = __ldg(n + 1), c = __ldg(n + 2);
-        const int4 e = __ldg(reinterpret_cast<const int4 *>(n + 3));
+        float4 a, bb, c, ef;
+        ldg32(n, a, bb);
+        ldg32(n + 2, c, ef);
+        const int4 e = make_int4(__float_as_int(ef.x), __float_as_int(ef.y), __float_as_int(ef.z), __float_as_int(ef.w));
         float t0, t1;
         const bool v0 = !SKIP || e.x != skip;
         const bool h0 = v0 && slab(s.ri, tmin, s.tcur, a.x, a.y, a.z, a.w, c.x, c.y, t0);
@@ -186,9 +188,12 @@ __device__ __forceinline__ void visit_interior(const TraceParams &p, RayState &s
         return;
     }
     const float4 *n = p.nodes + 8ull * (uint32_t)s.ref;
-    const float4 lx = __ldg(n), hx = __ldg(n + 1), ly = __ldg(n + 2), hy = __ldg(n + 3);
-    const float4 lz = __ldg(n + 4), hz = __ldg(n + 5);
-    const int4 ch = __ldg(reinterpret_cast<const int4 *>(n + 6));
+    float4 lx, hx, ly, hy, lz, hz, cf, spare;
+    ldg32(n, lx, hx);
+    ldg32(n + 2, ly, hy);
+    ldg32(n + 4, lz, hz);
+    ldg32(n + 6, cf, spare);  // children, then the parent row (unused here)
+    const int4 ch = make_int4(__float_as_int(cf.x), __float_as_int(cf.y), __float_as_int(cf.z), __float_as_int(cf.w));
     const float inf = __int_as_float(0x7F800000);
     float t0 = inf, t1 = inf, t2 = inf, t3 = inf, t;
     bool h0 = false, h1 = false, h2 = false, h3 = false;
