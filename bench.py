@@ -985,6 +985,11 @@ def main():
             granted = H.l2_set_aside(args.l2_set_aside_mb << 20)
         except H.HrppError:
             granted = 0
+        # every rank runs the variants (they hold collectives) or none does
+        if max_over_ranks(0.0 if granted else 1.0) > 0.0:
+            if granted:
+                H.l2_set_aside(0)
+            granted = 0
         if granted:
             l2_variants = {"set_aside_bytes": granted}
             for name in ("table", "nodes"):
