@@ -3,8 +3,8 @@
 Plain, slow, single-threaded CPU restatement of the HRPP hot path (hash,
 predictor table, predicted-leaf test, BVH traversal, ray-box and ray-triangle
 tests).  Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg
-may import this package; the library's product path never does.  It shares no
-code with the CUDA path.
+and reference arm may import this package; the library's product path never
+does.  It shares no code with the CUDA path.
 """
 from __future__ import annotations
 

@@ -3,8 +3,9 @@
  *
  * A plain, slow, single-threaded CPU restatement of what the HRPP hot path
  * computes.  Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline
- * leg may load it; the library's product path never does.  It shares no code
- * with the CUDA path (no headers, helpers or tables); the two meet only at the
+ * leg and reference arm may load it; the library's product path never does.
+ * It shares no code with the CUDA path (no headers, helpers or tables); the
+ * two meet only at the
  * input arrays the seeded generators make.
  *
  * Arithmetic is IEEE-754 single precision, the precision the paper states for
