@@ -5,8 +5,7 @@
  * computes.  Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline
  * leg and reference arm may load it; the library's product path never does.
  * It shares no code with the CUDA path (no headers, helpers or tables); the
- * two meet only at the
- * input arrays the seeded generators make.
+ * two meet only at the input arrays the seeded generators make.
  *
  * Arithmetic is IEEE-754 single precision, the precision the paper states for
  * ray origin and direction (Sec. 5).  Build with -ffp-contract=off so every
