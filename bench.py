@@ -1,9 +1,10 @@
 """HRPP throughput benchmark on GB300.
 
 One step = one frame of the terrain workload through the whole hot path:
-1920x1080 primary closest-hit rays, then 4 cosine-weighted ambient-occlusion
+1920x1080 primary closest-hit rays and 4 cosine-weighted ambient-occlusion
 any-hit rays per primary hit (tmax 0.5), each batch traced by HRPP against its
-own predictor table (two-phase updates included).  Scene: value-noise terrain
+own predictor table (two-phase updates included); the two batches are
+independent and run side by side on two streams.  Scene: value-noise terrain
 of 708x708 quads plus 64 icospheres, 2,313,248 triangles, 4-wide BVH.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hrpp|reference]
@@ -917,15 +918,33 @@ def main():
             tables[0].copy_from(snap_c)
             tables[1].copy_from(snap_a)
 
-    def run(steps, warm, tables, events=None, offset=0):
+    side = torch.cuda.Stream()
+
+    def run(steps, warm, tables, events=None, offset=0, concurrent=True):
+        """steps x (restore the tables, trace the primary and AO batches).
+        concurrent: the two batches (independent; one table each) are traced
+        side by side, the AO batch on a second stream, so that each launch's
+        tail overlaps the other; otherwise one after the other (with kernel
+        events, for timing each launch alone)."""
         total = 0
         for k in range(steps):
             ev = events[k] if events is not None else (None, None)
             restore(tables)
-            H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tables[0], hits=out_c,
-                    kernel_events=ev[0] if ev[0] else None, verify=verify, l2_persist=l2_kind[0])
-            H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tables[1], hits=out_a, kernel_events=ev[1] if ev[1] else None,
-                    l2_persist=l2_kind[0])
+            if concurrent:
+                fork = torch.cuda.Event()
+                fork.record(stream)
+                side.wait_event(fork)
+                H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tables[1], hits=out_a, stream=side, l2_persist=l2_kind[0])
+                H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tables[0], hits=out_c, verify=verify,
+                        l2_persist=l2_kind[0])
+                join = torch.cuda.Event()
+                join.record(side)
+                stream.wait_event(join)
+            else:
+                H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tables[0], hits=out_c,
+                        kernel_events=ev[0] if ev[0] else None, verify=verify, l2_persist=l2_kind[0])
+                H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tables[1], hits=out_a, kernel_events=ev[1] if ev[1] else None,
+                        l2_persist=l2_kind[0])
             total += rays_per_frame[0]
         return total
 
@@ -938,12 +957,16 @@ def main():
         return e
 
     def timed(tables, with_kernel_events):
-        run(args.warmup, True, tables, offset=0)
+        """Warm-up, then args.steps timed steps.  With kernel events the two
+        batches run one after the other and each launch is timed alone;
+        without, they run side by side (the step as measured)."""
+        conc = not with_kernel_events
+        run(args.warmup, True, tables, offset=0, concurrent=conc)
         events = [((mk(), mk()), (mk(), mk())) for _ in range(args.steps)] if with_kernel_events else None
         barrier()
         e0, e1 = mk(), mk()
         e0.record(stream)
-        rays = run(args.steps, False, tables, events=events, offset=args.warmup)
+        rays = run(args.steps, False, tables, events=events, offset=args.warmup, concurrent=conc)
         e1.record(stream)
         barrier()
         ms = e0.elapsed_time(e1)
@@ -968,14 +991,20 @@ def main():
     run(args.warmup, True, (tab_c, tab_a))
     barrier()
     clocks.mark(True)
-    rays, ms, kt = timed((tab_c, tab_a), True)
+    rays, ms, _ = timed((tab_c, tab_a), False)
     ms_max = max_over_ranks(ms)
     total_rays = sum_over_ranks(rays)
     value = job_mrays_per_s(total_rays, ms_max)
+    # each launch timed alone (the batches one after the other): the
+    # roofline's kernel durations, and the sequential step for reference
+    s_rays, s_ms, kt = timed((tab_c, tab_a), True)
+    seq_value = sum_over_ranks(s_rays) / (max_over_ranks(s_ms) * 1e-3) / 1e6
 
     # --- plain traversal on the same rays
-    p_rays, p_ms, p_kt = timed((None, None), True)
+    p_rays, p_ms, _ = timed((None, None), False)
     p_value = sum_over_ranks(p_rays) / (max_over_ranks(p_ms) * 1e-3) / 1e6
+    ps_rays, ps_ms, p_kt = timed((None, None), True)
+    p_seq_value = sum_over_ranks(ps_rays) / (max_over_ranks(ps_ms) * 1e-3) / 1e6
 
     # --- the same HRPP step with a persisting-L2 window over the table words
     # or over the interior nodes (a set-aside only for these runs)
@@ -994,9 +1023,8 @@ def main():
             l2_variants = {"set_aside_bytes": granted}
             for name in ("table", "nodes"):
                 l2_kind[0] = l2_kinds[name]
-                v_rays, v_ms, v_kt = timed((tab_c, tab_a), True)
-                l2_variants[name] = {"value": sum_over_ranks(v_rays) / (max_over_ranks(v_ms) * 1e-3) / 1e6,
-                                     "kernel_ms": v_kt}
+                v_rays, v_ms, _ = timed((tab_c, tab_a), False)
+                l2_variants[name] = {"value": sum_over_ranks(v_rays) / (max_over_ranks(v_ms) * 1e-3) / 1e6}
             l2_kind[0] = H.HRPP_L2_NONE
             H.l2_set_aside(0)
 
@@ -1084,7 +1112,7 @@ def main():
         # upload under the primary trace, the next step's uploads under this
         # step's AO trace, the downloads under the next step)
         comp = torch.cuda.current_stream()
-        up, down = torch.cuda.Stream(), torch.cuda.Stream()
+        up, down, comp2 = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
         dp = [torch.empty_like(f0["prim"]) for _ in range(2)]
         da = [torch.empty_like(f0["ao"]) for _ in range(2)]
         dhc = [torch.empty_like(out_c) for _ in range(2)]
@@ -1102,21 +1130,27 @@ def main():
             b = k % 2
             with torch.cuda.stream(up):
                 if consumed[b] is not None:      # step k-2's traces are done with these buffers
-                    up.wait_event(consumed[b])
+                    for e in consumed[b]:
+                        up.wait_event(e)
                 dp[b].copy_(hp, non_blocking=True)
                 up_p = event(up)
                 da[b].copy_(ha, non_blocking=True)
                 up_a = event(up)
             if downloaded[b] is not None:        # step k-2's hits have left these buffers
                 comp.wait_event(downloaded[b])
+                comp2.wait_event(downloaded[b])
             restore((tab_c, tab_a))
+            restored = event(comp)
+            # the two batches side by side, as in the device-resident step
+            comp2.wait_event(restored)
+            comp2.wait_event(up_a)
+            H.trace(g, da[b], H.HRPP_ANY_HIT, tab_a, hits=dha[b], stream=comp2)
+            done_a = event(comp2)
             comp.wait_event(up_p)
             H.trace(g, dp[b], H.HRPP_CLOSEST_HIT, tab_c, hits=dhc[b], verify=verify)
             done_c = event(comp)
-            comp.wait_event(up_a)
-            H.trace(g, da[b], H.HRPP_ANY_HIT, tab_a, hits=dha[b])
-            done_a = event(comp)
-            consumed[b] = done_a
+            comp.wait_event(done_a)              # the next restore rewrites the AO table
+            consumed[b] = (done_c, done_a)
             with torch.cuda.stream(down):
                 down.wait_event(done_c)
                 hoc[b].copy_(dhc[b], non_blocking=True)
@@ -1131,8 +1165,8 @@ def main():
                     and torch.equal(hoa[last] == -1, out_a.cpu() == -1))
         e2e = {"value": sum_over_ranks(n_step * args.steps) / dt_pipe / 1e6, "unit": "Mrays/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "how": "hrpp_trace on double-buffered device buffers; pinned-host uploads and downloads on two copy "
-                      "streams, overlapping the traces",
+               "how": "hrpp_trace on double-buffered device buffers, the two batches side by side; pinned-host "
+                      "uploads and downloads on two copy streams, overlapping the traces",
                "hits_checked": same,
                "staged": {"value": sum_over_ranks(n_step * args.steps) / dt_staged / 1e6, "unit": "Mrays/s",
                           "how": "hrpp_trace on host buffers: staged through device memory, one stream, no overlap"}}
@@ -1184,13 +1218,16 @@ def main():
         "config": {"workload": WORKLOAD, "tris": int(sw.n_tris), "bvh_width": width,
                    "rays_per_step": float(rays_per_frame[0]), "frames": args.frames,
                    "protocol": f"each step: restore the tables warmed by {args.frames - 1} other jittered frames, "
-                               "then trace frame 0 (closest-hit primaries, then AO) with two-phase updates",
+                               "then trace frame 0's closest-hit primaries and its AO rays (independent batches, one "
+                               "table each) side by side on two streams, two-phase updates included",
                    "table": {"log2_entries": args.log2_entries, "ways": args.ways, "precision": args.precision,
                              "update": args.update, "verify": args.verify, "l2_window": args.l2},
                    "l2": f"inputs larger than L2: {rays_per_frame[0] * 32 / 1e6:.0f} MB of rays per step; "
                          "scene resident"},
         "plain": {"value": p_value, "unit": "Mrays/s", "speedup_hrpp_over_plain": value / p_value,
                   "kernel_ms": p_kt},
+        "sequential": {"value": seq_value, "plain_value": p_seq_value, "unit": "Mrays/s",
+                       "how": "the same steps with the two batches one after the other (kernel times taken here)"},
         "per_mode_kernel_ms": kt,
         "l2_persist": l2_variants,
         "table_occupancy": occupancy,
