@@ -207,7 +207,8 @@ def algorithmic_bytes(st: dict, mode_closest: bool, width: int, ways: int) -> fl
     interior nodes, triangles (traversal and predicted leaves), insert records."""
     node_b = 64 if width == 2 else 128
     return (st["rays"] * (32 + (16 if mode_closest else 4)) + st["lookups"] * 8 * ways
-            + st["interior_nodes"] * node_b + (st["tri_tests"] + st["pred_tri_tests"]) * 48 + st["inserts"] * 16)
+            + (st["interior_nodes"] + st.get("pred_interior_nodes", 0)) * node_b
+            + (st["tri_tests"] + st["pred_tri_tests"]) * 48 + st["inserts"] * 16)
 
 
 def load_peaks():

@@ -47,3 +47,46 @@ def test_reference_arm_prints_its_line():
 def bench_threads():
     import bench
     return bench.host_threads()
+
+
+def test_algorithmic_bytes_per_ray_formula():
+    """32 B per ray + 16 (closest) or 4 (any) B of result + 8 B per way per
+    lookup + one node per interior visit (predicted subtrees included) + 48 B
+    per triangle test (predicted leaves included) + 16 B per insert."""
+    import bench
+    st = {"rays": 10, "lookups": 7, "interior_nodes": 100, "pred_interior_nodes": 5, "tri_tests": 40,
+          "pred_tri_tests": 3, "inserts": 2}
+    assert bench.algorithmic_bytes(st, True, 4, 2) == 10 * 48 + 7 * 16 + 105 * 128 + 43 * 48 + 2 * 16
+    assert bench.algorithmic_bytes(st, False, 2, 1) == 10 * 36 + 7 * 8 + 105 * 64 + 43 * 48 + 2 * 16
+
+
+def test_table_occupancy_counts_valid_words_per_set():
+    import bench
+    empty = np.uint64(0xFFFFFFFFFFFFFFFF)
+    words = np.full(8, empty, np.uint64)          # 4 sets of 2 ways
+    words[0] = words[1] = 5                        # set 0: 2 nodes
+    words[4] = 9                                   # set 2: 1 node
+    occ = bench.table_occupancy(words, 2)
+    assert occ["valid_words"] == 3 and occ["words"] == 8 and occ["fill"] == 3 / 8
+    assert occ["nodes_per_used_set"] == 1.5
+
+
+def test_traffic_record_lists_both_launches():
+    """profiles/traffic.txt holds DRAM bytes and warp instructions per launch
+    for the two traversal kernels, each with the kernel source hash it was
+    taken on."""
+    import re
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+    keys = {(r[0], r[1]) for r in rows}
+    for what in ("traffic", "inst"):
+        for kernel in ("bvh4_any", "bvh4_closest"):
+            assert (what, kernel) in keys
+    for r in rows:
+        assert int(r[2]) > 0 and re.fullmatch(r"[0-9a-f]{16}", r[3])
+
+
+def test_frames_differ_across_ranks():
+    import bench
+    seen = {bench.frame_index(f, rank) for rank in range(8) for f in range(4)}
+    assert len(seen) == 32
