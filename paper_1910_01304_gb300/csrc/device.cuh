@@ -96,11 +96,11 @@ __device__ __forceinline__ void ldg32(const float4 *p, float4 &a, float4 &b)
 __device__ __forceinline__ uint32_t hash_float(float f, int p, bool lsb)
 {
     const uint32_t b = __float_as_uint(f);
-    const uint32_t sign = b >> 31;
-    const uint32_t expo = (b >> 23) & 0xFFu;
-    const uint32_t mant = b & 0x7FFFFFu;
-    const uint32_t e = lsb ? (expo & ((1u << p) - 1u)) : (expo >> (8 - p));
-    return (sign << (2 * p)) | (e << p) | (mant >> (23 - p));
+    // the p exponent bits in one shift and mask: the MSBs are bits 30..31-p
+    // (shifting by 31 - p also brings the sign down, above them, and the
+    // mask drops it); the LSBs are bits 23+p-1..23
+    const uint32_t e = (b >> (lsb ? 23 : 31 - p)) & ((1u << p) - 1u);
+    return ((b >> 31) << (2 * p)) | (e << p) | ((b & 0x7FFFFFu) >> (23 - p));
 }
 
 // Sec. 5: origin hashes XOR the swizzled direction hashes (o.x^d.z, o.y^d.y,
