@@ -52,7 +52,7 @@ typedef enum {
     HRPP_ERR_OOM = 3,             /* a device or host allocation failed */
     HRPP_ERR_CUDA = 4,            /* a CUDA runtime call failed */
     HRPP_ERR_TRAVERSAL_LIMIT = 5, /* a ray exceeded its traversal step or stack bound */
-    HRPP_ERR_UNSUPPORTED = 6      /* valid but beyond this build's limits (HRPP_MAX_*) */
+    HRPP_ERR_UNSUPPORTED = 6      /* valid but beyond the library's compiled limits (HRPP_MAX_*) */
 } hrpp_status;
 
 /* Query paradigms (Sec. 4.1): shadow rays look for any intersection

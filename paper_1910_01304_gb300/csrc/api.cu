@@ -88,7 +88,7 @@ struct DeviceGuard {
 };
 
 // One stream-ordered memory pool per device for per-call scratch; it keeps
-// freed blocks so repeated calls do not go back to the driver.
+// freed blocks so repeated calls do not go back to the CUDA driver.
 std::mutex g_pool_mutex;
 cudaMemPool_t g_pools[64] = {};
 
