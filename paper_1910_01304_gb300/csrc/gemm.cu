@@ -118,6 +118,27 @@ cudaError_t launch(const void *a, const void *b, const umma::GemmArgs &g, int sp
     return launch_stages<BN, EPI, umma::STAGES, AMN, BMN>(a, b, g, splits, s);
 }
 
+// The persistent kernel: one CTA per SM over 128 x 256 tiles (EPI_F32,
+// K-major operands).
+cudaError_t launch_persistent(const void *a, const void *b, const umma::GemmArgs &g, cudaStream_t s)
+{
+    const size_t smem = umma::gemm_persistent_smem_bytes<>();
+    static SmemAttr attr;
+    cudaError_t e = attr.set((const void *)umma::k_gemm_persistent<>, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    CUtensorMap ma, mb;
+    e = make_map(&ma, a, (uint64_t)g.M, (uint64_t)g.K, umma::BM);
+    if (e == cudaSuccess) e = make_map(&mb, b, (uint64_t)g.N, (uint64_t)g.K, umma::PG_BN);
+    if (e != cudaSuccess) return e;
+    const int tiles = (g.M / umma::BM) * (g.N / umma::PG_BN);
+    const int grid = tiles < sms ? tiles : sms;
+    umma::k_gemm_persistent<><<<grid, umma::PG_THREADS, smem, s>>>(ma, mb, g);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 namespace {
@@ -151,6 +172,14 @@ cudaError_t softmax_xent(const void *h2, const void *w3, const umma::SoftmaxArgs
 cudaError_t softmax_argmax(const void *h2, const void *w3, const umma::SoftmaxArgs &g, cudaStream_t s)
 {
     return launch_output_layer<true>(h2, w3, g, s);
+}
+
+cudaError_t gemm_bf16_persistent(const void *a, const void *b, const umma::GemmArgs &g, cudaStream_t s)
+{
+    if (((uintptr_t)a & 15u) || ((uintptr_t)b & 15u) || ((uintptr_t)g.c32 & 31u) || g.N % umma::PG_BN != 0 ||
+        g.M % umma::BM != 0 || g.K % umma::BK != 0)
+        return cudaErrorInvalidValue;
+    return launch_persistent(a, b, g, s);
 }
 
 bool gemm_shape_ok(int m, int n, int k, int bn)
@@ -239,7 +268,14 @@ extern "C" hrpp_status hrpp_gemm_bf16_ex(const void *a, const void *b, float *c,
         g.c32 = c;
         g.m_valid = m;
         g.error = err;
-        e = hrpp::gemm_bf16(a, b, hrpp::umma::EPI_F32, bn, g, 1, (cudaStream_t)stream, layout);
+        // large K-major problems (two waves of 128 x 256 tiles or more) take
+        // the persistent kernel
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            layout == 0 && n % 256 == 0 && (m / 128) * (n / 256) >= 2 * sms)
+            e = hrpp::gemm_bf16_persistent(a, b, g, (cudaStream_t)stream);
+        else
+            e = hrpp::gemm_bf16(a, b, hrpp::umma::EPI_F32, bn, g, 1, (cudaStream_t)stream, layout);
     }
     unsigned int flag = 0;
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);

@@ -18,6 +18,10 @@ constexpr int GEMM_A_MN = 1, GEMM_B_MN = 2;
 // MN-major.
 cudaError_t gemm_bf16(const void *a, const void *b, int epi, int bn, const umma::GemmArgs &g, int splits,
                       cudaStream_t s, int layout = 0);
+// C = A B^T with the persistent kernel (EPI_F32, K-major operands, N a
+// multiple of 256): one CTA per SM walks the tiles, the epilogue of one tile
+// overlapping the MMAs of the next.
+cudaError_t gemm_bf16_persistent(const void *a, const void *b, const umma::GemmArgs &g, cudaStream_t s);
 // Fused output layer + softmax cross-entropy (umma_softmax.cuh): h2 [npad,
 // 256] and w3 [4096, 256] bf16, K-major; writes dZ (both layouts), adds the
 // loss and the labelled-row count.

@@ -85,6 +85,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     return false;
 }
 
+__device__ __forceinline__ void mbar_arrive_cta(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
 {
     asm volatile(
@@ -331,6 +336,162 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN) : "memory");
+}
+
+// Persistent form of k_gemm for large fp32-output problems (EPI_F32, both
+// operands K-major, 128 x 256 tiles): one CTA per SM walks the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...  The TMA ring and its phases run on
+// across tiles, and two TMEM accumulators of 256 columns let the epilogue of
+// one tile overlap the MMAs of the next, so the tensor pipe does not wait for
+// per-CTA set-up or for the epilogue.
+//   warp 0 lane 0   TMA producer
+//   warp 1 lane 0   MMA issuer
+//   warps 2-5       epilogue: warp w reads TMEM lanes 32 (w % 4) .. (rows)
+constexpr int PG_BN = 256;
+constexpr int PG_THREADS = 6 * 32;
+
+template <int NST = STAGES>
+constexpr size_t gemm_persistent_smem_bytes()
+{
+    return (size_t)NST * ((size_t)BM * BK * 2 + (size_t)PG_BN * BK * 2) + 1024;
+}
+
+template <int NST = STAGES>
+__global__ void __launch_bounds__(PG_THREADS, 1) k_gemm_persistent(const __grid_constant__ CUtensorMap tma_a,
+                                                                 const __grid_constant__ CUtensorMap tma_b,
+                                                                 const GemmArgs g)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[NST], empty_bar[NST], acc_full[2], acc_empty[2], drain;
+    __shared__ uint32_t tmem_base;
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr uint32_t kABytes = BM * BK * 2, kBBytes = PG_BN * BK * 2;
+    unsigned char *a_s = smem;
+    unsigned char *b_s = smem + NST * kABytes;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tiles_n = g.N / PG_BN;
+    const int n_tiles = (g.M / BM) * n_tiles_n;
+    const int n_kb = g.K / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+        }
+        mbar_init(&drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(2u * PG_BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    bool failed = false;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int i = 0, issued = 0;
+            for (int t = blockIdx.x; t < n_tiles && !failed; t += gridDim.x) {
+                const int m0 = (t / n_tiles_n) * BM, n0 = (t % n_tiles_n) * PG_BN;
+                for (int kb = 0; kb < n_kb; ++kb, ++i) {
+                    const int s = i % NST;
+                    if (!mbar_wait(&empty_bar[s], ((uint32_t)(i / NST) & 1u) ^ 1u)) {
+                        failed = true;
+                        break;
+                    }
+                    mbar_expect_tx(&full_bar[s], kABytes + kBBytes);
+                    tma_load_2d(a_s + s * kABytes, &tma_a, kb * BK, m0, &full_bar[s]);
+                    tma_load_2d(b_s + s * kBBytes, &tma_b, kb * BK, n0, &full_bar[s]);
+                    ++issued;
+                }
+            }
+            // copies still in flight after a timeout land before the CTA exits
+            if (failed)
+                for (int q = (issued > NST ? issued - NST : 0); q < issued; ++q)
+                    mbar_wait(&full_bar[q % NST], (uint32_t)(q / NST) & 1u);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = instr_desc(BM, PG_BN);
+            int i = 0, j = 0;
+            for (int t = blockIdx.x; t < n_tiles && !failed; t += gridDim.x, ++j) {
+                const int b = j & 1;
+                if (!mbar_wait(&acc_empty[b], ((uint32_t)(j >> 1) & 1u) ^ 1u)) {
+                    failed = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(b * PG_BN);
+                for (int kb = 0; kb < n_kb; ++kb, ++i) {
+                    const int s = i % NST;
+                    if (!mbar_wait(&full_bar[s], (uint32_t)(i / NST) & 1u)) {
+                        failed = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem_u32(a_s + s * kABytes), b0 = smem_u32(b_s + s * kBBytes);
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k)
+                        mma_bf16(d, smem_desc(a0 + 32u * k), smem_desc(b0 + 32u * k), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                    mma_commit(&empty_bar[s]);
+                }
+                if (failed) break;
+                mma_commit(&acc_full[b]);
+            }
+            // every MMA issued above completes before the CTA frees TMEM
+            mma_commit(&drain);
+            mbar_wait(&drain, 0);
+        }
+    } else {
+        // epilogue: warp w owns TMEM lanes 32 (w % 4) .. and those rows of each tile
+        const int q = warp & 3;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        int j = 0;
+        for (int t = blockIdx.x; t < n_tiles && !failed; t += gridDim.x, ++j) {
+            const int b = j & 1;
+            bool ok = mbar_wait(&acc_full[b], (uint32_t)(j >> 1) & 1u);
+            // tcgen05.ld is warp-collective: a warp reads TMEM only if all its lanes may
+            ok = __all_sync(0xFFFFFFFFu, ok);
+            if (!ok) {
+                failed = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int m0 = (t / n_tiles_n) * BM, n0 = (t % n_tiles_n) * PG_BN;
+            const int row = m0 + q * 32 + lane;
+            const uint32_t taddr = tmem + lane_base + (uint32_t)(b * PG_BN);
+#pragma unroll 1
+            for (int c0 = 0; c0 < PG_BN; c0 += 16) {
+                float v[16];
+                tmem_ld16(taddr + (uint32_t)c0, v);
+                if (row >= g.m_valid) continue;
+                float *dst = g.c32 + (size_t)row * g.N + n0 + c0;
+#pragma unroll
+                for (int h = 0; h < 16; h += 8) {
+                    uint32_t w[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) w[e] = __float_as_uint(v[h + e]);
+                    st_global_32b(dst + h, w);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cta(&acc_empty[b]);
+        }
+    }
+    if (failed && g.error) atomicExch(g.error, 1u);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * PG_BN) : "memory");
 }
 
 }  // namespace umma

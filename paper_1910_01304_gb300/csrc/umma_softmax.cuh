@@ -63,10 +63,6 @@ struct SoftmaxArgs {
     unsigned int *error;    // set to 1 when a bounded wait gives up
 };
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 
 // three-input maximum (one instruction); equals fmaxf twice for non-NaN inputs
 __device__ __forceinline__ float max3(float a, float b, float c)
@@ -293,7 +289,7 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
             });
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[b]);
+            if (lane == 0) mbar_arrive_cta(&acc_empty[b]);
         }
         // combine the four slices' statistics of each row; every epilogue warp
         // reaches this barrier once, also after a failed wait
@@ -366,7 +362,7 @@ __global__ void __launch_bounds__(SX_THREADS, 1) k_softmax_xent(const __grid_con
             });
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[b]);
+            if (lane == 0) mbar_arrive_cta(&acc_empty[b]);
         }
     }
     if (failed && g.error) atomicExch(g.error, 1u);

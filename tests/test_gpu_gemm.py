@@ -8,7 +8,11 @@ from gpu_util import hrpp_mod
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(128, 128, 64), (128, 256, 64), (256, 256, 128), (384, 512, 192), (128, 4096, 256), (1024, 256, 4096),
-          (256, 128, 1024)]
+          (256, 128, 1024),
+          # two waves of 128 x 256 tiles or more: the persistent kernel (one
+          # CTA per SM over the tiles, two TMEM accumulators); 624 tiles leave
+          # a partial last round
+          (4096, 4096, 512), (4992, 4096, 256)]
 
 
 @pytest.mark.parametrize("m,n,k", SHAPES)
