@@ -493,6 +493,51 @@ def test_l2_persisting_window_changes_nothing(H, small_pair, width_idx):
 
 
 @pytest.mark.parametrize("width_idx", [0, 1])
+def test_two_streams_two_tables_match_sequential(H, small_pair, width_idx):
+    """A frame's primary and shadow batches traced side by side on two
+    streams (one table each, one scene) give exactly the hits, counters and
+    table words of the same calls in sequence, frame after frame."""
+    import torch
+    s, g = small_pair[width_idx]
+    frames = []
+    for f in range(3):
+        prim = s.primary_rays(frame=f)
+        ph, _ = _oracle(s, prim, O.CLOSEST_HIT)
+        shadow, _ = W.secondary_shadow(s, prim, ph["t"], ph["prim"])
+        frames.append((torch.from_numpy(prim).cuda(), torch.from_numpy(shadow).cuda()))
+    seq = (H.Table(12, 2, 6), H.Table(12, 2, 6))
+    par = (H.Table(12, 2, 6), H.Table(12, 2, 6))
+    side = torch.cuda.Stream()
+    main = torch.cuda.current_stream()
+    for prim, shadow in frames:
+        hc, sc = H.trace(g, prim, H.HRPP_CLOSEST_HIT, seq[0], stats=True)
+        ha, sa = H.trace(g, shadow, H.HRPP_ANY_HIT, seq[1], stats=True)
+        # side by side: device stats so that neither call waits
+        st_c = torch.zeros(24, dtype=torch.int64, device="cuda")
+        st_a = torch.zeros(24, dtype=torch.int64, device="cuda")
+        oc = torch.empty_like(hc)
+        oa = torch.empty_like(ha)
+        fork = torch.cuda.Event()
+        fork.record(main)
+        side.wait_event(fork)
+        H.hrpp_trace(g.handle, par[1].handle, H._ptr(shadow), int(shadow.shape[0]), H.HRPP_ANY_HIT, H._ptr(oa),
+                     H._ptr(st_a), side.cuda_stream)
+        H.hrpp_trace(g.handle, par[0].handle, H._ptr(prim), int(prim.shape[0]), H.HRPP_CLOSEST_HIT, H._ptr(oc),
+                     H._ptr(st_c), main.cuda_stream)
+        join = torch.cuda.Event()
+        join.record(side)
+        main.wait_event(join)
+        torch.cuda.synchronize()
+        assert torch.equal(oc.view(torch.int32), hc.view(torch.int32))
+        assert torch.equal(oa, ha)
+        names = H.STAT_NAMES
+        assert [int(x) for x in st_c[:len(names)].cpu()] == [sc[n] for n in names]
+        assert [int(x) for x in st_a[:len(names)].cpu()] == [sa[n] for n in names]
+        assert np.array_equal(par[0].export(), seq[0].export())
+        assert np.array_equal(par[1].export(), seq[1].export())
+
+
+@pytest.mark.parametrize("width_idx", [0, 1])
 def test_step_budget_reports_traversal_limit(H, small_pair, width_idx):
     """Failure detection without a fault: a per-traversal step budget far
     below what the rays need stops them early.  The kernel's bounded loop sets
