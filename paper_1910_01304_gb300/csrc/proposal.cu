@@ -142,20 +142,29 @@ __global__ void __launch_bounds__(kFeatRows) k_featurize(const float4 *rays, uin
 }
 
 // out[c] += sum over rows of a bf16 [rows, cols] row-major matrix (the bias
-// gradients; cols a multiple of 256).  A block of 32 x 8 threads covers 256
-// columns and kColsumRows rows: thread (x, y) sums the 8 adjacent columns of
-// group x (one 16-byte load per row) over rows y, y + 8, ..., so each warp
-// reads 512 contiguous bytes per row; the 8 partial sums of a column meet in
-// shared memory and the block adds them with one atomic per column.
-constexpr uint32_t kColsumRows = 256;
+// gradients; cols a multiple of 256), for one or two matrices of one shape
+// (blockIdx.z picks the matrix).  A block of 32 x 8 threads covers 256
+// columns and SPAN rows (a multiple of 64): thread (x, y) sums the 8
+// adjacent columns of group x (one 16-byte load per row) over rows y, y + 8,
+// ..., so each warp reads 512 contiguous bytes per row; the 8 partial sums of
+// a column meet in shared memory and the block adds them with one atomic per
+// column.  The host picks SPAN so that the grid fills the GPU.
+struct ColsumJob {
+    const __nv_bfloat16 *a[2];
+    float *out[2];
+};
 
-__global__ void __launch_bounds__(256) k_colsum(const __nv_bfloat16 *a, uint32_t rows, uint32_t cols, float *out)
+template <uint32_t SPAN>
+__global__ void __launch_bounds__(256) k_colsum(const ColsumJob job, uint32_t rows, uint32_t cols)
 {
+    static_assert(SPAN % 64u == 0u, "whole unrolled rounds of 8 rows per thread");
     __shared__ float part[8][32 * 8 + 4];
+    const __nv_bfloat16 *a = blockIdx.z ? job.a[1] : job.a[0];
+    float *out = blockIdx.z ? job.out[1] : job.out[0];
     const uint32_t x = threadIdx.x, y = threadIdx.y;
     const uint32_t c = 8u * (blockIdx.x * 32u + x);
-    const uint32_t r0 = blockIdx.y * kColsumRows;
-    const uint32_t r1 = r0 + kColsumRows < rows ? r0 + kColsumRows : rows;
+    const uint32_t r0 = blockIdx.y * SPAN;
+    const uint32_t r1 = r0 + SPAN < rows ? r0 + SPAN : rows;
     float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     const __nv_bfloat16 *p = a + (size_t)(r0 + y) * cols + c;
 #pragma unroll 8
@@ -180,10 +189,26 @@ __global__ void __launch_bounds__(256) k_colsum(const __nv_bfloat16 *a, uint32_t
     atomicAdd(out + 8u * blockIdx.x * 32u + t, sum);
 }
 
-void colsum(const __nv_bfloat16 *a, uint32_t rows, uint32_t cols, float *out, cudaStream_t s)
+// Column sums of a (and of a2 into out2, when a2 is not null; same shape).
+// Rows per block: 256 when that still gives every SM work (a 16K x 4096
+// matrix: 1,024 blocks), else 64 (two 16K x 256 matrices: 512 blocks, where
+// 256 rows per block left most SMs idle).  A compile-time span lets the
+// row loop run as whole unrolled rounds; a runtime span measured 15 % slower
+// on the wide matrix.
+void colsum(const __nv_bfloat16 *a, uint32_t rows, uint32_t cols, float *out, int sms, cudaStream_t s,
+            const __nv_bfloat16 *a2 = nullptr, float *out2 = nullptr)
 {
-    const dim3 grid(cols / 256u, (rows + kColsumRows - 1) / kColsumRows);
-    k_colsum<<<grid, dim3(32, 8), 0, s>>>(a, rows, cols, out);
+    const uint32_t mats = a2 ? 2u : 1u;
+    const uint32_t col_blocks = cols / 256u;
+    const ColsumJob job{{a, a2 ? a2 : a}, {out, a2 ? out2 : out}};
+    const uint64_t blocks256 = (uint64_t)col_blocks * mats * ((rows + 255u) / 256u);
+    if (blocks256 >= 4ull * (uint64_t)(sms > 0 ? sms : 1)) {
+        const dim3 grid(col_blocks, (rows + 255u) / 256u, mats);
+        k_colsum<256><<<grid, dim3(32, 8), 0, s>>>(job, rows, cols);
+    } else {
+        const dim3 grid(col_blocks, (rows + 63u) / 64u, mats);
+        k_colsum<64><<<grid, dim3(32, 8), 0, s>>>(job, rows, cols);
+    }
 }
 
 // Adam on every parameter in one launch (masters laid out W1 | b1 | W2 | b2 |
@@ -242,6 +267,7 @@ __global__ void k_labels(const float4 *hits, uint32_t n, const int32_t *prim_cla
 
 struct hrpp_proposal {
     int device, width;
+    int sms;  // the device's SM count (grid sizes)
     uint32_t n_tris, n_nodes;
     float lo[3], scale[3];
     __nv_bfloat16 *sin_t;
@@ -382,7 +408,7 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     sx.error = p->err;
     if ((e = softmax_xent(H2, p->w3h, sx, s)) != cudaSuccess) return e;
     // db3 while part of the 134 MB dZ3 is still in L2
-    colsum(p->dZ3, npad, kCls, p->grad + ob3, s);
+    colsum(p->dZ3, npad, kCls, p->grad + ob3, p->sms, s);
     // the weight gradients reduce over rows: both operands MN-major
     constexpr int kMN = GEMM_A_MN | GEMM_B_MN;
     // dW3 = dZ3^T H2
@@ -418,8 +444,8 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     if ((e = gemm_bf16(p->dZ1, p->X, umma::EPI_F32_ATOMIC, 128, g, splits_for(kHid / 128, (int)npad), s, kMN)) !=
         cudaSuccess)
         return e;
-    colsum(p->dZ2, npad, kHid, p->grad + ob2, s);
-    colsum(p->dZ1, npad, kHid, p->grad + ob1, s);
+    // db2 and db1 in one launch
+    colsum(p->dZ2, npad, kHid, p->grad + ob2, p->sms, s, p->dZ1, p->grad + ob1);
     return cudaGetLastError();
 }
 
@@ -480,6 +506,11 @@ hrpp_status hrpp_proposal_create(const hrpp_scene *sc, const hrpp_bvh_node *node
     if (!p) return pfail(HRPP_ERR_OOM, "host allocation");
     p->device = sc->device;
     p->width = sc->width;
+    const cudaError_t ae = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, sc->device);
+    if (ae != cudaSuccess) {
+        delete p;
+        return pfail(HRPP_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(ae));
+    }
     p->n_tris = sc->n_tris;
     p->n_nodes = n_nodes;
     const hrpp_bvh_node &rn = nodes[root];
