@@ -284,6 +284,9 @@ struct hrpp_proposal {
     int32_t *lab;
     // inference chunk buffers (allocated on the first prediction)
     __nv_bfloat16 *Xi, *H1i, *H2i;
+    // the backward's second stream and its fork / join events
+    cudaStream_t side;
+    cudaEvent_t fork_dz3, fork_dz2, join;
 };
 
 namespace {
@@ -295,6 +298,9 @@ void proposal_free(hrpp_proposal *p)
                     p->w3h, p->X, p->H1, p->H2, p->dZ3, p->dZ2, p->dZ1, p->loss_sum, p->count, p->err, p->call_loss, p->call_count,
                     p->lab, p->Xi, p->H1i, p->H2i};
     for (void *q : ptrs) cudaFree(q);
+    if (p->side) cudaStreamDestroy(p->side);
+    for (cudaEvent_t ev : {p->fork_dz3, p->fork_dz2, p->join})
+        if (ev) cudaEventDestroy(ev);
     delete p;
 }
 
@@ -357,6 +363,55 @@ int splits_for(int m_tiles, int k)
     return s;
 }
 
+// The gradients of one minibatch from dZ3 (softmax output minus one-hot):
+// weight gradients and db3 on `side`, activation gradients and db2, db1 on
+// `s`; `side` waits for dZ2 before dW2.  The caller forks `side` from `s`
+// after dZ3 and joins it back.
+cudaError_t backward(hrpp_proposal *p, uint32_t npad, cudaStream_t s, cudaStream_t side)
+{
+    cudaError_t e;
+    umma::GemmArgs g;
+    // the weight gradients reduce over rows: both operands MN-major
+    constexpr int kMN = GEMM_A_MN | GEMM_B_MN;
+    // side: db3, then dW3 = dZ3^T H2
+    colsum(p->dZ3, npad, kCls, p->grad + ob3, p->sms, side);
+    g = args(kCls, kHid, (int)npad, p);
+    g.c32 = p->grad + oW3;
+    if ((e = gemm_bf16(p->dZ3, p->H2, umma::EPI_F32_ATOMIC, 256, g, splits_for(kCls / 128, (int)npad), side, kMN)) !=
+        cudaSuccess)
+        return e;
+    // s: dZ2 = (dZ3 W3) * (H2 > 0); B = W3 stored [4096, 256]: read MN-major
+    g = args((int)npad, kHid, kCls, p);
+    g.act = p->H2;
+    g.c16 = p->dZ2;
+    if ((e = gemm_bf16(p->dZ3, p->w3h, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid, kCls), g, 1, s, GEMM_B_MN)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaEventRecord(p->fork_dz2, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(side, p->fork_dz2, 0)) != cudaSuccess) return e;
+    // side: dW2 = dZ2^T H1
+    g = args(kHid, kHid, (int)npad, p);
+    g.c32 = p->grad + oW2;
+    if ((e = gemm_bf16(p->dZ2, p->H1, umma::EPI_F32_ATOMIC, 256, g, splits_for(kHid / 128, (int)npad), side, kMN)) !=
+        cudaSuccess)
+        return e;
+    // s: dZ1 = (dZ2 W2) * (H1 > 0)
+    g = args((int)npad, kHid, kHid, p);
+    g.act = p->H1;
+    g.c16 = p->dZ1;
+    if ((e = gemm_bf16(p->dZ2, p->w2h, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid, kHid), g, 1, s, GEMM_B_MN)) !=
+        cudaSuccess)
+        return e;
+    // s: dW1 = dZ1^T X, then db2 and db1 in one launch
+    g = args(kHid, kIn, (int)npad, p);
+    g.c32 = p->grad + oW1;
+    if ((e = gemm_bf16(p->dZ1, p->X, umma::EPI_F32_ATOMIC, 128, g, splits_for(kHid / 128, (int)npad), s, kMN)) !=
+        cudaSuccess)
+        return e;
+    colsum(p->dZ2, npad, kHid, p->grad + ob2, p->sms, s, p->dZ1, p->grad + ob1);
+    return cudaGetLastError();
+}
+
 // forward (and, when train, the backward into p->grad) on rows [0, n) of
 // rays, padded to npad rows; labels (device) when train
 cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const int32_t *labels, bool train,
@@ -407,46 +462,19 @@ cudaError_t run_batch(hrpp_proposal *p, const hrpp_ray *rays, uint32_t n, const 
     sx.count = p->count;
     sx.error = p->err;
     if ((e = softmax_xent(H2, p->w3h, sx, s)) != cudaSuccess) return e;
-    // db3 while part of the 134 MB dZ3 is still in L2
-    colsum(p->dZ3, npad, kCls, p->grad + ob3, p->sms, s);
-    // the weight gradients reduce over rows: both operands MN-major
-    constexpr int kMN = GEMM_A_MN | GEMM_B_MN;
-    // dW3 = dZ3^T H2
-    g = args(kCls, kHid, (int)npad, p);
-    g.c32 = p->grad + oW3;
-    if ((e = gemm_bf16(p->dZ3, p->H2, umma::EPI_F32_ATOMIC, 256, g, splits_for(kCls / 128, (int)npad), s, kMN)) !=
-        cudaSuccess)
-        return e;
-    // dZ2 = (dZ3 W3) * (H2 > 0)
-    g = args((int)npad, kHid, kCls, p);
-    g.act = p->H2;
-    g.c16 = p->dZ2;
-    // B = W3 stored [4096, 256]: read MN-major
-    if ((e = gemm_bf16(p->dZ3, p->w3h, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid, kCls), g, 1, s, GEMM_B_MN)) !=
-        cudaSuccess)
-        return e;
-    // dW2 = dZ2^T H1
-    g = args(kHid, kHid, (int)npad, p);
-    g.c32 = p->grad + oW2;
-    if ((e = gemm_bf16(p->dZ2, p->H1, umma::EPI_F32_ATOMIC, 256, g, splits_for(kHid / 128, (int)npad), s, kMN)) !=
-        cudaSuccess)
-        return e;
-    // dZ1 = (dZ2 W2) * (H1 > 0)
-    g = args((int)npad, kHid, kHid, p);
-    g.act = p->H1;
-    g.c16 = p->dZ1;
-    if ((e = gemm_bf16(p->dZ2, p->w2h, umma::EPI_RELU_GRAD, tile_n((int)npad, kHid, kHid), g, 1, s, GEMM_B_MN)) !=
-        cudaSuccess)
-        return e;
-    // dW1 = dZ1^T X
-    g = args(kHid, kIn, (int)npad, p);
-    g.c32 = p->grad + oW1;
-    if ((e = gemm_bf16(p->dZ1, p->X, umma::EPI_F32_ATOMIC, 128, g, splits_for(kHid / 128, (int)npad), s, kMN)) !=
-        cudaSuccess)
-        return e;
-    // db2 and db1 in one launch
-    colsum(p->dZ2, npad, kHid, p->grad + ob2, p->sms, s, p->dZ1, p->grad + ob1);
-    return cudaGetLastError();
+    // The backward on two streams.  dZ3 feeds db3, dW3 and dZ2; dZ2 feeds dW2
+    // and dZ1.  The weight gradients (and db3) go to p->side while the
+    // activation gradients stay on s, so each pair shares the SMs (a 128-CTA
+    // GEMM alone leaves 24 of 152 idle) and reads its common input once from
+    // HBM while the other still finds it in L2.  The join comes before the
+    // call returns, on every path, so that s orders everything after it.
+    if ((e = cudaEventRecord(p->fork_dz3, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(p->side, p->fork_dz3, 0)) != cudaSuccess) return e;
+    e = backward(p, npad, s, p->side);
+    const cudaError_t ej = cudaEventRecord(p->join, p->side);
+    const cudaError_t ew = ej == cudaSuccess ? cudaStreamWaitEvent(s, p->join, 0) : ej;
+    if (e != cudaSuccess) return e;
+    return ew != cudaSuccess ? ew : cudaGetLastError();
 }
 
 cudaError_t adam(hrpp_proposal *p, float lr, cudaStream_t s)
@@ -594,6 +622,9 @@ hrpp_status hrpp_proposal_create(const hrpp_scene *sc, const hrpp_bvh_node *node
     alloc(&p->call_loss, 4);
     alloc(&p->call_count, 4);
     alloc(&p->lab, rows * 4);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&p->fork_dz3, &p->fork_dz2, &p->join})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemcpy(p->sin_t, sin_h.data(), 65536 * 2, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->class_node, p->h_class_node.data(), kCls * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->prim_class, prim_class.data(), (size_t)sc->n_tris * 4, cudaMemcpyHostToDevice);
