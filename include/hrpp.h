@@ -436,8 +436,8 @@ hrpp_status hrpp_proposal_labels(hrpp_proposal *p, const hrpp_hit *hits, uint32_
  * taken before its own step (the call then waits); 0 if none was labelled.
  * Each minibatch's backward pass forks onto a stream the network owns and
  * joins `stream` again before its Adam step, so the call is ordered on
- * `stream` like a single-stream one (and may be captured in a graph).
- * Calls on one network must not run concurrently. */
+ * `stream` like a single-stream one.  Calls on one network must not run
+ * concurrently. */
 hrpp_status hrpp_proposal_train(hrpp_proposal *p, const hrpp_ray *rays, const int32_t *labels, uint32_t n, float lr,
                                 float *out_mean_loss, void *stream);
 /* Loss and gradients of one batch (n <= 16384) without updating: host_grads
