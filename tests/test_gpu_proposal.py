@@ -267,3 +267,48 @@ def test_train_loss_covers_every_minibatch(env):
         total += l * k
         count += k
     assert loss == pytest.approx(total / count, rel=2e-3)
+
+
+def test_adam_steps_follow_the_update_rule(env):
+    """Two train calls of one minibatch each move every weight as Adam with
+    bias correction does (beta1 0.9, beta2 0.999, eps 1e-8; Kingma and Ba's
+    update) on the gradients that hrpp_proposal_gradients reports at the same
+    weights.  The first step has a closed form, -lr g / (|g| + eps): lr against
+    the sign of every gradient clear of zero.  Gradients are recomputed inside
+    the train call with fp32 atomics in another order, so the check keeps to
+    entries whose gradients are far from zero (relative noise ~1e-6); every
+    other entry moves by no more than Adam's bound on a step."""
+    import torch
+    H, s, g, prop = env
+    w0 = P.Weights.random(23, scale=0.4).flat()
+    rays = torch.from_numpy(_rays(s, 3000, seed=5)).cuda()
+    labels = torch.from_numpy(np.random.default_rng(6).integers(0, 4096, 3000).astype(np.int32)).cuda()
+    lr = 1e-3
+    prop.set_weights(w0)
+    _, g1 = prop.gradients(rays, labels)
+    prop.train(rays, labels, lr=lr)
+    w1 = prop.get_weights()
+    _, g2 = prop.gradients(rays, labels)
+    prop.train(rays, labels, lr=lr)
+    w2 = prop.get_weights()
+    ga, gb = g1.astype(np.float64), g2.astype(np.float64)
+    step1 = -lr * ga / (np.abs(ga) + 1e-8)
+    m = 0.09 * ga + 0.1 * gb
+    v = 0.999 * 0.001 * ga * ga + 0.001 * gb * gb
+    step2 = -lr * (m / (1 - 0.9 ** 2)) / (np.sqrt(v / (1 - 0.999 ** 2)) + 1e-8)
+    off = 0
+    for k, shape in P.Weights.SHAPES:
+        n = int(np.prod(shape))
+        sl = slice(off, off + n)
+        off += n
+        big = lambda x: np.abs(x) > max(1e-4 * np.abs(x).max(), 1e-6)
+        keep1, keep2 = big(ga[sl]), big(ga[sl]) & big(gb[sl])
+        assert keep1.mean() > 0.25 and keep2.mean() > 0.25, (k, keep1.mean(), keep2.mean())
+        d1 = w1[sl].astype(np.float64) - w0[sl]
+        d2 = w2[sl].astype(np.float64) - w1[sl]
+        tol = 1e-3 * lr + 1e-7
+        assert np.abs(d1 - step1[sl])[keep1].max() < tol, k
+        assert np.abs(d2 - step2[sl])[keep2].max() < tol, k
+        # |m_hat| / sqrt(v_hat) <= 1 at step 1 and <= 1.0014 at step 2 (Cauchy-Schwarz)
+        assert np.abs(d1).max() <= lr * 1.0001 + 1e-7 and np.abs(d2).max() <= lr * 1.002 + 1e-7, k
+    assert off == len(w0)
