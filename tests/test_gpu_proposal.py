@@ -216,13 +216,17 @@ def test_predictions_across_inference_chunks(env):
     assert np.array_equal(nodes.cpu().numpy(), to_node[classes])
 
 
-def test_gradients_of_a_ragged_batch(env):
-    """9,000 rays (70 full 128-row tiles and a tail of 40)."""
+@pytest.mark.parametrize("n", [9000, 16384])
+def test_gradients_of_a_ragged_batch(env, n):
+    """9,000 rays (70 full 128-row tiles and a tail of 40), and a full
+    16,384-row minibatch: the size at which the 4096-column bias gradient
+    takes 256 rows per block and the weight gradients their full split-K
+    grids."""
     import torch
     H, s, g, prop = env
     w = P.Weights.random(17, scale=0.4)
     prop.set_weights(w.flat())
-    rays = _many_rays(s, 9000, 6)
+    rays = _many_rays(s, n, 6)
     labels = np.random.default_rng(7).integers(-1, 4096, len(rays)).astype(np.int32)
     loss_g, grads = prop.gradients(torch.from_numpy(rays).cuda(), torch.from_numpy(labels).cuda())
     lo, hi = _box(s)
