@@ -64,9 +64,13 @@ typedef enum { HRPP_ANY_HIT = 0, HRPP_CLOSEST_HIT = 1 } hrpp_mode;
  *              when the call started; after the batch, each slot keeps the
  *              insert of the highest ray index aimed at it.  Deterministic:
  *              results, table and statistics repeat bit for bit.
- *   ONLINE     inserts are written while the batch runs (64-bit atomic
- *              exchange), so later rays may see them.  Results stay exact;
- *              table contents and statistics depend on scheduling.
+ *   ONLINE     inserts are written while the batch runs, so later rays may
+ *              see them: a 64-bit compare-and-swap claims the set's first
+ *              empty way or, with every way valid, replaces way (ray index
+ *              mod ways); a CAS beaten by another ray re-reads the set (at
+ *              most 4 attempts, then the insert is dropped as a duplicate).
+ *              Results stay exact; table contents and statistics depend on
+ *              scheduling, except when no two rays of a call share a set.
  *   FROZEN     lookups only; the table is never written. */
 typedef enum { HRPP_UPDATE_TWO_PHASE = 0, HRPP_UPDATE_ONLINE = 1, HRPP_UPDATE_FROZEN = 2 } hrpp_update_mode;
 
@@ -109,8 +113,8 @@ typedef struct hrpp_hit {
  *                     a closer hit than the predicted leaves (Sec. 4.3)
  *   inserts           rays that asked to insert the leaf they reached
  *   dup_inserts       two-phase: inserts that lost their slot to a later ray
- *                     of the same batch; online: inserts of a value the slot
- *                     already held
+ *                     of the same batch; online: inserts whose word another
+ *                     ray of the call stored first, or that lost 4 CAS tries
  *   evictions         inserts that overwrote a valid table word
  *   interior_nodes,   interior nodes entered, child boxes tested, leaves
  *   box_tests,        entered and triangles tested by traversal
@@ -354,7 +358,12 @@ hrpp_status hrpp_l2_set_aside(size_t bytes, size_t *granted);
  *     call's contents (each call clears the control block it needs): calls
  *     whose work overlaps on the GPU, e.g. on two streams, race; order them,
  *     for instance on one stream.
- * Results, statistics and table updates equal hrpp_trace's. */
+ *   - The array's address is kept for the life of the device's context.
+ *     cudaDeviceReset ends that context and every scene and table with it:
+ *     the library is not used across a reset.
+ * Results, statistics, table updates and the returned status equal
+ * hrpp_trace's: with host out_stats the call waits, and a ray stopped early
+ * returns HRPP_ERR_TRAVERSAL_LIMIT (clearing the scene's flag). */
 #define HRPP_NOALLOC_MAX_RAYS (1u << 20)
 hrpp_status hrpp_trace_noalloc(const hrpp_scene *scene, hrpp_table *table, const hrpp_ray *rays, uint32_t n_rays,
                                hrpp_mode mode, void *out_hits, hrpp_stats *out_stats, void *stream);

@@ -22,7 +22,7 @@ _lock = threading.Lock()
 _lib = None
 
 ANY_HIT, CLOSEST_HIT = 0, 1
-TWO_PHASE, SEQUENTIAL, UNBOUNDED = 0, 1, 2
+TWO_PHASE, SEQUENTIAL, UNBOUNDED, ONLINE = 0, 1, 2, 3
 VERIFY_ROOT, VERIFY_BOTTOM_UP, VERIFY_NONE = 0, 1, 2
 HASH_EXP_MSB, HASH_EXP_LSB = 0, 1
 NO_HIT = 0xFFFFFFFF

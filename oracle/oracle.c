@@ -69,7 +69,11 @@ typedef struct {
 } orc_scene;
 
 enum { ORC_ANY = 0, ORC_CLOSEST = 1 };
-enum { ORC_TWO_PHASE = 0, ORC_SEQUENTIAL = 1, ORC_UNBOUNDED = 2 };
+/* when and where inserts land: after the batch (two-phase), before the next
+ * ray in the leaf's hashed way (sequential), in the unbounded map, or before
+ * the next ray in the set's first empty way, else way (ray index mod W)
+ * (online: the GPU's compare-and-swap placement, without its races) */
+enum { ORC_TWO_PHASE = 0, ORC_SEQUENTIAL = 1, ORC_UNBOUNDED = 2, ORC_ONLINE = 3 };
 /* how a closest-hit true positive is verified: a traversal from the root
  * bounded by the predicted hit, a climb from the predicted leaf testing the
  * siblings on the way up, or not at all (the paper's semantics, Sec. 4.3:
@@ -630,7 +634,9 @@ static const orc_node *find_leaf(const orc_scene *sc, uint32_t leaf)
  *      highest ray index targeting a slot wins it after the batch; a record
  *      that loses counts as dup_inserts, a winner that overwrites a valid
  *      word as an eviction.  Sequential: each insert lands before the next
- *      ray.  Unbounded: the leaf is appended to the key's list.
+ *      ray.  Online: each insert lands before the next ray, in the set's
+ *      first empty way, else in way (ray index mod W) as an eviction.
+ *      Unbounded: the leaf is appended to the key's list.
  * out: closest -> 4 words per ray (t, prim, u, v); any -> prim or NO_HIT.
  * outcome (optional): OUT_* code per ray.  ray_box_tests (optional): box tests
  * each ray's traversal made.  Returns 0, or 1 on bad arguments / no memory.
@@ -757,6 +763,16 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
                             if (old == value) stats[S_DUP_INSERTS] += 1;
                             else if (old != EMPTY_WORD) stats[S_EVICTIONS] += 1;
                             tab->words[slot] = value;
+                        } else if (tab->update_mode == ORC_ONLINE) {
+                            /* the set's first empty way; with none, way (i mod W) */
+                            uint64_t *sw = tab->words + set * ways;
+                            uint32_t k = 0;
+                            while (k < ways && sw[k] != EMPTY_WORD) ++k;
+                            if (k == ways) {
+                                k = i & (ways - 1u);
+                                stats[S_EVICTIONS] += 1;
+                            }
+                            sw[k] = value;
                         } else {
                             recs[n_recs].slot = slot;
                             recs[n_recs].value = value;

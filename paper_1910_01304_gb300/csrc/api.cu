@@ -19,26 +19,29 @@
 
 using namespace hrpp;
 
-cudaError_t hrpp::device_malloc(void **ptr, size_t bytes)
+bool hrpp::allocation_refused()
 {
     static std::mutex mu;
     static std::string seen;
     static long long made = 0;
     const char *v = std::getenv("HRPP_FAIL_ALLOC_AFTER");
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        if (!v || !*v) {
-            seen.clear();  // unset: the next value counts from zero
-        } else {
-            if (seen != v) {
-                seen = v;
-                made = 0;
-            }
-            if (made++ >= std::atoll(v)) {
-                *ptr = nullptr;
-                return cudaErrorMemoryAllocation;
-            }
-        }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!v || !*v) {
+        seen.clear();  // unset: the next value counts from zero
+        return false;
+    }
+    if (seen != v) {
+        seen = v;
+        made = 0;
+    }
+    return made++ >= std::atoll(v);
+}
+
+cudaError_t hrpp::device_malloc(void **ptr, size_t bytes)
+{
+    if (allocation_refused()) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
     }
     return cudaMalloc(ptr, bytes);
 }
@@ -649,6 +652,7 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
     const size_t hit_off = off;
     if (hits_host) off += (hit_bytes + 255) & ~size_t(255);
     char *scratch = nullptr;
+    if (allocation_refused()) return cuda_fail(cudaErrorMemoryAllocation, "scratch allocation (injected)");
     if ((e = cudaMallocFromPoolAsync((void **)&scratch, off, pool, stream)) != cudaSuccess)
         return cuda_fail(e, "scratch allocation");
     Ctl *ctl = reinterpret_cast<Ctl *>(scratch + ctl_off);

@@ -10,10 +10,13 @@
 #include "hrpp.h"
 
 namespace hrpp {
-// cudaMalloc with host-side fault injection for tests: while the environment
-// holds HRPP_FAIL_ALLOC_AFTER=N, the allocations after the first N made since
-// that value was set fail with cudaErrorMemoryAllocation (nothing is
-// allocated).  Every object-creating entry point allocates through it.
+// Host-side fault injection for tests: while the environment holds
+// HRPP_FAIL_ALLOC_AFTER=N, every device allocation after the first N made
+// since that value was set is refused (true: fail it, allocate nothing).
+// device_malloc (every object-creating entry point) and hrpp_trace's per-call
+// scratch consult it; hrpp_trace_noalloc allocates nothing and never does.
+bool allocation_refused();
+// cudaMalloc unless allocation_refused(), then cudaErrorMemoryAllocation.
 cudaError_t device_malloc(void **ptr, size_t bytes);
 
 // Names an entry point's host-side span in profiler timelines (NVTX; a no-op

@@ -47,7 +47,10 @@ hrpp_status noalloc_fail(hrpp_status s, const char *fmt, ...)
 
 // Device address of the scratch array on the current device.  Host code only
 // sees a host-side stand-in under the array's name, so the address has to be
-// asked for once per device, with that device current.
+// asked for once per device, with that device current.  The cached address
+// lives as long as the device's context: cudaDeviceReset ends the context
+// (and with it every scene and table of this library), so the library is
+// not used across a reset.
 cudaError_t scratch_on(int dev, unsigned char **out)
 {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
@@ -182,6 +185,21 @@ extern "C" hrpp_status hrpp_trace_noalloc(const hrpp_scene *sc, hrpp_table *tabl
             if (e == cudaSuccess && stats_host) e = cudaStreamSynchronize(stream);
             if (e != cudaSuccess) {
                 status = noalloc_fail(HRPP_ERR_CUDA, "stats copy: %s", cudaGetErrorString(e));
+                break;
+            }
+        }
+        if (stats_host) {
+            // the call has waited: report a ray stopped early exactly as
+            // hrpp_trace does, and clear the scene's flag (a plain copy into a
+            // host variable and a memset allocate nothing)
+            uint32_t flag = 0;
+            if ((e = cudaMemcpy(&flag, sc->d_error, sizeof flag, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+                status = noalloc_fail(HRPP_ERR_CUDA, "reading the error flag: %s", cudaGetErrorString(e));
+                break;
+            }
+            if (flag) {
+                cudaMemset(sc->d_error, 0, sizeof(uint32_t));
+                status = noalloc_fail(HRPP_ERR_TRAVERSAL_LIMIT, "a ray was stopped early (flag %u)", flag);
                 break;
             }
         }

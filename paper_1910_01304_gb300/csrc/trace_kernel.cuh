@@ -15,7 +15,7 @@
 //      stack lives in local memory (HRPP_MAX_STACK entries).
 //   4. A ray whose traversal produced its final hit inserts that hit's leaf:
 //      two-phase mode records it (atomicMax on the slot's winner + a record
-//      appended with one atomic per warp); online mode exchanges the word.
+//      appended with one atomic per warp); online mode claims a way by CAS.
 //
 // Two schedules over the ray pool (Ctl::next_ray), identical per-ray work:
 //   k_trace      a warp takes 32 rays, traces them to completion, repeats.
@@ -379,8 +379,51 @@ __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayS
     return traverse;
 }
 
+// Online insert (Sec. 5: the node a conflicting ray reached joins its entry,
+// with no duplicate nodes): a 64-bit compare-and-swap claims the set's first
+// empty way or, with every way valid, replaces way (ray mod W).  A CAS that
+// another ray beat re-reads the set, and finding its own word there makes it
+// a duplicate.  After kOnlineTries lost attempts the insert is dropped and
+// counted as a duplicate; results never depend on the table's contents.
+constexpr int kOnlineTries = 4;
+
+template <bool STATS>
+__device__ __forceinline__ void online_insert(const TraceParams &p, uint32_t set, uint32_t ray, uint64_t word,
+                                              Counters<STATS> &cnt)
+{
+    unsigned long long *base = reinterpret_cast<unsigned long long *>(p.table) + ((uint64_t)set << p.log2_ways);
+    const uint32_t ways = 1u << p.log2_ways;
+    for (int attempt = 0; attempt < kOnlineTries; ++attempt) {
+        uint32_t target = ways;
+        for (uint32_t k = 0; k < ways; ++k) {
+            const unsigned long long wd = __ldcg(base + k);
+            if (wd == word) {
+                cnt.add(ST_DUP_INSERTS);
+                return;
+            }
+            if (wd == HRPP_EMPTY_WORD && target == ways) target = k;
+        }
+        unsigned long long expected = HRPP_EMPTY_WORD;
+        if (target == ways) {
+            target = ray & (ways - 1u);
+            expected = __ldcg(base + target);
+            if (expected == HRPP_EMPTY_WORD) continue;  // emptied meanwhile: rescan
+        }
+        const unsigned long long old = atomicCAS(base + target, expected, (unsigned long long)word);
+        if (old == expected) {
+            if (expected != HRPP_EMPTY_WORD) cnt.add(ST_EVICTIONS);
+            return;
+        }
+        if (old == word) {
+            cnt.add(ST_DUP_INSERTS);
+            return;
+        }
+    }
+    cnt.add(ST_DUP_INSERTS);
+}
+
 // Writes ray i's result and decides its insert (two-phase: returns the record
-// to append; online: exchanges the word now).
+// to append; online: inserts the word now).
 template <bool CLOSEST, bool STATS>
 __device__ __forceinline__ bool finish_ray(const TraceParams &p, uint32_t i, const RayState &s, Counters<STATS> &cnt,
                                            uint32_t &slot, uint64_t &word)
@@ -412,13 +455,11 @@ __device__ __forceinline__ bool finish_ray(const TraceParams &p, uint32_t i, con
             present |= (p.update_mode == HRPP_UPDATE_ONLINE ? __ldcg(set + k) : __ldg(set + k)) == w;
         if (storable && !present) {
             cnt.add(ST_INSERTS);
-            slot = (s.set << p.log2_ways) | way_of(node, p.log2_ways);
             word = w;
             if (p.update_mode == HRPP_UPDATE_ONLINE) {
-                const unsigned long long old = atomicExch(reinterpret_cast<unsigned long long *>(p.table + slot), word);
-                if (old == word) cnt.add(ST_DUP_INSERTS);
-                else if (old != HRPP_EMPTY_WORD) cnt.add(ST_EVICTIONS);
+                online_insert(p, s.set, i, word, cnt);
             } else {
+                slot = (s.set << p.log2_ways) | way_of(node, p.log2_ways);
                 want_record = true;  // append_records claims the slot
             }
         }

@@ -157,6 +157,50 @@ def test_online_mode_is_exact(H, small_pair, mode):
     assert st["true_pos"] > 0
 
 
+def _one_ray_per_set(rays, p, log2_sets, batch):
+    """Splits rays into batches in which no two rays share a table set (keys
+    and sets from the oracle's Sec. 5 hash and index)."""
+    sets = np.array([O.set_and_tag(O.ray_key(r, p), log2_sets)[0] for r in rays])
+    out, cur, used = [], [], set()
+    for i, st in enumerate(sets):
+        if st in used:
+            continue
+        cur.append(i)
+        used.add(st)
+        if len(cur) == batch:
+            out.append(rays[cur])
+            cur, used = [], set()
+    return out
+
+
+@pytest.mark.parametrize("mode", [O.CLOSEST_HIT, O.ANY_HIT])
+@pytest.mark.parametrize("width_idx", [0, 1])
+def test_online_insert_matches_oracle_without_races(H, small_pair, mode, width_idx):
+    """Online mode's compare-and-swap insert (the set's first empty way, else
+    way ray mod W): in batches where no two rays share a set no insert races,
+    so hits, every counter and every table word equal the oracle's online
+    mode over batch after batch, through fills and evictions."""
+    s, g = small_pair[width_idx]
+    log2_entries, ways = 10, 4
+    tab = H.Table(log2_entries, ways, 6, H.HRPP_UPDATE_ONLINE)
+    otab = O.Table(log2_entries, ways, 6, O.ONLINE)
+    pool = np.concatenate([s.primary_rays(frame=f)[::5] for f in range(3)])
+    if mode == O.ANY_HIT:
+        h, _ = _oracle(s, pool, O.CLOSEST_HIT)
+        pool, _ = W.secondary_shadow(s, pool, h["t"], h["prim"])
+    batches = _one_ray_per_set(pool, 6, log2_entries - 2, 200)[:30]
+    assert len(batches) >= 8
+    evictions = 0
+    for k, rays in enumerate(batches):
+        oh, ost = _oracle(s, rays, mode, otab)
+        gh, gst = gpu_trace(H, g, rays, mode, tab)
+        assert_same_hits(mode, gh, oh, f"batch {k}")
+        assert_same_stats(gst, ost, msg=f"batch {k}")
+        assert np.array_equal(tab.export(), otab.words), f"batch {k}: table words differ"
+        evictions += gst["evictions"]
+    assert evictions > 0
+
+
 def test_frozen_mode_never_writes(H, small_pair):
     s, g = small_pair[0]
     tab = H.Table(12, 1, 6)

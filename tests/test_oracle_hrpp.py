@@ -140,6 +140,78 @@ def test_single_key_direct_mapped_winner_and_reuse(small):
     assert s2["positives"] == n and s2["pred_leaves"] == n
 
 
+def _online_rays(small, n, seed):
+    """Camera rays toward random points of the small scene: nearly all hit,
+    and they spread over many leaves and keys."""
+    rng = np.random.default_rng(seed)
+    o = np.array([0.0, 2.5, 6.0])
+    tgt = np.stack([rng.uniform(-3.5, 3.5, n), rng.uniform(0.0, 1.5, n), rng.uniform(-3.5, 3.5, n)], 1)
+    d = tgt - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    rays = np.zeros((n, 8), np.float32)
+    rays[:, 0:3], rays[:, 4:7], rays[:, 7] = o, d, np.inf
+    return rays
+
+
+def _word_of(small, ray, p, log2_sets, leaf_of):
+    """The table word ray `ray` inserts, from independent pieces: its key
+    (Sec. 5 hash, pinned by worked values), the leaf holding its brute-force
+    closest hit (found by walking the BVH's leaves) and the set/tag split."""
+    key = O.ray_key(ray, p)
+    _, tag = O.set_and_tag(key, log2_sets)
+    hb, _ = O.brute(ray[None], small.tris, O.CLOSEST_HIT)
+    prim = int(hb["prim"][0])
+    return None if prim == O.NO_HIT else (tag << O.LEAF_BITS) | leaf_of[prim]
+
+
+def test_online_fills_empty_ways_then_evicts(small):
+    """Online mode, one set of four ways (every ray maps to it): inserts fill
+    the empty ways first, every later insert evicts exactly one word, a set
+    never holds a word twice (Sec. 5), and results are plain's."""
+    tab = O.Table(2, 4, 6, O.ONLINE)
+    rays = _online_rays(small, 300, seed=5)
+    hp, _ = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.CLOSEST_HIT)
+    hh, st = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.CLOSEST_HIT, tab)
+    assert np.array_equal(hp, hh)
+    assert st["inserts"] > 50
+    assert st["evictions"] == st["inserts"] - 4
+    assert st["dup_inserts"] == 0
+    assert np.all(tab.words != np.uint64(O.EMPTY_WORD))
+    assert len(set(tab.words.tolist())) == 4
+
+
+def test_online_full_set_replaces_the_way_of_the_ray_index(small):
+    """When a set is full, the insert of the call's ray i replaces way
+    (i mod W): single-ray calls only ever rewrite way 0, and a four-ray call
+    whose rays all insert leaves way k holding ray k's word, built from the
+    ray's key and the leaf of its brute-force hit."""
+    leaf_of = _leaf_of_prim(small.nodes, small.prim_index)
+    tab = O.Table(2, 4, 6, O.ONLINE)
+    rays = _online_rays(small, 400, seed=6)
+    filled = None
+    for k in range(200):
+        _, st = O.trace(small.tris, small.nodes, small.prim_index, 0, rays[k:k + 1], O.CLOSEST_HIT, tab)
+        if filled is None:
+            if np.all(tab.words != np.uint64(O.EMPTY_WORD)):
+                filled = tab.words.copy()
+            continue
+        assert np.array_equal(tab.words[1:], filled[1:]), k
+    assert filled is not None
+    # a batch of four inserting rays (distinct words, none already present)
+    present = set(tab.words.tolist())
+    batch, words = [], []
+    for r in rays[200:]:
+        w = _word_of(small, r, 6, 0, leaf_of)
+        if w is not None and w not in present and w not in words:
+            batch.append(r)
+            words.append(w)
+        if len(batch) == 4:
+            break
+    _, st = O.trace(small.tris, small.nodes, small.prim_index, 0, np.array(batch), O.CLOSEST_HIT, tab)
+    assert st["inserts"] == 4 and st["evictions"] == 4
+    assert tab.words.tolist() == words
+
+
 def test_two_phase_vs_sequential_within_a_batch(small):
     """Two-phase lookups see the table as it was at batch start; sequential
     lookups see earlier rays' inserts."""
