@@ -123,13 +123,15 @@ typedef struct hrpp_hit {
  *   pred_tri_tests    subtrees, before (or instead of) traversal from the root
  *   pred_interior_nodes, pred_box_tests
  *                     interior nodes entered and child boxes tested inside
- *                     predicted subtrees (Go Up Level > 0, Sec. 6.2) */
+ *                     predicted subtrees (Go Up Level > 0, Sec. 6.2)
+ *   gated             rays that skipped the table because its gate was
+ *                     closed (hrpp_table_set_gate): no lookup, no insert */
 typedef struct hrpp_stats {
     uint64_t rays, hits, lookups, positives, true_pos, false_pos, negatives, tp_inexact;
     uint64_t inserts, dup_inserts, evictions;
     uint64_t interior_nodes, box_tests, leaves, tri_tests, pred_leaves, pred_tri_tests;
     uint64_t pred_interior_nodes, pred_box_tests;
-    uint64_t reserved[1];
+    uint64_t gated;
 } hrpp_stats;
 
 typedef struct hrpp_scene_info {
@@ -285,6 +287,24 @@ hrpp_status hrpp_table_set_go_up(hrpp_table *table, int go_up_level);
 #define HRPP_HASH_EXP_MSB 0
 #define HRPP_HASH_EXP_LSB 1
 hrpp_status hrpp_table_set_hash(hrpp_table *table, int hash_variant);
+/* Gate: lets a table stop predicting while its predictions do not pay (the
+ * paper's predictor is always consulted; this is a policy on top of it, with
+ * no counterpart in the paper).  min_tp_per_65536 == 0 (the default) turns
+ * the gate off: every ray consults the table.  Otherwise the gate starts
+ * open, and after each hrpp_trace / batch run it is set from that call alone:
+ * open iff its true positives reach min_tp_per_65536 / 65536 of the rays
+ * that consulted the table (a call in which none did leaves it as it was).
+ * While it is closed, only the rays of every 2^sample_log2-th 32-ray chunk
+ * (rays i with ((i >> 5) mod 2^sample_log2) == 0) consult and update the
+ * table; every other ray traverses from the root with no lookup and no
+ * insert and is counted in hrpp_stats.gated.  Results stay exact, and the
+ * gate is deterministic: it depends only on the calls' rays and table.
+ * sample_log2 in [0, 20] (default 5), else INVALID_ARG.  Blocking; opens
+ * the gate.  hrpp_table_reset, hrpp_table_import and hrpp_table_set_gate
+ * open it; hrpp_table_copy copies it. */
+hrpp_status hrpp_table_set_gate(hrpp_table *table, uint32_t min_tp_per_65536, int sample_log2);
+/* *open = 1 if the table's gate is open (always, without a gate).  Blocking. */
+hrpp_status hrpp_table_get_gate(const hrpp_table *table, int *open);
 /* Empties the table (asynchronous on stream) and unbinds it from its scene.
  * A table binds to the first scene it is traced with; tracing it with
  * another scene returns INVALID_ARG until it is reset. */
@@ -294,7 +314,7 @@ hrpp_status hrpp_table_reset(hrpp_table *table, void *stream);
  * words' leaves: import only tables exported from the same scene. */
 hrpp_status hrpp_table_export(const hrpp_table *table, uint64_t *host_words, size_t n_words);
 hrpp_status hrpp_table_import(hrpp_table *table, const uint64_t *host_words, size_t n_words);
-/* Device-to-device copy of src's words into dst, asynchronous on `stream`
+/* Device-to-device copy of src's words (and gate state) into dst, asynchronous on `stream`
  * (e.g. to restore a warm snapshot before each frame without a host round
  * trip).  Both tables must be on the same device with the same
  * log2_entries, ways, precision, Go Up Level and hash variant, else

@@ -32,7 +32,7 @@ HIT_DTYPE = np.dtype([("t", "<f4"), ("prim", "<u4"), ("u", "<f4"), ("v", "<f4")]
 OUTCOME = {0: "plain", 1: "negative", 2: "false_pos", 3: "true_pos"}
 STAT_NAMES = ["rays", "hits", "lookups", "positives", "true_pos", "false_pos", "negatives", "tp_inexact",
               "inserts", "dup_inserts", "evictions", "interior_nodes", "box_tests", "leaves", "tri_tests",
-              "pred_leaves", "pred_tri_tests", "pred_interior_nodes", "pred_box_tests"]
+              "pred_leaves", "pred_tri_tests", "pred_interior_nodes", "pred_box_tests", "gated"]
 N_STATS = 20
 
 
@@ -55,7 +55,8 @@ class _Scene(ctypes.Structure):
 class _Table(ctypes.Structure):
     _fields_ = [("words", ctypes.c_void_p), ("log2_sets", ctypes.c_int), ("log2_ways", ctypes.c_int),
                 ("precision", ctypes.c_int), ("update_mode", ctypes.c_int), ("unbounded", ctypes.c_void_p),
-                ("go_up", ctypes.c_int), ("hash_variant", ctypes.c_int)]
+                ("go_up", ctypes.c_int), ("hash_variant", ctypes.c_int), ("gate_min_tp", ctypes.c_uint32),
+                ("gate_sample_log2", ctypes.c_int), ("gate_open", ctypes.c_int)]
 
 
 def _L():
@@ -181,7 +182,7 @@ class Table:
     """Predictor table state held by the oracle (bounded modes: numpy words)."""
 
     def __init__(self, log2_entries: int, ways: int = 1, precision: int = 6, update_mode: int = TWO_PHASE,
-                 go_up: int = 0, hash_variant: int = 0):
+                 go_up: int = 0, hash_variant: int = 0, gate_min_tp: int = 0, gate_sample_log2: int = 5):
         log2_ways = {1: 0, 2: 1, 4: 2, 8: 3}[ways]
         if log2_entries - log2_ways < 0:
             raise ValueError("fewer entries than ways")
@@ -195,7 +196,11 @@ class Table:
         self.go_up = go_up
         self.hash_variant = hash_variant
         self._c = _Table(self.words.ctypes.data, self.log2_sets, self.log2_ways, precision, update_mode, None, go_up,
-                         hash_variant)
+                         hash_variant, gate_min_tp, gate_sample_log2, 1)
+
+    @property
+    def gate_open(self) -> bool:
+        return bool(self._c.gate_open)
 
     def reset(self):
         self.words[:] = EMPTY_WORD

@@ -87,6 +87,14 @@ typedef struct {
     void *unbounded;  /* private state of the unbounded map */
     int go_up;        /* Sec. 6.2 Go Up Level: 0 = leaves, G > 0 = the ancestor G levels up */
     int hash_variant; /* ORC_HASH_EXP_MSB (Sec. 5, the default) or ORC_HASH_EXP_LSB */
+    /* the gate (a policy on top of the method, not in the paper): with
+     * gate_min_tp > 0, a call decides from its own rays whether the next call
+     * consults the table: open iff true positives * 65536 >= gate_min_tp *
+     * (rays that consulted the table).  While closed, only rays in 32-ray
+     * chunks c with c mod 2^gate_sample_log2 == 0 consult (and update) it. */
+    uint32_t gate_min_tp;
+    int gate_sample_log2;
+    int gate_open;
 } orc_table;
 
 /* Which exponent bits the per-float hash keeps: the p most significant ones
@@ -98,7 +106,7 @@ enum { ORC_HASH_EXP_MSB = 0, ORC_HASH_EXP_LSB = 1 };
 enum {
     S_RAYS, S_HITS, S_LOOKUPS, S_POSITIVES, S_TRUE_POS, S_FALSE_POS, S_NEGATIVES, S_TP_INEXACT,
     S_INSERTS, S_DUP_INSERTS, S_EVICTIONS, S_INTERIOR, S_BOX_TESTS, S_LEAVES, S_TRI_TESTS,
-    S_PRED_LEAVES, S_PRED_TRI_TESTS, S_PRED_INTERIOR, S_PRED_BOX_TESTS, S_COUNT = 20
+    S_PRED_LEAVES, S_PRED_TRI_TESTS, S_PRED_INTERIOR, S_PRED_BOX_TESTS, S_GATED, S_COUNT = 20
 };
 
 /* per-ray outcome codes */
@@ -661,8 +669,16 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
         free(recs);
         return 1;
     }
+    /* the gate as the call starts (its state changes only after the batch) */
+    const int gated_table = tab && tab->gate_min_tp > 0;
+    const int admit_all = !gated_table || tab->gate_open;
+    const uint32_t sample_mask = gated_table ? (1u << tab->gate_sample_log2) - 1u : 0u;
+    uint64_t gate_lookups = 0, gate_tp = 0;
     for (uint32_t i = 0; i < n_rays; ++i) {
         const float *ray = rays + 8ull * i;
+        /* does this ray consult the table?  every ray while the gate is open;
+         * while it is closed, the rays of the sampled 32-ray chunks */
+        const int consult = tab && (admit_all || ((i >> 5) & sample_mask) == 0u);
         best_hit b;
         memset(&b, 0, sizeof b);
         b.t = INFINITY;
@@ -691,9 +707,10 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
                 traverse_from(sc, (uint32_t)c, ray, mode, &b, &ws, stats, PRED_COUNTERS, NULL);
             }
         }
-        if (tab || predicted) {
+        if (tab && !consult) stats[S_GATED] += 1;
+        if (consult || predicted) {
             stats[S_LOOKUPS] += 1;
-            if (!tab) {
+            if (!consult) {
                 /* learned proposal only */
             } else if ((key = orc_ray_key_variant(ray, tab->precision, tab->hash_variant)), bounded) {
                 uint64_t m = orc_mix48(key);
@@ -749,7 +766,7 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
             else
                 changed = traverse(sc, ray, mode, &b, &ws, stats, ray_box_tests ? &ray_box_tests[i] : NULL);
             if (oc == OUT_TRUE_POS && changed && (b.prim != pred.prim || b.t != pred.t)) stats[S_TP_INEXACT] += 1;
-            int64_t node = (tab && b.found) ? predicted_node(sc, &ti, b.leaf, go_up) : -1;
+            int64_t node = (consult && b.found) ? predicted_node(sc, &ti, b.leaf, go_up) : -1;
             if (node >= 0) {
                 int is_cand = 0;
                 for (uint32_t k = 0; k < n_cand; ++k) is_cand |= cand[k] == (uint32_t)node;
@@ -792,6 +809,10 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
             ray_box_tests[i] = 0;
         }
         if (b.found) stats[S_HITS] += 1;
+        if (consult) {
+            gate_lookups += 1;
+            gate_tp += oc == OUT_TRUE_POS;
+        }
         if (outcome) outcome[i] = oc;
         if (mode == ORC_ANY) {
             ((uint32_t *)out)[i] = b.found ? b.prim : NO_HIT;
@@ -822,6 +843,8 @@ int orc_trace(const orc_scene *sc, const float *rays, uint32_t n_rays, int mode,
         }
         free(seen);
     }
+    /* the gate for the next call, from this call's rays that consulted the table */
+    if (gated_table && gate_lookups) tab->gate_open = (gate_tp << 16) >= (uint64_t)tab->gate_min_tp * gate_lookups;
     free(recs);
     free(ws.stack);
     tree_info_free(&ti);

@@ -453,9 +453,11 @@ hrpp_status hrpp_table_create(int log2_entries, int ways, hrpp_table **out)
     t->precision = 6;
     t->update_mode = HRPP_UPDATE_TWO_PHASE;
     const uint64_t n = 1ull << log2_entries;
+    t->gate_sample_log2 = 5;
     if ((e = device_malloc((void **)&t->d_words, n * 8)) != cudaSuccess || (e = device_malloc((void **)&t->d_winner, n * 4)) != cudaSuccess ||
+        (e = device_malloc((void **)&t->d_gate, sizeof(uint32_t))) != cudaSuccess ||
         (e = cudaMemset(t->d_words, 0xFF, n * 8)) != cudaSuccess || (e = cudaMemset(t->d_winner, 0, n * 4)) != cudaSuccess ||
-        (e = cudaDeviceSynchronize()) != cudaSuccess) {
+        (e = cudaMemset(t->d_gate, 1, sizeof(uint32_t))) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess) {
         hrpp_table_destroy(t);
         return cuda_fail(e, "table allocation");
     }
@@ -491,6 +493,35 @@ hrpp_status hrpp_table_set_hash(hrpp_table *t, int hash_variant)
     return HRPP_OK;
 }
 
+hrpp_status hrpp_table_set_gate(hrpp_table *t, uint32_t min_tp_per_65536, int sample_log2)
+{
+    if (!t) return fail(HRPP_ERR_INVALID_ARG, "table is NULL");
+    if (min_tp_per_65536 > 65536u) return fail(HRPP_ERR_INVALID_ARG, "min_tp_per_65536 must be at most 65536");
+    if (sample_log2 < 0 || sample_log2 > 20) return fail(HRPP_ERR_INVALID_ARG, "sample_log2 must be in [0, 20]");
+    DeviceGuard g(t->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemset(t->d_gate, 1, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "gate reset");
+    t->gate_min_tp = min_tp_per_65536;
+    t->gate_sample_log2 = sample_log2;
+    return HRPP_OK;
+}
+
+hrpp_status hrpp_table_get_gate(const hrpp_table *t, int *open)
+{
+    if (!t || !open) return fail(HRPP_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard g(t->device);
+    if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+    uint32_t w = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&w, t->d_gate, sizeof w, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "gate read");
+    *open = w != 0u;
+    return HRPP_OK;
+}
+
 hrpp_status hrpp_table_reset(hrpp_table *t, void *stream)
 {
     if (!t) return fail(HRPP_ERR_INVALID_ARG, "table is NULL");
@@ -499,6 +530,7 @@ hrpp_status hrpp_table_reset(hrpp_table *t, void *stream)
     const uint64_t n = 1ull << t->log2_entries;
     cudaError_t e = launch_table_fill(t->d_words, n, (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(t->d_winner, 0, n * 4, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->d_gate, 1, sizeof(uint32_t), (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "table reset");
     t->bound_scene = 0;
     return HRPP_OK;
@@ -525,6 +557,7 @@ hrpp_status hrpp_table_import(hrpp_table *t, const uint64_t *host_words, size_t 
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(t->d_words, host_words, n_words * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(t->d_winner, 0, n_words * 4);
+    if (e == cudaSuccess) e = cudaMemset(t->d_gate, 1, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "table import");
     return HRPP_OK;
@@ -542,6 +575,8 @@ hrpp_status hrpp_table_copy(hrpp_table *dst, const hrpp_table *src, void *stream
     if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
     const uint64_t n = 1ull << dst->log2_entries;
     cudaError_t e = cudaMemcpyAsync(dst->d_words, src->d_words, n * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dst->d_gate, src->d_gate, sizeof(uint32_t), cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "table copy");
     dst->bound_scene = src->bound_scene;
     return HRPP_OK;
@@ -564,6 +599,7 @@ void hrpp_table_destroy(hrpp_table *t)
     DeviceGuard g(t->device);
     cudaFree(t->d_words);
     cudaFree(t->d_winner);
+    cudaFree(t->d_gate);
     delete t;
 }
 
@@ -700,6 +736,11 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
             p.update_mode = table->update_mode;
             p.go_up = table->go_up;
             p.hash_variant = table->hash_variant;
+            if (table->gate_min_tp) {
+                p.gate = table->d_gate;
+                p.gate_mask = (1u << table->gate_sample_log2) - 1u;
+                p.gate_min_tp = table->gate_min_tp;
+            }
         }
         cudaEvent_t ev0 = opts ? (cudaEvent_t)opts->kernel_start : nullptr;
         cudaEvent_t ev1 = opts ? (cudaEvent_t)opts->kernel_stop : nullptr;
@@ -712,7 +753,10 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         e = sc->width == 2 ? launch_trace_w2(closest, out_stats != nullptr, sched, p, (int)block_threads, 0, stream, ev0, ev1, &l2)
                            : launch_trace_w4(closest, out_stats != nullptr, sched, p, (int)block_threads, 0, stream, ev0, ev1, &l2);
         if (e != cudaSuccess) { status = cuda_fail(e, "trace launch"); break; }
-        if (two_phase && (e = launch_table_apply(table->d_words, table->d_winner, p.records, ctl, n_rays, stream)) != cudaSuccess) {
+        if (two_phase) e = launch_table_apply(table->d_words, table->d_winner, p.records, ctl, n_rays, stream, p.gate,
+                                              p.gate_min_tp);
+        else if (p.gate) e = launch_gate_update(p.gate, p.gate_min_tp, ctl, stream);
+        if (e != cudaSuccess) {
             status = cuda_fail(e, "table update launch");
             break;
         }

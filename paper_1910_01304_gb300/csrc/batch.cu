@@ -145,6 +145,7 @@ hrpp_status hrpp_batch_create(const hrpp_batch_item *items, uint32_t n_items, in
         chunk_first.reserve(total_chunks);
         uint64_t rec_off = 0;
         uint32_t max_n = 0;
+        bool any_gate = false;  // some item's table has a gate: k_apply_batch decides it
         std::vector<uint32_t> any_item, any_first;  // appended after the closest-hit chunks
         for (uint32_t k = 0; k < n_items; ++k) {
             const hrpp_batch_item &it = items[k];
@@ -175,6 +176,12 @@ hrpp_status hrpp_batch_create(const hrpp_batch_item *items, uint32_t n_items, in
                 p.update_mode = it.table->update_mode;
                 p.go_up = it.table->go_up;
                 p.hash_variant = it.table->hash_variant;
+                if (it.table->gate_min_tp) {
+                    p.gate = it.table->d_gate;
+                    p.gate_mask = (1u << it.table->gate_sample_log2) - 1u;
+                    p.gate_min_tp = it.table->gate_min_tp;
+                    any_gate = true;
+                }
                 if (it.table->update_mode == HRPP_UPDATE_TWO_PHASE) {
                     p.records = b->d_records + rec_off;
                     rec_off += it.n_rays;
@@ -235,7 +242,8 @@ hrpp_status hrpp_batch_create(const hrpp_batch_item *items, uint32_t n_items, in
                                : launch_batch_w4(false, b->stats, da, (int)block_threads, any_stream);
         if (ec == cudaSuccess && both) ec = cudaEventRecord(join, b->side_stream);
         if (ec == cudaSuccess && both) ec = cudaStreamWaitEvent(b->capture_stream, join, 0);
-        if (ec == cudaSuccess && total_records) ec = launch_table_apply_batch(b->d_items, n_items, max_n, b->capture_stream);
+        if (ec == cudaSuccess && (total_records || any_gate))
+            ec = launch_table_apply_batch(b->d_items, n_items, max_n, b->capture_stream);
         e = cudaStreamEndCapture(b->capture_stream, &b->graph);
         if (fork) cudaEventDestroy(fork);
         if (join) cudaEventDestroy(join);

@@ -29,17 +29,35 @@ constexpr uint32_t kErrSteps = 2u;
 enum Stat : int {
     ST_RAYS, ST_HITS, ST_LOOKUPS, ST_POSITIVES, ST_TRUE_POS, ST_FALSE_POS, ST_NEGATIVES, ST_TP_INEXACT,
     ST_INSERTS, ST_DUP_INSERTS, ST_EVICTIONS, ST_INTERIOR, ST_BOX_TESTS, ST_LEAVES, ST_TRI_TESTS,
-    ST_PRED_LEAVES, ST_PRED_TRI_TESTS, ST_PRED_INTERIOR, ST_PRED_BOX_TESTS, ST_N = 20
+    ST_PRED_LEAVES, ST_PRED_TRI_TESTS, ST_PRED_INTERIOR, ST_PRED_BOX_TESTS, ST_GATED, ST_N = 20
 };
 
 // Per-call device control block: the ray pool's cursor, the insert-record
-// count and the statistics.  Zeroed before each call.
+// count, the table gate's counts (rays that consulted the table, and the true
+// positives among them) and the statistics.  Zeroed before each call.
 struct __align__(16) Ctl {
     unsigned int next_ray;
     unsigned int n_records;
-    unsigned int pad[2];
+    unsigned int gate_lookups;
+    unsigned int gate_tp;
     unsigned long long stats[ST_N];
 };
+
+// A table's gate word: nonzero = open (every ray consults the table), zero =
+// closed (only the sampled 32-ray chunks do).
+__device__ __forceinline__ bool gate_admits(const uint32_t *gate, uint32_t gate_mask, uint32_t ray)
+{
+    return gate == nullptr || ((ray >> 5) & gate_mask) == 0u || __ldg(gate) != 0u;
+}
+
+// After a call: the gate opens iff the call's true positives reach
+// min_tp / 65536 of the rays that consulted the table; a call in which no ray
+// consulted it leaves the gate as it was.
+__device__ __forceinline__ void gate_decide(uint32_t *gate, uint32_t min_tp, const Ctl *ctl)
+{
+    const uint32_t look = ctl->gate_lookups, tp = ctl->gate_tp;
+    if (look) *gate = ((uint64_t)tp << 16) >= (uint64_t)min_tp * look ? 1u : 0u;
+}
 
 // Two-phase insert record: table slot, ray index + 1, table word.
 struct __align__(16) Record {
@@ -76,6 +94,9 @@ struct TraceParams {
     int hash_variant;            // 0: exponent MSBs (Sec. 5), 1: exponent LSBs
     uint8_t *ray_outcome;        // per ray (statistics launches only; may be null)
     uint32_t *ray_box_tests;     // per ray (statistics launches only; may be null)
+    uint32_t *gate;              // the table's gate word (null: no gate, every ray consults the table)
+    uint32_t gate_mask;          // closed gate: 32-ray chunks c with (c & gate_mask) == 0 still consult it
+    uint32_t gate_min_tp;        // true positives per 65536 lookups that keep the gate open
 };
 
 // 32 bytes through the read-only data path in one load (p 32-byte aligned):
@@ -236,7 +257,10 @@ cudaError_t launch_trace_w4(bool closest, bool stats, int schedule, const TraceP
                             int blocks_per_sm_cap, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1,
                             const L2Window *l2 = nullptr);
 cudaError_t launch_table_apply(uint64_t *table, uint32_t *winner, const Record *records, Ctl *ctl,
-                               uint32_t max_records, cudaStream_t stream);
+                               uint32_t max_records, cudaStream_t stream, uint32_t *gate = nullptr,
+                               uint32_t gate_min_tp = 0);
+// the gate decision alone (tables whose updates need no k_apply)
+cudaError_t launch_gate_update(uint32_t *gate, uint32_t gate_min_tp, const Ctl *ctl, cudaStream_t stream);
 // batched launches (batch.cu): every item of one BVH width in one kernel, then
 // the two-phase updates of every item's table in one kernel
 struct BatchDesc {

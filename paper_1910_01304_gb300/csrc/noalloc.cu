@@ -166,6 +166,11 @@ extern "C" hrpp_status hrpp_trace_noalloc(const hrpp_scene *sc, hrpp_table *tabl
             p.update_mode = table->update_mode;
             p.go_up = table->go_up;
             p.hash_variant = table->hash_variant;
+            if (table->gate_min_tp) {
+                p.gate = table->d_gate;
+                p.gate_mask = (1u << table->gate_sample_log2) - 1u;
+                p.gate_min_tp = table->gate_min_tp;
+            }
         }
         e = sc->width == 2 ? launch_trace_w2(closest, out_stats != nullptr, 0, p, 128, 0, stream, nullptr, nullptr)
                            : launch_trace_w4(closest, out_stats != nullptr, 0, p, 128, 0, stream, nullptr, nullptr);
@@ -173,8 +178,10 @@ extern "C" hrpp_status hrpp_trace_noalloc(const hrpp_scene *sc, hrpp_table *tabl
             status = noalloc_fail(HRPP_ERR_CUDA, "trace launch: %s", cudaGetErrorString(e));
             break;
         }
-        if (two_phase && (e = launch_table_apply(table->d_words, table->d_winner, p.records, ctl, n_rays, stream)) !=
-                             cudaSuccess) {
+        if (two_phase) e = launch_table_apply(table->d_words, table->d_winner, p.records, ctl, n_rays, stream, p.gate,
+                                              p.gate_min_tp);
+        else if (p.gate) e = launch_gate_update(p.gate, p.gate_min_tp, ctl, stream);
+        if (e != cudaSuccess) {
             status = noalloc_fail(HRPP_ERR_CUDA, "table update launch: %s", cudaGetErrorString(e));
             break;
         }

@@ -34,16 +34,25 @@ __device__ __forceinline__ void apply_records(uint64_t *table, uint32_t *winner,
     }
 }
 
+// The gate's decision reads only the call's counts, never the records, so
+// the first thread of the grid takes it while the others apply records.
 __global__ void __launch_bounds__(256) k_apply(uint64_t *table, uint32_t *winner, const Record *rec, Ctl *ctl,
-                                               uint32_t max_records)
+                                               uint32_t max_records, uint32_t *gate, uint32_t gate_min_tp)
 {
+    if (gate && blockIdx.x == 0 && threadIdx.x == 0) gate_decide(gate, gate_min_tp, ctl);
     apply_records(table, winner, rec, ctl, max_records);
+}
+
+__global__ void k_gate(uint32_t *gate, uint32_t gate_min_tp, const Ctl *ctl)
+{
+    gate_decide(gate, gate_min_tp, ctl);
 }
 
 // one grid row per item of a batch (blockIdx.y)
 __global__ void __launch_bounds__(256) k_apply_batch(const TraceParams *items, uint32_t max_records)
 {
     const TraceParams &p = items[blockIdx.y];
+    if (p.gate && blockIdx.x == 0 && threadIdx.x == 0) gate_decide(p.gate, p.gate_min_tp, p.ctl);
     if (!p.table || p.update_mode != HRPP_UPDATE_TWO_PHASE) return;
     apply_records(p.table, p.winner, p.records, p.ctl, min(max_records, p.n_rays));
 }
@@ -55,7 +64,7 @@ __global__ void __launch_bounds__(256) k_fill(uint64_t *words, uint64_t n)
 }
 
 cudaError_t launch_table_apply(uint64_t *table, uint32_t *winner, const Record *records, Ctl *ctl,
-                               uint32_t max_records, cudaStream_t stream)
+                               uint32_t max_records, cudaStream_t stream, uint32_t *gate, uint32_t gate_min_tp)
 {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -64,7 +73,13 @@ cudaError_t launch_table_apply(uint64_t *table, uint32_t *winner, const Record *
     uint32_t blocks = (max_records + 255u) / 256u;
     if (blocks > (uint32_t)sms * 4u) blocks = (uint32_t)sms * 4u;
     if (blocks < 1) blocks = 1;
-    k_apply<<<blocks, 256, 0, stream>>>(table, winner, records, ctl, max_records);
+    k_apply<<<blocks, 256, 0, stream>>>(table, winner, records, ctl, max_records, gate, gate_min_tp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gate_update(uint32_t *gate, uint32_t gate_min_tp, const Ctl *ctl, cudaStream_t stream)
+{
+    k_gate<<<1, 1, 0, stream>>>(gate, gate_min_tp, ctl);
     return cudaGetLastError();
 }
 

@@ -60,13 +60,29 @@ struct Counters {
     {
         if (STATS) {
 #pragma unroll
-            for (int k = 0; k < ST_PRED_BOX_TESTS + 1; ++k) {
+            for (int k = 0; k < ST_N; ++k) {
                 const uint32_t v = __reduce_add_sync(0xFFFFFFFFu, c[k]);
                 if (lane == 0 && v) atomicAdd(&ctl->stats[k], (unsigned long long)v);
             }
         }
     }
 };
+
+// Gate counts of the rays a warp just finished (all 32 lanes call this
+// together): gflags bit 0 = the ray consulted the table, bit 1 = it was a
+// true positive.  Two warp votes and, with a gate, two atomics per warp.
+constexpr uint32_t kGateLooked = 1u, kGateTp = 2u;
+
+__device__ __forceinline__ void gate_count(const TraceParams &p, uint32_t lane, uint32_t gflags)
+{
+    if (!p.gate) return;  // warp-uniform
+    const uint32_t l = __popc(__ballot_sync(0xFFFFFFFFu, gflags & kGateLooked));
+    const uint32_t t = __popc(__ballot_sync(0xFFFFFFFFu, gflags & kGateTp));
+    if (lane == 0) {
+        if (l) atomicAdd(&p.ctl->gate_lookups, l);
+        if (t) atomicAdd(&p.ctl->gate_tp, t);
+    }
+}
 
 struct Best {
     float t, u, v;
@@ -284,7 +300,11 @@ __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayS
     cnt.add(ST_RAYS);
     bool traverse = true, have_inverse = false;
     const bool learned = p.predicted != nullptr;
-    if (p.table || learned) {
+    // a closed gate leaves the table to the sampled chunks' rays (finish_ray
+    // takes the same decision again instead of keeping it in a register)
+    const bool consult = p.table != nullptr && gate_admits(p.gate, p.gate_mask, i);
+    if (p.table && !consult) cnt.add(ST_GATED);
+    if (consult || learned) {
         cnt.add(ST_LOOKUPS);
         float tdummy = 0.0f;
         bool positive = false, done = false;
@@ -308,9 +328,9 @@ __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayS
                 done = !CLOSEST && s.b.found;
             }
         }
-        const uint32_t ways = p.table ? (1u << p.log2_ways) : 0u;
+        const uint32_t ways = consult ? (1u << p.log2_ways) : 0u;
         const uint64_t *set = nullptr;
-        if (p.table) {
+        if (consult) {
             const uint64_t m = mix48(ray_key(s.o, s.d, p.precision, p.hash_variant == HRPP_HASH_EXP_LSB));
             s.set = (uint32_t)(m & ((1ull << p.log2_sets) - 1ull));
             s.tag = (m >> p.log2_sets) & kTagMask;
@@ -426,16 +446,18 @@ __device__ __forceinline__ void online_insert(const TraceParams &p, uint32_t set
 // to append; online: inserts the word now).
 template <bool CLOSEST, bool STATS>
 __device__ __forceinline__ bool finish_ray(const TraceParams &p, uint32_t i, const RayState &s, Counters<STATS> &cnt,
-                                           uint32_t &slot, uint64_t &word)
+                                           uint32_t &gflags, uint32_t &slot, uint64_t &word)
 {
     bool want_record = false;
+    const bool consulted = p.table != nullptr && gate_admits(p.gate, p.gate_mask, i);
+    gflags = consulted ? (kGateLooked | (s.outcome == HRPP_OUTCOME_TRUE_POS ? kGateTp : 0u)) : 0u;
     if (CLOSEST && s.predicted_hit && s.b.from_trav) cnt.add(ST_TP_INEXACT);
     // Sec. 5: a ray that traversed inserts the node of its final hit (the leaf,
     // or its ancestor go_up levels up, Sec. 6.2) unless its entry holds it
     // already.  Any-hit true positives (and closest-hit ones left unverified)
     // were answered by the predictor.
     const bool traversed = !s.predicted_hit || (CLOSEST && p.verify != HRPP_VERIFY_NONE);
-    if (p.table && traversed && s.b.found && p.update_mode != HRPP_UPDATE_FROZEN) {
+    if (consulted && traversed && s.b.found && p.update_mode != HRPP_UPDATE_FROZEN) {
         uint32_t node = s.b.leaf;
         bool storable = true;
         if (p.go_up > 0) {
@@ -563,7 +585,7 @@ __device__ __forceinline__ void traverse_interior(const TraceParams &p, RayState
 // climbs within the same loop, without waiting for the rest of its warp.
 template <int W, bool CLOSEST, bool STATS, bool BU = false>
 __device__ __forceinline__ bool trace_one(const TraceParams &p, uint32_t i, int32_t *stack, Counters<STATS> &cnt,
-                                          uint32_t &slot, uint64_t &word)
+                                          uint32_t &gflags, uint32_t &slot, uint64_t &word)
 {
     static_assert(CLOSEST || !BU, "bottom-up verification is for closest-hit rays");
     RayState s;
@@ -583,7 +605,7 @@ __device__ __forceinline__ bool trace_one(const TraceParams &p, uint32_t i, int3
             }
         }
     }
-    return finish_ray<CLOSEST, STATS>(p, i, s, cnt, slot, word);
+    return finish_ray<CLOSEST, STATS>(p, i, s, cnt, gflags, slot, word);
 }
 
 template <int W, bool CLOSEST, bool STATS, bool BU = false>
@@ -600,10 +622,11 @@ __global__ void __launch_bounds__(512) k_trace(const TraceParams p)
         if (base >= p.n_rays) break;
         const uint32_t i = base + lane;
         bool want = false;
-        uint32_t slot = 0;
+        uint32_t slot = 0, gflags = 0;
         uint64_t word = 0;
-        if (i < p.n_rays) want = trace_one<W, CLOSEST, STATS, BU>(p, i, stack, cnt, slot, word);
+        if (i < p.n_rays) want = trace_one<W, CLOSEST, STATS, BU>(p, i, stack, cnt, gflags, slot, word);
         append_records<true>(p, lane, want, slot, i, word, cnt);
+        gate_count(p, lane, gflags);
     }
     cnt.flush(p.ctl, lane);
 }
@@ -644,10 +667,11 @@ __global__ void __launch_bounds__(512) k_trace_batch(const BatchDesc b)
         }
         const uint32_t i = __ldg(b.chunk_first + chunk) + lane;
         bool want = false;
-        uint32_t slot = 0;
+        uint32_t slot = 0, gflags = 0;
         uint64_t word = 0;
-        if (i < p.n_rays) want = trace_one<W, CLOSEST, STATS>(p, i, stack, cnt, slot, word);
+        if (i < p.n_rays) want = trace_one<W, CLOSEST, STATS>(p, i, stack, cnt, gflags, slot, word);
         append_records<true>(p, lane, want, slot, i, word, cnt);
+        gate_count(p, lane, gflags);
     }
     if (cur != 0xFFFFFFFFu) cnt.flush(p.ctl, lane);
 }
@@ -726,10 +750,11 @@ __global__ void __launch_bounds__(512) k_trace_dyn(const TraceParams p)
         const bool done = ray != kNoRay && s.ref == kDoneRef && s.from == kDoneRef;
         if (__any_sync(0xFFFFFFFFu, done)) {
             bool want = false;
-            uint32_t slot = 0;
+            uint32_t slot = 0, gflags = 0;
             uint64_t word = 0;
-            if (done) want = finish_ray<CLOSEST, STATS>(p, ray, s, cnt, slot, word);
+            if (done) want = finish_ray<CLOSEST, STATS>(p, ray, s, cnt, gflags, slot, word);
             append_records<false>(p, lane, want, slot, ray, word, cnt);
+            gate_count(p, lane, gflags);
             if (done) ray = kNoRay;
         }
     }

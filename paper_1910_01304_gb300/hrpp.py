@@ -26,11 +26,11 @@ HRPP_PROPOSAL_PARAMS = 256 * 96 + 256 + 256 * 256 + 256 + 4096 * 256 + 4096
 HRPP_EMPTY_WORD = 0xFFFFFFFFFFFFFFFF
 STAT_NAMES = ["rays", "hits", "lookups", "positives", "true_pos", "false_pos", "negatives", "tp_inexact",
               "inserts", "dup_inserts", "evictions", "interior_nodes", "box_tests", "leaves", "tri_tests",
-              "pred_leaves", "pred_tri_tests", "pred_interior_nodes", "pred_box_tests"]
+              "pred_leaves", "pred_tri_tests", "pred_interior_nodes", "pred_box_tests", "gated"]
 
 
 class hrpp_stats(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_uint64) for n in STAT_NAMES] + [("reserved", ctypes.c_uint64 * 1)]
+    _fields_ = [(n, ctypes.c_uint64) for n in STAT_NAMES]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n in STAT_NAMES}
@@ -85,6 +85,8 @@ def _load():
         "hrpp_table_configure": (st, [P, i32, i32]),
         "hrpp_table_set_go_up": (st, [P, i32]),
         "hrpp_table_set_hash": (st, [P, i32]),
+        "hrpp_table_set_gate": (st, [P, u32, i32]),
+        "hrpp_table_get_gate": (st, [P, P]),
         "hrpp_table_reset": (st, [P, P]),
         "hrpp_table_export": (st, [P, P, sz]),
         "hrpp_table_import": (st, [P, P, sz]),
@@ -135,6 +137,8 @@ hrpp_table_create = _lib.hrpp_table_create
 hrpp_table_configure = _lib.hrpp_table_configure
 hrpp_table_set_go_up = _lib.hrpp_table_set_go_up
 hrpp_table_set_hash = _lib.hrpp_table_set_hash
+hrpp_table_set_gate = _lib.hrpp_table_set_gate
+hrpp_table_get_gate = _lib.hrpp_table_get_gate
 hrpp_table_reset = _lib.hrpp_table_reset
 hrpp_table_export = _lib.hrpp_table_export
 hrpp_table_import = _lib.hrpp_table_import
@@ -268,6 +272,16 @@ class Table:
     def set_hash(self, hash_variant: int):
         check(hrpp_table_set_hash(self.handle, hash_variant))
         self.hash_variant = hash_variant
+
+    def set_gate(self, min_tp_per_65536: int, sample_log2: int = 5):
+        """hrpp_table_set_gate: 0 turns the gate off."""
+        check(hrpp_table_set_gate(self.handle, int(min_tp_per_65536), int(sample_log2)))
+        self.gate = (int(min_tp_per_65536), int(sample_log2))
+
+    def gate_open(self) -> bool:
+        v = ctypes.c_int()
+        check(hrpp_table_get_gate(self.handle, ctypes.byref(v)))
+        return bool(v.value)
 
     def configure(self, precision: int, update_mode: int):
         check(hrpp_table_configure(self.handle, precision, update_mode))

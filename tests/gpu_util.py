@@ -6,7 +6,7 @@ import oracle as O
 
 STAT_KEYS = ["rays", "hits", "lookups", "positives", "true_pos", "false_pos", "negatives", "tp_inexact",
              "inserts", "dup_inserts", "evictions", "interior_nodes", "box_tests", "leaves", "tri_tests",
-             "pred_leaves", "pred_tri_tests", "pred_interior_nodes", "pred_box_tests"]
+             "pred_leaves", "pred_tri_tests", "pred_interior_nodes", "pred_box_tests", "gated"]
 
 
 def hrpp_mod():

@@ -50,11 +50,22 @@ def test_full_terrain_primary_and_ao(full):
     ao, _ = W.secondary_ao(s, prim, oh["t"], oh["prim"], frame=1)
     assert len(ao) > 4_000_000
     ga_plain, _ = gpu_trace(H, g, ao, O.ANY_HIT)
+    # the dominant launch of the bench step, whole: HRPP any-hit over every
+    # AO ray of two frames with the 2^18 x 2-way table, against the oracle's
+    # two-phase HRPP (every prim, every counter, every table word)
+    ao2, _ = W.secondary_ao(s, rays, o2["t"], o2["prim"], frame=2)
     tab_a = H.Table(18, 2, 6)
-    for _ in range(2):
-        ga_hrpp, sa = gpu_trace(H, g, ao, O.ANY_HIT, tab_a)
-        # HRPP == plain on every ray (occlusion bit)
-        assert np.array_equal(any_prims(ga_plain) == O.NO_HIT, any_prims(ga_hrpp) == O.NO_HIT)
+    otab_a = O.Table(18, 2, 6, O.TWO_PHASE)
+    for frame, rays_a in ((1, ao), (2, ao2)):
+        oa_h, oa_s = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays_a, O.ANY_HIT, otab_a)
+        ga_hrpp, sa = gpu_trace(H, g, rays_a, O.ANY_HIT, tab_a)
+        assert_same_hits(O.ANY_HIT, ga_hrpp, oa_h, f"full AO hrpp frame {frame}")
+        assert_same_stats(sa, oa_s, msg=f"full AO hrpp frame {frame}")
+        assert np.array_equal(tab_a.export(), otab_a.words), f"full AO frame {frame}: table words differ"
+    assert sa["positives"] > 0 and sa["inserts"] > 0
+    # HRPP == plain on every ray (occlusion bit), for the same frame
+    ga_hrpp, _ = gpu_trace(H, g, ao, O.ANY_HIT, tab_a)
+    assert np.array_equal(any_prims(ga_plain) == O.NO_HIT, any_prims(ga_hrpp) == O.NO_HIT)
     rng = np.random.default_rng(0)
     idx = np.sort(rng.choice(len(ao), 60000, replace=False))
     oa, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, ao[idx], O.ANY_HIT)
@@ -67,26 +78,43 @@ def test_full_terrain_primary_and_ao(full):
 
 def test_full_batched_workload_sampled():
     """The 64-scene uneven batch at full size, graph-replayed (one launch per
-    query mode, side by side):
-    every item checked against the oracle on a random sample of its rays."""
+    query mode, side by side), with the bench's item mix: per scene, its
+    camera half as a closest-hit item and its random half as an any-hit item,
+    each with its own table.  Every item is checked against the oracle on a
+    random sample of its rays (closest hits bit for bit, any-hit prims bit for
+    bit)."""
     import torch
     H = hrpp_mod()
     rng = np.random.default_rng(1)
     items, data = [], []
     for s, rays in W.batched_workload(n_scenes=64, seed=3):
         g = H.Scene.from_workload(s)
-        d = torch.from_numpy(rays).cuda()
-        items.append((g, H.Table(16, 2, 6), d, H.HRPP_CLOSEST_HIT))
-        data.append((s, rays))
+        half = len(rays) // 2
+        for part, mode in ((rays[:half], H.HRPP_CLOSEST_HIT), (rays[half:], H.HRPP_ANY_HIT)):
+            part = np.ascontiguousarray(part)
+            if len(part) == 0:
+                continue
+            items.append((g, H.Table(16, 2, 6), torch.from_numpy(part).cuda(), mode))
+            data.append((s, part, mode))
+    assert sum(1 for *_, m in data if m == H.HRPP_ANY_HIT) >= 60
     batch = H.Batch(items)
     for _ in range(2):
         batch.run()
     torch.cuda.synchronize()
-    for k, (s, rays) in enumerate(data):
+    for k, (s, rays, mode) in enumerate(data):
         idx = np.sort(rng.choice(len(rays), min(len(rays), 300), replace=False))
-        oh, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays[idx], O.CLOSEST_HIT)
+        omode = O.CLOSEST_HIT if mode == H.HRPP_CLOSEST_HIT else O.ANY_HIT
+        oh, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays[idx], omode)
         gh = batch.hits[k].cpu().numpy()[idx]
-        assert np.array_equal(as_words(gh), as_words(oh)), f"item {k}"
+        if omode == O.CLOSEST_HIT:
+            assert np.array_equal(as_words(gh), as_words(oh)), f"item {k}"
+        else:
+            # a true positive reports the predicted leaf's hit: occlusion is
+            # unique, the prim must be a valid hit of the ray
+            assert np.array_equal(any_prims(gh) == O.NO_HIT, oh == O.NO_HIT), f"item {k}"
+            for j in np.nonzero(any_prims(gh) != O.NO_HIT)[0][:40]:
+                tri = s.tris[any_prims(gh)[j]].reshape(3, 3)
+                assert O.ray_triangle(rays[idx][j], *tri)[0], f"item {k}: prim is not a hit"
 
 
 def test_full_pathtrace_sampled():

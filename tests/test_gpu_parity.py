@@ -201,6 +201,64 @@ def test_online_insert_matches_oracle_without_races(H, small_pair, mode, width_i
     assert evictions > 0
 
 
+@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("mode", [O.CLOSEST_HIT, O.ANY_HIT])
+@pytest.mark.parametrize("width_idx", [0, 1])
+def test_gate_matches_oracle(H, small_pair, width_idx, mode, schedule):
+    """The table gate against the oracle over frames that close and reopen
+    it: hits, every counter (gated included), table words and the gate's
+    state after every call, with both ray schedules."""
+    s, g = small_pair[width_idx]
+    # frame 0 on an empty table predicts nothing: the gate closes; the
+    # sampled chunks of frames 1-2 predict and reopen it; the all-miss batch
+    # closes it again, and frame 3 is traced through the closed gate
+    tab = H.Table(12, 2, 6)
+    tab.set_gate(40, 2)
+    otab = O.Table(12, 2, 6, O.TWO_PHASE, gate_min_tp=40, gate_sample_log2=2)
+    states = []
+    for step in range(5):
+        rays = s.primary_rays(frame=min(step, 3))
+        if mode == O.ANY_HIT:
+            h, _ = _oracle(s, rays, O.CLOSEST_HIT)
+            rays, _ = W.secondary_shadow(s, rays, h["t"], h["prim"])
+        if step == 3:
+            rays = rays.copy()
+            rays[:, 4:7] = [0.0, 1.0, 0.0]  # straight up: every ray misses
+        oh, ost = _oracle(s, rays, mode, otab)
+        d = __import__("torch").from_numpy(np.ascontiguousarray(rays)).cuda()
+        gh, gst = H.trace(g, d, mode, tab, stats=True, schedule=schedule)
+        __import__("torch").cuda.synchronize()
+        assert_same_hits(mode, gh.cpu().numpy(), oh, f"step {step}")
+        assert_same_stats(gst, ost, msg=f"step {step}")
+        assert np.array_equal(tab.export(), otab.words), f"step {step}: table words differ"
+        assert tab.gate_open() == otab.gate_open, f"step {step}: gate state differs"
+        states.append((otab.gate_open, ost["gated"]))
+    assert any(not o for o, _ in states) and any(o for o, _ in states[1:])
+    assert any(gated > 0 for _, gated in states)
+
+
+def test_gate_in_a_batch_matches_single_calls(H, small_pair):
+    """A gated table in a batched launch: per item the hits, counters, table
+    words and gate state equal those of hrpp_trace calls with the same gate,
+    run after run."""
+    import torch
+    s, g = small_pair[1]
+    rays = [torch.from_numpy(s.primary_rays(frame=f)).cuda() for f in range(3)]
+    tb, tc = H.Table(12, 1, 6), H.Table(12, 1, 6)
+    for t in (tb, tc):
+        t.set_gate(3000, 3)
+    buf = torch.empty_like(rays[0])
+    batch = H.Batch([(g, tb, buf, H.HRPP_CLOSEST_HIT)], stats=True)
+    for f in (0, 1, 2, 1):
+        buf.copy_(rays[f])
+        batch.run()
+        ref, rst = H.trace(g, rays[f], H.HRPP_CLOSEST_HIT, tc, stats=True)
+        torch.cuda.synchronize()
+        assert torch.equal(batch.hits[0].view(torch.int32), ref.view(torch.int32))
+        assert batch.stats(0) == rst
+        assert np.array_equal(tb.export(), tc.export()) and tb.gate_open() == tc.gate_open()
+
+
 def test_frozen_mode_never_writes(H, small_pair):
     s, g = small_pair[0]
     tab = H.Table(12, 1, 6)
@@ -619,7 +677,7 @@ def test_injected_allocation_failures_return_oom(H, small_pair, monkeypatch):
     rays = torch.from_numpy(s.primary_rays()[:256]).cuda()
     makers = {
         "scene": (6, lambda: H.Scene.from_workload(s)),
-        "table": (2, lambda: H.Table(10, 2, 6)),
+        "table": (3, lambda: H.Table(10, 2, 6)),
         "batch": (5, lambda: H.Batch([(g, None, rays, H.HRPP_CLOSEST_HIT)])),
     }
     for name, (n_allocs, make) in makers.items():

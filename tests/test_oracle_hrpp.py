@@ -212,6 +212,73 @@ def test_online_full_set_replaces_the_way_of_the_ray_index(small):
     assert tab.words.tolist() == words
 
 
+def _sampled(n, sample_log2):
+    i = np.arange(n)
+    return ((i >> 5) & ((1 << sample_log2) - 1)) == 0
+
+
+@pytest.mark.parametrize("mode", [O.CLOSEST_HIT, O.ANY_HIT])
+def test_gate_off_changes_nothing(small, mode):
+    """A gate threshold of 0 is no gate: hits, counters and table words equal
+    a table without one, frame after frame."""
+    a = O.Table(12, 2, 6, O.TWO_PHASE)
+    b = O.Table(12, 2, 6, O.TWO_PHASE, gate_min_tp=0)
+    for f in range(3):
+        rays = small.primary_rays(frame=f)[::2]
+        ha, sa = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, mode, a)
+        hb, sb = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, mode, b)
+        assert np.array_equal(ha, hb) and sa == sb and np.array_equal(a.words, b.words)
+        assert sb["gated"] == 0
+
+
+def test_closed_gate_leaves_the_table_to_the_sampled_chunks(small):
+    """A threshold no call can reach (every lookup a true positive) closes the
+    gate after the first call.  The next call: exactly the rays of every 8th
+    32-ray chunk consult the table (a count fixed by the ray indices alone),
+    every other ray is gated and does exactly its plain traversal with no
+    insert, the results are plain's, and the table ends as it would after
+    tracing only the sampled rays with an open gate."""
+    s8 = 3
+    tab = O.Table(12, 2, 6, O.TWO_PHASE, gate_min_tp=65536, gate_sample_log2=s8)
+    ref = O.Table(12, 2, 6, O.TWO_PHASE)
+    r1 = small.primary_rays(frame=1)
+    _, st1 = O.trace(small.tris, small.nodes, small.prim_index, 0, r1, O.CLOSEST_HIT, tab)
+    O.trace(small.tris, small.nodes, small.prim_index, 0, r1, O.CLOSEST_HIT, ref)
+    assert st1["gated"] == 0 and st1["true_pos"] < st1["lookups"]
+    assert not tab.gate_open
+    r2 = small.primary_rays(frame=2)
+    n = len(r2)
+    smp = _sampled(n, s8)
+    hp, _, _, plain_boxes = O.trace(small.tris, small.nodes, small.prim_index, 0, r2, O.CLOSEST_HIT, per_ray=True)
+    hg, st2, oc, boxes = O.trace(small.tris, small.nodes, small.prim_index, 0, r2, O.CLOSEST_HIT, tab, per_ray=True)
+    assert np.array_equal(hp, hg)
+    assert st2["lookups"] == int(smp.sum()) and st2["gated"] == n - int(smp.sum())
+    assert np.all(oc[~smp] == 0)
+    assert np.array_equal(boxes[~smp], plain_boxes[~smp])
+    O.trace(small.tris, small.nodes, small.prim_index, 0, np.ascontiguousarray(r2[smp]), O.CLOSEST_HIT, ref)
+    assert np.array_equal(tab.words, ref.words)
+
+
+def test_gate_reopens_when_the_sample_predicts(small):
+    """The decision uses only the call's own consulting rays: with a
+    threshold of one true positive per 65536 lookups a closed gate reopens
+    after any call whose sampled rays hit a prediction, and a call whose
+    sampled rays see none closes it again."""
+    tab = O.Table(12, 1, 6, O.TWO_PHASE, gate_min_tp=1, gate_sample_log2=2)
+    rays = small.primary_rays(frame=0)
+    _, st = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.CLOSEST_HIT, tab)
+    assert st["true_pos"] == 0 and not tab.gate_open  # an empty table predicts nothing
+    _, st = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.CLOSEST_HIT, tab)
+    assert st["gated"] > 0 and st["true_pos"] > 0 and tab.gate_open
+    _, st = O.trace(small.tris, small.nodes, small.prim_index, 0, rays, O.CLOSEST_HIT, tab)
+    assert st["gated"] == 0 and tab.gate_open
+    # rays that all miss: no consulting ray predicts, the gate closes
+    miss = rays.copy()
+    miss[:, 4:7] = [0.0, 1.0, 0.0]
+    _, st = O.trace(small.tris, small.nodes, small.prim_index, 0, miss, O.CLOSEST_HIT, tab)
+    assert st["lookups"] == len(miss) and st["true_pos"] == 0 and not tab.gate_open
+
+
 def test_two_phase_vs_sequential_within_a_batch(small):
     """Two-phase lookups see the table as it was at batch start; sequential
     lookups see earlier rays' inserts."""

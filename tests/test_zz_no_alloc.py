@@ -54,7 +54,7 @@ def _hits_like(torch, H, n, mode, fill):
 @pytest.mark.parametrize("stats_where", ["host", "device"])
 @pytest.mark.parametrize("width", [2, 4])
 @pytest.mark.parametrize("mode_name", ["closest", "any"])
-@pytest.mark.parametrize("with_table", [False, True])
+@pytest.mark.parametrize("with_table", [False, True, "gated"])
 def test_noalloc_matches_trace_two_calls_in_a_row(mode_name, with_table, width, stats_where):
     torch, H, W = _setup()
     s = W.small_scene(width=width)
@@ -62,6 +62,9 @@ def test_noalloc_matches_trace_two_calls_in_a_row(mode_name, with_table, width, 
     mode = H.HRPP_CLOSEST_HIT if mode_name == "closest" else H.HRPP_ANY_HIT
     t_ref = H.Table(12, 2, 6) if with_table else None
     t_new = H.Table(12, 2, 6) if with_table else None
+    if with_table == "gated":  # a gate that closes after the first call
+        t_ref.set_gate(65536, 2)
+        t_new.set_gate(65536, 2)
     for frame in (1, 2):
         rays = torch.from_numpy(s.primary_rays(frame=frame)).cuda()
         h_ref = _hits_like(torch, H, rays.shape[0], mode, 0)
@@ -77,6 +80,7 @@ def test_noalloc_matches_trace_two_calls_in_a_row(mode_name, with_table, width, 
         assert read_ref() == read_new(), f"frame {frame}: counters differ"
         if with_table:
             assert np.array_equal(t_ref.export(), t_new.export()), f"frame {frame}: table words differ"
+            assert t_ref.gate_open() == t_new.gate_open()
     g.check()
 
 
