@@ -146,15 +146,29 @@ typedef struct hrpp_scene_info {
  * others change only speed.
  *   kernel_start/kernel_stop  cudaEvent_t (as void*) recorded on `stream`
  *                             immediately before and after the traversal
- *                             kernel, for timing it alone
+ *                             kernel (both launches of the COMPACT
+ *                             schedule), for timing it alone
  *   block_threads             threads per block of the traversal kernel:
  *                             0 = default, else 64, 128, 256 or 512
  *   schedule                  how warps take rays from the batch:
  *                             HRPP_SCHEDULE_DEFAULT, HRPP_SCHEDULE_BATCH (a
  *                             warp traces 32 rays to completion, then takes
- *                             32 more) or HRPP_SCHEDULE_REFILL (lanes whose
+ *                             32 more), HRPP_SCHEDULE_REFILL (lanes whose
  *                             ray is done take new rays while the rest of
- *                             the warp keeps traversing)
+ *                             the warp keeps traversing) or
+ *                             HRPP_SCHEDULE_COMPACT (the paper's ray pool,
+ *                             Sec. 4.1-4.2, in two launches: every ray's
+ *                             lookup first, one thread per ray; rays whose
+ *                             prediction answered them -- any-hit true
+ *                             positives, and closest-hit ones under
+ *                             HRPP_VERIFY_NONE -- are done, and only the
+ *                             others are queued and traversed, so no warp
+ *                             carries answered rays; 16 bytes of scratch per
+ *                             ray.  It applies to table lookups of leaves
+ *                             (Go Up Level 0) without learned predictions
+ *                             or bottom-up verification; other calls, and
+ *                             calls without a table, run BATCH.  No L2
+ *                             window is set on its launches.)
  *   refill_min                REFILL: idle lanes needed before a warp refills,
  *                             1..32 (0 = default, 24)
  *   max_steps                 node visits allowed per traversal (0 = the
@@ -197,6 +211,7 @@ typedef struct hrpp_scene_info {
 #define HRPP_SCHEDULE_DEFAULT 0u
 #define HRPP_SCHEDULE_BATCH 1u
 #define HRPP_SCHEDULE_REFILL 2u
+#define HRPP_SCHEDULE_COMPACT 3u
 #define HRPP_VERIFY_ROOT 0u
 #define HRPP_VERIFY_BOTTOM_UP 1u
 #define HRPP_VERIFY_NONE 2u
@@ -333,8 +348,14 @@ void hrpp_table_destroy(hrpp_table *table);
  *   out_stats NULL, or one hrpp_stats in device or host memory.  A host
  *             pointer makes the call wait for its kernels.
  * Host ray/hit buffers are staged through device memory the call allocates
- * and frees (stream-ordered); the call then returns after the results are
- * back in host memory.  Device buffers keep the call fully asynchronous.
+ * and frees (stream-ordered), in chunks of a multiple of 32 rays (up to 8
+ * chunks of at least 2^18 rays): chunk k+1 uploads on a library-owned copy
+ * stream and chunk k-1 downloads on another while chunk k traces on
+ * `stream`, so page-locked (pinned) buffers overlap copies with tracing.
+ * Every chunk looks up the table as the call found it and two-phase inserts
+ * land once, after the last chunk: results, counters and table equal those
+ * of the same call on device buffers.  The call returns after the results
+ * are back in host memory.  Device buffers keep the call fully asynchronous.
  * Calls that use the same table must be ordered on one stream.
  * n_rays == 0 does nothing (stats, if requested, are zeroed); n_rays above
  * 2^31 returns UNSUPPORTED.

@@ -3,6 +3,7 @@
 // the per-call orchestration of hrpp_trace.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -112,6 +113,48 @@ cudaError_t get_pool(int dev, cudaMemPool_t *pool)
     }
     *pool = g_pools[dev];
     return cudaSuccess;
+}
+
+// Staged host buffers: at most kStagedChunks chunks of at least
+// kStagedMinChunk rays (a chunk's launch still fills the GPU).
+constexpr uint32_t kStagedChunks = 8;
+constexpr uint64_t kStagedMinChunk = 1u << 18;
+
+// A pair of library-owned copy streams (uploads, downloads) for one staged
+// call; idle pairs are kept per device and reused, so concurrent staged calls
+// from several host threads each get their own pair.
+struct CopyStreams {
+    cudaStream_t up = nullptr, down = nullptr;
+};
+std::mutex g_copy_mutex;
+std::vector<CopyStreams> g_copy_idle[64];
+
+cudaError_t acquire_copy_streams(int dev, CopyStreams *out)
+{
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lk(g_copy_mutex);
+        if (!g_copy_idle[dev].empty()) {
+            *out = g_copy_idle[dev].back();
+            g_copy_idle[dev].pop_back();
+            return cudaSuccess;
+        }
+    }
+    CopyStreams c;
+    cudaError_t e = cudaStreamCreateWithFlags(&c.up, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.down, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        if (c.up) cudaStreamDestroy(c.up);
+        return e;
+    }
+    *out = c;
+    return cudaSuccess;
+}
+
+void release_copy_streams(int dev, const CopyStreams &c)
+{
+    std::lock_guard<std::mutex> lk(g_copy_mutex);
+    g_copy_idle[dev].push_back(c);
 }
 
 bool is_host_pointer(const void *ptr, bool *ok)
@@ -632,7 +675,8 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
     }
     uint32_t schedule = kDefaultSchedule, refill_min = kDefaultRefillMin;
     if (opts && opts->schedule) {
-        if (opts->schedule != HRPP_SCHEDULE_BATCH && opts->schedule != HRPP_SCHEDULE_REFILL)
+        if (opts->schedule != HRPP_SCHEDULE_BATCH && opts->schedule != HRPP_SCHEDULE_REFILL &&
+            opts->schedule != HRPP_SCHEDULE_COMPACT)
             return fail(HRPP_ERR_INVALID_ARG, "unknown schedule %u", opts->schedule);
         schedule = opts->schedule;
     }
@@ -675,14 +719,32 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
     cudaMemPool_t pool;
     if ((e = get_pool(sc->device, &pool)) != cudaSuccess) return cuda_fail(e, "memory pool");
     const bool two_phase = table && table->update_mode == HRPP_UPDATE_TWO_PHASE;
-    const size_t hit_bytes = (size_t)n_rays * (closest ? sizeof(hrpp_hit) : sizeof(uint32_t));
+    // the two-pass schedule serves table lookups of leaves (Go Up Level 0)
+    // with root or no verification; other calls run the BATCH schedule
+    const bool compact = schedule == HRPP_SCHEDULE_COMPACT && table && table->go_up == 0 &&
+                         !(opts && opts->predicted_nodes) && !(opts && opts->verify == HRPP_VERIFY_BOTTOM_UP);
+    const size_t hit_size = closest ? sizeof(hrpp_hit) : sizeof(uint32_t);
+    const size_t hit_bytes = (size_t)n_rays * hit_size;
     const size_t ray_bytes = (size_t)n_rays * sizeof(hrpp_ray);
-    // scratch: control block, insert records, staged host buffers
+    // Host buffers are staged in chunks (a multiple of 32 rays each): chunk
+    // k+1 uploads on one copy stream and chunk k-1 downloads on another while
+    // chunk k traces on the caller's stream.  Every chunk looks up the table
+    // as the call found it; the two-phase update runs once, after the last.
+    const bool staged = rays_host || hits_host;
+    uint32_t n_chunks = 1, chunk = n_rays;
+    if (staged) {
+        n_chunks = (uint32_t)std::min<uint64_t>(kStagedChunks, (n_rays + kStagedMinChunk - 1) / kStagedMinChunk);
+        chunk = (uint32_t)((((uint64_t)n_rays + n_chunks - 1) / n_chunks + 31u) & ~31ull);
+        n_chunks = (uint32_t)(((uint64_t)n_rays + chunk - 1) / chunk);
+    }
+    // scratch: control block, insert records, two-pass queue, staged buffers
     size_t off = 0;
     const size_t ctl_off = off;
     off += 256;
     const size_t rec_off = off;
     if (two_phase) off += (size_t)n_rays * sizeof(Record);
+    const size_t queue_off = off;
+    if (compact) off += (size_t)chunk * 16u;
     const size_t ray_off = off;
     if (rays_host) off += (ray_bytes + 255) & ~size_t(255);
     const size_t hit_off = off;
@@ -692,14 +754,26 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
     if ((e = cudaMallocFromPoolAsync((void **)&scratch, off, pool, stream)) != cudaSuccess)
         return cuda_fail(e, "scratch allocation");
     Ctl *ctl = reinterpret_cast<Ctl *>(scratch + ctl_off);
-    const hrpp_ray *d_rays = rays_host ? reinterpret_cast<const hrpp_ray *>(scratch + ray_off) : rays;
-    void *d_hits = hits_host ? (void *)(scratch + hit_off) : out_hits;
+    char *d_rays = rays_host ? scratch + ray_off : (char *)rays;
+    char *d_hits = hits_host ? scratch + hit_off : (char *)out_hits;
+    CopyStreams cs;
+    std::vector<cudaEvent_t> events;
+    auto event = [&](cudaEvent_t *ev) {
+        cudaError_t err = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        if (err == cudaSuccess) events.push_back(*ev);
+        return err;
+    };
     hrpp_status status = HRPP_OK;
     do {
         if ((e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), stream)) != cudaSuccess) { status = cuda_fail(e, "memset"); break; }
-        if (rays_host && (e = cudaMemcpyAsync((void *)d_rays, rays, ray_bytes, cudaMemcpyHostToDevice, stream)) != cudaSuccess) {
-            status = cuda_fail(e, "ray upload");
-            break;
+        if (staged) {
+            if ((e = acquire_copy_streams(sc->device, &cs)) != cudaSuccess) { status = cuda_fail(e, "copy streams"); break; }
+            cudaEvent_t ready;
+            if ((e = event(&ready)) != cudaSuccess || (e = cudaEventRecord(ready, stream)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(cs.up, ready, 0)) != cudaSuccess) {
+                status = cuda_fail(e, "staging order");
+                break;
+            }
         }
         TraceParams p;
         memset(&p, 0, sizeof p);
@@ -710,13 +784,6 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         p.max_steps = sc->n_interior + sc->n_leaves + 8u;
         if (opts && opts->max_steps > 0u && opts->max_steps < p.max_steps) p.max_steps = opts->max_steps;
         p.verify = opts ? (int)opts->verify : 0;
-        if (opts && out_stats) {
-            p.ray_outcome = opts->ray_outcome;
-            p.ray_box_tests = opts->ray_box_tests;
-        }
-        p.rays = reinterpret_cast<const float4 *>(d_rays);
-        p.n_rays = n_rays;
-        p.hits = d_hits;
         p.ctl = ctl;
         p.error = sc->d_error;
         p.refill_min = refill_min;
@@ -725,7 +792,6 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         p.leaf_parent = sc->d_leaf_parent;
         p.canon_ref = sc->d_canon_ref;
         p.n_nodes = sc->n_nodes;
-        p.predicted = opts ? opts->predicted_nodes : nullptr;
         if (table) {
             p.table = table->d_words;
             p.winner = table->d_winner;
@@ -750,9 +816,56 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
             l2 = L2Window{table->d_words, sizeof(uint64_t) << table->log2_entries};
         else if (opts && opts->l2_persist == HRPP_L2_NODES)
             l2 = L2Window{sc->d_nodes, (size_t)sc->n_interior * (sc->width == 2 ? 64u : 128u)};
-        e = sc->width == 2 ? launch_trace_w2(closest, out_stats != nullptr, sched, p, (int)block_threads, 0, stream, ev0, ev1, &l2)
-                           : launch_trace_w4(closest, out_stats != nullptr, sched, p, (int)block_threads, 0, stream, ev0, ev1, &l2);
-        if (e != cudaSuccess) { status = cuda_fail(e, "trace launch"); break; }
+        for (uint32_t k = 0; k < n_chunks && status == HRPP_OK; ++k) {
+            const uint64_t first = (uint64_t)k * chunk;
+            const uint32_t cnt = (uint32_t)std::min<uint64_t>(chunk, n_rays - first);
+            if (rays_host) {
+                cudaEvent_t up_done;
+                if ((e = cudaMemcpyAsync(d_rays + first * sizeof(hrpp_ray), (const char *)rays + first * sizeof(hrpp_ray),
+                                         (size_t)cnt * sizeof(hrpp_ray), cudaMemcpyHostToDevice, cs.up)) != cudaSuccess ||
+                    (e = event(&up_done)) != cudaSuccess || (e = cudaEventRecord(up_done, cs.up)) != cudaSuccess ||
+                    (e = cudaStreamWaitEvent(stream, up_done, 0)) != cudaSuccess) {
+                    status = cuda_fail(e, "ray upload");
+                    break;
+                }
+            }
+            // each chunk restarts the ray pool's cursor and the queue
+            if (k > 0 && (e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned int), stream)) != cudaSuccess) {
+                status = cuda_fail(e, "memset");
+                break;
+            }
+            TraceParams pk = p;
+            pk.rays = reinterpret_cast<const float4 *>(d_rays + first * sizeof(hrpp_ray));
+            pk.hits = d_hits + first * hit_size;
+            pk.n_rays = cnt;
+            pk.ray_offset = (uint32_t)first;
+            pk.predicted = (opts && opts->predicted_nodes) ? opts->predicted_nodes + first : nullptr;
+            if (opts && out_stats) {
+                pk.ray_outcome = opts->ray_outcome ? opts->ray_outcome + first : nullptr;
+                pk.ray_box_tests = opts->ray_box_tests ? opts->ray_box_tests + first : nullptr;
+            }
+            cudaEvent_t e0 = k == 0 ? ev0 : nullptr, e1 = k + 1 == n_chunks ? ev1 : nullptr;
+            if (compact)
+                e = sc->width == 2 ? launch_compact_w2(closest, out_stats != nullptr, pk, scratch + queue_off, (int)block_threads,
+                                                       stream, e0, e1)
+                                   : launch_compact_w4(closest, out_stats != nullptr, pk, scratch + queue_off, (int)block_threads,
+                                                       stream, e0, e1);
+            else
+                e = sc->width == 2 ? launch_trace_w2(closest, out_stats != nullptr, sched, pk, (int)block_threads, 0, stream, e0, e1, &l2)
+                                   : launch_trace_w4(closest, out_stats != nullptr, sched, pk, (int)block_threads, 0, stream, e0, e1, &l2);
+            if (e != cudaSuccess) { status = cuda_fail(e, "trace launch"); break; }
+            if (hits_host) {
+                cudaEvent_t traced;
+                if ((e = event(&traced)) != cudaSuccess || (e = cudaEventRecord(traced, stream)) != cudaSuccess ||
+                    (e = cudaStreamWaitEvent(cs.down, traced, 0)) != cudaSuccess ||
+                    (e = cudaMemcpyAsync((char *)out_hits + first * hit_size, d_hits + first * hit_size, (size_t)cnt * hit_size,
+                                         cudaMemcpyDeviceToHost, cs.down)) != cudaSuccess) {
+                    status = cuda_fail(e, "hit download");
+                    break;
+                }
+            }
+        }
+        if (status != HRPP_OK) break;
         if (two_phase) e = launch_table_apply(table->d_words, table->d_winner, p.records, ctl, n_rays, stream, p.gate,
                                               p.gate_min_tp);
         else if (p.gate) e = launch_gate_update(p.gate, p.gate_min_tp, ctl, stream);
@@ -761,21 +874,34 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
             break;
         }
         if (table) table->bound_scene = sc->id;
-        if (hits_host && (e = cudaMemcpyAsync(out_hits, d_hits, hit_bytes, cudaMemcpyDeviceToHost, stream)) != cudaSuccess) {
-            status = cuda_fail(e, "hit download");
-            break;
-        }
         if (out_stats) {
             e = cudaMemcpyAsync(out_stats, ctl->stats, sizeof(hrpp_stats),
                                 stats_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, stream);
             if (e != cudaSuccess) { status = cuda_fail(e, "stats copy"); break; }
         }
     } while (false);
+    if (cs.up) {
+        // the scratch is freed in stream order: after the last download
+        cudaEvent_t drained = nullptr;
+        cudaError_t ed = event(&drained);
+        if (ed == cudaSuccess) ed = cudaEventRecord(drained, cs.down);
+        if (ed == cudaSuccess) ed = cudaStreamWaitEvent(stream, drained, 0);
+        if (ed != cudaSuccess) {
+            cudaStreamSynchronize(cs.up);
+            cudaStreamSynchronize(cs.down);
+        }
+        if (ed != cudaSuccess && status == HRPP_OK) status = cuda_fail(ed, "staging order");
+    }
     cudaError_t ef = cudaFreeAsync(scratch, stream);
+    if (staged || stats_host) {
+        if ((e = cudaStreamSynchronize(stream)) != cudaSuccess && status == HRPP_OK)
+            status = cuda_fail(e, "cudaStreamSynchronize");
+    }
+    if (cs.up) release_copy_streams(sc->device, cs);
+    for (cudaEvent_t ev : events) cudaEventDestroy(ev);
     if (status != HRPP_OK) return status;
     if (ef != cudaSuccess) return cuda_fail(ef, "scratch free");
-    if (stats_host || hits_host) {
-        if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (stats_host || staged) {
         uint32_t flag = 0;
         if ((e = cudaMemcpy(&flag, sc->d_error, sizeof flag, cudaMemcpyDeviceToHost)) != cudaSuccess)
             return cuda_fail(e, "reading the error flag");

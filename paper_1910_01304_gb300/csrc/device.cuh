@@ -32,16 +32,21 @@ enum Stat : int {
     ST_PRED_LEAVES, ST_PRED_TRI_TESTS, ST_PRED_INTERIOR, ST_PRED_BOX_TESTS, ST_GATED, ST_N = 20
 };
 
-// Per-call device control block: the ray pool's cursor, the insert-record
-// count, the table gate's counts (rays that consulted the table, and the true
-// positives among them) and the statistics.  Zeroed before each call.
+// Per-call device control block: the ray pool's cursor and the two-pass
+// schedule's queue length (both restarted for every chunk of a staged call),
+// the insert-record count, the table gate's counts (rays that consulted the
+// table, and the true positives among them) and the statistics.  Zeroed
+// before each call.
 struct __align__(16) Ctl {
     unsigned int next_ray;
+    unsigned int queue_len;
     unsigned int n_records;
     unsigned int gate_lookups;
     unsigned int gate_tp;
+    unsigned int pad[3];
     unsigned long long stats[ST_N];
 };
+static_assert(sizeof(Ctl) <= 256, "the control block has 256 bytes of scratch");
 
 // A table's gate word: nonzero = open (every ray consults the table), zero =
 // closed (only the sampled 32-ray chunks do).
@@ -97,6 +102,9 @@ struct TraceParams {
     uint32_t *gate;              // the table's gate word (null: no gate, every ray consults the table)
     uint32_t gate_mask;          // closed gate: 32-ray chunks c with (c & gate_mask) == 0 still consult it
     uint32_t gate_min_tp;        // true positives per 65536 lookups that keep the gate open
+    uint32_t ray_offset;         // index of this launch's first ray in its call (a multiple of 32): rays,
+                                 // hits and per-ray arrays start there, while insert order, the gate's
+                                 // chunks and the online way use the call's ray index i + ray_offset
 };
 
 // 32 bytes through the read-only data path in one load (p 32-byte aligned):
@@ -256,6 +264,12 @@ cudaError_t launch_trace_w2(bool closest, bool stats, int schedule, const TraceP
 cudaError_t launch_trace_w4(bool closest, bool stats, int schedule, const TraceParams &p, int block_threads,
                             int blocks_per_sm_cap, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1,
                             const L2Window *l2 = nullptr);
+// two-pass schedule (compact.cuh): k_predict, then k_trace_queue over the
+// queue (16 bytes per ray of scratch, 16-byte aligned)
+cudaError_t launch_compact_w2(bool closest, bool stats, const TraceParams &p, void *queue, int block_threads,
+                              cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1);
+cudaError_t launch_compact_w4(bool closest, bool stats, const TraceParams &p, void *queue, int block_threads,
+                              cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1);
 cudaError_t launch_table_apply(uint64_t *table, uint32_t *winner, const Record *records, Ctl *ctl,
                                uint32_t max_records, cudaStream_t stream, uint32_t *gate = nullptr,
                                uint32_t gate_min_tp = 0);

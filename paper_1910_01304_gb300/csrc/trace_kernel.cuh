@@ -35,6 +35,7 @@
 namespace hrpp {
 
 constexpr int32_t kDoneRef = INT32_MIN + 1;  // traversal finished
+constexpr int kMaxWarps = 16;                // warps per block (512 threads)
 constexpr uint32_t kNoRay = 0xFFFFFFFFu;
 
 __device__ __forceinline__ uint32_t lanemask_lt()
@@ -70,18 +71,30 @@ struct Counters {
 
 // Gate counts of the rays a warp just finished (all 32 lanes call this
 // together): gflags bit 0 = the ray consulted the table, bit 1 = it was a
-// true positive.  Two warp votes and, with a gate, two atomics per warp.
+// true positive.  Two warp votes, summed by lane 0 into the warp's own
+// shared-memory slot (no register stays live across the traversal, and no
+// global atomic per chunk); gate_flush adds the slot to the call's counts.
 constexpr uint32_t kGateLooked = 1u, kGateTp = 2u;
 
-__device__ __forceinline__ void gate_count(const TraceParams &p, uint32_t lane, uint32_t gflags)
+__device__ __forceinline__ void gate_count(const TraceParams &p, uint32_t lane, uint32_t gflags, uint2 &acc)
 {
     if (!p.gate) return;  // warp-uniform
     const uint32_t l = __popc(__ballot_sync(0xFFFFFFFFu, gflags & kGateLooked));
     const uint32_t t = __popc(__ballot_sync(0xFFFFFFFFu, gflags & kGateTp));
     if (lane == 0) {
-        if (l) atomicAdd(&p.ctl->gate_lookups, l);
-        if (t) atomicAdd(&p.ctl->gate_tp, t);
+        acc.x += l;
+        acc.y += t;
     }
+}
+
+__device__ __forceinline__ void gate_flush(const TraceParams &p, uint32_t lane, uint2 &acc)
+{
+    if (lane == 0) {
+        if (p.gate && acc.x) atomicAdd(&p.ctl->gate_lookups, acc.x);
+        if (p.gate && acc.y) atomicAdd(&p.ctl->gate_tp, acc.y);
+        acc = make_uint2(0u, 0u);
+    }
+    __syncwarp();
 }
 
 struct Best {
@@ -302,7 +315,7 @@ __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayS
     const bool learned = p.predicted != nullptr;
     // a closed gate leaves the table to the sampled chunks' rays (finish_ray
     // takes the same decision again instead of keeping it in a register)
-    const bool consult = p.table != nullptr && gate_admits(p.gate, p.gate_mask, i);
+    const bool consult = p.table != nullptr && gate_admits(p.gate, p.gate_mask, i + p.ray_offset);
     if (p.table && !consult) cnt.add(ST_GATED);
     if (consult || learned) {
         cnt.add(ST_LOOKUPS);
@@ -449,7 +462,7 @@ __device__ __forceinline__ bool finish_ray(const TraceParams &p, uint32_t i, con
                                            uint32_t &gflags, uint32_t &slot, uint64_t &word)
 {
     bool want_record = false;
-    const bool consulted = p.table != nullptr && gate_admits(p.gate, p.gate_mask, i);
+    const bool consulted = p.table != nullptr && gate_admits(p.gate, p.gate_mask, i + p.ray_offset);
     gflags = consulted ? (kGateLooked | (s.outcome == HRPP_OUTCOME_TRUE_POS ? kGateTp : 0u)) : 0u;
     if (CLOSEST && s.predicted_hit && s.b.from_trav) cnt.add(ST_TP_INEXACT);
     // Sec. 5: a ray that traversed inserts the node of its final hit (the leaf,
@@ -479,7 +492,7 @@ __device__ __forceinline__ bool finish_ray(const TraceParams &p, uint32_t i, con
             cnt.add(ST_INSERTS);
             word = w;
             if (p.update_mode == HRPP_UPDATE_ONLINE) {
-                online_insert(p, s.set, i, word, cnt);
+                online_insert(p, s.set, i + p.ray_offset, word, cnt);
             } else {
                 slot = (s.set << p.log2_ways) | way_of(node, p.log2_ways);
                 want_record = true;  // append_records claims the slot
@@ -518,7 +531,7 @@ __device__ __forceinline__ void append_records(const TraceParams &p, uint32_t la
             want = false;
         }
     }
-    if (want) atomicMax(p.winner + slot, ray + 1u);
+    if (want) atomicMax(p.winner + slot, p.ray_offset + ray + 1u);
     const uint32_t m = __ballot_sync(0xFFFFFFFFu, want);
     const uint32_t leader = __ffs(m) - 1;
     uint32_t rb = 0;
@@ -527,7 +540,7 @@ __device__ __forceinline__ void append_records(const TraceParams &p, uint32_t la
     if (want) {
         Record r;
         r.slot = slot;
-        r.ray1 = ray + 1u;
+        r.ray1 = p.ray_offset + ray + 1u;
         r.word = word;
         p.records[rb + __popc(m & lanemask_lt())] = r;
     }
@@ -611,7 +624,11 @@ __device__ __forceinline__ bool trace_one(const TraceParams &p, uint32_t i, int3
 template <int W, bool CLOSEST, bool STATS, bool BU = false>
 __global__ void __launch_bounds__(512) k_trace(const TraceParams p)
 {
+    __shared__ uint2 gate_acc[kMaxWarps];
     const uint32_t lane = threadIdx.x & 31u;
+    uint2 &gacc = gate_acc[threadIdx.x >> 5];
+    if (lane == 0) gacc = make_uint2(0u, 0u);
+    __syncwarp();
     Counters<STATS> cnt;
     cnt.init();
     int32_t stack[kStack];
@@ -626,9 +643,10 @@ __global__ void __launch_bounds__(512) k_trace(const TraceParams p)
         uint64_t word = 0;
         if (i < p.n_rays) want = trace_one<W, CLOSEST, STATS, BU>(p, i, stack, cnt, gflags, slot, word);
         append_records<true>(p, lane, want, slot, i, word, cnt);
-        gate_count(p, lane, gflags);
+        gate_count(p, lane, gflags, gacc);
     }
     cnt.flush(p.ctl, lane);
+    gate_flush(p, lane, gacc);
 }
 
 // Many (scene, table, rays) items of one query mode in one persistent
@@ -643,8 +661,11 @@ template <int W, bool CLOSEST, bool STATS>
 __global__ void __launch_bounds__(512) k_trace_batch(const BatchDesc b)
 {
     __shared__ TraceParams item_params[kBatchMaxWarps];
+    __shared__ uint2 gate_acc[kBatchMaxWarps];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     TraceParams &p = item_params[warp];
+    uint2 &gacc = gate_acc[warp];
+    if (lane == 0) gacc = make_uint2(0u, 0u);
     Counters<STATS> cnt;
     cnt.init();
     int32_t stack[kStack];
@@ -656,7 +677,10 @@ __global__ void __launch_bounds__(512) k_trace_batch(const BatchDesc b)
         if (chunk >= b.n_chunks) break;
         const uint32_t item = __ldg(b.chunk_item + chunk);
         if (item != cur) {
-            if (cur != 0xFFFFFFFFu) cnt.flush(p.ctl, lane);
+            if (cur != 0xFFFFFFFFu) {
+                cnt.flush(p.ctl, lane);
+                gate_flush(p, lane, gacc);
+            }
             cnt.init();
             __syncwarp();
             const uint32_t *src = reinterpret_cast<const uint32_t *>(b.items + item);
@@ -671,9 +695,12 @@ __global__ void __launch_bounds__(512) k_trace_batch(const BatchDesc b)
         uint64_t word = 0;
         if (i < p.n_rays) want = trace_one<W, CLOSEST, STATS>(p, i, stack, cnt, gflags, slot, word);
         append_records<true>(p, lane, want, slot, i, word, cnt);
-        gate_count(p, lane, gflags);
+        gate_count(p, lane, gflags, gacc);
     }
-    if (cur != 0xFFFFFFFFu) cnt.flush(p.ctl, lane);
+    if (cur != 0xFFFFFFFFu) {
+        cnt.flush(p.ctl, lane);
+        gate_flush(p, lane, gacc);
+    }
 }
 
 template <int W>
@@ -705,7 +732,11 @@ constexpr int kRefillSteps = 16;
 template <int W, bool CLOSEST, bool STATS, bool BU = false>
 __global__ void __launch_bounds__(512) k_trace_dyn(const TraceParams p)
 {
+    __shared__ uint2 gate_acc[kMaxWarps];
     const uint32_t lane = threadIdx.x & 31u;
+    uint2 &gacc = gate_acc[threadIdx.x >> 5];
+    if (lane == 0) gacc = make_uint2(0u, 0u);
+    __syncwarp();
     Counters<STATS> cnt;
     cnt.init();
     int32_t stack[kStack];
@@ -754,11 +785,12 @@ __global__ void __launch_bounds__(512) k_trace_dyn(const TraceParams p)
             uint64_t word = 0;
             if (done) want = finish_ray<CLOSEST, STATS>(p, ray, s, cnt, gflags, slot, word);
             append_records<false>(p, lane, want, slot, ray, word, cnt);
-            gate_count(p, lane, gflags);
+            gate_count(p, lane, gflags, gacc);
             if (done) ray = kNoRay;
         }
     }
     cnt.flush(p.ctl, lane);
+    gate_flush(p, lane, gacc);
 }
 
 template <int W>

@@ -50,7 +50,7 @@ class hrpp_trace_opts(ctypes.Structure):
                 ("ray_outcome", ctypes.c_void_p), ("ray_box_tests", ctypes.c_void_p)]
 
 
-HRPP_SCHEDULE_DEFAULT, HRPP_SCHEDULE_BATCH, HRPP_SCHEDULE_REFILL = 0, 1, 2
+HRPP_SCHEDULE_DEFAULT, HRPP_SCHEDULE_BATCH, HRPP_SCHEDULE_REFILL, HRPP_SCHEDULE_COMPACT = 0, 1, 2, 3
 HRPP_VERIFY_ROOT, HRPP_VERIFY_BOTTOM_UP, HRPP_VERIFY_NONE = 0, 1, 2
 HRPP_HASH_EXP_MSB, HRPP_HASH_EXP_LSB = 0, 1
 HRPP_GEMM_A_MN_MAJOR, HRPP_GEMM_B_MN_MAJOR = 1, 2

@@ -357,6 +357,42 @@ def test_table_copy_restores_a_snapshot(H, small_pair):
         assert err.value.status == H.HRPP_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("schedule", [1, 3])
+@pytest.mark.parametrize("mode", [O.CLOSEST_HIT, O.ANY_HIT])
+def test_staged_host_buffers_in_chunks_match_device_path(H, small_pair, mode, schedule):
+    """Host ray and hit buffers above the staging chunk size (here 3 chunks
+    with a ragged tail): pinned and pageable host memory give exactly the
+    device path's hits, counters and table words over two calls, with a
+    two-phase table whose gate samples by the call's ray index."""
+    import torch
+    s, g = small_pair[1]
+    n = 10 * 65536 + 17
+    frames = [np.concatenate([s.primary_rays(frame=f) for f in range(k, k + 11)])[:n] for k in (0, 11)]
+    if mode == O.ANY_HIT:
+        out = []
+        for r in frames:
+            h, _ = H.trace(g, torch.from_numpy(r).cuda(), H.HRPP_CLOSEST_HIT)
+            hh = h.cpu().numpy()
+            out.append(np.ascontiguousarray(W.secondary_shadow(s, r, hh[:, 0], hh[:, 1].view(np.uint32))[0]))
+        frames = out
+    for pinned in (True, False):
+        t_dev, t_host = H.Table(14, 2, 6), H.Table(14, 2, 6)
+        for t in (t_dev, t_host):
+            t.set_gate(2000, 2)
+        for rays in frames:
+            ref, rst = H.trace(g, torch.from_numpy(rays).cuda(), mode, t_dev, stats=True, schedule=schedule)
+            hr = torch.from_numpy(rays)
+            hits = torch.empty(tuple(ref.shape), dtype=ref.dtype)
+            if pinned:
+                hr, hits = hr.pin_memory(), hits.pin_memory()
+            got, gst = H.trace(g, hr, mode, t_host, hits=hits, stats=True, schedule=schedule)
+            torch.cuda.synchronize()
+            assert torch.equal(got.view(torch.int32), ref.cpu().view(torch.int32)), f"pinned={pinned}"
+            assert gst == rst, f"pinned={pinned}"
+            assert np.array_equal(t_dev.export(), t_host.export()) and t_dev.gate_open() == t_host.gate_open()
+        assert rst["rays"] == n and (rst["gated"] > 0 or rst["lookups"] == n)
+
+
 def test_block_sizes_give_identical_results(H, small_pair):
     s, g = small_pair[1]
     rays = s.primary_rays(frame=5)
@@ -398,7 +434,8 @@ def test_schedules_give_identical_results(H, small_pair, width_idx, mode):
     s, g = small_pair[width_idx]
     variants = [dict(schedule=H.HRPP_SCHEDULE_BATCH), dict(schedule=H.HRPP_SCHEDULE_REFILL, refill_min=1),
                 dict(schedule=H.HRPP_SCHEDULE_REFILL, refill_min=8, block_threads=256),
-                dict(schedule=H.HRPP_SCHEDULE_REFILL, refill_min=32, block_threads=64)]
+                dict(schedule=H.HRPP_SCHEDULE_REFILL, refill_min=32, block_threads=64),
+                dict(schedule=H.HRPP_SCHEDULE_COMPACT), dict(schedule=H.HRPP_SCHEDULE_COMPACT, block_threads=512)]
     prim = s.primary_rays(frame=2)
     ph, _ = _oracle(s, prim, O.CLOSEST_HIT)
     rays = prim if mode == O.CLOSEST_HIT else W.secondary_shadow(s, prim, ph["t"], ph["prim"])[0]
@@ -416,6 +453,53 @@ def test_schedules_give_identical_results(H, small_pair, width_idx, mode):
         assert_same_hits(mode, gh.cpu().numpy(), oh, str(v))
         assert_same_stats(gst, ost, msg=str(v))
         assert np.array_equal(tab.export(), otab.words), str(v)
+
+
+@pytest.mark.parametrize("verify", [0, 2])
+@pytest.mark.parametrize("gated", [False, True])
+def test_compact_schedule_matches_oracle(H, verify, gated):
+    """The two-pass schedule (the ray pool of Sec. 4.1-4.2: lookups first,
+    answered rays leave, the rest are queued and traversed) on the terrain
+    recipe at reduced size, over frames whose any-hit AO rays and closest-hit
+    primaries are partly predicted: hits, every counter, per-ray outcomes and
+    box tests, table words and gate state equal the oracle's, with root
+    verification (exact) and without (the paper's semantics).  The batches
+    are ragged (not multiples of the 256-ray pass-1 block)."""
+    import torch
+    s = W.terrain_scene(quads=96, n_spheres=6, subdiv=3, res=(203, 117))
+    g = H.Scene.from_workload(s)
+    gate = (2500, 3) if gated else (0, 5)
+    tabs = {m: H.Table(14, 2, 6) for m in (O.CLOSEST_HIT, O.ANY_HIT)}
+    otabs = {m: O.Table(14, 2, 6, O.TWO_PHASE, gate_min_tp=gate[0], gate_sample_log2=gate[1])
+             for m in (O.CLOSEST_HIT, O.ANY_HIT)}
+    for t in tabs.values():
+        t.set_gate(*gate)
+    answered = 0
+    for frame in range(4):
+        prim = s.primary_rays(frame=frame % 3)
+        ph, _ = _oracle(s, prim, O.CLOSEST_HIT)
+        ao, _ = W.secondary_ao(s, prim, ph["t"], ph["prim"], frame=frame % 3)
+        for mode, rays in ((O.CLOSEST_HIT, prim), (O.ANY_HIT, ao)):
+            v = verify if mode == O.CLOSEST_HIT else 0
+            oh, ost, ooc, obx = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, mode, otabs[mode],
+                                        per_ray=True, verify=v)
+            d = torch.from_numpy(rays).cuda()
+            oc = torch.full((len(rays),), 255, dtype=torch.uint8, device="cuda")
+            bx = torch.full((len(rays),), -1, dtype=torch.int32, device="cuda")
+            gh, gst = H.trace(g, d, mode, tabs[mode], stats=True, schedule=H.HRPP_SCHEDULE_COMPACT, verify=v,
+                              ray_outcome=oc, ray_box_tests=bx)
+            torch.cuda.synchronize()
+            g.check()
+            msg = f"frame {frame} mode {mode}"
+            assert_same_hits(mode, gh.cpu().numpy(), oh, msg)
+            assert_same_stats(gst, ost, msg=msg)
+            assert np.array_equal(oc.cpu().numpy(), ooc), msg
+            assert np.array_equal(bx.cpu().numpy().view(np.uint32), obx), msg
+            assert np.array_equal(tabs[mode].export(), otabs[mode].words), msg
+            assert tabs[mode].gate_open() == otabs[mode].gate_open, msg
+            if mode == O.ANY_HIT or verify == 2:
+                answered += gst["true_pos"]
+    assert answered > 0
 
 
 @pytest.mark.parametrize("go_up", [1, 2, 5])
