@@ -10,12 +10,14 @@ of 708x708 quads plus 64 icospheres, 2,313,248 triangles, 4-wide BVH.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hrpp|reference]
 
 Prints one JSON line (rank 0).  `value` is HRPP Mrays/s over all ranks with
-the rays already resident on the GPU; `e2e` is the same from pinned host
-memory, every step's rays uploaded and hits downloaded inside the timed region
-(a double-buffered frame loop whose copies overlap the traces; `e2e.staged`
-is hrpp_trace on host buffers, one stream); `plain` gives the same library
-with no table on the same rays.  The reference arm times the CPU
-oracle on a bounded sample of the same workload.
+the rays already resident on the GPU; `e2e` is the same through hrpp_trace on
+pinned host buffers, every step's rays uploaded and hits downloaded inside the
+timed region (the library stages each batch in chunks whose copies overlap
+its traces; `e2e.torch_pipeline` is a device-buffer frame loop with its own
+copy streams); `plain` gives the same library with no table on the same rays;
+`gated` the same tables under a gate policy; `configs` the small-scene and
+path-tracing workloads (configs 1 and 5) with their own rooflines.  The
+reference arm times the CPU oracle on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -65,6 +67,10 @@ def parse():
                     help="terrain: the headline step; batched: the 64-scene uneven mix in one graph-replayed launch")
     ap.add_argument("--scenes", type=int, default=64)
     ap.add_argument("--no-learned", action="store_true", help="pathtrace: skip the learned proposal")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="terrain: leave out the small-scene and path-tracing sub-results")
+    ap.add_argument("--l2-variants", action="store_true",
+                    help="terrain: also time the step with persisting-L2 windows over the table and the nodes")
     return ap.parse_args()
 
 
@@ -168,7 +174,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("trace_kernel.cuh", "device.cuh", "table.cu"):
+    for f in ("trace_kernel.cuh", "compact.cuh", "device.cuh", "table.cu"):
         with open(os.path.join(ROOT, "paper_1910_01304_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -569,13 +575,68 @@ def run_batched(args):
     return 0
 
 
-def run_small(args):
+# Gate thresholds (true positives per 65536 lookups) of the "gated" variants:
+# an any-hit true positive saves a whole traversal, and on these workloads a
+# lookup costs about 4 % of one (the terrain AO launch: 1.108 against
+# 1.066 ms), so hit-any tables keep predicting above 4 %; an exact closest-hit
+# true positive still traverses, bounded by its hit, which saved at most
+# 3.4 % of its box tests here -- less than the lookup costs -- so hit-all
+# tables stay closed (100 %) and keep only their 1-in-32 sample.
+GATE = {"closest": 65536, "any": 2621}
+GATE_SAMPLE_LOG2 = 5
+
+
+def make_tables(H, log2e, ways, precision, gated: bool, update=0):
+    """(closest, any) tables, with the gate policy when gated."""
+    out = []
+    for name in ("closest", "any"):
+        t = H.Table(log2e, ways, precision, update)
+        if gated:
+            t.set_gate(GATE[name], GATE_SAMPLE_LOG2)
+        out.append(t)
+    return tuple(out)
+
+
+def summarize_config(line: dict) -> dict:
+    """The part of a config's own bench line that the headline line carries."""
+    keep = ("value", "unit", "ms_per_step", "plain", "gated", "per_mode_kernel_ms", "skipped", "roofline", "config",
+            "sequential", "per_bounce")
+    out = {k: line[k] for k in keep if k in line}
+    out["speedup_hrpp_over_plain"] = line["plain"]["speedup_hrpp_over_plain"]
+    return out
+
+
+def limit_study() -> dict | None:
+    """The paper's limit study on configs 1 and 2 (unbounded sequential table,
+    8 jittered frames as 8 spp), computed by the oracle and stored by
+    tests/golden/make_limit_study.py; None if it was not generated."""
+    path = os.path.join(ROOT, "tests", "golden", "limit_study.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    return {"what": d["what"],
+            "entries": [{k: e[k] for k in ("workload", "query", "precision", "rays", "prediction_ratio",
+                                           "skipped_limit_box_tests", "table_mb")} for e in d["entries"]]}
+
+
+def max_sm_mhz():
+    """The SM clock the issue-rate peak assumes when no clock was sampled:
+    the maximum MEASURED_PEAKS.json records (2,070 MHz on GB300)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return float(json.load(fh).get("sm_max_mhz", 2070.0))
+    return 2070.0
+
+
+def run_small(args, emit: bool = True, sm_mhz=None):
     """Config 1: the small scene (1,792 tris, binary BVH), 256x256 primary
     closest-hit rays and one shadow any-hit ray per hit, 2^12-entry
     direct-mapped tables.  Each step restores the tables warmed by the other
     frames and traces frame 0's two batches side by side; the step is
     captured into a CUDA graph (these launches are latency-bound) and
-    replayed."""
+    replayed.  Returns the line (printed when emit)."""
     rank, world, local = dist_env()
     import torch
     torch.cuda.set_device(local)
@@ -592,13 +653,17 @@ def run_small(args):
         hh = hits.cpu().numpy()
         shadow, _ = W.secondary_shadow(s, prim, hh[:, 0], hh[:, 1].view(np.uint32))
         frames.append((torch.from_numpy(prim).cuda(), torch.from_numpy(shadow).cuda()))
-    tab_c, tab_a = H.Table(12, 1, 6), H.Table(12, 1, 6)
-    for prim, shadow in frames[1:]:
-        H.trace(g, prim, H.HRPP_CLOSEST_HIT, tab_c)
-        H.trace(g, shadow, H.HRPP_ANY_HIT, tab_a)
-    snap_c, snap_a = H.Table(12, 1, 6), H.Table(12, 1, 6)
-    snap_c.copy_from(tab_c)
-    snap_a.copy_from(tab_a)
+
+    def warm(gated):
+        tabs = make_tables(H, 12, 1, 6, gated)
+        for prim, shadow in frames[1:]:
+            H.trace(g, prim, H.HRPP_CLOSEST_HIT, tabs[0])
+            H.trace(g, shadow, H.HRPP_ANY_HIT, tabs[1])
+        snaps = make_tables(H, 12, 1, 6, gated)
+        snaps[0].copy_from(tabs[0])
+        snaps[1].copy_from(tabs[1])
+        return tabs, snaps
+
     prim, shadow = frames[0]
     out_c = torch.empty((prim.shape[0], 4), dtype=torch.float32, device="cuda")
     out_a = torch.empty((shadow.shape[0],), dtype=torch.int32, device="cuda")
@@ -606,13 +671,13 @@ def run_small(args):
 
     fork_stream = torch.cuda.Stream()
 
-    def step(tables):
+    def step(tables, snaps):
         # the primary and shadow batches are independent inputs with one
         # table each: traced side by side (fork and join, also under capture)
         cur = torch.cuda.current_stream()
         if tables[0] is not None:
-            tables[0].copy_from(snap_c)
-            tables[1].copy_from(snap_a)
+            tables[0].copy_from(snaps[0])
+            tables[1].copy_from(snaps[1])
         fork = torch.cuda.Event()
         fork.record(cur)
         fork_stream.wait_event(fork)
@@ -622,18 +687,18 @@ def run_small(args):
         join.record(fork_stream)
         cur.wait_event(join)
 
-    def timed(tables):
-        graph, replay = None, lambda: step(tables)
+    def timed(tables, snaps):
+        graph, replay = None, lambda: step(tables, snaps)
         try:
             side = torch.cuda.Stream()
             side.wait_stream(torch.cuda.current_stream())
             with torch.cuda.stream(side):
                 for _ in range(3):
-                    step(tables)
+                    step(tables, snaps)
             torch.cuda.current_stream().wait_stream(side)
             graph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(graph):
-                step(tables)
+                step(tables, snaps)
             replay = graph.replay
         except Exception as exc:  # capture unsupported: time plain launches
             print(f"CUDA graph capture failed ({exc}); timing launches", file=sys.stderr)
@@ -649,20 +714,58 @@ def run_small(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / args.steps, graph is not None
 
-    ms, graphed = timed((tab_c, tab_a))
-    p_ms, p_graphed = timed((None, None))
-    tab_c.copy_from(snap_c)
-    tab_a.copy_from(snap_a)
-    _, sc = H.trace(g, prim, H.HRPP_CLOSEST_HIT, tab_c, stats=True)
-    _, sa = H.trace(g, shadow, H.HRPP_ANY_HIT, tab_a, stats=True)
+    tabs, snaps = warm(False)
+    gtabs, gsnaps = warm(True)
+    ms, graphed = timed(tabs, snaps)
+    g_ms, _ = timed(gtabs, gsnaps)
+    p_ms, p_graphed = timed((None, None), (None, None))
+
+    # each launch alone (no graph), from the restored tables: the roofline's
+    # kernel times, and the counters of one step
+    def launch_ms(rays, mode, table, snap, hits, reps=20):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record(); b.record()
+        for e in [None] * 3 + ev:
+            if table is not None:
+                table.copy_from(snap)
+            H.trace(g, rays, mode, table, hits=hits, kernel_events=e)
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in ev]))
+    kt = {"closest": launch_ms(prim, H.HRPP_CLOSEST_HIT, tabs[0], snaps[0], out_c),
+          "any": launch_ms(shadow, H.HRPP_ANY_HIT, tabs[1], snaps[1], out_a)}
+    # one restored step under an NVTX range (ncu --nvtx-include profile_small/)
+    torch.cuda.nvtx.range_push("profile_small")
+    for t, sn in zip(tabs, snaps):
+        t.copy_from(sn)
+    H.trace(g, prim, H.HRPP_CLOSEST_HIT, tabs[0], hits=out_c)
+    H.trace(g, shadow, H.HRPP_ANY_HIT, tabs[1], hits=out_a)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    for t, sn in zip(tabs, snaps):
+        t.copy_from(sn)
+    for t, sn in zip(gtabs, gsnaps):
+        t.copy_from(sn)
+    _, sc = H.trace(g, prim, H.HRPP_CLOSEST_HIT, tabs[0], stats=True)
+    _, sa = H.trace(g, shadow, H.HRPP_ANY_HIT, tabs[1], stats=True)
+    _, gc = H.trace(g, prim, H.HRPP_CLOSEST_HIT, gtabs[0], stats=True)
+    _, ga = H.trace(g, shadow, H.HRPP_ANY_HIT, gtabs[1], stats=True)
     _, pc = H.trace(g, prim, H.HRPP_CLOSEST_HIT, None, stats=True)
     _, pa = H.trace(g, shadow, H.HRPP_ANY_HIT, None, stats=True)
     g.check()
 
     def skipped(h, p):
         return {"prediction_ratio": h["true_pos"] / max(1, h["rays"]),
-                "skipped_exact_box_tests": 1.0 - h["box_tests"] / max(1, p["box_tests"]), "rays": h["rays"]}
+                "skipped_exact_box_tests": 1.0 - h["box_tests"] / max(1, p["box_tests"]), "rays": h["rays"],
+                "gated": h["gated"]}
 
+    peak, peak_kind = load_peaks()
+    dom = "any" if kt["any"] >= kt["closest"] else "closest"
+    st_dom = sa if dom == "any" else sc
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    roof = roofline_block(f"small_bvh2_{dom}", f"k_trace<2, {dom}, hrpp> (small scene)", kt[dom],
+                          algorithmic_bytes(st_dom, dom == "closest", 2, 1), st_dom, peak, peak_kind,
+                          sm_mhz or max_sm_mhz(), n_sm)
     value = job_mrays_per_s(n_rays, ms)
     line = {"metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -675,18 +778,25 @@ def run_small(args):
                                     "batches side by side)",
                        "cuda_graph": graphed and p_graphed},
             "plain": {"value": job_mrays_per_s(n_rays, p_ms), "ms_per_step": p_ms, "speedup_hrpp_over_plain": p_ms / ms},
+            "gated": {"value": job_mrays_per_s(n_rays, g_ms), "ms_per_step": g_ms, "speedup_over_plain": p_ms / g_ms,
+                      "gate": {"min_tp_per_65536": GATE, "sample_log2": GATE_SAMPLE_LOG2},
+                      "skipped": {"closest": skipped(gc, pc), "any": skipped(ga, pa)}},
+            "per_mode_kernel_ms": kt,
             "skipped": {"closest": skipped(sc, pc), "any": skipped(sa, pa)},
+            "roofline": roof,
             "gpu_launches": 4 * args.steps}
-    print(json.dumps(line), flush=True)
-    return 0
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_pathtrace(args):
+def run_pathtrace(args, emit: bool = True, sm_mhz=None):
     """Config 5: 1280x720 x 4 spp x 5 diffuse bounces (+ one shadow ray per
     bounce) on the 4.28M-triangle closed terrain, HRPP vs plain per bounce.
     Each step restores the tables warmed by the other frames and traces frame
     0, the closest-hit and shadow chains side by side; a second pass in
-    sequence times every launch alone."""
+    sequence times every launch alone.  Returns the line (printed when
+    emit)."""
     rank, world, local = dist_env()
     import torch
     torch.cuda.set_device(local)
@@ -703,33 +813,35 @@ def run_pathtrace(args):
         return h[:, 0].copy(), h[:, 1].view(np.uint32).copy()
 
     frames = []
-    for f in range(args.frames):
-        bs = W.path_bounces(s, W.path_primary(s, spp=4, frame=f), gpu_closest, bounces=5, frame=f)
+    for f in range(max(2, args.frames)):
+        bs = W.path_bounces(s, W.path_primary(s, spp=4, frame=frame_index(f, rank)), gpu_closest, bounces=5,
+                            frame=frame_index(f, rank))
         frames.append([(torch.from_numpy(c).cuda(), torch.from_numpy(sh).cuda()) for c, sh in bs])
     nb = len(frames[0])
     stream = torch.cuda.current_stream()
     side = torch.cuda.Stream()
-    tab_c = H.Table(args.log2_entries, args.ways, args.precision)
-    tab_a = H.Table(args.log2_entries, args.ways, args.precision)
+
     # the terrain protocol: the other frames warm the tables once, a device
     # snapshot is restored at the start of every step, which then traces
     # frame 0's bounces in order (no ray meets its own insert)
-    for fr in frames[1:]:
-        for c, sh in fr:
-            H.trace(g, c, H.HRPP_CLOSEST_HIT, tab_c)
-            H.trace(g, sh, H.HRPP_ANY_HIT, tab_a)
-    snap_c = H.Table(args.log2_entries, args.ways, args.precision)
-    snap_a = H.Table(args.log2_entries, args.ways, args.precision)
-    snap_c.copy_from(tab_c)
-    snap_a.copy_from(tab_a)
+    def warm(gated):
+        tabs = make_tables(H, args.log2_entries, args.ways, args.precision, gated)
+        for fr in frames[1:]:
+            for c, sh in fr:
+                H.trace(g, c, H.HRPP_CLOSEST_HIT, tabs[0])
+                H.trace(g, sh, H.HRPP_ANY_HIT, tabs[1])
+        snaps = make_tables(H, args.log2_entries, args.ways, args.precision, gated)
+        snaps[0].copy_from(tabs[0])
+        snaps[1].copy_from(tabs[1])
+        return tabs, snaps
 
-    def step(tables, ev=None, concurrent=True):
+    def step(tables, snaps, ev=None, concurrent=True):
         """Restore the tables, then trace frame 0's bounces.  concurrent: the
         closest-hit chain and the shadow chain (one table each, independent)
         run side by side; otherwise in sequence, each launch timed alone."""
         if tables[0] is not None:
-            tables[0].copy_from(snap_c)
-            tables[1].copy_from(snap_a)
+            tables[0].copy_from(snaps[0])
+            tables[1].copy_from(snaps[1])
         if concurrent:
             fork = torch.cuda.Event()
             fork.record(stream)
@@ -748,56 +860,81 @@ def run_pathtrace(args):
         e.record(stream)
         return e
 
+    variants = {"hrpp": warm(False), "gated": warm(True), "plain": ((None, None), (None, None))}
     out = {}
-    for name, tables in (("hrpp", (tab_c, tab_a)), ("plain", (None, None))):
+    for name, (tables, snaps) in variants.items():
         res = []
-        for conc in (True, False):
+        for conc in ((True, False) if name != "gated" else (True,)):
             for _ in range(args.warmup):
-                step(tables, concurrent=conc)
+                step(tables, snaps, concurrent=conc)
             evs = None if conc else [[[(mk(), mk()), (mk(), mk())] for _ in range(nb)] for _ in range(args.steps)]
             torch.cuda.synchronize()
             e0, e1 = mk(), mk()
             e0.record(stream)
             for k in range(args.steps):
-                step(tables, evs[k] if evs else None, concurrent=conc)
+                step(tables, snaps, evs[k] if evs else None, concurrent=conc)
             e1.record(stream)
             torch.cuda.synchronize()
             res.append(e0.elapsed_time(e1) / args.steps)
-        per_b = [[sum(evs[k][b][m][0].elapsed_time(evs[k][b][m][1]) for k in range(args.steps)) / args.steps
-                  for m in range(2)] for b in range(nb)]
-        out[name] = (res[0], per_b, res[1])
+        per_b = None
+        if not conc:
+            per_b = [[sum(evs[k][b][m][0].elapsed_time(evs[k][b][m][1]) for k in range(args.steps)) / args.steps
+                      for m in range(2)] for b in range(nb)]
+        out[name] = (res[0], per_b, res[1] if len(res) > 1 else None)
     rays_frame = sum(int(c.shape[0] + sh.shape[0]) for c, sh in frames[0])
     per_bounce = []
+    (tab_c, tab_a), (snap_c, snap_a) = variants["hrpp"]
+    # one restored step in sequence under an NVTX range (ncu --nvtx-include
+    # profile_pathtrace/; its second closest-hit launch is bounce 1)
+    torch.cuda.nvtx.range_push("profile_pathtrace")
+    step((tab_c, tab_a), (snap_c, snap_a), concurrent=False)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     tab_c.copy_from(snap_c)
     tab_a.copy_from(snap_a)
+    stats_b = []
     for b, (c, sh) in enumerate(frames[0]):
         _, sc = H.trace(g, c, H.HRPP_CLOSEST_HIT, tab_c, stats=True)
         _, sa = H.trace(g, sh, H.HRPP_ANY_HIT, tab_a, stats=True)
+        stats_b.append((sc, sa))
         hc, ha = out["hrpp"][1][b]
         pc, pa = out["plain"][1][b]
         per_bounce.append({"bounce": b, "closest_rays": int(c.shape[0]), "shadow_rays": int(sh.shape[0]),
                            "closest_mrays": {"hrpp": c.shape[0] / hc / 1e3, "plain": c.shape[0] / pc / 1e3},
                            "shadow_mrays": {"hrpp": sh.shape[0] / ha / 1e3, "plain": sh.shape[0] / pa / 1e3},
                            "prediction_ratio": {"closest": sc["true_pos"] / sc["rays"], "any": sa["true_pos"] / sa["rays"]}})
+    g.check()
+    # roofline: the bounce-1 closest-hit launch (incoherent rays over a scene
+    # larger than L2)
+    peak, peak_kind = load_peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    b1 = min(1, nb - 1)
+    roof = roofline_block("pt_bvh4_closest_b1", "k_trace<4, closest, hrpp> (path tracing, bounce 1)",
+                          out["hrpp"][1][b1][0], algorithmic_bytes(stats_b[b1][0], True, 4, args.ways), stats_b[b1][0],
+                          peak, peak_kind, sm_mhz or max_sm_mhz(), n_sm)
     learned = None if args.no_learned else pathtrace_learned(H, g, s, frames, per_bounce, stream)
     line = {"metric": METRIC, "value": rays_frame / (out["hrpp"][0] * 1e-3) / 1e6, "unit": "Mrays/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["hrpp"][0], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"path tracing: {s.n_tris} tris (2048x1024-quad terrain, 256 icospheres, dome), "
                                    "1280x720 x 4 spp x 5 diffuse bounces + 1 shadow ray per bounce",
-                       "rays_per_step": rays_frame, "frames": args.frames,
-                       "protocol": f"each step: restore the tables warmed by {args.frames - 1} other frame(s), then "
-                                   "trace frame 0's bounces in order, the closest-hit chain and the shadow chain "
+                       "rays_per_step": rays_frame, "frames": max(2, args.frames),
+                       "protocol": f"each step: restore the tables warmed by {max(2, args.frames) - 1} other frame(s), "
+                                   "then trace frame 0's bounces in order, the closest-hit chain and the shadow chain "
                                    "side by side (one table each)",
                        "table": {"log2_entries": args.log2_entries, "ways": args.ways, "precision": args.precision}},
             "plain": {"value": rays_frame / (out["plain"][0] * 1e-3) / 1e6, "ms_per_step": out["plain"][0],
                       "speedup_hrpp_over_plain": out["plain"][0] / out["hrpp"][0]},
+            "gated": {"value": rays_frame / (out["gated"][0] * 1e-3) / 1e6, "ms_per_step": out["gated"][0],
+                      "speedup_over_plain": out["plain"][0] / out["gated"][0],
+                      "gate": {"min_tp_per_65536": GATE, "sample_log2": GATE_SAMPLE_LOG2}},
             "sequential": {"value": rays_frame / (out["hrpp"][2] * 1e-3) / 1e6,
                            "plain_value": rays_frame / (out["plain"][2] * 1e-3) / 1e6, "unit": "Mrays/s",
                            "how": "the same steps with every launch in sequence (per-bounce kernel times taken here)"},
-            "per_bounce": per_bounce, "learned": learned, "gpu_launches": 4 * nb * args.steps}
-    print(json.dumps(line), flush=True)
-    return 0
+            "per_bounce": per_bounce, "roofline": roof, "learned": learned, "gpu_launches": 4 * nb * args.steps}
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def pathtrace_learned(H, g, s, frames, per_bounce, stream):
@@ -977,11 +1114,13 @@ def main():
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "pathtrace":
-        return run_pathtrace(args)
+        run_pathtrace(args)
+        return 0
     if args.workload == "learned":
         return run_learned(args)
     if args.workload == "small":
-        return run_small(args)
+        run_small(args)
+        return 0
     rank, world, local = dist_env()
     import torch
     if not torch.cuda.is_available():
@@ -1031,12 +1170,21 @@ def main():
     snap_a = H.Table(args.log2_entries, args.ways, args.precision, upd)
     snap_c.copy_from(tab_c)
     snap_a.copy_from(tab_a)
+    # the same tables under the gate policy (GATE), warmed the same way
+    gtab_c, gtab_a = make_tables(H, args.log2_entries, args.ways, args.precision, True, upd)
+    for f in frames[1:]:
+        H.trace(g, f["prim"], H.HRPP_CLOSEST_HIT, gtab_c, verify=verify)
+        H.trace(g, f["ao"], H.HRPP_ANY_HIT, gtab_a)
+    gsnap_c, gsnap_a = make_tables(H, args.log2_entries, args.ways, args.precision, True, upd)
+    gsnap_c.copy_from(gtab_c)
+    gsnap_a.copy_from(gtab_a)
+    snapshot_of = {id(tab_c): snap_c, id(tab_a): snap_a, id(gtab_c): gsnap_c, id(gtab_a): gsnap_a}
     f0 = frames[0]
 
     def restore(tables):
-        if tables[0] is not None:
-            tables[0].copy_from(snap_c)
-            tables[1].copy_from(snap_a)
+        for t in tables:
+            if t is not None:
+                t.copy_from(snapshot_of[id(t)])
 
     side = torch.cuda.Stream()
 
@@ -1126,10 +1274,14 @@ def main():
     ps_rays, ps_ms, p_kt = timed((None, None), True)
     p_seq_value = sum_over_ranks(ps_rays) / (max_over_ranks(ps_ms) * 1e-3) / 1e6
 
+    # --- the gate policy: tables that stop predicting while it does not pay
+    g_rays, g_ms, _ = timed((gtab_c, gtab_a), False)
+    g_value = sum_over_ranks(g_rays) / (max_over_ranks(g_ms) * 1e-3) / 1e6
+
     # --- the same HRPP step with a persisting-L2 window over the table words
     # or over the interior nodes (a set-aside only for these runs)
     l2_variants = None
-    if args.l2 == "none":
+    if args.l2 == "none" and args.l2_variants:
         try:
             granted = H.l2_set_aside(args.l2_set_aside_mb << 20)
         except H.HrppError:
@@ -1147,6 +1299,15 @@ def main():
                 l2_variants[name] = {"value": sum_over_ranks(v_rays) / (max_over_ranks(v_ms) * 1e-3) / 1e6}
             l2_kind[0] = H.HRPP_L2_NONE
             H.l2_set_aside(0)
+
+    # --- one restored step under an NVTX range: the launches an ncu capture of
+    # this workload selects (--nvtx --nvtx-include profile_terrain/)
+    torch.cuda.nvtx.range_push("profile_terrain")
+    restore((tab_c, tab_a))
+    H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tab_c, hits=out_c, verify=verify)
+    H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tab_a, hits=out_a)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
 
     # --- counters of one step (from the restored warm tables), with per-ray
     # outcomes of HRPP and per-ray box tests of plain traversal
@@ -1175,16 +1336,34 @@ def main():
     out_plain = torch.empty_like(out_c)
     H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, None, hits=out_plain)
 
-    def paper_step(e):
+    def paper_step(e, schedule=0):
         restore((tab_c, tab_a))
-        H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tab_c, hits=out_c, kernel_events=e, verify=H.HRPP_VERIFY_NONE)
+        H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tab_c, hits=out_c, kernel_events=e, verify=H.HRPP_VERIFY_NONE,
+                schedule=schedule)
 
     paper_ms = kernel_ms(paper_step)
     paper_wrong = float((out_c.view(torch.int32) != out_plain.view(torch.int32)).any(dim=1).double().mean())
+    paper_compact_ms = kernel_ms(lambda e: paper_step(e, H.HRPP_SCHEDULE_COMPACT))
     plain_ms = kernel_ms(lambda e: H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, None, hits=out_plain, kernel_events=e))
+
+    def any_ms(schedule):
+        def fn(e):
+            restore((tab_c, tab_a))
+            H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tab_a, hits=out_a, kernel_events=e, schedule=schedule)
+        return kernel_ms(fn)
+    compact = {"closest_exact_ms": kernel_ms(lambda e: (restore((tab_c, tab_a)), H.trace(
+                   g, f0["prim"], H.HRPP_CLOSEST_HIT, tab_c, hits=out_c, kernel_events=e, verify=verify,
+                   schedule=H.HRPP_SCHEDULE_COMPACT))),
+               "closest_exact_batch_ms": kernel_ms(lambda e: (restore((tab_c, tab_a)), H.trace(
+                   g, f0["prim"], H.HRPP_CLOSEST_HIT, tab_c, hits=out_c, kernel_events=e, verify=verify))),
+               "any_ms": any_ms(H.HRPP_SCHEDULE_COMPACT), "any_batch_ms": any_ms(H.HRPP_SCHEDULE_BATCH),
+               "how": "HRPP_SCHEDULE_COMPACT (lookups first, answered rays leave, the rest queued and traversed) "
+                      "against the fused BATCH schedule, kernel time of each launch from the restored tables"}
     paper_semantics = {"closest_mrays": f0["prim"].shape[0] / paper_ms / 1e3,
+                       "closest_mrays_compact": f0["prim"].shape[0] / paper_compact_ms / 1e3,
                        "plain_closest_mrays": f0["prim"].shape[0] / plain_ms / 1e3,
-                       "speedup_over_plain": plain_ms / paper_ms, "rays_with_another_hit": paper_wrong,
+                       "speedup_over_plain": plain_ms / paper_ms,
+                       "speedup_over_plain_compact": plain_ms / paper_compact_ms, "rays_with_another_hit": paper_wrong,
                        "note": "not exact: true positives return the predicted hit unverified (Sec. 4.3)"}
 
     def skipped_limit(name):
@@ -1214,23 +1393,45 @@ def main():
             barrier()
             return max_over_ranks(time.perf_counter() - t0)
 
-        # (1) the plainest use: hrpp_trace on host buffers, which stages the
-        # rays and hits through device memory and returns with the hits in
-        # host memory (one stream, no overlap)
+        # (1) the library's own host path: hrpp_trace on pinned host buffers,
+        # which stages each batch in chunks (uploads and downloads on copy
+        # streams of its own, overlapping the chunks' traces) and returns with
+        # the hits in host memory.  The two batches are independent, so two
+        # host threads issue them side by side, each on its own stream.
         oc = torch.empty((hp.shape[0], 4), dtype=torch.float32).pin_memory()
         oa = torch.empty((ha.shape[0],), dtype=torch.int32).pin_memory()
+        s_c, s_a = torch.cuda.Stream(), torch.cuda.Stream()
+        from concurrent.futures import ThreadPoolExecutor
+        workers = ThreadPoolExecutor(2)
 
-        def staged_step(k):
+        def library_step(k):
+            restore((tab_c, tab_a))
+            ready = torch.cuda.Event()
+            ready.record(stream)
+            s_c.wait_event(ready)
+            s_a.wait_event(ready)
+            fa = workers.submit(H.trace, g, ha, H.HRPP_ANY_HIT, tab_a, hits=oa, stream=s_a)
+            fc = workers.submit(H.trace, g, hp, H.HRPP_CLOSEST_HIT, tab_c, hits=oc, verify=verify, stream=s_c)
+            fa.result()
+            fc.result()
+        dt_lib = timed_loop(library_step)
+        lib_same = bool(torch.equal(oc.view(torch.int32), out_plain.cpu().view(torch.int32))
+                        and torch.equal(oa == -1, out_a.cpu() == -1))
+
+        # (2) one host thread, one stream: the same calls one after the other
+        def serial_step(k):
             restore((tab_c, tab_a))
             H.trace(g, hp, H.HRPP_CLOSEST_HIT, tab_c, hits=oc, verify=verify)
             H.trace(g, ha, H.HRPP_ANY_HIT, tab_a, hits=oa)
-        dt_staged = timed_loop(staged_step)
+        dt_serial = timed_loop(serial_step)
+        workers.shutdown()
 
-        # (2) a frame loop as a renderer would run it: hrpp_trace on device
-        # buffers, double-buffered, with uploads on one copy stream and
-        # downloads on another, so that copies overlap the traces (the AO
-        # upload under the primary trace, the next step's uploads under this
-        # step's AO trace, the downloads under the next step)
+        # (3) a frame loop orchestrated around device buffers, as a renderer
+        # with its own copy engine would run it: hrpp_trace on double-buffered
+        # device buffers, uploads on one copy stream and downloads on another,
+        # so that copies overlap the traces across steps (the AO upload under
+        # the primary trace, the next step's uploads under this step's AO
+        # trace, the downloads under the next step)
         comp = torch.cuda.current_stream()
         up, down, comp2 = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
         dp = [torch.empty_like(f0["prim"]) for _ in range(2)]
@@ -1281,18 +1482,37 @@ def main():
         last = (args.warmup + args.steps - 1) % 2
         # closest hits bit for bit against plain traversal; any-hit rays by
         # whether they are occluded (any valid hit may be reported)
-        same = bool(torch.equal(hoc[last].view(torch.int32), out_plain.cpu().view(torch.int32))
-                    and torch.equal(hoa[last] == -1, out_a.cpu() == -1))
-        e2e = {"value": sum_over_ranks(n_step * args.steps) / dt_pipe / 1e6, "unit": "Mrays/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "how": "hrpp_trace on double-buffered device buffers, the two batches side by side; pinned-host "
-                      "uploads and downloads on two copy streams, overlapping the traces",
-               "hits_checked": same,
-               "staged": {"value": sum_over_ranks(n_step * args.steps) / dt_staged / 1e6, "unit": "Mrays/s",
-                          "how": "hrpp_trace on host buffers: staged through device memory, one stream, no overlap"}}
+        pipe_same = bool(torch.equal(hoc[last].view(torch.int32), out_plain.cpu().view(torch.int32))
+                         and torch.equal(hoa[last] == -1, out_a.cpu() == -1))
+        mrays = lambda dt: sum_over_ranks(n_step * args.steps) / dt / 1e6
+        e2e = {"value": mrays(dt_lib), "unit": "Mrays/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "how": "hrpp_trace on pinned host buffers (the library stages each batch in chunks whose uploads and "
+                      "downloads overlap the traces on copy streams of its own); the two batches issued side by side "
+                      "from two host threads, one stream each; every step's rays uploaded and hits downloaded",
+               "hits_checked": lib_same,
+               "serial": {"value": mrays(dt_serial), "unit": "Mrays/s",
+                          "how": "the same hrpp_trace host-buffer calls one after the other on one thread"},
+               "torch_pipeline": {"value": mrays(dt_pipe), "unit": "Mrays/s", "hits_checked": pipe_same,
+                                  "how": "hrpp_trace on double-buffered device buffers, the two batches side by "
+                                         "side; pinned-host uploads and downloads on two copy streams, overlapping "
+                                         "the traces across steps"}}
 
-    # the clock record covers every timed GPU loop above (HRPP, plain, the L2
-    # windows, both end-to-end loops)
+    # --- configs 1 and 5 beside the headline (one GPU only: a sub-result per
+    # config, each with its own kernel-event roofline)
+    configs = None
+    if world == 1 and not args.no_configs:
+        configs = {}
+        import copy
+        a = copy.copy(args)
+        a.steps, a.warmup, a.frames = max(5, min(args.steps, 20)), max(3, args.warmup), 4
+        configs["small"] = summarize_config(run_small(a, emit=False))
+        a = copy.copy(args)
+        a.steps, a.warmup, a.frames, a.no_learned = max(3, min(args.steps, 5)), 3, 2, True
+        a.log2_entries, a.ways, a.precision = 18, 2, 6
+        configs["pathtrace"] = summarize_config(run_pathtrace(a, emit=False))
+
+    # the clock record covers every timed GPU loop above (HRPP, plain, gated,
+    # the end-to-end loops, the config sub-results)
     clocks.mark(False)
     clk = clocks.stop()
 
@@ -1319,7 +1539,7 @@ def main():
                 "tp_inexact": h["tp_inexact"], "rays": h["rays"]}
 
     cpu = None if args.no_cpu else cpu_baseline(args, sw, frames)
-    launches_per_step = 2 + (2 if args.update == "two_phase" else 0)
+    launches_per_step = 2 + (2 if args.update == "two_phase" else 0)  # per batch: trace + k_apply
     line = {
         "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -1340,11 +1560,18 @@ def main():
         "per_mode_kernel_ms": kt,
         "l2_persist": l2_variants,
         "table_occupancy": occupancy,
+        "gated": {"value": g_value, "unit": "Mrays/s", "speedup_over_plain": g_value / p_value,
+                  "gate": {"min_tp_per_65536": GATE, "sample_log2": GATE_SAMPLE_LOG2},
+                  "how": "the same step with each table's gate set: a table stops consulting (except every 32nd "
+                         "32-ray chunk) after a call whose true positives fall below the threshold"},
+        "compact_schedule": compact,
         "paper_semantics": paper_semantics,
         "skipped": {"closest": skipped(sc, pc, skipped_limit("closest")),
                     "any": skipped(sa, pa, skipped_limit("any")),
+                    "limit_study": limit_study(),
                     "paper_context": "paper Table 1 (PBRT limit study, no hardware stated): 30-69% hit-all, "
                                      "<1-48% hit-any savings"},
+        "configs": configs,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
