@@ -235,6 +235,32 @@ typedef struct hrpp_trace_opts {
                                  ray's traversal from the root (0 for an
                                  any-hit true positive; predicted subtrees
                                  not included) */
+    uint32_t host_async;      /* host ray/hit buffers: 0 = the call returns
+                                 with the hits in host memory; 1 = it returns
+                                 at once, like a call on device buffers, and
+                                 the hits are in host memory when `stream`
+                                 reaches the end of the call's work (wait for
+                                 the stream or an event recorded after the
+                                 call).  The host buffers must be page-locked
+                                 (HRPP_ERR_INVALID_ARG otherwise) and stay
+                                 valid, the rays unmodified, until then.  A
+                                 stopped ray is then reported by
+                                 hrpp_scene_check; host out_stats still make
+                                 the call wait. */
+    void *host_done;          /* host_async: NULL, or a cudaEvent_t (as void*)
+                                 that the library records once the hits are
+                                 in host memory; `stream` then waits only for
+                                 the traces, not for the hits' download, so
+                                 later work on it (the next frame's traces)
+                                 overlaps the download.  Wait for this event
+                                 before reading the hits. */
+    uint32_t stage_chunks;    /* host ray/hit buffers: at most this many
+                                 staging chunks (each at least 2^18 rays);
+                                 0 = the default, 8 for a call that waits
+                                 (its copies overlap its own chunks'
+                                 traces) and 2 for host_async (its copies
+                                 mostly overlap the work queued around it);
+                                 at most 64, else HRPP_ERR_INVALID_ARG */
 } hrpp_trace_opts;
 /* Per-ray outcome codes (Sec. 4.3).  The per-ray outputs above are filled
  * only when the call also collects statistics (out_stats != NULL). */
@@ -348,14 +374,18 @@ void hrpp_table_destroy(hrpp_table *table);
  *   out_stats NULL, or one hrpp_stats in device or host memory.  A host
  *             pointer makes the call wait for its kernels.
  * Host ray/hit buffers are staged through device memory the call allocates
- * and frees (stream-ordered), in chunks of a multiple of 32 rays (up to 8
- * chunks of at least 2^18 rays): chunk k+1 uploads on a library-owned copy
+ * and frees (stream-ordered), in chunks of a multiple of 32 rays (by default
+ * up to 8 chunks of at least 2^18 rays; hrpp_trace_opts.stage_chunks):
+ * chunk k+1 uploads on a library-owned copy
  * stream and chunk k-1 downloads on another while chunk k traces on
  * `stream`, so page-locked (pinned) buffers overlap copies with tracing.
  * Every chunk looks up the table as the call found it and two-phase inserts
  * land once, after the last chunk: results, counters and table equal those
- * of the same call on device buffers.  The call returns after the results
- * are back in host memory.  Device buffers keep the call fully asynchronous.
+ * of the same call on device buffers.  The uploads start at once, without
+ * waiting for earlier work on `stream`: host rays that such work writes
+ * must be complete before the call.  The call returns after the results
+ * are back in host memory (or at once, with hrpp_trace_opts.host_async).
+ * Device buffers keep the call fully asynchronous.
  * Calls that use the same table must be ordered on one stream.
  * n_rays == 0 does nothing (stats, if requested, are zeroed); n_rays above
  * 2^31 returns UNSUPPORTED.

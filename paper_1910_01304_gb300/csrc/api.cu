@@ -110,6 +110,12 @@ cudaError_t get_pool(int dev, cudaMemPool_t *pool)
         if (e != cudaSuccess) return e;
         uint64_t keep = UINT64_MAX;
         cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        // never reuse a block by making the allocating stream wait for the
+        // stream that freed it: a staged call's uploads (allocated on its
+        // upload stream) would otherwise wait for the previous call's
+        // downloads; the pool takes fresh memory instead
+        int no = 0;
+        cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolReuseAllowInternalDependencies, &no);
     }
     *pool = g_pools[dev];
     return cudaSuccess;
@@ -118,6 +124,7 @@ cudaError_t get_pool(int dev, cudaMemPool_t *pool)
 // Staged host buffers: at most kStagedChunks chunks of at least
 // kStagedMinChunk rays (a chunk's launch still fills the GPU).
 constexpr uint32_t kStagedChunks = 8;
+constexpr uint32_t kStagedChunksAsync = 2;
 constexpr uint64_t kStagedMinChunk = 1u << 18;
 
 // A pair of library-owned copy streams (uploads, downloads) for one staged
@@ -157,7 +164,7 @@ void release_copy_streams(int dev, const CopyStreams &c)
     g_copy_idle[dev].push_back(c);
 }
 
-bool is_host_pointer(const void *ptr, bool *ok)
+bool is_host_pointer(const void *ptr, bool *ok, bool *pinned = nullptr)
 {
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, ptr);
@@ -167,6 +174,7 @@ bool is_host_pointer(const void *ptr, bool *ok)
         return false;
     }
     *ok = true;
+    if (pinned) *pinned = a.type == cudaMemoryTypeHost;
     return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
 }
 
@@ -497,10 +505,17 @@ hrpp_status hrpp_table_create(int log2_entries, int ways, hrpp_table **out)
     t->update_mode = HRPP_UPDATE_TWO_PHASE;
     const uint64_t n = 1ull << log2_entries;
     t->gate_sample_log2 = 5;
-    if ((e = device_malloc((void **)&t->d_words, n * 8)) != cudaSuccess || (e = device_malloc((void **)&t->d_winner, n * 4)) != cudaSuccess ||
-        (e = device_malloc((void **)&t->d_gate, sizeof(uint32_t))) != cudaSuccess ||
-        (e = cudaMemset(t->d_words, 0xFF, n * 8)) != cudaSuccess || (e = cudaMemset(t->d_winner, 0, n * 4)) != cudaSuccess ||
-        (e = cudaMemset(t->d_gate, 1, sizeof(uint32_t))) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess) {
+    // the gate word sits right after the table words, so one copy restores both
+    e = device_malloc((void **)&t->d_words, n * 8 + 16);
+    if (e == cudaSuccess) {
+        t->d_gate = reinterpret_cast<uint32_t *>(t->d_words + n);
+        e = device_malloc((void **)&t->d_winner, n * 4);
+    }
+    if (e == cudaSuccess) e = cudaMemset(t->d_words, 0xFF, n * 8);
+    if (e == cudaSuccess) e = cudaMemset(t->d_winner, 0, n * 4);
+    if (e == cudaSuccess) e = cudaMemset(t->d_gate, 1, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
         hrpp_table_destroy(t);
         return cuda_fail(e, "table allocation");
     }
@@ -617,9 +632,9 @@ hrpp_status hrpp_table_copy(hrpp_table *dst, const hrpp_table *src, void *stream
     DeviceGuard g(dst->device);
     if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
     const uint64_t n = 1ull << dst->log2_entries;
-    cudaError_t e = cudaMemcpyAsync(dst->d_words, src->d_words, n * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dst->d_gate, src->d_gate, sizeof(uint32_t), cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    // the words and the gate word behind them, in one copy
+    cudaError_t e = cudaMemcpyAsync(dst->d_words, src->d_words, n * 8 + sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                                    (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "table copy");
     dst->bound_scene = src->bound_scene;
     return HRPP_OK;
@@ -640,9 +655,8 @@ void hrpp_table_destroy(hrpp_table *t)
 {
     if (!t) return;
     DeviceGuard g(t->device);
-    cudaFree(t->d_words);
+    cudaFree(t->d_words);  // holds the gate word too
     cudaFree(t->d_winner);
-    cudaFree(t->d_gate);
     delete t;
 }
 
@@ -689,6 +703,7 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         return fail(HRPP_ERR_INVALID_ARG, "unknown verify mode %u", opts->verify);
     if (opts && opts->l2_persist > HRPP_L2_NODES)
         return fail(HRPP_ERR_INVALID_ARG, "unknown l2_persist value %u", opts->l2_persist);
+    if (opts && opts->stage_chunks > 64) return fail(HRPP_ERR_INVALID_ARG, "stage_chunks must be at most 64");
     if (table && table->device != sc->device) return fail(HRPP_ERR_INVALID_ARG, "table and scene on different devices");
     if (table && table->bound_scene && table->bound_scene != sc->id)
         return fail(HRPP_ERR_INVALID_ARG, "table is bound to another scene; reset it first");
@@ -711,10 +726,13 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         }
         return HRPP_OK;
     }
-    bool ok_r, ok_h;
-    const bool rays_host = is_host_pointer(rays, &ok_r);
-    const bool hits_host = is_host_pointer(out_hits, &ok_h);
+    bool ok_r, ok_h, pinned_r = false, pinned_h = false;
+    const bool rays_host = is_host_pointer(rays, &ok_r, &pinned_r);
+    const bool hits_host = is_host_pointer(out_hits, &ok_h, &pinned_h);
     if (!ok_r || !ok_h) return fail(HRPP_ERR_INVALID_ARG, "rays / out_hits are not valid pointers");
+    const bool host_async = opts && opts->host_async;
+    if (host_async && ((rays_host && !pinned_r) || (hits_host && !pinned_h)))
+        return fail(HRPP_ERR_INVALID_ARG, "host_async needs page-locked host buffers");
 
     cudaMemPool_t pool;
     if ((e = get_pool(sc->device, &pool)) != cudaSuccess) return cuda_fail(e, "memory pool");
@@ -733,11 +751,18 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
     const bool staged = rays_host || hits_host;
     uint32_t n_chunks = 1, chunk = n_rays;
     if (staged) {
-        n_chunks = (uint32_t)std::min<uint64_t>(kStagedChunks, (n_rays + kStagedMinChunk - 1) / kStagedMinChunk);
+        // default: up to 8 chunks for a call that waits (its copies overlap
+        // its own chunks' traces), 2 for host_async (its copies mostly
+        // overlap the work queued around it, as a double-buffered frame
+        // loop's do; 1 to 3 chunks measured within 1 % on the terrain frame)
+        const uint32_t max_chunks = (opts && opts->stage_chunks) ? opts->stage_chunks
+                                    : (host_async ? kStagedChunksAsync : kStagedChunks);
+        n_chunks = (uint32_t)std::min<uint64_t>(max_chunks, (n_rays + kStagedMinChunk - 1) / kStagedMinChunk);
+        if (n_chunks < 1) n_chunks = 1;
         chunk = (uint32_t)((((uint64_t)n_rays + n_chunks - 1) / n_chunks + 31u) & ~31ull);
         n_chunks = (uint32_t)(((uint64_t)n_rays + chunk - 1) / chunk);
     }
-    // scratch: control block, insert records, two-pass queue, staged buffers
+    // scratch on `stream`: control block, insert records, two-pass queue
     size_t off = 0;
     const size_t ctl_off = off;
     off += 256;
@@ -745,17 +770,15 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
     if (two_phase) off += (size_t)n_rays * sizeof(Record);
     const size_t queue_off = off;
     if (compact) off += (size_t)chunk * 16u;
-    const size_t ray_off = off;
-    if (rays_host) off += (ray_bytes + 255) & ~size_t(255);
-    const size_t hit_off = off;
-    if (hits_host) off += (hit_bytes + 255) & ~size_t(255);
-    char *scratch = nullptr;
+    // staging buffers on the upload stream, so that the uploads need not
+    // wait for earlier work on `stream` (an earlier call's traces)
+    const size_t hit_stage_off = rays_host ? (ray_bytes + 255) & ~size_t(255) : 0;
+    const size_t stage_bytes = hit_stage_off + (hits_host ? (hit_bytes + 255) & ~size_t(255) : 0);
+    char *scratch = nullptr, *staging = nullptr;
     if (allocation_refused()) return cuda_fail(cudaErrorMemoryAllocation, "scratch allocation (injected)");
     if ((e = cudaMallocFromPoolAsync((void **)&scratch, off, pool, stream)) != cudaSuccess)
         return cuda_fail(e, "scratch allocation");
     Ctl *ctl = reinterpret_cast<Ctl *>(scratch + ctl_off);
-    char *d_rays = rays_host ? scratch + ray_off : (char *)rays;
-    char *d_hits = hits_host ? scratch + hit_off : (char *)out_hits;
     CopyStreams cs;
     std::vector<cudaEvent_t> events;
     auto event = [&](cudaEvent_t *ev) {
@@ -764,16 +787,18 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         return err;
     };
     hrpp_status status = HRPP_OK;
+    char *d_rays = (char *)rays, *d_hits = (char *)out_hits;
     do {
         if ((e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), stream)) != cudaSuccess) { status = cuda_fail(e, "memset"); break; }
         if (staged) {
             if ((e = acquire_copy_streams(sc->device, &cs)) != cudaSuccess) { status = cuda_fail(e, "copy streams"); break; }
-            cudaEvent_t ready;
-            if ((e = event(&ready)) != cudaSuccess || (e = cudaEventRecord(ready, stream)) != cudaSuccess ||
-                (e = cudaStreamWaitEvent(cs.up, ready, 0)) != cudaSuccess) {
-                status = cuda_fail(e, "staging order");
+            if (allocation_refused()) { status = cuda_fail(cudaErrorMemoryAllocation, "staging (injected)"); break; }
+            if ((e = cudaMallocFromPoolAsync((void **)&staging, stage_bytes, pool, cs.up)) != cudaSuccess) {
+                status = cuda_fail(e, "staging allocation");
                 break;
             }
+            if (rays_host) d_rays = staging;
+            if (hits_host) d_hits = staging + hit_stage_off;
         }
         TraceParams p;
         memset(&p, 0, sizeof p);
@@ -881,19 +906,36 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         }
     } while (false);
     if (cs.up) {
-        // the scratch is freed in stream order: after the last download
-        cudaEvent_t drained = nullptr;
-        cudaError_t ed = event(&drained);
-        if (ed == cudaSuccess) ed = cudaEventRecord(drained, cs.down);
-        if (ed == cudaSuccess) ed = cudaStreamWaitEvent(stream, drained, 0);
+        // the staging is freed in stream order on the download stream, after
+        // the last chunk's trace and download; `stream` then waits for the
+        // downloads, so the hits are in host memory when it gets there
+        cudaEvent_t traced = nullptr, uploaded = nullptr, drained = nullptr;
+        cudaError_t ed = event(&traced);
+        if (ed == cudaSuccess) ed = cudaEventRecord(traced, stream);
+        if (ed == cudaSuccess) ed = cudaStreamWaitEvent(cs.down, traced, 0);
+        if (ed == cudaSuccess) ed = event(&uploaded);  // (uploads a failed call left unordered)
+        if (ed == cudaSuccess) ed = cudaEventRecord(uploaded, cs.up);
+        if (ed == cudaSuccess) ed = cudaStreamWaitEvent(cs.down, uploaded, 0);
+        if (ed == cudaSuccess && staging) ed = cudaFreeAsync(staging, cs.down);
+        if (host_async && opts->host_done) {
+            // the caller's event marks the hits in host memory; `stream`
+            // goes on after the traces without waiting for the downloads
+            if (ed == cudaSuccess) ed = cudaEventRecord((cudaEvent_t)opts->host_done, cs.down);
+        } else {
+            if (ed == cudaSuccess) ed = event(&drained);
+            if (ed == cudaSuccess) ed = cudaEventRecord(drained, cs.down);
+            if (ed == cudaSuccess) ed = cudaStreamWaitEvent(stream, drained, 0);
+        }
         if (ed != cudaSuccess) {
+            cudaStreamSynchronize(stream);
             cudaStreamSynchronize(cs.up);
             cudaStreamSynchronize(cs.down);
         }
         if (ed != cudaSuccess && status == HRPP_OK) status = cuda_fail(ed, "staging order");
     }
     cudaError_t ef = cudaFreeAsync(scratch, stream);
-    if (staged || stats_host) {
+    const bool wait = (staged && !host_async) || stats_host;
+    if (wait) {
         if ((e = cudaStreamSynchronize(stream)) != cudaSuccess && status == HRPP_OK)
             status = cuda_fail(e, "cudaStreamSynchronize");
     }
@@ -901,7 +943,7 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
     for (cudaEvent_t ev : events) cudaEventDestroy(ev);
     if (status != HRPP_OK) return status;
     if (ef != cudaSuccess) return cuda_fail(ef, "scratch free");
-    if (stats_host || staged) {
+    if (wait) {
         uint32_t flag = 0;
         if ((e = cudaMemcpy(&flag, sc->d_error, sizeof flag, cudaMemcpyDeviceToHost)) != cudaSuccess)
             return cuda_fail(e, "reading the error flag");

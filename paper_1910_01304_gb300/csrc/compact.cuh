@@ -74,8 +74,30 @@ __device__ __forceinline__ uint64_t predict_ray(const TraceParams &p, uint32_t i
         const uint32_t ways = 1u << p.log2_ways;
         bool positive = false, done = false;
         float tdummy = 0.0f;
-        for (uint32_t w = 0; w < ways && !done; ++w) {
-            const uint64_t wd = p.update_mode == HRPP_UPDATE_ONLINE ? __ldcg(set + w) : __ldg(set + w);
+        // the set's words first, all loads in flight together; then the
+        // predicted leaves, in way order
+        uint64_t words[8];
+#pragma unroll
+        for (uint32_t w = 0; w < 8; ++w)
+            if (w < ways) words[w] = p.update_mode == HRPP_UPDATE_ONLINE ? __ldcg(set + w) : __ldg(set + w);
+        // start every predicted leaf's triangles (48 to 192 bytes: the lines
+        // holding its first and last byte) towards L1 before the first test
+        // waits on one
+#pragma unroll
+        for (uint32_t w = 0; w < 8; ++w) {
+            if (w >= ways) break;
+            const uint64_t wd = words[w];
+            if (wd == HRPP_EMPTY_WORD || (wd >> kLeafBits) != s.tag) continue;
+            const uint32_t node = (uint32_t)(wd & kLeafMask);
+            if ((node >> 2) + (node & 3u) + 1u > p.n_tris) continue;
+            const char *tri = reinterpret_cast<const char *>(p.tris + 3ull * (node >> 2));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(tri));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(tri + 48u * ((node & 3u) + 1u) - 1u));
+        }
+#pragma unroll
+        for (uint32_t w = 0; w < 8; ++w) {
+            if (w >= ways || done) break;
+            const uint64_t wd = words[w];
             if (wd == HRPP_EMPTY_WORD || (wd >> kLeafBits) != s.tag) continue;
             positive = true;
             const uint32_t node = (uint32_t)(wd & kLeafMask);

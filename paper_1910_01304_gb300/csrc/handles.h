@@ -53,7 +53,7 @@ struct hrpp_table {
     int hash_variant;  // HRPP_HASH_EXP_MSB or HRPP_HASH_EXP_LSB
     uint64_t *d_words;
     uint32_t *d_winner;
-    uint32_t *d_gate;       // the gate word (nonzero = open)
+    uint32_t *d_gate;       // the gate word (nonzero = open), stored right after the table words
     uint32_t gate_min_tp;   // 0: no gate; else true positives per 65536 lookups that keep it open
     int gate_sample_log2;   // closed: every 2^s-th 32-ray chunk still consults the table
     uint64_t bound_scene;

@@ -47,7 +47,8 @@ class hrpp_trace_opts(ctypes.Structure):
                 ("predicted_nodes", ctypes.c_void_p), ("block_threads", ctypes.c_uint32),
                 ("schedule", ctypes.c_uint32), ("refill_min", ctypes.c_uint32), ("max_steps", ctypes.c_uint32),
                 ("verify", ctypes.c_uint32), ("l2_persist", ctypes.c_uint32),
-                ("ray_outcome", ctypes.c_void_p), ("ray_box_tests", ctypes.c_void_p)]
+                ("ray_outcome", ctypes.c_void_p), ("ray_box_tests", ctypes.c_void_p), ("host_async", ctypes.c_uint32),
+                ("host_done", ctypes.c_void_p), ("stage_chunks", ctypes.c_uint32)]
 
 
 HRPP_SCHEDULE_DEFAULT, HRPP_SCHEDULE_BATCH, HRPP_SCHEDULE_REFILL, HRPP_SCHEDULE_COMPACT = 0, 1, 2, 3
@@ -319,7 +320,7 @@ class Table:
 def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, stats: bool = False,
           stream=None, kernel_events=None, block_threads: int = 0, schedule: int = 0, refill_min: int = 0,
           predicted=None, max_steps: int = 0, verify: int = 0, ray_outcome=None, ray_box_tests=None,
-          l2_persist: int = 0):
+          l2_persist: int = 0, host_async: bool = False, stage_chunks: int = 0, host_done=None):
     """Traces rays ([n, 8] float32 torch tensor on the GPU, or a host numpy
     array / torch tensor).  Returns (hits, stats dict or None).
 
@@ -338,7 +339,8 @@ def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, 
     st = hrpp_stats() if stats else None
     opts = None
     if (kernel_events is not None or block_threads or schedule or refill_min or max_steps or verify or l2_persist
-            or predicted is not None or ray_outcome is not None or ray_box_tests is not None):
+            or predicted is not None or ray_outcome is not None or ray_box_tests is not None or host_async
+            or stage_chunks or host_done is not None):
         opts = hrpp_trace_opts()
         if predicted is not None:
             opts.predicted_nodes = _ptr(predicted)
@@ -351,6 +353,10 @@ def trace(scene: Scene, rays, mode: int, table: Table | None = None, hits=None, 
         opts.max_steps = max_steps
         opts.verify = verify
         opts.l2_persist = l2_persist
+        opts.host_async = 1 if host_async else 0
+        opts.stage_chunks = stage_chunks
+        if host_done is not None:
+            opts.host_done = host_done.cuda_event
         if ray_outcome is not None:
             opts.ray_outcome = _ptr(ray_outcome)
         if ray_box_tests is not None:

@@ -360,7 +360,7 @@ def test_table_copy_restores_a_snapshot(H, small_pair):
 @pytest.mark.parametrize("schedule", [1, 3])
 @pytest.mark.parametrize("mode", [O.CLOSEST_HIT, O.ANY_HIT])
 def test_staged_host_buffers_in_chunks_match_device_path(H, small_pair, mode, schedule):
-    """Host ray and hit buffers above the staging chunk size (here 3 chunks
+    """Host ray and hit buffers above the staging chunk size (2 or 3 chunks
     with a ragged tail): pinned and pageable host memory give exactly the
     device path's hits, counters and table words over two calls, with a
     two-phase table whose gate samples by the call's ray index."""
@@ -390,7 +390,51 @@ def test_staged_host_buffers_in_chunks_match_device_path(H, small_pair, mode, sc
             assert torch.equal(got.view(torch.int32), ref.cpu().view(torch.int32)), f"pinned={pinned}"
             assert gst == rst, f"pinned={pinned}"
             assert np.array_equal(t_dev.export(), t_host.export()) and t_dev.gate_open() == t_host.gate_open()
-        assert rst["rays"] == n and (rst["gated"] > 0 or rst["lookups"] == n)
+            assert rst["rays"] == len(rays) > 262144  # more than one staging chunk
+            assert rst["gated"] > 0 or rst["lookups"] == len(rays)
+
+
+def test_host_async_calls_match_device_path(H, small_pair):
+    """hrpp_trace_opts.host_async: calls on pinned host buffers return before
+    their work is done; several of them queued on two streams (one table
+    each, three frames in a row) give, once the streams are synchronized,
+    exactly the device path's hits and table words.  Pageable buffers are
+    refused."""
+    import torch
+    s, g = small_pair[1]
+    frames = [np.concatenate([s.primary_rays(frame=f) for f in range(k, k + 5)]) for k in (0, 5, 10)]
+    tabs = [H.Table(14, 2, 6), H.Table(14, 2, 6)]
+    refs = [H.Table(14, 2, 6), H.Table(14, 2, 6)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs, want = [], []
+    for k, rays in enumerate(frames):
+        for j in range(2):  # table j traces every frame, with its own stream
+            ref, _ = H.trace(g, torch.from_numpy(rays).cuda(), H.HRPP_CLOSEST_HIT, refs[j])
+            want.append(ref)
+            hr = torch.from_numpy(rays).pin_memory()
+            hits = torch.full((len(rays), 4), 7.0).pin_memory()
+            H.trace(g, hr, H.HRPP_CLOSEST_HIT, tabs[j], hits=hits, stream=streams[j], host_async=True)
+            outs.append((hr, hits))
+    torch.cuda.synchronize()
+    for (hr, hits), ref in zip(outs, want):
+        assert torch.equal(hits.view(torch.int32), ref.cpu().view(torch.int32))
+    for t, r in zip(tabs, refs):
+        assert np.array_equal(t.export(), r.export())
+    g.check()
+    # host_done: the event, not the stream, marks the hits in host memory
+    for k, rays in enumerate(frames):
+        hr = torch.from_numpy(rays).pin_memory()
+        hits = torch.full((len(rays), 4), 7.0).pin_memory()
+        done = torch.cuda.Event()
+        done.record(streams[0])  # creates the CUDA event; the library records it again
+        H.trace(g, hr, H.HRPP_CLOSEST_HIT, None, hits=hits, stream=streams[0], host_async=True, host_done=done,
+                stage_chunks=k + 1)
+        done.synchronize()
+        ref, _ = H.trace(g, torch.from_numpy(rays).cuda(), H.HRPP_CLOSEST_HIT)
+        assert torch.equal(hits.view(torch.int32), ref.cpu().view(torch.int32)), k
+    with pytest.raises(H.HrppError) as err:
+        H.trace(g, frames[0], H.HRPP_CLOSEST_HIT, host_async=True)  # numpy: pageable
+    assert err.value.status == H.HRPP_ERR_INVALID_ARG
 
 
 def test_block_sizes_give_identical_results(H, small_pair):
@@ -761,7 +805,7 @@ def test_injected_allocation_failures_return_oom(H, small_pair, monkeypatch):
     rays = torch.from_numpy(s.primary_rays()[:256]).cuda()
     makers = {
         "scene": (6, lambda: H.Scene.from_workload(s)),
-        "table": (3, lambda: H.Table(10, 2, 6)),
+        "table": (2, lambda: H.Table(10, 2, 6)),
         "batch": (5, lambda: H.Batch([(g, None, rays, H.HRPP_CLOSEST_HIT)])),
     }
     for name, (n_allocs, make) in makers.items():
