@@ -673,14 +673,15 @@ def run_small(args, emit: bool = True, sm_mhz=None):
 
     def step(tables, snaps):
         # the primary and shadow batches are independent inputs with one
-        # table each: traced side by side (fork and join, also under capture)
+        # table each: each branch restores its table and traces its batch,
+        # side by side (fork and join, also under capture)
         cur = torch.cuda.current_stream()
-        if tables[0] is not None:
-            tables[0].copy_from(snaps[0])
-            tables[1].copy_from(snaps[1])
         fork = torch.cuda.Event()
         fork.record(cur)
         fork_stream.wait_event(fork)
+        if tables[0] is not None:
+            tables[1].copy_from(snaps[1], stream=fork_stream)
+            tables[0].copy_from(snaps[0])
         H.trace(g, shadow, H.HRPP_ANY_HIT, tables[1], hits=out_a, stream=fork_stream)
         H.trace(g, prim, H.HRPP_CLOSEST_HIT, tables[0], hits=out_c)
         join = torch.cuda.Event()

@@ -72,18 +72,27 @@ def test_table_occupancy_counts_valid_words_per_set():
 
 
 def test_traffic_record_lists_both_launches():
-    """profiles/traffic.txt holds DRAM bytes and warp instructions per launch
-    for the two traversal kernels, each with the kernel source hash it was
-    taken on."""
+    """profiles/traffic.txt holds DRAM bytes, warp instructions and the L2
+    share per launch for the terrain, small-scene and path-tracing launches
+    the bench's rooflines name, each with the kernel source hash it was
+    taken on; a record on the current source is what the bench reads."""
     import re
+    import bench
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
     keys = {(r[0], r[1]) for r in rows}
-    for what in ("traffic", "inst"):
-        for kernel in ("bvh4_any", "bvh4_closest"):
+    for what in ("traffic", "inst", "l2pct"):
+        for kernel in ("bvh4_any", "bvh4_closest", "small_bvh2_any", "small_bvh2_closest", "pt_bvh4_closest_b1"):
             assert (what, kernel) in keys
     for r in rows:
-        assert int(r[2]) > 0 and re.fullmatch(r"[0-9a-f]{16}", r[3])
+        assert float(r[2]) > 0 and re.fullmatch(r"[0-9a-f]{16}", r[3])
+        if r[0] in ("traffic", "inst"):
+            assert float(r[2]) == int(r[2])
+        else:
+            assert 0 < float(r[2]) <= 100
+    value, src = bench.recorded_traffic("bvh4_any")
+    if src == bench.kernel_source_hash():
+        assert value is not None and value > 0
 
 
 def test_frames_differ_across_ranks():
