@@ -51,8 +51,10 @@ def parse():
     ap.add_argument("--ways", type=int, default=2)
     ap.add_argument("--precision", type=int, default=6)
     ap.add_argument("--update", default="two_phase", choices=["two_phase", "online"])
-    ap.add_argument("--verify", default="root", choices=["root", "bottom_up"],
-                    help="how closest-hit true positives are verified")
+    ap.add_argument("--verify", default="root", choices=["root", "bottom_up", "none"],
+                    help="how closest-hit true positives are verified (none: the paper's semantics, not exact)")
+    ap.add_argument("--schedule", default="batch", choices=["batch", "compact"],
+                    help="terrain: the HRPP launches' schedule (compact: the two-pass ray pool)")
     ap.add_argument("--quads", type=int, default=708)
     ap.add_argument("--spheres", type=int, default=64)
     ap.add_argument("--res", default="1920x1080")
@@ -1154,7 +1156,8 @@ def main():
         if pg is not None:
             pg.barrier()
 
-    verify = H.HRPP_VERIFY_BOTTOM_UP if args.verify == "bottom_up" else H.HRPP_VERIFY_ROOT
+    verify = {"root": H.HRPP_VERIFY_ROOT, "bottom_up": H.HRPP_VERIFY_BOTTOM_UP, "none": H.HRPP_VERIFY_NONE}[args.verify]
+    sched = H.HRPP_SCHEDULE_COMPACT if args.schedule == "compact" else H.HRPP_SCHEDULE_BATCH
     l2_kinds = {"none": H.HRPP_L2_NONE, "table": H.HRPP_L2_TABLE, "nodes": H.HRPP_L2_NODES}
     l2_kind = [l2_kinds[args.l2]]
     if args.l2 != "none":
@@ -1203,17 +1206,18 @@ def main():
                 fork = torch.cuda.Event()
                 fork.record(stream)
                 side.wait_event(fork)
-                H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tables[1], hits=out_a, stream=side, l2_persist=l2_kind[0])
+                H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tables[1], hits=out_a, stream=side, l2_persist=l2_kind[0],
+                        schedule=sched)
                 H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tables[0], hits=out_c, verify=verify,
-                        l2_persist=l2_kind[0])
+                        l2_persist=l2_kind[0], schedule=sched)
                 join = torch.cuda.Event()
                 join.record(side)
                 stream.wait_event(join)
             else:
                 H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tables[0], hits=out_c,
-                        kernel_events=ev[0] if ev[0] else None, verify=verify, l2_persist=l2_kind[0])
+                        kernel_events=ev[0] if ev[0] else None, verify=verify, l2_persist=l2_kind[0], schedule=sched)
                 H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tables[1], hits=out_a, kernel_events=ev[1] if ev[1] else None,
-                        l2_persist=l2_kind[0])
+                        l2_persist=l2_kind[0], schedule=sched)
             total += rays_per_frame[0]
         return total
 
@@ -1305,8 +1309,8 @@ def main():
     # this workload selects (--nvtx --nvtx-include profile_terrain/)
     torch.cuda.nvtx.range_push("profile_terrain")
     restore((tab_c, tab_a))
-    H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tab_c, hits=out_c, verify=verify)
-    H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tab_a, hits=out_a)
+    H.trace(g, f0["prim"], H.HRPP_CLOSEST_HIT, tab_c, hits=out_c, verify=verify, schedule=sched)
+    H.trace(g, f0["ao"], H.HRPP_ANY_HIT, tab_a, hits=out_a, schedule=sched)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
 
@@ -1553,9 +1557,11 @@ def main():
     st_dom = sa if dom == "any" else sc
     bytes_launch = algorithmic_bytes(st_dom, dom == "closest", width, args.ways)
     kname = f"k_trace<{width}, {'closest' if dom == 'closest' else 'any'}, hrpp>"
+    key = f"bvh{width}_{dom}"
+    if args.schedule == "compact":  # both launches of the two-pass schedule; no record of its own
+        kname, key = f"k_predict + k_trace_queue<{width}, {dom}> (two-pass)", f"compact_bvh{width}_{dom}"
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    roof = roofline_block(f"bvh{width}_{dom}", kname, kt[dom], bytes_launch, st_dom, peak, peak_kind,
-                          clk.get("sm_mhz"), n_sm)
+    roof = roofline_block(key, kname, kt[dom], bytes_launch, st_dom, peak, peak_kind, clk.get("sm_mhz"), n_sm)
 
     def skipped(h, p, limit):
         return {"prediction_ratio": h["true_pos"] / max(1, h["rays"]),
@@ -1578,6 +1584,8 @@ def main():
                                "table each) side by side on two streams, two-phase updates included",
                    "table": {"log2_entries": args.log2_entries, "ways": args.ways, "precision": args.precision,
                              "update": args.update, "verify": args.verify, "l2_window": args.l2},
+                   "schedule": args.schedule,
+                   "exact": args.verify != "none",
                    "l2": f"inputs larger than L2: {rays_per_frame[0] * 32 / 1e6:.0f} MB of rays per step; "
                          "scene resident"},
         "plain": {"value": p_value, "unit": "Mrays/s", "speedup_hrpp_over_plain": value / p_value,
