@@ -63,6 +63,11 @@ def test_full_terrain_primary_and_ao(full):
         assert_same_stats(sa, oa_s, msg=f"full AO hrpp frame {frame}")
         assert np.array_equal(tab_a.export(), otab_a.words), f"full AO frame {frame}: table words differ"
     assert sa["positives"] > 0 and sa["inserts"] > 0
+    # the two-pass schedule and a gated table on the same full-size launches:
+    # equal to the fused launches just checked against the oracle (hits,
+    # every counter, table words), frame after frame
+    _compact_and_gate_match_fused(H, g, ((prim, O.CLOSEST_HIT), (rays, O.CLOSEST_HIT), (ao, O.ANY_HIT),
+                                         (ao2, O.ANY_HIT)))
     # HRPP == plain on every ray (occlusion bit), for the same frame
     ga_hrpp, _ = gpu_trace(H, g, ao, O.ANY_HIT, tab_a)
     assert np.array_equal(any_prims(ga_plain) == O.NO_HIT, any_prims(ga_hrpp) == O.NO_HIT)
@@ -74,6 +79,36 @@ def test_full_terrain_primary_and_ao(full):
     gc, _ = gpu_trace(H, g, ao[idx], O.CLOSEST_HIT)
     oc, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, ao[idx], O.CLOSEST_HIT)
     assert np.array_equal(as_words(gc), as_words(oc))
+
+
+def _compact_and_gate_match_fused(H, g, batches):
+    """Per query mode, three tables traced batch after batch: fused BATCH
+    (the reference), two-pass COMPACT, and BATCH under a gate; COMPACT must
+    equal the reference in hits, counters and table words, and the gated
+    table must give plain's results with gated + lookups = rays."""
+    import torch
+    tabs = {}
+    for rays_np, mode in batches:
+        if mode not in tabs:
+            gated = H.Table(18, 2, 6)
+            gated.set_gate(2621, 5)
+            tabs[mode] = (H.Table(18, 2, 6), H.Table(18, 2, 6), gated)
+        ref_t, cmp_t, gate_t = tabs[mode]
+        d = torch.from_numpy(np.ascontiguousarray(rays_np)).cuda()
+        h_ref, s_ref = H.trace(g, d, mode, ref_t, stats=True)
+        h_cmp, s_cmp = H.trace(g, d, mode, cmp_t, stats=True, schedule=H.HRPP_SCHEDULE_COMPACT)
+        h_gate, s_gate = H.trace(g, d, mode, gate_t, stats=True)
+        h_plain, _ = H.trace(g, d, mode)
+        torch.cuda.synchronize()
+        g.check()
+        assert torch.equal(h_ref.view(torch.int32), h_cmp.view(torch.int32)), mode
+        assert s_ref == s_cmp, (mode, s_ref, s_cmp)
+        assert np.array_equal(ref_t.export(), cmp_t.export()), mode
+        if mode == H.HRPP_CLOSEST_HIT:
+            assert torch.equal(h_gate.view(torch.int32), h_plain.view(torch.int32))
+        else:
+            assert torch.equal(h_gate == -1, h_plain == -1)
+        assert s_gate["gated"] + s_gate["lookups"] == s_gate["rays"] == len(rays_np)
 
 
 def test_full_batched_workload_sampled():

@@ -437,6 +437,41 @@ def test_host_async_calls_match_device_path(H, small_pair):
     assert err.value.status == H.HRPP_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("n", [0, 1, 31, 33, 257])
+def test_edge_sizes_through_every_path(H, small_pair, n):
+    """Empty, single-ray and ragged batches through the two-pass schedule,
+    a gated table, the staged host path (synchronous and host_async) and
+    the device path: identical hits, counters and table words (zero counters
+    and no work for an empty batch)."""
+    import torch
+    s, g = small_pair[0]
+    rays = np.ascontiguousarray(s.primary_rays(frame=2)[:n])
+    variants = [dict(), dict(schedule=H.HRPP_SCHEDULE_COMPACT), dict(host=True), dict(host=True, host_async=True)]
+    out = []
+    for v in variants:
+        tab = H.Table(12, 2, 6)
+        tab.set_gate(1000, 1)
+        for frame in range(2):
+            if v.get("host"):
+                hr = torch.from_numpy(rays).pin_memory()
+                hits = torch.full((n, 4), 7.0).pin_memory()
+                h, st = H.trace(g, hr, H.HRPP_CLOSEST_HIT, tab, hits=hits, stats=True,
+                                host_async=v.get("host_async", False))
+            else:
+                h, st = H.trace(g, torch.from_numpy(rays).cuda(), H.HRPP_CLOSEST_HIT, tab, stats=True,
+                                schedule=v.get("schedule", 0))
+            torch.cuda.synchronize()
+        out.append((h.cpu().view(torch.int32).clone(), st, tab.export(), tab.gate_open()))
+    ref = out[0]
+    for v, o in zip(variants[1:], out[1:]):
+        assert torch.equal(o[0], ref[0]), v
+        assert o[1] == ref[1], (v, o[1], ref[1])
+        assert np.array_equal(o[2], ref[2]) and o[3] == ref[3], v
+    assert ref[1]["rays"] == n
+    if n == 0:
+        assert all(v == 0 for v in ref[1].values())
+
+
 def test_block_sizes_give_identical_results(H, small_pair):
     s, g = small_pair[1]
     rays = s.primary_rays(frame=5)
