@@ -249,9 +249,10 @@ typedef struct hrpp_trace_opts {
                                  the call wait. */
     void *host_done;          /* host_async: NULL, or a cudaEvent_t (as void*)
                                  that the library records once the hits are
-                                 in host memory; `stream` then waits only for
-                                 the traces, not for the hits' download, so
-                                 later work on it (the next frame's traces)
+                                 in host memory (device buffers: once they
+                                 are final); `stream` then waits only for the
+                                 traces, not for the hits' download, so later
+                                 work on it (the next frame's traces)
                                  overlaps the download.  Wait for this event
                                  before reading the hits. */
     uint32_t stage_chunks;    /* host ray/hit buffers: at most this many

@@ -934,6 +934,11 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         if (ed != cudaSuccess && status == HRPP_OK) status = cuda_fail(ed, "staging order");
     }
     cudaError_t ef = cudaFreeAsync(scratch, stream);
+    // with device buffers the hits are final where `stream` gets to now
+    if (!cs.up && host_async && opts->host_done && status == HRPP_OK) {
+        if ((e = cudaEventRecord((cudaEvent_t)opts->host_done, stream)) != cudaSuccess)
+            status = cuda_fail(e, "host_done record");
+    }
     const bool wait = (staged && !host_async) || stats_host;
     if (wait) {
         if ((e = cudaStreamSynchronize(stream)) != cudaSuccess && status == HRPP_OK)
