@@ -1105,6 +1105,13 @@ def run_learned(args):
                 k: (v[0], v[-1]) if v else None for k, v in losses.items()},
                 "gemm_tflops": train_tflops, "tensor_peak_sustained_tflops": peak,
                 "frac": (train_tflops / peak) if (train_tflops and peak) else None},
+            "roofline": {"bound": "tensor", "kernel": "MLP training: tcgen05 GEMMs and the fused softmax cross-entropy "
+                                                      "(train calls, forward + backward + Adam)",
+                         "achieved": train_tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": (train_tflops / peak) if (train_tflops and peak) else None,
+                         "peak_kind": "measured sustained bf16 (MEASURED_PEAKS.json)" if peak else None,
+                         "what": "GEMM work of the train calls (3x the forward's 2.3 MFLOP per trace) over their "
+                                 "CUDA-event time; the K = 256 layers are epilogue- and HBM-bound"},
             "eval": res}
     print(json.dumps(line), flush=True)
     return 0
