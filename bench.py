@@ -465,8 +465,7 @@ def batched_roofline(step_ms: float, algo_bytes: float, peak: float, peak_kind: 
     launches it is bound by instruction issue; the algorithmic bytes, mostly
     L1/L2 hits, are reported as effective_gbs."""
     sec = step_ms * 1e-3
-    parts = [recorded_traffic(k)[0] for k in ("batch4_closest", "batch4_any", "batch_apply")]
-    traffic = sum(parts) if all(x is not None for x in parts) else None
+    traffic, _ = recorded_traffic("batched_step")  # all launches of one replay
     dram = traffic / sec / 1e9 if traffic is not None else None
     return {"bound": "issue", "kernel": "k_trace_batch<4, closest> || k_trace_batch<4, any> + k_apply_batch (graph)",
             "achieved": dram, "peak": peak, "unit": "GB/s", "frac": dram / peak if dram is not None else None,
@@ -525,6 +524,16 @@ def run_batched(args):
         setup = autotune.BatchSetup(items, frames, cfg[0], cfg[1], tuned["block_threads"])
         res[name] = timed(setup)
         setup.close()
+    # one replay of the tuned batch under an NVTX range (ncu --nvtx-include
+    # profile_batched/: the step's launches, whose DRAM bytes the roofline reads)
+    setup = autotune.BatchSetup(items, frames, tuned["closest"], tuned["any"], tuned["block_threads"])
+    setup.step()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("profile_batched")
+    setup.step()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    setup.close()
     setup = autotune.BatchSetup(items, frames, tuned["closest"], tuned["any"], tuned["block_threads"], stats=True)
     setup.step()
     torch.cuda.synchronize()
