@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--traces", type=int, default=50_000_000, help="learned workload: training traces")
-    ap.add_argument("--workload", default="terrain", choices=["terrain", "small", "batched", "pathtrace", "learned"],
+    ap.add_argument("--workload", default="terrain",
+                    choices=["terrain", "small", "batched", "pathtrace", "learned", "shadow"],
                     help="terrain: the headline step; batched: the 64-scene uneven mix in one graph-replayed launch")
     ap.add_argument("--scenes", type=int, default=64)
     ap.add_argument("--no-learned", action="store_true", help="pathtrace: skip the learned proposal")
@@ -949,6 +950,110 @@ def run_pathtrace(args, emit: bool = True, sm_mhz=None):
     return line
 
 
+def run_shadow(args, emit: bool = True):
+    """Hit-any locality on the terrain scene: its primary hits' shadow rays
+    toward a low point light (workloads.TERRAIN_SUN, which shadows 86 % of
+    the hits) instead of AO rays, the simple-lighting case in which the
+    paper finds hit-any locality (Sec. 6.1).  Any-hit true positives are
+    exact, so every skip is kept.  Each timed call restores a table warmed by
+    3 other jittered frames and traces frame 0's shadow rays; the events
+    bracket the whole call (traversal and table update).  Plain, the fused
+    BATCH schedule and the two-pass COMPACT schedule, with config 2's table
+    (2^18 x 2) and a larger one (2^22 x 4).  Not one of the five configs: a
+    measurement of what exact HRPP gains where the rays have the locality the
+    method needs."""
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1910_01304_gb300 import hrpp as H
+    from paper_1910_01304_gb300.scenes import workloads as W
+    s = W.terrain_scene()
+    g = H.Scene.from_workload(s)
+    frames = []
+    for f in range(4):
+        prim = s.primary_rays(frame=frame_index(f, rank))
+        hits, _ = H.trace(g, torch.from_numpy(prim).cuda(), H.HRPP_CLOSEST_HIT)
+        hh = hits.cpu().numpy()
+        sh, _ = W.secondary_shadow(s, prim, hh[:, 0], hh[:, 1].view(np.uint32), light=W.TERRAIN_SUN)
+        frames.append(torch.from_numpy(sh).cuda())
+    rays0 = frames[0]
+    n = int(rays0.shape[0])
+    out = torch.empty((n,), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    reps = max(5, args.steps)
+
+    def call_ms(fn):
+        """Median over reps of one call bracketed by events (setup() before)."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for _ in range(max(3, args.warmup)):
+            fn(None)
+        torch.cuda.synchronize()
+        for e in ev:
+            fn(e)
+        torch.cuda.synchronize()
+        return float(np.median([a.elapsed_time(b) for a, b in ev]))
+
+    def plain_call(e):
+        if e:
+            e[0].record(stream)
+        H.trace(g, rays0, H.HRPP_ANY_HIT, None, hits=out)
+        if e:
+            e[1].record(stream)
+    plain_ms = call_ms(plain_call)
+    _, pst = H.trace(g, rays0, H.HRPP_ANY_HIT, None, stats=True)
+    tables = {}
+    for log2e, ways in ((18, 2), (22, 4)):
+        tab, snap = H.Table(log2e, ways, 6), H.Table(log2e, ways, 6)
+        for f in frames[1:]:
+            H.trace(g, f, H.HRPP_ANY_HIT, tab)
+        snap.copy_from(tab)
+        row = {}
+        for sched, name in ((H.HRPP_SCHEDULE_BATCH, "batch"), (H.HRPP_SCHEDULE_COMPACT, "compact")):
+            def hrpp_call(e, sched=sched):
+                tab.copy_from(snap)
+                if e:
+                    e[0].record(stream)
+                H.trace(g, rays0, H.HRPP_ANY_HIT, tab, hits=out, schedule=sched)
+                if e:
+                    e[1].record(stream)
+            ms = call_ms(hrpp_call)
+            row[name] = {"ms": ms, "mrays": n / ms / 1e3, "speedup_over_plain": plain_ms / ms}
+        tab.copy_from(snap)
+        if log2e == 22:
+            # one restored two-pass call under an NVTX range (ncu --nvtx-include profile_shadow/)
+            torch.cuda.nvtx.range_push("profile_shadow")
+            H.trace(g, rays0, H.HRPP_ANY_HIT, tab, hits=out, schedule=H.HRPP_SCHEDULE_COMPACT)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+            tab.copy_from(snap)
+        hh, st = H.trace(g, rays0, H.HRPP_ANY_HIT, tab, stats=True)
+        ph, _ = H.trace(g, rays0, H.HRPP_ANY_HIT)
+        torch.cuda.synchronize()
+        row["occlusion_checked"] = bool(torch.equal(hh == -1, ph == -1))
+        row["prediction_ratio"] = st["true_pos"] / st["rays"]
+        row["false_pos"] = st["false_pos"] / st["rays"]
+        row["skipped_exact_box_tests"] = 1.0 - st["box_tests"] / pst["box_tests"]
+        tables[f"2^{log2e}x{ways}"] = row
+    g.check()
+    best = max((r[k]["mrays"], name, k) for name, r in tables.items() for k in ("batch", "compact"))
+    line = {"metric": METRIC, "value": best[0], "unit": "Mrays/s", "n_gpus": 1, "steps": reps,
+            "warmup": max(3, args.warmup), "ms_per_step": n / best[0] / 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"terrain (2,313,248 tris) shadow rays toward a low point light "
+                                   f"{W.TERRAIN_SUN} from frame 0's primary hits ({n} rays, "
+                                   f"{pst['hits'] / n:.0%} occluded); not one of the five configs",
+                       "best": {"table": best[1], "schedule": best[2]},
+                       "protocol": "each call restores a table warmed by 3 other jittered frames; events bracket "
+                                   "the whole call (traversal + table update); median of the calls"},
+            "plain": {"value": n / plain_ms / 1e3, "ms": plain_ms, "speedup_hrpp_over_plain": plain_ms * best[0] * 1e3 / n},
+            "tables": tables, "occluded": pst["hits"] / n}
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
 def pathtrace_learned(H, g, s, frames, per_bounce, stream):
     """The learned treelet proposal on the path-tracing workload: one model
     per query mode, trained on every bounce of the first frame (labels from
@@ -1139,6 +1244,9 @@ def main():
         return run_learned(args)
     if args.workload == "small":
         run_small(args)
+        return 0
+    if args.workload == "shadow":
+        run_shadow(args)
         return 0
     rank, world, local = dist_env()
     import torch
@@ -1546,7 +1654,7 @@ def main():
 
     # --- configs 1 and 5 beside the headline (one GPU only: a sub-result per
     # config, each with its own kernel-event roofline)
-    configs = None
+    configs = locality_demo = None
     if world == 1 and not args.no_configs:
         configs = {}
         import copy
@@ -1557,6 +1665,10 @@ def main():
         a.steps, a.warmup, a.frames, a.no_learned = max(3, min(args.steps, 5)), 3, 2, True
         a.log2_entries, a.ways, a.precision = 18, 2, 6
         configs["pathtrace"] = summarize_config(run_pathtrace(a, emit=False))
+        a = copy.copy(args)
+        a.steps, a.warmup = 11, 3
+        demo = run_shadow(a, emit=False)
+        locality_demo = {k: demo[k] for k in ("value", "unit", "config", "plain", "tables", "occluded")}
 
     # the clock record covers every timed GPU loop above (HRPP, plain, gated,
     # the end-to-end loops, the config sub-results)
@@ -1623,6 +1735,7 @@ def main():
                     "paper_context": "paper Table 1 (PBRT limit study, no hardware stated): 30-69% hit-all, "
                                      "<1-48% hit-any savings"},
         "configs": configs,
+        "locality_demo": locality_demo,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,

