@@ -9,7 +9,9 @@ namespace hrpp {
 // with the highest ray index aimed at it (its index + 1 is in winner[slot]).
 // The winning record writes the word and zeroes winner[slot] for the next
 // call; a losing record reads either the winner's index or zero, never its
-// own, so the outcome does not depend on scheduling.
+// own, so the outcome does not depend on scheduling.  The slot's old word
+// (wanted only by the winner, for the eviction count) is read beside the
+// winner index, so each record waits on two dependent loads, not three.
 __device__ __forceinline__ void apply_records(uint64_t *table, uint32_t *winner, const Record *rec, Ctl *ctl,
                                               uint32_t max_records)
 {
@@ -17,8 +19,9 @@ __device__ __forceinline__ void apply_records(uint64_t *table, uint32_t *winner,
     uint32_t evict = 0, lost = 0;
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const Record x = rec[r];
-        if (winner[x.slot] == x.ray1) {
-            const uint64_t old = table[x.slot];
+        const uint32_t w = __ldcg(winner + x.slot);
+        const uint64_t old = __ldcg(reinterpret_cast<const unsigned long long *>(table) + x.slot);
+        if (w == x.ray1) {
             table[x.slot] = x.word;
             winner[x.slot] = 0u;
             evict += old != HRPP_EMPTY_WORD;
@@ -70,8 +73,10 @@ cudaError_t launch_table_apply(uint64_t *table, uint32_t *winner, const Record *
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    // one record per thread while they last: the update is a chain of
+    // dependent random reads, so it wants every resident warp in flight
     uint32_t blocks = (max_records + 255u) / 256u;
-    if (blocks > (uint32_t)sms * 4u) blocks = (uint32_t)sms * 4u;
+    if (blocks > (uint32_t)sms * 16u) blocks = (uint32_t)sms * 16u;
     if (blocks < 1) blocks = 1;
     k_apply<<<blocks, 256, 0, stream>>>(table, winner, records, ctl, max_records, gate, gate_min_tp);
     return cudaGetLastError();
@@ -86,8 +91,15 @@ cudaError_t launch_gate_update(uint32_t *gate, uint32_t gate_min_tp, const Ctl *
 cudaError_t launch_table_apply_batch(const TraceParams *items, uint32_t n_items, uint32_t max_records,
                                      cudaStream_t stream)
 {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // the items share the resident warps of the single-call grid, 64 blocks each at least
+    uint32_t cap = n_items ? (uint32_t)sms * 16u / n_items : 64u;
+    if (cap < 64u) cap = 64u;
     uint32_t bx = (max_records + 255u) / 256u;
-    if (bx > 64u) bx = 64u;
+    if (bx > cap) bx = cap;
     if (bx < 1u) bx = 1u;
     k_apply_batch<<<dim3(bx, n_items), 256, 0, stream>>>(items, max_records);
     return cudaGetLastError();
