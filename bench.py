@@ -177,7 +177,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("trace_kernel.cuh", "compact.cuh", "device.cuh"):
+    for f in ("trace_kernel.cuh", "device.cuh"):
         with open(os.path.join(ROOT, "paper_1910_01304_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
