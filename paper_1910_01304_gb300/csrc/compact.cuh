@@ -40,13 +40,20 @@ constexpr uint32_t kQConsulted = 1u << 28, kQTruePos = 2u << 28, kQFalsePos = 4u
 constexpr uint32_t kQLeafMask = (1u << 28) - 1u;
 
 constexpr int kPredictThreads = 256;
+// k_predict waits on dependent loads (ray, set, triangles): 6 resident blocks
+// per SM (40 registers) ran the lookups of 1.14M terrain shadow rays faster
+// than 5 (48 registers, nothing spilled) or 8 (32 registers, more spills).
+constexpr int kPredictMinBlocks = 6;
 
 // The lookup of ray i (Go Up Level 0): fills s (hit found in a predicted
 // leaf, outcome, set and tag) and returns m = mix48(key) (0 when the table
-// was not consulted).
+// was not consulted).  The ray's predicted leaves go to its column of `cand`
+// (shared memory, kPredictThreads entries per row) and are tested in one
+// loop over their triangles in way order, so a warp takes as many steps as
+// its longest list, not the sum over ways of each way's largest leaf.
 template <bool CLOSEST, bool STATS>
 __device__ __forceinline__ uint64_t predict_ray(const TraceParams &p, uint32_t i, RayState &s, Counters<STATS> &cnt,
-                                                bool &consulted)
+                                                bool &consulted, uint32_t *cand)
 {
     s.o = __ldg(p.rays + 2ull * i);
     s.d = __ldg(p.rays + 2ull * i + 1);
@@ -72,38 +79,46 @@ __device__ __forceinline__ uint64_t predict_ray(const TraceParams &p, uint32_t i
         s.tag = (m >> p.log2_sets) & kTagMask;
         const uint64_t *set = p.table + ((uint64_t)s.set << p.log2_ways);
         const uint32_t ways = 1u << p.log2_ways;
-        bool positive = false, done = false;
-        float tdummy = 0.0f;
-        // the set's words first, all loads in flight together; then the
-        // predicted leaves, in way order
+        bool positive = false;
+        // the set's words first, all loads in flight together
         uint64_t words[8];
 #pragma unroll
         for (uint32_t w = 0; w < 8; ++w)
             if (w < ways) words[w] = p.update_mode == HRPP_UPDATE_ONLINE ? __ldcg(set + w) : __ldg(set + w);
-        // start every predicted leaf's triangles (48 to 192 bytes: the lines
-        // holding its first and last byte) towards L1 before the first test
-        // waits on one
+        // the predicted leaves of this scene, in way order; each one's
+        // triangles (48 to 192 bytes: the lines holding its first and last
+        // byte) start towards L1 before the first test waits on one
+        uint32_t nc = 0;
 #pragma unroll
         for (uint32_t w = 0; w < 8; ++w) {
             if (w >= ways) break;
             const uint64_t wd = words[w];
             if (wd == HRPP_EMPTY_WORD || (wd >> kLeafBits) != s.tag) continue;
+            positive = true;
             const uint32_t node = (uint32_t)(wd & kLeafMask);
-            if ((node >> 2) + (node & 3u) + 1u > p.n_tris) continue;
+            if ((node >> 2) + (node & 3u) + 1u > p.n_tris) continue;  // not a leaf of this scene
+            cand[nc * kPredictThreads] = node;
+            ++nc;
             const char *tri = reinterpret_cast<const char *>(p.tris + 3ull * (node >> 2));
             asm volatile("prefetch.global.L1 [%0];" ::"l"(tri));
             asm volatile("prefetch.global.L1 [%0];" ::"l"(tri + 48u * ((node & 3u) + 1u) - 1u));
         }
-#pragma unroll
-        for (uint32_t w = 0; w < 8; ++w) {
-            if (w >= ways || done) break;
-            const uint64_t wd = words[w];
-            if (wd == HRPP_EMPTY_WORD || (wd >> kLeafBits) != s.tag) continue;
-            positive = true;
-            const uint32_t node = (uint32_t)(wd & kLeafMask);
-            if ((node >> 2) + (node & 3u) + 1u > p.n_tris) continue;  // not a leaf of this scene
+        if (nc) {
+            float tdummy = 0.0f;
+            uint32_t k = 0, j = 0, node = cand[0];
             cnt.add(ST_PRED_LEAVES);
-            done = test_leaf<CLOSEST, STATS>(p, node, s.o, s.d, s.b, tdummy, false, cnt, ST_PRED_TRI_TESTS);
+            for (;;) {
+                // any-hit: the first hit ends the lookup
+                if (test_tri<CLOSEST, STATS>(p.tris + 3ull * (node >> 2), j, node, s.o, s.d, s.b, tdummy, false, cnt,
+                                             ST_PRED_TRI_TESTS))
+                    break;
+                if (++j > (node & 3u)) {
+                    if (++k == nc) break;
+                    node = cand[k * kPredictThreads];
+                    j = 0;
+                    cnt.add(ST_PRED_LEAVES);
+                }
+            }
         }
         if (!positive) {
             cnt.add(ST_NEGATIVES);
@@ -125,11 +140,12 @@ __device__ __forceinline__ uint64_t predict_ray(const TraceParams &p, uint32_t i
 }
 
 template <bool CLOSEST, bool STATS>
-__global__ void __launch_bounds__(kPredictThreads) k_predict(const TraceParams p, QueueEntry *queue)
+__global__ void __launch_bounds__(kPredictThreads, kPredictMinBlocks) k_predict(const TraceParams p, QueueEntry *queue)
 {
     __shared__ uint32_t warp_base[kPredictThreads / 32];
     __shared__ uint32_t block_base;
     __shared__ uint2 gate_acc[kPredictThreads / 32];
+    __shared__ uint32_t cand[8 * kPredictThreads];  // predicted leaves, one column per thread
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t i = blockIdx.x * (uint32_t)kPredictThreads + threadIdx.x;
     Counters<STATS> cnt;
@@ -143,7 +159,7 @@ __global__ void __launch_bounds__(kPredictThreads) k_predict(const TraceParams p
     if (i < p.n_rays) {
         RayState s;
         bool consulted = false;
-        e.m = predict_ray<CLOSEST, STATS>(p, i, s, cnt, consulted);
+        e.m = predict_ray<CLOSEST, STATS>(p, i, s, cnt, consulted, cand + threadIdx.x);
         // answered by the prediction: any-hit true positives, and closest-hit
         // ones when they are not verified (the paper's semantics)
         const bool answered = s.b.found && (!CLOSEST || p.verify == HRPP_VERIFY_NONE);

@@ -349,32 +349,58 @@ __device__ __forceinline__ bool start_ray(const TraceParams &p, uint32_t i, RayS
             s.tag = (m >> p.log2_sets) & kTagMask;
             set = p.table + ((uint64_t)s.set << p.log2_ways);
         }
-        for (uint32_t w = 0; w < ways && !done; ++w) {
+        if (p.go_up == 0) {
+            // the predicted leaves of this scene, in way order, wait in the
+            // (still empty) traversal stack; their triangles are then tested
+            // in one loop, so a warp takes as many steps as its longest list
+            // rather than, way by way, its largest leaf
+            uint32_t nc = 0;
+            for (uint32_t w = 0; w < ways && !done; ++w) {
+                const uint64_t wd = p.update_mode == HRPP_UPDATE_ONLINE ? __ldcg(set + w) : __ldg(set + w);
+                if (wd == HRPP_EMPTY_WORD || (wd >> kLeafBits) != s.tag) continue;
+                positive = true;
+                const uint32_t node = (uint32_t)(wd & kLeafMask);
+                if ((node >> 2) + (node & 3u) + 1u > p.n_tris) continue;  // not a leaf of this scene
+                stack[nc++] = (int32_t)node;
+            }
+            if (nc) {
+                uint32_t k = 0, j = 0, node = (uint32_t)stack[0];
+                cnt.add(ST_PRED_LEAVES);
+                for (;;) {
+                    // any-hit: the first hit ends the lookup
+                    if (test_tri<CLOSEST, STATS>(p.tris + 3ull * (node >> 2), j, node, s.o, s.d, s.b, tdummy, false,
+                                                 cnt, ST_PRED_TRI_TESTS))
+                        break;
+                    if (++j > (node & 3u)) {
+                        if (++k == nc) break;
+                        node = (uint32_t)stack[k];
+                        j = 0;
+                        cnt.add(ST_PRED_LEAVES);
+                    }
+                }
+            }
+        }
+        // Go Up Level > 0: each predicted subtree is traversed in way order
+        for (uint32_t w = 0; p.go_up != 0 && w < ways && !done; ++w) {
             const uint64_t wd = p.update_mode == HRPP_UPDATE_ONLINE ? __ldcg(set + w) : __ldg(set + w);
             if (wd == HRPP_EMPTY_WORD || (wd >> kLeafBits) != s.tag) continue;
             positive = true;
             const uint32_t node = (uint32_t)(wd & kLeafMask);
-            if (p.go_up == 0) {
-                if ((node >> 2) + (node & 3u) + 1u > p.n_tris) continue;  // not a leaf of this scene
-                cnt.add(ST_PRED_LEAVES);
-                done = test_leaf<CLOSEST, STATS>(p, node, s.o, s.d, s.b, tdummy, false, cnt, ST_PRED_TRI_TESTS);
-            } else {
-                if (node >= p.n_interior) continue;  // not an interior node of this scene
-                if (!have_inverse) {
-                    s.ri = ray_inverse(s.o, s.d);
-                    have_inverse = true;
-                }
-                s.tcur = (CLOSEST && s.b.found) ? s.b.t : s.d.w;
-                s.sp = 0;
-                s.ref = (int32_t)node;
-                s.steps = 0;
-                while (s.ref != kDoneRef) {
-                    if (over_budget(p, s)) break;
-                    if (s.ref >= 0) visit_interior<W, STATS, true>(p, s, stack, cnt);
-                    else visit_leaf<CLOSEST, STATS, true>(p, s, stack, cnt);
-                }
-                done = !CLOSEST && s.b.found;
+            if (node >= p.n_interior) continue;  // not an interior node of this scene
+            if (!have_inverse) {
+                s.ri = ray_inverse(s.o, s.d);
+                have_inverse = true;
             }
+            s.tcur = (CLOSEST && s.b.found) ? s.b.t : s.d.w;
+            s.sp = 0;
+            s.ref = (int32_t)node;
+            s.steps = 0;
+            while (s.ref != kDoneRef) {
+                if (over_budget(p, s)) break;
+                if (s.ref >= 0) visit_interior<W, STATS, true>(p, s, stack, cnt);
+                else visit_leaf<CLOSEST, STATS, true>(p, s, stack, cnt);
+            }
+            done = !CLOSEST && s.b.found;
         }
         if (!positive) {
             cnt.add(ST_NEGATIVES);
