@@ -581,6 +581,48 @@ def test_compact_schedule_matches_oracle(H, verify, gated):
     assert answered > 0
 
 
+@pytest.mark.parametrize("ways", [4, 8])
+@pytest.mark.parametrize("schedule", ["batch", "compact"])
+def test_many_predicted_leaves_per_ray_match_oracle(H, ways, schedule):
+    """Lookups that find several predicted leaves: shadow rays toward a low
+    light over the reduced terrain recipe (keys repeat across neighbouring
+    hits and a key keeps several leaves), 4- and 8-way sets at p = 5, both
+    schedules.  Every ray's candidates are tested in one loop over their
+    triangles in way order (Sec. 4.2); hits, counters (predicted leaves and
+    triangle tests up to an any-hit ray's first hit), per-ray outcomes and
+    table words equal the oracle's, which tests leaf by leaf."""
+    import torch
+    s = W.terrain_scene(quads=96, n_spheres=6, subdiv=3, res=(203, 117))
+    g = H.Scene.from_workload(s)
+    sched = H.HRPP_SCHEDULE_COMPACT if schedule == "compact" else H.HRPP_SCHEDULE_BATCH
+    tabs = {m: H.Table(12, ways, 5) for m in (O.CLOSEST_HIT, O.ANY_HIT)}
+    otabs = {m: O.Table(12, ways, 5, O.TWO_PHASE) for m in (O.CLOSEST_HIT, O.ANY_HIT)}
+    tot = {m: {"pred_leaves": 0, "positives": 0, "true_pos": 0} for m in tabs}
+    for frame in range(4):
+        prim = s.primary_rays(frame=frame % 3)
+        ph, _ = _oracle(s, prim, O.CLOSEST_HIT)
+        shadow, _ = W.secondary_shadow(s, prim, ph["t"], ph["prim"], light=W.TERRAIN_SUN)
+        for mode, rays in ((O.CLOSEST_HIT, prim), (O.ANY_HIT, shadow)):
+            oh, ost, ooc, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, rays, mode, otabs[mode], per_ray=True)
+            d = torch.from_numpy(rays).cuda()
+            oc = torch.full((len(rays),), 255, dtype=torch.uint8, device="cuda")
+            gh, gst = H.trace(g, d, mode, tabs[mode], stats=True, schedule=sched, ray_outcome=oc)
+            torch.cuda.synchronize()
+            g.check()
+            msg = f"frame {frame} mode {mode} ways {ways} {schedule}"
+            assert_same_hits(mode, gh.cpu().numpy(), oh, msg)
+            assert_same_stats(gst, ost, msg=msg)
+            assert np.array_equal(oc.cpu().numpy(), ooc), msg
+            assert np.array_equal(tabs[mode].export(), otabs[mode].words), msg
+            for k in tot[mode]:
+                tot[mode][k] += gst[k]
+    # the case under test happened: positive rays with more than one
+    # candidate leaf, and any-hit true positives
+    for m in tabs:
+        assert tot[m]["pred_leaves"] > tot[m]["positives"] > 0, (m, tot[m])
+    assert tot[O.ANY_HIT]["true_pos"] > 0
+
+
 @pytest.mark.parametrize("go_up", [1, 2, 5])
 @pytest.mark.parametrize("width_idx", [0, 1])
 def test_go_up_levels_match_oracle(H, small_pair, go_up, width_idx):
