@@ -81,6 +81,43 @@ def test_full_terrain_primary_and_ao(full):
     assert np.array_equal(as_words(gc), as_words(oc))
 
 
+def test_full_terrain_shadow_rays_both_schedules(full):
+    """The terrain's shadow rays toward the low light (the workload of
+    bench.py --workload shadow, where any-hit predictions pay) at full size,
+    with its 2^22-entry 4-way table at precision 6: two warming frames, then
+    frame 0 traced from the warmed table by the fused schedule and again,
+    from the same table, by the two-pass schedule.  Every prim, every counter
+    and every table word equals the oracle's two-phase HRPP."""
+    import torch
+    H, s, g = full
+    shadows = {}
+    for f in (1, 2, 0):
+        prim = s.primary_rays(frame=f)
+        oh, _ = O.trace(s.tris, s.nodes, s.prim_index, s.root, prim, O.CLOSEST_HIT)
+        shadows[f], _ = W.secondary_shadow(s, prim, oh["t"], oh["prim"], light=W.TERRAIN_SUN)
+    assert len(shadows[0]) > 1_000_000
+    tab, snap = H.Table(22, 4, 6), H.Table(22, 4, 6)
+    otab = O.Table(22, 4, 6, O.TWO_PHASE)
+    for f in (1, 2):
+        oh, ost = O.trace(s.tris, s.nodes, s.prim_index, s.root, shadows[f], O.ANY_HIT, otab)
+        gh, gst = gpu_trace(H, g, shadows[f], O.ANY_HIT, tab)
+        assert_same_hits(O.ANY_HIT, gh, oh, f"full shadow frame {f}")
+        assert_same_stats(gst, ost, msg=f"full shadow frame {f}")
+    snap.copy_from(tab)
+    oh, ost = O.trace(s.tris, s.nodes, s.prim_index, s.root, shadows[0], O.ANY_HIT, otab)
+    assert ost["true_pos"] > 0.3 * len(shadows[0])
+    d0 = torch.from_numpy(shadows[0]).cuda()
+    for sched in (H.HRPP_SCHEDULE_BATCH, H.HRPP_SCHEDULE_COMPACT):
+        tab.copy_from(snap)
+        gh, gst = H.trace(g, d0, O.ANY_HIT, tab, stats=True, schedule=sched)
+        torch.cuda.synchronize()
+        g.check()
+        msg = f"full shadow frame 0 schedule {sched}"
+        assert_same_hits(O.ANY_HIT, gh.cpu().numpy(), oh, msg)
+        assert_same_stats(gst, ost, msg=msg)
+        assert np.array_equal(tab.export(), otab.words), msg
+
+
 def _compact_and_gate_match_fused(H, g, batches):
     """Per query mode, three tables traced batch after batch: fused BATCH
     (the reference), two-pass COMPACT, and BATCH under a gate; COMPACT must
