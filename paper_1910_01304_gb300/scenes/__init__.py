@@ -60,6 +60,7 @@ def _L():
                 "sg_soup": (u32, [u32, u64, f32, f32, f32, P]),
                 "sg_place_spheres": (None, [u32, u64, f32, f32, f32, f32, f32, f32, u64, i32, f32, f32, P]),
                 "sg_build_bvh2": (i32, [P, u32, i32, P, P, P]),
+                "sg_build_bvh2_sah": (i32, [P, u32, i32, P, P, P]),
                 "sg_collapse_bvh4": (i32, [P, u32, P, P]),
                 "sg_pinhole": (None, [P, P, f32, u32, u32, u64, u32, u32, u32, P]),
                 "sg_shadow_rays": (u32, [P, P, P, u32, P, P, P, P]),
@@ -142,11 +143,14 @@ def place_spheres(count: int, seed: int, rmin: float, rmax: float, x0: float, x1
 # ------------------------------------------------------------------ BVH --
 
 
-def build_bvh(tris: np.ndarray, width: int = 2, max_leaf: int = 4):
-    """Deterministic median-split BVH; width 2 (binary) or 4 (collapsed).
+def build_bvh(tris: np.ndarray, width: int = 2, max_leaf: int = 4, method: str = "sah"):
+    """Deterministic binary BVH, binned surface-area heuristic ("sah", the
+    default) or median split ("median"); width 2 (binary) or 4 (collapsed).
 
     Returns (nodes, prim_index, root) in the canonical format; root is 0.
     """
+    if method not in ("sah", "median"):
+        raise ValueError("method must be 'sah' or 'median'")
     tris = np.ascontiguousarray(tris, dtype=np.float32).reshape(-1, 9)
     n = tris.shape[0]
     if n == 0:
@@ -154,9 +158,10 @@ def build_bvh(tris: np.ndarray, width: int = 2, max_leaf: int = 4):
     nodes2 = np.zeros(2 * n, NODE_DTYPE)
     prim = np.empty(n, np.uint32)
     cnt = ctypes.c_uint32(0)
-    rc = _L().sg_build_bvh2(_p(tris), n, max_leaf, _p(nodes2), ctypes.byref(cnt), _p(prim))
+    build2 = _L().sg_build_bvh2_sah if method == "sah" else _L().sg_build_bvh2
+    rc = build2(_p(tris), n, max_leaf, _p(nodes2), ctypes.byref(cnt), _p(prim))
     if rc != 0:
-        raise RuntimeError(f"sg_build_bvh2 failed ({rc})")
+        raise RuntimeError(f"BVH build failed ({rc})")
     nodes2 = nodes2[: cnt.value].copy()
     if width == 2:
         return nodes2, prim, 0

@@ -6,8 +6,9 @@
  * table, no ray-box or ray-triangle test and no traversal.  It makes
  *   - triangle soups for the stand-in scenes (icosphere, quad grid, value-noise
  *     terrain, uniform triangle soup),
- *   - a deterministic median-split binary BVH and its 4-wide collapse, written
- *     in the canonical node format `hrpp_scene_create` takes,
+ *   - deterministic binary BVHs (binned surface-area heuristic, or median
+ *     split) and their 4-wide collapse, written in the canonical node format
+ *     `hrpp_scene_create` takes,
  *   - camera, shadow, ambient-occlusion and uniform-sphere rays.
  * Random numbers come from PCG32 (O'Neill 2014, "PCG: A Family of Simple Fast
  * Space-Efficient Statistically Good Algorithms for Random Number Generation")
@@ -276,6 +277,7 @@ typedef struct {
     uint64_t rng;
     int axis;
     int err;
+    float *tb; /* SAH builder: 6 per triangle, its box (lo xyz, hi xyz) */
 } bctx;
 
 static int key_less(const bctx *c, uint32_t a, uint32_t b)
@@ -406,6 +408,207 @@ int sg_build_bvh2(const float *tris, uint32_t n_tris, int max_leaf, sg_node *nod
     c.rng = 0x853C49E6748FEA9Bull;
     build_rec(&c, 0, n_tris);
     free(c.cent);
+    if (c.err) return 3;
+    pad_boxes(tris, n_tris, nodes, c.n_nodes);
+    *n_nodes = c.n_nodes;
+    return 0;
+}
+
+/* Binned surface-area-heuristic split (Wald 2007, "On fast Construction of
+ * SAH-based Bounding Volume Hierarchies"): each axis's centroid range is cut
+ * into SAH_BINS bins; the plane between two bins with the least
+ * area(left) * count(left) + area(right) * count(right) wins (ties to the lower
+ * axis, then the lower plane).  Nodes of at most max_leaf triangles are
+ * leaves; a node whose centroids all fall in one bin on every axis is split
+ * at its median instead.  Partitions are stable, so the tree depends only on
+ * the input. */
+#define SAH_BINS 32
+
+typedef struct {
+    float lo[3], hi[3];
+    uint32_t n;
+} sbin;
+
+static uint32_t bin_of(float cent, float clo, double scale)
+{
+    double b = ((double)cent - (double)clo) * scale;
+    if (!(b > 0.0)) return 0;
+    if (b >= (double)(SAH_BINS - 1)) return SAH_BINS - 1;
+    return (uint32_t)b;
+}
+
+static double box_area(const float lo[3], const float hi[3])
+{
+    double dx = (double)hi[0] - lo[0], dy = (double)hi[1] - lo[1], dz = (double)hi[2] - lo[2];
+    return 2.0 * (dx * dy + dy * dz + dz * dx);
+}
+
+static void box_grow(float lo[3], float hi[3], const float blo[3], const float bhi[3])
+{
+    for (int k = 0; k < 3; ++k) {
+        if (blo[k] < lo[k]) lo[k] = blo[k];
+        if (bhi[k] > hi[k]) hi[k] = bhi[k];
+    }
+}
+
+static int32_t sah_rec(bctx *c, uint32_t *tmp, uint32_t begin, uint32_t end)
+{
+    if (c->n_nodes >= c->cap) {
+        c->err = 1;
+        return -1;
+    }
+    int32_t id = (int32_t)c->n_nodes++;
+    sg_node *n = &c->nodes[id];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (uint32_t i = begin; i < end; ++i) {
+        const float *tb = c->tb + 6ull * c->idx[i];
+        const float *ce = c->cent + 3ull * c->idx[i];
+        box_grow(lo, hi, tb, tb + 3);
+        box_grow(clo, chi, ce, ce);
+    }
+    memcpy(n->lo, lo, sizeof lo);
+    memcpy(n->hi, hi, sizeof hi);
+    n->child[0] = n->child[1] = n->child[2] = n->child[3] = -1;
+    if (end - begin <= (uint32_t)c->max_leaf) {
+        n->first = begin;
+        n->count = end - begin;
+        return id;
+    }
+    n->first = 0;
+    n->count = 0;
+    /* bin every triangle on the three axes in one pass */
+    sbin bins[3][SAH_BINS];
+    double scale[3];
+    int live[3];
+    for (int axis = 0; axis < 3; ++axis) {
+        const float ext = chi[axis] - clo[axis];
+        live[axis] = ext > 0.0f;
+        scale[axis] = live[axis] ? (double)SAH_BINS / (double)ext : 0.0;
+        for (int b = 0; b < SAH_BINS; ++b) {
+            for (int k = 0; k < 3; ++k) {
+                bins[axis][b].lo[k] = INFINITY;
+                bins[axis][b].hi[k] = -INFINITY;
+            }
+            bins[axis][b].n = 0;
+        }
+    }
+    for (uint32_t i = begin; i < end; ++i) {
+        const uint32_t t = c->idx[i];
+        const float *tb = c->tb + 6ull * t;
+        const float *ce = c->cent + 3ull * t;
+        for (int axis = 0; axis < 3; ++axis) {
+            if (!live[axis]) continue;
+            sbin *bn = &bins[axis][bin_of(ce[axis], clo[axis], scale[axis])];
+            box_grow(bn->lo, bn->hi, tb, tb + 3);
+            ++bn->n;
+        }
+    }
+    double best = INFINITY;
+    int best_axis = -1;
+    uint32_t best_plane = 0;
+    for (int axis = 0; axis < 3; ++axis) {
+        if (!live[axis]) continue;
+        /* left sweep: area and count of bins [0, b] */
+        double left_area[SAH_BINS];
+        uint32_t left_n[SAH_BINS];
+        float l_lo[3] = {INFINITY, INFINITY, INFINITY}, l_hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        uint32_t ln = 0;
+        for (int b = 0; b < SAH_BINS - 1; ++b) {
+            if (bins[axis][b].n) box_grow(l_lo, l_hi, bins[axis][b].lo, bins[axis][b].hi);
+            ln += bins[axis][b].n;
+            left_n[b] = ln;
+            left_area[b] = ln ? box_area(l_lo, l_hi) : 0.0;
+        }
+        /* right sweep: the plane below bin b splits [0, b) from [b, SAH_BINS) */
+        float r_lo[3] = {INFINITY, INFINITY, INFINITY}, r_hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        uint32_t rn = 0;
+        double right_cost[SAH_BINS];
+        for (int b = SAH_BINS - 1; b >= 1; --b) {
+            if (bins[axis][b].n) box_grow(r_lo, r_hi, bins[axis][b].lo, bins[axis][b].hi);
+            rn += bins[axis][b].n;
+            right_cost[b] = rn ? box_area(r_lo, r_hi) * (double)rn : 0.0;
+        }
+        for (int b = 1; b < SAH_BINS; ++b) {
+            const uint32_t nl = left_n[b - 1], nr = (end - begin) - nl;
+            if (nl == 0 || nr == 0) continue;
+            const double cost = left_area[b - 1] * (double)nl + right_cost[b];
+            if (cost < best) {
+                best = cost;
+                best_axis = axis;
+                best_plane = (uint32_t)b;
+            }
+        }
+    }
+    uint32_t mid;
+    if (best_axis < 0) {
+        /* every centroid in one bin: the median on the longest centroid axis */
+        int axis = 0;
+        float ext = chi[0] - clo[0];
+        for (int k = 1; k < 3; ++k)
+            if (chi[k] - clo[k] > ext) {
+                ext = chi[k] - clo[k];
+                axis = k;
+            }
+        c->axis = axis;
+        mid = begin + (end - begin) / 2;
+        select_kth(c, begin, end, mid);
+    } else {
+        uint32_t nl = 0, nr = 0;
+        for (uint32_t i = begin; i < end; ++i) {
+            const uint32_t t = c->idx[i];
+            if (bin_of(c->cent[3ull * t + best_axis], clo[best_axis], scale[best_axis]) < best_plane)
+                c->idx[begin + nl++] = t;
+            else
+                tmp[nr++] = t;
+        }
+        memcpy(c->idx + begin + nl, tmp, sizeof(uint32_t) * nr);
+        mid = begin + nl;
+    }
+    int32_t l = sah_rec(c, tmp, begin, mid);
+    int32_t r = sah_rec(c, tmp, mid, end);
+    c->nodes[id].child[0] = l;
+    c->nodes[id].child[1] = r;
+    return id;
+}
+
+/* Binned-SAH binary BVH, <= max_leaf triangles per leaf, nodes in preorder,
+ * boxes padded as sg_build_bvh2's.  Same arguments and results. */
+int sg_build_bvh2_sah(const float *tris, uint32_t n_tris, int max_leaf, sg_node *nodes, uint32_t *n_nodes,
+                      uint32_t *prim_index)
+{
+    if (n_tris == 0 || max_leaf < 1) return 1;
+    bctx c;
+    memset(&c, 0, sizeof c);
+    c.tris = tris;
+    c.cent = (float *)malloc(sizeof(float) * 3ull * n_tris);
+    uint32_t *tmp = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n_tris);
+    c.tb = (float *)malloc(sizeof(float) * 6ull * n_tris);
+    if (!c.cent || !tmp || !c.tb) {
+        free(c.cent);
+        free(tmp);
+        free(c.tb);
+        return 2;
+    }
+    for (uint32_t t = 0; t < n_tris; ++t) {
+        const float *v = tris + 9ull * t;
+        float *tb = c.tb + 6ull * t;
+        for (int k = 0; k < 3; ++k) {
+            c.cent[3ull * t + k] = (float)(((double)v[k] + v[3 + k] + v[6 + k]) / 3.0);
+            tb[k] = fminf(fminf(v[k], v[3 + k]), v[6 + k]);
+            tb[3 + k] = fmaxf(fmaxf(v[k], v[3 + k]), v[6 + k]);
+        }
+    }
+    c.idx = prim_index;
+    for (uint32_t t = 0; t < n_tris; ++t) prim_index[t] = t;
+    c.nodes = nodes;
+    c.cap = 2u * n_tris;
+    c.max_leaf = max_leaf;
+    c.rng = 0x853C49E6748FEA9Bull;
+    sah_rec(&c, tmp, 0, n_tris);
+    free(c.cent);
+    free(tmp);
+    free(c.tb);
     if (c.err) return 3;
     pad_boxes(tris, n_tris, nodes, c.n_nodes);
     *n_nodes = c.n_nodes;

@@ -22,6 +22,8 @@ Both take size parameters so tests can run the same recipe at reduced size.
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass
 
 import numpy as np
@@ -154,10 +156,15 @@ def batched_workload(n_scenes: int = 64, tris_range=(10_000, 2_000_000), rays_ra
     turn) and log-uniform ray batch sizes in rays_range.  Yields (scene, rays)."""
     rng = np.random.default_rng(seed)
     kinds = ("terrain", "spheres", "soup")
+    specs = []
     for k in range(n_scenes):
         nt = int(np.exp(rng.uniform(np.log(tris_range[0]), np.log(tris_range[1]))))
         nr = int(np.exp(rng.uniform(np.log(rays_range[0]), np.log(rays_range[1]))))
-        yield batched_item(kinds[k % 3], nt, nr, seed * 1000 + k, width)
+        specs.append((kinds[k % 3], nt, nr, seed * 1000 + k, width))
+    # the items are independent and their generators and BVH builds run in C
+    # outside the interpreter lock: build them on host threads, yield in order
+    with ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
+        yield from ex.map(lambda a: batched_item(*a), specs)
 
 
 # ------------------------------------------------------- path tracing --

@@ -43,12 +43,13 @@ def _rays(seed, n=96):
     return r
 
 
+@pytest.mark.parametrize("method", ["sah", "median"])
 @pytest.mark.parametrize("width", [2, 4])
-def test_traversal_equals_brute_force(width):
+def test_traversal_equals_brute_force(width, method):
     n_cmp = 0
     for seed in range(240):
         tris = _tiny_scene(seed)
-        nodes, prim, root = S.build_bvh(tris, width=width)
+        nodes, prim, root = S.build_bvh(tris, width=width, method=method)
         rays = _rays(seed)
         hc, _ = O.trace(tris, nodes, prim, root, rays, O.CLOSEST_HIT)
         bc, tie = O.brute(rays, tris, O.CLOSEST_HIT)
