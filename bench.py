@@ -176,9 +176,12 @@ class ClockSampler:
 
 
 def kernel_source_hash():
+    """Hash of what a recorded ncu figure depends on: the sources the recorded
+    traversal kernels compile from and the generator of the scenes and BVHs
+    they ran on."""
     h = hashlib.sha256()
-    for f in ("trace_kernel.cuh", "device.cuh"):
-        with open(os.path.join(ROOT, "paper_1910_01304_gb300", "csrc", f), "rb") as fh:
+    for f in ("csrc/trace_kernel.cuh", "csrc/device.cuh", "scenes/scenegen.c"):
+        with open(os.path.join(ROOT, "paper_1910_01304_gb300", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
