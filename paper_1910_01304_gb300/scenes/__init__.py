@@ -60,7 +60,7 @@ def _L():
                 "sg_soup": (u32, [u32, u64, f32, f32, f32, P]),
                 "sg_place_spheres": (None, [u32, u64, f32, f32, f32, f32, f32, f32, u64, i32, f32, f32, P]),
                 "sg_build_bvh2": (i32, [P, u32, i32, P, P, P]),
-                "sg_build_bvh2_sah": (i32, [P, u32, i32, P, P, P]),
+                "sg_build_bvh2_sah": (i32, [P, u32, i32, f64, P, P, P]),
                 "sg_collapse_bvh4": (i32, [P, u32, P, P]),
                 "sg_pinhole": (None, [P, P, f32, u32, u32, u64, u32, u32, u32, P]),
                 "sg_shadow_rays": (u32, [P, P, P, u32, P, P, P, P]),
@@ -143,9 +143,13 @@ def place_spheres(count: int, seed: int, rmin: float, rmax: float, x0: float, x1
 # ------------------------------------------------------------------ BVH --
 
 
-def build_bvh(tris: np.ndarray, width: int = 2, max_leaf: int = 4, method: str = "sah"):
+def build_bvh(tris: np.ndarray, width: int = 2, max_leaf: int = 4, method: str = "sah", trav_cost: float = 1.0):
     """Deterministic binary BVH, binned surface-area heuristic ("sah", the
     default) or median split ("median"); width 2 (binary) or 4 (collapsed).
+    Leaves hold at most max_leaf triangles.  SAH: a node of up to max_leaf
+    triangles still splits when trav_cost x its area plus its children's
+    area x count is below its own area x count (one triangle test costing 1;
+    trav_cost = 0 makes every such node a leaf).
 
     Returns (nodes, prim_index, root) in the canonical format; root is 0.
     """
@@ -158,8 +162,10 @@ def build_bvh(tris: np.ndarray, width: int = 2, max_leaf: int = 4, method: str =
     nodes2 = np.zeros(2 * n, NODE_DTYPE)
     prim = np.empty(n, np.uint32)
     cnt = ctypes.c_uint32(0)
-    build2 = _L().sg_build_bvh2_sah if method == "sah" else _L().sg_build_bvh2
-    rc = build2(_p(tris), n, max_leaf, _p(nodes2), ctypes.byref(cnt), _p(prim))
+    if method == "sah":
+        rc = _L().sg_build_bvh2_sah(_p(tris), n, max_leaf, trav_cost, _p(nodes2), ctypes.byref(cnt), _p(prim))
+    else:
+        rc = _L().sg_build_bvh2(_p(tris), n, max_leaf, _p(nodes2), ctypes.byref(cnt), _p(prim))
     if rc != 0:
         raise RuntimeError(f"BVH build failed ({rc})")
     nodes2 = nodes2[: cnt.value].copy()

@@ -278,6 +278,7 @@ typedef struct {
     int axis;
     int err;
     float *tb; /* SAH builder: 6 per triangle, its box (lo xyz, hi xyz) */
+    double trav_cost; /* SAH builder: > 0 lets small nodes split when that is cheaper */
 } bctx;
 
 static int key_less(const bctx *c, uint32_t a, uint32_t b)
@@ -470,9 +471,10 @@ static int32_t sah_rec(bctx *c, uint32_t *tmp, uint32_t begin, uint32_t end)
     memcpy(n->lo, lo, sizeof lo);
     memcpy(n->hi, hi, sizeof hi);
     n->child[0] = n->child[1] = n->child[2] = n->child[3] = -1;
-    if (end - begin <= (uint32_t)c->max_leaf) {
+    const uint32_t count = end - begin;
+    if (count == 1 || (count <= (uint32_t)c->max_leaf && !(c->trav_cost > 0.0))) {
         n->first = begin;
-        n->count = end - begin;
+        n->count = count;
         return id;
     }
     n->first = 0;
@@ -540,6 +542,17 @@ static int32_t sah_rec(bctx *c, uint32_t *tmp, uint32_t begin, uint32_t end)
             }
         }
     }
+    if (count <= (uint32_t)c->max_leaf) {
+        /* a node that may be a leaf splits only if the split's expected cost,
+         * trav_cost x area + the children's area x count, is below the leaf's
+         * area x count (triangle tests costing 1) */
+        const double a = box_area(lo, hi);
+        if (best_axis < 0 || !(c->trav_cost * a + best < a * (double)count)) {
+            n->first = begin;
+            n->count = count;
+            return id;
+        }
+    }
     uint32_t mid;
     if (best_axis < 0) {
         /* every centroid in one bin: the median on the longest centroid axis */
@@ -574,8 +587,8 @@ static int32_t sah_rec(bctx *c, uint32_t *tmp, uint32_t begin, uint32_t end)
 
 /* Binned-SAH binary BVH, <= max_leaf triangles per leaf, nodes in preorder,
  * boxes padded as sg_build_bvh2's.  Same arguments and results. */
-int sg_build_bvh2_sah(const float *tris, uint32_t n_tris, int max_leaf, sg_node *nodes, uint32_t *n_nodes,
-                      uint32_t *prim_index)
+int sg_build_bvh2_sah(const float *tris, uint32_t n_tris, int max_leaf, double trav_cost, sg_node *nodes,
+                      uint32_t *n_nodes, uint32_t *prim_index)
 {
     if (n_tris == 0 || max_leaf < 1) return 1;
     bctx c;
@@ -604,6 +617,7 @@ int sg_build_bvh2_sah(const float *tris, uint32_t n_tris, int max_leaf, sg_node 
     c.nodes = nodes;
     c.cap = 2u * n_tris;
     c.max_leaf = max_leaf;
+    c.trav_cost = trav_cost;
     c.rng = 0x853C49E6748FEA9Bull;
     sah_rec(&c, tmp, 0, n_tris);
     free(c.cent);

@@ -104,7 +104,7 @@ def test_validate_limits_and_arguments(H):
     tris, nodes, prim, root = _scene()
     # a leaf with 5 triangles exceeds HRPP_MAX_LEAF_TRIS
     from paper_1910_01304_gb300 import scenes as S
-    n5, p5, _ = S.build_bvh(tris, width=2, max_leaf=5)
+    n5, p5, _ = S.build_bvh(tris, width=2, max_leaf=5, trav_cost=0.0)
     if (n5["count"] > 4).any():
         _expect(H, H.HRPP_ERR_UNSUPPORTED, tris, n5, p5)
     _expect(H, H.HRPP_ERR_INVALID_ARG, tris, nodes, prim, width=3)

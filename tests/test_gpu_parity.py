@@ -130,7 +130,7 @@ def test_edge_cases_ragged_and_degenerate(H, small_pair):
 
 def test_root_leaf_scene(H):
     tris = S.soup(3, 2, 0, 1, 0.5)
-    nodes, prim, root = S.build_bvh(tris)
+    nodes, prim, root = S.build_bvh(tris, trav_cost=0.0)  # 3 triangles: one leaf
     g = H.Scene(tris, nodes, prim, root, 2)
     assert g.info()["root_is_leaf"] == 1
     rays = S.sphere_rays(300, 1, -0.5, 1.5)

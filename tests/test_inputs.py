@@ -47,13 +47,18 @@ def _validate(nodes, prim, n_tris, tris, width):
     assert np.all(reached == 1)
 
 
-@pytest.mark.parametrize("method", ["sah", "median"])
+@pytest.mark.parametrize("method,trav_cost", [("sah", 1.0), ("sah", 0.0), ("median", 0.0)])
 @pytest.mark.parametrize("width", [2, 4])
-def test_bvh_valid(width, method):
+def test_bvh_valid(width, method, trav_cost):
     for seed in range(5):
         tris = S.soup(300 + 37 * seed, seed)
-        nodes, prim, root = S.build_bvh(tris, width=width, method=method)
+        nodes, prim, root = S.build_bvh(tris, width=width, method=method, trav_cost=trav_cost)
         _validate(nodes, prim, len(tris), tris, width)
+        if method == "sah" and trav_cost == 0.0:
+            # without the leaf cost every node of <= 4 triangles is a leaf
+            kids = nodes["child"][nodes["count"] == 0]
+            sizes = [nodes["count"][c] for row in kids for c in row if c >= 0 and nodes["count"][c] > 0]
+            assert min(sizes) >= 1
     s = W.small_scene(width=width)
     _validate(s.nodes, s.prim_index, s.n_tris, s.tris, width)
 
@@ -105,5 +110,11 @@ def test_sah_tree_is_cheaper_than_median():
     same = np.tile(np.array([0, 0, 0, 1, 0, 0, 0, 1, 0], np.float32), (50, 1))
     nodes, prim, root = S.build_bvh(same, width=4)
     _validate(nodes, prim, len(same), same, 4)
+    # the leaf cost splits small nodes only where that is cheaper: leaves get
+    # smaller on average, never larger than max_leaf
+    split, _, _ = S.build_bvh(s.tris, width=2, method="sah", trav_cost=1.0)
+    fixed, _, _ = S.build_bvh(s.tris, width=2, method="sah", trav_cost=0.0)
+    leaf = lambda n: n["count"][n["count"] > 0]
+    assert leaf(split).max() <= 4 and leaf(split).mean() < leaf(fixed).mean()
     with pytest.raises(ValueError):
         S.build_bvh(s.tris, method="other")

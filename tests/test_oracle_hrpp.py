@@ -564,7 +564,7 @@ def test_bottom_up_on_a_root_leaf_scene():
     test is the whole answer."""
     from paper_1910_01304_gb300 import scenes as S
     tris = S.soup(3, 2, 0, 1, 0.5)
-    nodes, prim, root = S.build_bvh(tris)
+    nodes, prim, root = S.build_bvh(tris, trav_cost=0.0)  # 3 triangles: one leaf
     assert nodes[root]["count"] > 0
     rays = S.sphere_rays(300, 1, -0.5, 1.5)
     hp, _ = O.trace(tris, nodes, prim, root, rays, O.CLOSEST_HIT)

@@ -91,7 +91,7 @@ def test_traversal_counts_binary_vs_wide(small, small4):
 
 def test_root_leaf_scene():
     tris = S.soup(3, 1, 0, 1, 0.4)
-    nodes, prim, root = S.build_bvh(tris, width=2)
+    nodes, prim, root = S.build_bvh(tris, width=2, trav_cost=0.0)  # 3 triangles: one leaf
     assert len(nodes) == 1 and nodes[0]["count"] == 3
     rays = _rays(3, 64)
     h, st = O.trace(tris, nodes, prim, root, rays, O.CLOSEST_HIT)
