@@ -246,7 +246,10 @@ typedef struct hrpp_trace_opts {
                                  valid, the rays unmodified, until then.  A
                                  stopped ray is then reported by
                                  hrpp_scene_check; host out_stats still make
-                                 the call wait. */
+                                 the call wait.  At most 4 staged calls per
+                                 device hold staging memory at once: a
+                                 further one first waits on the host for
+                                 the oldest one's downloads to finish. */
     void *host_done;          /* host_async: NULL, or a cudaEvent_t (as void*)
                                  that the library records once the hits are
                                  in host memory (device buffers: once they

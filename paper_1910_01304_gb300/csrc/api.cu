@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -162,6 +163,45 @@ void release_copy_streams(int dev, const CopyStreams &c)
 {
     std::lock_guard<std::mutex> lk(g_copy_mutex);
     g_copy_idle[dev].push_back(c);
+}
+
+// Staged calls in flight per device.  Each holds a staging block from the
+// pool until its downloads are done; a caller that queues host_async calls
+// without waiting would otherwise make the pool grow by one block per call
+// (new device memory, mapped on the host thread inside the call).  A staged
+// call that finds kStagedInFlight calls still holding staging waits on the
+// host for the oldest one's block to be freed.  The work it waits for is
+// already queued, so the wait ends.
+constexpr size_t kStagedInFlight = 4;
+std::mutex g_inflight_mutex;
+std::deque<cudaEvent_t> g_inflight[64];
+
+cudaError_t wait_for_staging_slot(int dev)
+{
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    for (;;) {
+        cudaEvent_t oldest = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(g_inflight_mutex);
+            if (g_inflight[dev].size() < kStagedInFlight) return cudaSuccess;
+            oldest = g_inflight[dev].front();
+            g_inflight[dev].pop_front();
+        }
+        const cudaError_t e = cudaEventSynchronize(oldest);
+        cudaEventDestroy(oldest);
+        if (e != cudaSuccess) return e;
+    }
+}
+
+// `freed` is recorded after a staged call's block is freed; the list owns it.
+void note_staging_in_flight(int dev, cudaEvent_t freed)
+{
+    if (dev < 0 || dev >= 64) {
+        cudaEventDestroy(freed);
+        return;
+    }
+    std::lock_guard<std::mutex> lk(g_inflight_mutex);
+    g_inflight[dev].push_back(freed);
 }
 
 bool is_host_pointer(const void *ptr, bool *ok, bool *pinned = nullptr)
@@ -791,6 +831,7 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
     do {
         if ((e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), stream)) != cudaSuccess) { status = cuda_fail(e, "memset"); break; }
         if (staged) {
+            if ((e = wait_for_staging_slot(sc->device)) != cudaSuccess) { status = cuda_fail(e, "staging wait"); break; }
             if ((e = acquire_copy_streams(sc->device, &cs)) != cudaSuccess) { status = cuda_fail(e, "copy streams"); break; }
             if (allocation_refused()) { status = cuda_fail(cudaErrorMemoryAllocation, "staging (injected)"); break; }
             if ((e = cudaMallocFromPoolAsync((void **)&staging, stage_bytes, pool, cs.up)) != cudaSuccess) {
@@ -917,6 +958,12 @@ hrpp_status hrpp_trace_ex(const hrpp_scene *sc, hrpp_table *table, const hrpp_ra
         if (ed == cudaSuccess) ed = cudaEventRecord(uploaded, cs.up);
         if (ed == cudaSuccess) ed = cudaStreamWaitEvent(cs.down, uploaded, 0);
         if (ed == cudaSuccess && staging) ed = cudaFreeAsync(staging, cs.down);
+        if (ed == cudaSuccess && staging) {
+            cudaEvent_t freed = nullptr;
+            ed = cudaEventCreateWithFlags(&freed, cudaEventDisableTiming);
+            if (ed == cudaSuccess && (ed = cudaEventRecord(freed, cs.down)) != cudaSuccess) cudaEventDestroy(freed);
+            if (ed == cudaSuccess) note_staging_in_flight(sc->device, freed);
+        }
         if (host_async && opts->host_done) {
             // the caller's event marks the hits in host memory; `stream`
             // goes on after the traces without waiting for the downloads

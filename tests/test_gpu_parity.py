@@ -394,6 +394,35 @@ def test_staged_host_buffers_in_chunks_match_device_path(H, small_pair, mode, sc
             assert rst["gated"] > 0 or rst["lookups"] == len(rays)
 
 
+def test_queued_host_async_calls_hold_bounded_staging(H, small_pair):
+    """Twelve host_async calls queued without waiting (each with its own
+    pinned buffers and a host_done event): every one returns the device
+    path's hits, and the device memory they take stays within a few staging
+    blocks, since at most 4 staged calls hold staging at once."""
+    import torch
+    s, g = small_pair[1]
+    rays = np.concatenate([s.primary_rays(frame=f) for f in range(5)])
+    ref, _ = H.trace(g, torch.from_numpy(rays).cuda(), H.HRPP_CLOSEST_HIT)
+    block = len(rays) * (32 + 16)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    calls = []
+    for k in range(12):
+        hr = torch.from_numpy(rays).pin_memory()
+        hits = torch.full((len(rays), 4), 7.0).pin_memory()
+        done = torch.cuda.Event()
+        done.record(stream)  # creates the CUDA event; the library records it again
+        H.trace(g, hr, H.HRPP_CLOSEST_HIT, None, hits=hits, stream=stream, host_async=True, host_done=done)
+        calls.append((hr, hits, done))
+    for hr, hits, done in calls:
+        done.synchronize()
+        assert torch.equal(hits.view(torch.int32), ref.cpu().view(torch.int32))
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free0 - free1 <= 6 * (block + (2 << 20)), (free0 - free1, block)
+
+
 def test_host_async_calls_match_device_path(H, small_pair):
     """hrpp_trace_opts.host_async: calls on pinned host buffers return before
     their work is done; several of them queued on two streams (one table
