@@ -246,7 +246,7 @@ typedef struct hrpp_trace_opts {
                                  valid, the rays unmodified, until then.  A
                                  stopped ray is then reported by
                                  hrpp_scene_check; host out_stats still make
-                                 the call wait.  At most 4 staged calls per
+                                 the call wait.  At most 6 staged calls per
                                  device hold staging memory at once: a
                                  further one first waits on the host for
                                  the oldest one's downloads to finish. */

@@ -171,8 +171,10 @@ void release_copy_streams(int dev, const CopyStreams &c)
 // (new device memory, mapped on the host thread inside the call).  A staged
 // call that finds kStagedInFlight calls still holding staging waits on the
 // host for the oldest one's block to be freed.  The work it waits for is
-// already queued, so the wait ends.
-constexpr size_t kStagedInFlight = 4;
+// already queued, so the wait ends.  Six (three two-batch frames ahead)
+// measured as fast as 8 or 16 on the terrain frame loop; 4 sometimes stalled
+// the uploads.
+constexpr size_t kStagedInFlight = 6;
 std::mutex g_inflight_mutex;
 std::deque<cudaEvent_t> g_inflight[64];
 

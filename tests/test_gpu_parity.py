@@ -398,7 +398,7 @@ def test_queued_host_async_calls_hold_bounded_staging(H, small_pair):
     """Twelve host_async calls queued without waiting (each with its own
     pinned buffers and a host_done event): every one returns the device
     path's hits, and the device memory they take stays within a few staging
-    blocks, since at most 4 staged calls hold staging at once."""
+    blocks, since at most 6 staged calls hold staging at once."""
     import torch
     s, g = small_pair[1]
     rays = np.concatenate([s.primary_rays(frame=f) for f in range(5)])
@@ -420,7 +420,7 @@ def test_queued_host_async_calls_hold_bounded_staging(H, small_pair):
         assert torch.equal(hits.view(torch.int32), ref.cpu().view(torch.int32))
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
-    assert free0 - free1 <= 6 * (block + (2 << 20)), (free0 - free1, block)
+    assert free0 - free1 <= 8 * (block + (2 << 20)), (free0 - free1, block)
 
 
 def test_host_async_calls_match_device_path(H, small_pair):
